@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the ACSE hot path on GB300 (one JSON line on rank 0).
+
+A step is one Euler step of Eq. (update) through the C ABI (`acse_step`): the residual A at D
+(1-RDM, M, pair-pair and particle-hole GEMMs, B and G assembly, FP64 norm), the update
+U = 1/2 G(A) with the same reconstruction, D <- D + eps U and the FP64 energy.  The workload is
+the r = 48, N = 20, CAS(8e,8o) system (synthetic integrals, seed 0).  The metric is ACSE
+residual evaluations per second (one per step) over all ranks; TFLOP/s counts the O(r^6)
+GEMM work, 2 M N K summed over the GEMMs (32 r^6 per contraction pass, two passes per step).
+
+--impl reference times the FP64 numpy oracle on the host cores instead (rank 0 only).
+Multi-GPU: independent replicas (one problem per rank, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# measured on this machine's GB300 by `python bench.py --peaks` (torch.matmul, best of 5-10):
+# cuBLAS DGEMM 8192^3 1.10 TFLOP/s, TF32 1041 TFLOP/s; used where MEASURED_PEAKS.json has no entry
+FP64_PEAK_TFLOPS = 1.10
+TF32_PEAK_TFLOPS = 1041.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32"])
+    ap.add_argument("--r", type=int, default=48, help="orbitals (48: the CAS(8e,8o) workload)")
+    ap.add_argument("--eps", type=float, default=0.1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--peaks", action="store_true", help="measure FP64/TF32/BF16 matmul peaks and exit")
+    return ap.parse_args()
+
+
+def default_prec():
+    # the tensor-core path when this build provides it, else FP64
+    try:
+        from paper_2604_02550_gb300 import _lib
+        return "bf16x3" if getattr(_lib, "HAS_TC", False) else "fp64"
+    except Exception:
+        return "fp64"
+
+
+def workload(r, seed=0):
+    import acse_inputs as I
+    if r == 48:
+        return I.config_problem(3, seed)
+    if r == 24:
+        return I.config_problem(2, seed)
+    if r == 32:
+        return I.config_problem(5, seed)
+    # other sizes: CAS(4e,4o) above a core, N = r/2 rounded to even
+    n = max(6, (r // 2) & ~1)
+    nc = (n - 4) // 2
+    return I.make_problem(r, n, seed, "cas", core=range(nc), active=range(nc, nc + 4), nelecas=4,
+                          name=f"cas44_r{r}")
+
+
+def flops_per_pass(r):
+    """2 M N K over the O(r^6) GEMMs of one contraction pass G(W):
+    pair-pair: 3 spin sectors x ([M; D] (2 r^2 rows) x r^2 x r^2); particle-hole: one
+    (2r^2)^3 diagonal-sector GEMM and two (r^2)^3 spin-flip GEMMs  ->  32 r^6."""
+    R2 = r * r
+    return 2 * (3 * (2 * R2) * R2 * R2 + (2 * R2) ** 3 + 2 * R2 ** 3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_timing(p, n_evals=1):
+    """The FP64 oracle (spin-orbital numpy, all host cores) on `n_evals` residual evaluations."""
+    import numpy as np
+    from oracle import acse_oracle as O
+    K = O.reduced_hamiltonian(p.h, p.V, p.N)
+    D = O.so_from_blocks(p.Daa, p.Dab, p.Dbb)
+    t0 = time.perf_counter()
+    for _ in range(n_evals):
+        A = O.residual(K, D, p.N)
+    dt = time.perf_counter() - t0
+    del A
+    return n_evals / dt, dt, os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = workload(args.r)
+    for _ in range(min(args.warmup, 1)):
+        pass   # numpy has nothing to warm up; the first timed evaluation includes no compilation
+    times = []
+    for _ in range(args.steps):
+        v, dt, cores = cpu_oracle_timing(p, 1)
+        times.append(dt)
+    total = sum(times)
+    val = args.steps / total
+    line = {"metric": "acse_residual_evals_per_s", "value": val, "unit": "residual evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": "fp64 (numpy oracle, spin-orbital basis)"},
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "residual evals/s", "cores": os.cpu_count(),
+                             "sample": f"one full oracle residual evaluation of {p.name} per step"},
+            "e2e": {"value": val, "unit": "residual evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def measure_peaks():
+    import torch
+    out = {}
+
+    def mm(dtype, n, iters, tf32=False):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(3):
+            a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(iters):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return 2 * n ** 3 / best / 1e12
+
+    out["fp64_tflops"] = mm(torch.float64, 8192, 5)
+    out["tf32_tflops"] = mm(torch.float32, 8192, 10, tf32=True)
+    out["fp32_simt_tflops"] = mm(torch.float32, 8192, 5)
+    out["bf16_tflops"] = mm(torch.bfloat16, 8192, 10)
+    out["how"] = "torch.matmul n=8192, best of 5-10 after 3 warm-up calls, CUDA events"
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    if args.peaks:
+        measure_peaks()
+        return
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_02550_gb300 import _lib, api
+    prec = args.prec or default_prec()
+    p = workload(args.r, seed=rank)
+    stream = torch.cuda.Stream()
+    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream)
+    with torch.cuda.stream(stream):
+        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+        for _ in range(args.warmup):
+            ctx.step(D, args.eps)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    _lib.acse_profile(ctx.ctx, 1)
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            E, n2, _ = ctx.step(D, args.eps)
+        e1.record(stream)
+    stream.synchronize()
+    gemm_ms, gemm_n, launches = _lib.acse_profile_read(ctx.ctx)
+    _lib.acse_profile(ctx.ctx, 0)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t)
+    per_step = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+    fl = flops_per_pass(p.r)
+    split = 3 if prec == "bf16x3" else 1
+    # dominant kernel: the grouped O(r^6) GEMM launch (one per contraction pass)
+    gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1e3
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        peaks = json.load(open(PEAKS_FILE))
+    if prec == "fp64":
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "measured cuBLAS DGEMM 8192^3 on this pool (bench.py --peaks); DFMA pipe"}
+        ach = fl / gemm_avg_s / 1e12
+    elif prec == "bf16x3":
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks.get("bf16_tflops", 1887.4),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1.9 PF"}
+        ach = split * fl / gemm_avg_s / 1e12
+    else:
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": TF32_PEAK_TFLOPS,
+                "peak_source": "measured cuBLAS TF32 8192^3 on this pool (bench.py --peaks)"}
+        ach = fl / gemm_avg_s / 1e12
+    roof.update({"achieved": ach, "frac": ach / roof["peak"], "traffic": None, "kernel": "grouped O(r^6) GEMM",
+                 "flops_per_launch": split * fl, "launch_ms": 1e3 * gemm_avg_s,
+                 "gemm_share_of_step": (gemm_ms / args.steps) / per_step})
+    line = {"metric": "acse_residual_evals_per_s", "value": value, "unit": "residual evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16x3 (f32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "eps": args.eps,
+                       "step": "acse_step: residual + update + axpy + energy",
+                       "l2": "inputs larger than L2 (about 1.5 GB of r^4 tensors touched per step)",
+                       "parallelism": f"replicas x{world}"},
+            "tflops": world * 2 * fl / (ms_max / 1e3 / args.steps) / 1e12,
+            "gpu_launches": launches, "clocks": clocks, "roofline": roof}
+    ctx_e2e = None
+    if not args.no_e2e and rank == 0:
+        # end to end: host (pinned) buffers through the same C ABI; H2D, compute, D2H inside the loop
+        Dh = [torch.from_numpy(x.copy()).pin_memory() for x in (p.Daa, p.Dab, p.Dbb)]
+        Eh = torch.zeros(1, dtype=torch.float64).pin_memory()
+        Nh = torch.zeros(1, dtype=torch.float64).pin_memory()
+        Sh = torch.zeros(1, dtype=torch.float64).pin_memory()
+        ctx_e2e = ctx
+        for _ in range(2):
+            _lib.acse_step(ctx.ctx, *Dh, args.eps, Eh, Nh, Sh)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _lib.acse_step(ctx.ctx, *Dh, args.eps, Eh, Nh, Sh)
+        dt = time.perf_counter() - t0
+        n4 = p.r ** 4
+        line["e2e"] = {"value": args.steps / dt, "unit": "residual evals/s", "h2d_bytes_per_step": 3 * n4 * 8,
+                       "d2h_bytes_per_step": 3 * n4 * 8 + 3 * 8,
+                       "how": "acse_step on pinned host D blocks: staged H2D, step, D2H of D, E, ||A||^2, eps"}
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        v, dt, cores = cpu_oracle_timing(p, 1)
+        line["cpu_baseline"] = {"value": v, "unit": "residual evals/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one FP64 oracle residual evaluation of {p.name} ({dt:.1f} s)"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

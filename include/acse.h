@@ -1,0 +1,137 @@
+/*
+ * acse.h -- C ABI of libacse: the ACSE residual / propagation hot path on one GB300 GPU.
+ *
+ * Method (arXiv 2604.02550): the anti-Hermitian contracted Schroedinger equation residual
+ *     A^{ij}_{kl} = <psi| [a+_i a+_j a_l a_k, H] |psi>                         (Eq. residual_2quant)
+ * written in the 2-RDM 2D and the 3-RDM 3D (Eq. residual, Appendix B), with 3D replaced by
+ * the Valdemoro reconstruction from the 1-RDM and the 2-cumulant (Eq. 3rdm_recon,
+ * Appendix C) and contracted without ever being stored, and the Euler propagation step
+ *     2U^{ij}_{kl} = <psi| [a+_i a+_j a_l a_k, A^] |psi>,  2D <- 2D + eps 2U     (Eq. update).
+ *
+ * Conventions (fixed by brute-force Fock-space checks where the printed equations are garbled):
+ *   * 2D^{pq}_{rs} = 1/2 <a+_p a+_q a_s a_r>;  Tr 2D = N(N-1)/2.
+ *   * Spin blocks, spatial indices 0..r-1, full-square row-major [i][j][k][l]:
+ *       X_aa = X^{ia ja}_{ka la},  X_ab = X^{ia jb}_{ka lb},  X_bb = X^{ib jb}_{kb lb}.
+ *     Each block is r^4 doubles.  The aa and bb blocks are antisymmetric in (i,j) and in (k,l).
+ *   * h: r x r one-electron integrals; V: r^4 two-electron integrals in chemist's notation
+ *     (pq|rs) stored [p][q][r][s].
+ *   * Reduced Hamiltonian (Eq. 2):  K = 1/2(<pq|rs> - <pq|sr>)
+ *         + (h_pr d_qs + h_qs d_pr - h_ps d_qr - h_qr d_ps) / (2(N-1)),  <pq|rs> = (pr|qs),
+ *     so that E = sum K.2D = sum_aa + sum_bb + 4 sum_ab.
+ *   * A is the commutator itself; the printed Eq. (residual) equals -A.
+ *   * 2U = 1/2 <[a+a+aa, A^]> with A^ = sum A^{pq}_{rs} a+_p a+_q a_s a_r (so dE/deps = -||A||^2).
+ *   * ||A||^2 = ||A_aa||^2 + ||A_bb||^2 + 4 ||A_ab||^2 (spin-orbital Frobenius norm), taken
+ *     before the optional all-active mask (Results: norms before zeroing).
+ *
+ * Pointers: every array argument may be a device pointer or a host pointer (pageable or
+ * pinned); the library checks each with cudaPointerGetAttributes.  Device pointers are used
+ * in place and the call is asynchronous on the context's stream.  Host arguments are staged
+ * through context-owned device buffers; a call with any host output returns only after the
+ * stream has finished it.  The caller owns every buffer it passes; the library never frees
+ * them.  Scalar outputs (E, norm2, eps) follow the same rule.
+ *
+ * Errors: every function returns ACSE_OK (0) or a negative acse_status.  No exception or
+ * abort crosses the ABI.  The last error is also latched in the context (acse_last_error).
+ */
+#ifndef ACSE_H
+#define ACSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acse_ctx acse_ctx;
+
+typedef enum {
+    ACSE_OK = 0,
+    ACSE_ERR_ARG = -1,        /* null or inconsistent argument                         */
+    ACSE_ERR_SHAPE = -2,      /* r, N or active range out of the supported range        */
+    ACSE_ERR_NONFINITE = -3,  /* NaN or Inf detected in an input or a result           */
+    ACSE_ERR_TRACE = -4,      /* Tr 2D differs from N(N-1)/2 beyond 1e-8 relative        */
+    ACSE_ERR_CUDA = -5,       /* a CUDA runtime / driver call failed                   */
+    ACSE_ERR_TIMEOUT = -6,    /* a bounded device-side wait ran out                    */
+    ACSE_ERR_NOMEM = -7,      /* device allocation failed at context creation          */
+    ACSE_ERR_UNSUPPORTED = -8 /* option not built (e.g. a reconstruction not available) */
+} acse_status;
+
+typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2 } acse_prec;
+typedef enum { ACSE_RECON_V = 0 } acse_recon;
+
+typedef struct {
+    int r;             /* spatial orbitals, 2 <= r <= 64                                    */
+    int n_alpha;       /* alpha electrons                                                   */
+    int n_beta;        /* beta electrons; N = n_alpha + n_beta >= 2                         */
+    int prec;          /* acse_prec: arithmetic of the O(r^6) contractions                  */
+    int recon;         /* acse_recon                                                        */
+    int mask_active;   /* 1: zero A where i,j,k,l all lie in [act_lo, act_hi) (Methods)     */
+    int act_lo, act_hi;
+    int line_search;   /* 1: acse_step picks eps from ||A(D + e U)||^2 at {0, e0, 2 e0}     */
+    double eps0;       /* initial trial step of the line search (e0); 0 -> 0.1              */
+    int check_inputs;  /* 1: acse_residual / acse_step verify Tr 2D and finiteness (syncs)  */
+} acse_opts;
+
+/* Create a context for one problem.  h (r*r) and V (r^4, chemist's (pq|rs)) are read once to
+ * build the spin-blocked reduced Hamiltonian K of Eq. (2); they may be freed afterwards.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream) on which every call of this
+ * context is ordered.  All device workspace is allocated here (about 40 r^4 doubles plus the
+ * split-precision operand copies), so later calls allocate nothing. */
+int acse_create(acse_ctx** ctx, const acse_opts* opts, const double* h, const double* V,
+                void* cuda_stream);
+
+/* Free the context and its workspace (synchronises its stream first). */
+int acse_destroy(acse_ctx* ctx);
+
+/* Energy E = sum K.2D (Eq. 2 with the convention above), FP64 with a fixed reduction order.
+ * D blocks: 3 x r^4 doubles; E: one double. */
+int acse_energy(acse_ctx* ctx, const double* Daa, const double* Dab, const double* Dbb, double* E);
+
+/* Residual A = <[a+_i a+_j a_l a_k, H]> (Eq. residual with the Valdemoro 3-RDM of App. C,
+ * contracted without storing it) for the 2-RDM D.  Writes the three A blocks (3 x r^4 doubles)
+ * and ||A||^2 (one double, before the mask).  The mask, if enabled, is applied to A. */
+int acse_residual(acse_ctx* ctx, const double* Daa, const double* Dab, const double* Dbb,
+                  double* Aaa, double* Aab, double* Abb, double* norm2);
+
+/* One Euler step of Eq. (update) in place: A = residual(D) (masked if enabled),
+ * U = 1/2 <[a+a+aa, A^]> with the same reconstructed 3-RDM, D <- D + eps U.
+ * eps: the fixed step, or ignored when opts.line_search = 1 (then eps is chosen on the
+ * device from ||A(D + e U)||^2 at e in {0, e0, 2 e0}: the minimiser of the parabola through
+ * them when it is convex, clamped to [e0/4, 2 e0], otherwise the better of e0 and 2 e0; the
+ * next step's e0 is the accepted eps).
+ * Outputs (each may be NULL): E_out = E after the step, norm2_out = ||A||^2 at the D before the
+ * step, eps_used = the step taken. */
+int acse_step(acse_ctx* ctx, double* Daa, double* Dab, double* Dbb, double eps,
+              double* E_out, double* norm2_out, double* eps_used);
+
+/* Adjoint (not in the paper).  For f = wE * E(D_n) + wN * ||A(D_n)||^2 after n fixed Euler steps
+ * D_{k+1} = D_k + eps U(D_k) from D_0 (mask as in opts, no line search), returns the gradient of
+ * f with respect to h (r*r), V (r^4, chemist's order) and the three blocks of D_0.
+ * D_ckpt: n_steps+1 checkpoints, D_ckpt[3k+0..2] = (Daa, Dab, Dbb) of D_k (any of them may be
+ * NULL except D_0; missing ones are recomputed from the previous one).  dh and dV are
+ * symmetrised (h: p<->q; V: the 8-fold permutational symmetry); dD is projected onto tensors
+ * with the symmetries of a 2-RDM (antisymmetric within pairs, pair-Hermitian).  Each output
+ * may be NULL. */
+int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_steps, double eps,
+                           double wE, double wN, double* dh, double* dV,
+                           double* dDaa, double* dDab, double* dDbb);
+
+/* Profiling (not part of the method).  acse_profile(ctx, 1) resets the counters and starts
+ * recording a CUDA-event pair around every O(r^6) GEMM launch of this context (up to 256
+ * launches between reads); acse_profile(ctx, 0) stops.  acse_profile_read synchronises the
+ * context's stream and returns the summed GEMM time in ms, the number of timed GEMM launches,
+ * and the number of kernels this context launched since the last reset.  Host pointers. */
+int acse_profile(acse_ctx* ctx, int enable);
+int acse_profile_read(acse_ctx* ctx, double* gemm_ms, long long* gemm_launches, long long* launches);
+
+/* Text of a status code. */
+const char* acse_strerror(int status);
+
+/* Last error latched in the context (ACSE_OK if none since creation). */
+int acse_last_error(const acse_ctx* ctx);
+
+/* Version string of the library build. */
+const char* acse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACSE_H */

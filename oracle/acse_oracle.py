@@ -315,3 +315,39 @@ def complex_step_dir(h, V, N, D0, eps, nsteps, dh, dV, dD0, wE=1.0, wN=0.0, mask
     (complex step: Im f(x + i t d) / t)."""
     f = objective(h + 1j * t * dh, V + 1j * t * dV, N, D0 + 1j * t * dD0, eps, nsteps, wE, wN, mask)
     return float(np.imag(f) / t)
+
+
+# ----------------------------------------------------------------------------------------
+# single entries at any size (sampled parity)
+# ----------------------------------------------------------------------------------------
+
+def d3_elements(M, g, a, b, c, d, e, f):
+    """3D^{abc}_{def} from Eq. (3rdm_recon) with 3Delta = 0, for integer or broadcastable index
+    arrays; (a,b,c,d,e,f) play the roles of (i,j,p,r,q,l) there."""
+    return (M[a, b, d, e] * g[c, f] - M[a, b, f, e] * g[c, d] - M[a, b, d, f] * g[c, e]
+            - M[a, c, d, e] * g[b, f] + M[a, c, f, e] * g[b, d] + M[a, c, d, f] * g[b, e]
+            + M[b, c, d, e] * g[a, f] - M[b, c, f, e] * g[a, d] - M[b, c, d, f] * g[a, e]) / 9.0
+
+
+def residual_entries(h, V, N, Daa, Dab, Dbb, entries):
+    """A^{ij}_{kl} (spin-orbital indices) for each (i, j, k, l) in `entries`: the printed
+    Eq. (residual) term by term, with each 3D element evaluated from the nine M.1D terms and
+    the overall sign of reading R2.  Holds K, 2D and M (n^4 each) but never 3D."""
+    K = reduced_hamiltonian(h, V, N)
+    D = so_from_blocks(Daa, Dab, Dbb)
+    g = gamma(D, N)
+    M, _ = cumulant_M(D, g)
+    n = D.shape[0]
+    P = np.arange(n)[:, None, None]
+    Rr = np.arange(n)[None, :, None]
+    Qq = np.arange(n)[None, None, :]
+    out = []
+    for (i, j, k, l) in entries:
+        t = 2.0 * np.sum(K[i, j] * D[k, l]) - 2.0 * np.sum(K[k, l] * D[i, j])
+        t += 6.0 * np.sum(K[k][P, Rr, Qq] * d3_elements(M, g, i, j, P, Rr, Qq, l))
+        t -= 6.0 * np.sum(K[l][P, Rr, Qq] * d3_elements(M, g, i, j, P, Rr, Qq, k))
+        # (p, q, r) grids for the last two terms: K^{pq}_{ri} 3D^{jpq}_{rlk}
+        t -= 6.0 * np.sum(K[P, Rr, Qq, i] * d3_elements(M, g, j, P, Rr, Qq, l, k))
+        t += 6.0 * np.sum(K[P, Rr, Qq, j] * d3_elements(M, g, i, P, Rr, Qq, l, k))
+        out.append(-t)
+    return np.array(out)

@@ -1,0 +1,149 @@
+"""ctypes binding of libacse (include/acse.h).  Argument marshalling only: every step of the
+hot path runs in the library's CUDA kernels.  There is no fallback: if the shared library is
+missing or fails to load, every call raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libacse.so")
+
+ACSE_FP64, ACSE_BF16X3, ACSE_TF32 = 0, 1, 2
+PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32}
+
+# symbols declared in include/acse.h
+EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
+           "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_strerror",
+           "acse_last_error", "acse_version")
+
+
+class AcseOpts(ctypes.Structure):
+    _fields_ = [("r", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("prec", c_int), ("recon", c_int),
+                ("mask_active", c_int), ("act_lo", c_int), ("act_hi", c_int), ("line_search", c_int),
+                ("eps0", c_double), ("check_inputs", c_int)]
+
+
+class AcseError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: status {status} ({strerror(status)})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libacse.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.acse_create.argtypes = [POINTER(c_void_p), POINTER(AcseOpts), c_void_p, c_void_p, c_void_p]
+        L.acse_destroy.argtypes = [c_void_p]
+        L.acse_energy.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.acse_residual.argtypes = [c_void_p] + [c_void_p] * 7
+        L.acse_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]
+        L.acse_residual_backward.argtypes = [c_void_p, POINTER(c_void_p), c_int, c_double, c_double, c_double,
+                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.acse_strerror.argtypes = [c_int]
+        L.acse_strerror.restype = ctypes.c_char_p
+        L.acse_last_error.argtypes = [c_void_p]
+        L.acse_version.restype = ctypes.c_char_p
+        L.acse_profile.argtypes = [c_void_p, c_int]
+        L.acse_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(ctypes.c_longlong),
+                                        POINTER(ctypes.c_longlong)]
+        for name in ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
+                     "acse_residual_backward", "acse_last_error", "acse_profile", "acse_profile_read"):
+            getattr(L, name).restype = c_int
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().acse_strerror(int(status)).decode()
+
+
+def version() -> str:
+    return lib().acse_version().decode()
+
+
+def ptr(x):
+    """Raw address of a torch tensor (device or host) or a numpy array (host); None -> NULL."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported argument type {type(x)}")
+
+
+def _check(status, what):
+    if status != 0:
+        raise AcseError(status, what)
+
+
+def current_stream_handle():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=0.1,
+                check_inputs=False, stream=None):
+    o = AcseOpts()
+    o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.recon = 0
+    if mask is not None:
+        o.mask_active, o.act_lo, o.act_hi = 1, int(mask[0]), int(mask[1])
+    o.line_search = int(bool(line_search))
+    o.eps0 = float(eps0)
+    o.check_inputs = int(bool(check_inputs))
+    h_ = c_void_p()
+    st = current_stream_handle() if stream is None else stream
+    _check(lib().acse_create(byref(h_), byref(o), ptr(h), ptr(V), st), "acse_create")
+    return h_
+
+
+def acse_destroy(ctx):
+    _check(lib().acse_destroy(ctx), "acse_destroy")
+
+
+def acse_energy(ctx, Daa, Dab, Dbb, E):
+    _check(lib().acse_energy(ctx, ptr(Daa), ptr(Dab), ptr(Dbb), ptr(E)), "acse_energy")
+
+
+def acse_residual(ctx, Daa, Dab, Dbb, Aaa, Aab, Abb, norm2):
+    _check(lib().acse_residual(ctx, ptr(Daa), ptr(Dab), ptr(Dbb), ptr(Aaa), ptr(Aab), ptr(Abb), ptr(norm2)),
+           "acse_residual")
+
+
+def acse_step(ctx, Daa, Dab, Dbb, eps, E_out=None, norm2_out=None, eps_used=None):
+    _check(lib().acse_step(ctx, ptr(Daa), ptr(Dab), ptr(Dbb), float(eps), ptr(E_out), ptr(norm2_out),
+                           ptr(eps_used)), "acse_step")
+
+
+def acse_residual_backward(ctx, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb):
+    arr = (c_void_p * len(D_ckpt))(*[ptr(x) for x in D_ckpt])
+    _check(lib().acse_residual_backward(ctx, arr, int(n_steps), float(eps), float(wE), float(wN), ptr(dh),
+                                        ptr(dV), ptr(dDaa), ptr(dDab), ptr(dDbb)), "acse_residual_backward")
+
+
+def acse_profile(ctx, enable):
+    _check(lib().acse_profile(ctx, int(enable)), "acse_profile")
+
+
+def acse_profile_read(ctx):
+    """(GEMM milliseconds, timed GEMM launches, kernels launched) since the last reset."""
+    ms = c_double()
+    ng = ctypes.c_longlong()
+    nl = ctypes.c_longlong()
+    _check(lib().acse_profile_read(ctx, byref(ms), byref(ng), byref(nl)), "acse_profile_read")
+    return ms.value, ng.value, nl.value

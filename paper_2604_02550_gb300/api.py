@@ -1,0 +1,80 @@
+"""Torch-facing convenience layer over the C ABI (marshalling only).
+
+Spin blocks are passed as a tuple (Daa, Dab, Dbb) of contiguous float64 tensors of shape
+(r, r, r, r) on the context's device; scalar results are returned as 1-element float64 device
+tensors so that nothing synchronises unless the caller reads them.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+def _dev(x, device):
+    t = torch.as_tensor(x, dtype=torch.float64)
+    return t.to(device).contiguous()
+
+
+class ACSE:
+    """One ACSE problem (integrals and options) bound to a CUDA stream."""
+
+    def __init__(self, r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=0.1,
+                 check_inputs=False, device="cuda", stream=None):
+        self.r, self.n_alpha, self.n_beta = r, n_alpha, n_beta
+        self.device = torch.device(device)
+        self.prec = prec
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.stream(self.stream):
+            h_t = _dev(h, self.device)
+            V_t = _dev(V, self.device)
+            self.ctx = _lib.acse_create(r, n_alpha, n_beta, h_t, V_t, prec, mask, line_search, eps0, check_inputs,
+                                        stream=self.stream.cuda_stream)
+        self._scal = torch.zeros(3, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            _lib.acse_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros_blocks(self):
+        return tuple(torch.zeros((self.r,) * 4, dtype=torch.float64, device=self.device) for _ in range(3))
+
+    def to_blocks(self, blocks):
+        return tuple(_dev(b, self.device) for b in blocks)
+
+    def energy(self, D):
+        E = torch.empty(1, dtype=torch.float64, device=self.device)
+        _lib.acse_energy(self.ctx, *D, E)
+        return E
+
+    def residual(self, D, out=None):
+        A = out if out is not None else self.zeros_blocks()
+        n2 = torch.empty(1, dtype=torch.float64, device=self.device)
+        _lib.acse_residual(self.ctx, *D, *A, n2)
+        return A, n2
+
+    def step(self, D, eps=0.0):
+        """In-place Euler step on D; returns (E_after, norm2_before, eps_used) device tensors."""
+        s = torch.empty(3, dtype=torch.float64, device=self.device)
+        _lib.acse_step(self.ctx, *D, eps, s[0:1], s[1:2], s[2:3])
+        return s[0:1], s[1:2], s[2:3]
+
+    def backward(self, D_ckpt, n_steps, eps, wE=1.0, wN=0.0):
+        """Gradient of wE E(D_n) + wN ||A(D_n)||^2 w.r.t. (h, V, D0 blocks)."""
+        r = self.r
+        dh = torch.empty((r, r), dtype=torch.float64, device=self.device)
+        dV = torch.empty((r,) * 4, dtype=torch.float64, device=self.device)
+        dD = self.zeros_blocks()
+        flat = []
+        for k in range(n_steps + 1):
+            blk = D_ckpt[k] if k < len(D_ckpt) else None
+            flat.extend(blk if blk is not None else (None, None, None))
+        _lib.acse_residual_backward(self.ctx, flat, n_steps, eps, wE, wN, dh, dV, *dD)
+        return dh, dV, dD

@@ -1,0 +1,417 @@
+// C ABI of libacse: context management, argument staging and the order of the hot-path passes.
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#include "acse_internal.h"
+
+int tc_plan_create(acse_ctx* c);
+void tc_plan_destroy(acse_ctx* c);
+int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
+
+static const char* k_version = "libacse 0.1 (sm_103a; FP64 DFMA + tcgen05 split-precision GEMMs)";
+
+extern "C" const char* acse_version(void) { return k_version; }
+
+extern "C" const char* acse_strerror(int s) {
+    switch (s) {
+        case ACSE_OK: return "ok";
+        case ACSE_ERR_ARG: return "invalid argument";
+        case ACSE_ERR_SHAPE: return "unsupported shape (r, N or active range)";
+        case ACSE_ERR_NONFINITE: return "non-finite value in input or result";
+        case ACSE_ERR_TRACE: return "2-RDM trace differs from N(N-1)/2";
+        case ACSE_ERR_CUDA: return "CUDA runtime error";
+        case ACSE_ERR_TIMEOUT: return "device-side wait timed out";
+        case ACSE_ERR_NOMEM: return "device allocation failed";
+        case ACSE_ERR_UNSUPPORTED: return "option not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int acse_last_error(const acse_ctx* c) { return c ? c->last_error : ACSE_ERR_ARG; }
+
+static int latch(acse_ctx* c, int s) {
+    if (c && s != ACSE_OK) c->last_error = s;
+    return s;
+}
+
+// 1 if p is host memory (pageable or pinned), 0 if device or managed, -1 on error.
+static int is_host_ptr(const void* p) {
+    if (!p) return 0;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 0 : 1;
+}
+
+static size_t n4_of(const acse_ctx* c) { return (size_t)c->r * c->r * c->r * c->r; }
+
+// ------------------------------------------------------------------------------- create
+static int alloc_d(void** p, size_t bytes, size_t* total) {
+    *total += bytes;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ACSE_ERR_NOMEM;
+    }
+    return ACSE_OK;
+}
+
+static void free_work(acse_ctx* c) {
+    Work& w = c->w;
+    void* ptrs[] = {w.Kh[0], w.Kh[1], w.Kh[2], w.gam, w.M[0], w.M[1], w.M[2], w.Md, w.Mf1, w.Mf2, w.Zd, w.Zf1,
+                    w.Zf2, w.w, w.Q, w.X[0], w.X[1], w.X[2], w.Y[0], w.Y[1], w.Y[2], w.X5d, w.X5f1, w.X5f2,
+                    w.T[0], w.T[1], w.T[2], w.T[3], w.A[0], w.A[1], w.A[2], w.U[0], w.U[1], w.U[2], w.Dt[0],
+                    w.Dt[1], w.Dt[2], w.stage_in[0], w.stage_in[1], w.stage_in[2], w.stage_out[0],
+                    w.stage_out[1], w.stage_out[2], w.h, w.V, w.scal, w.partial};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    memset(&c->w, 0, sizeof(Work));
+}
+
+static int alloc_work(acse_ctx* c) {
+    Work& w = c->w;
+    memset(&w, 0, sizeof(Work));
+    const size_t n4 = n4_of(c), R2 = (size_t)c->r * c->r;
+    const size_t b4 = n4 * sizeof(double);
+    size_t tot = 0;
+#define A_(p, bytes) ACSE_TRY(alloc_d((void**)&(p), (bytes), &tot))
+    for (int s = 0; s < 3; ++s) {
+        A_(w.Kh[s], b4); A_(w.M[s], b4); A_(w.X[s], b4); A_(w.Y[s], b4);
+        A_(w.A[s], b4); A_(w.U[s], b4); A_(w.Dt[s], b4);
+        A_(w.stage_in[s], b4); A_(w.stage_out[s], b4);
+    }
+    for (int t = 0; t < 4; ++t) A_(w.T[t], b4);
+    A_(w.gam, 2 * R2 * sizeof(double));
+    A_(w.w, 2 * R2 * sizeof(double));
+    A_(w.Q, 2 * R2 * sizeof(double));
+    A_(w.Md, 4 * b4); A_(w.Mf1, b4); A_(w.Mf2, b4);
+    A_(w.Zd, 4 * b4); A_(w.Zf1, b4); A_(w.Zf2, b4);
+    A_(w.X5d, 4 * b4); A_(w.X5f1, b4); A_(w.X5f2, b4);
+    A_(w.h, R2 * sizeof(double));
+    A_(w.V, b4);
+    A_(w.scal, 16 * sizeof(double));
+    w.npartial = 4096;
+    A_(w.partial, (size_t)w.npartial * sizeof(double));
+#undef A_
+    ACSE_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), c->stream));
+    return ACSE_OK;
+}
+
+__global__ void k_set1(double* dst, double v) { *dst = v; }
+
+extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, const double* V, void* stream) {
+    if (!out || !o || !h || !V) return ACSE_ERR_ARG;
+    *out = nullptr;
+    const int N = o->n_alpha + o->n_beta;
+    if (o->r < 2 || o->r > ACSE_MAX_R || o->n_alpha < 0 || o->n_beta < 0 || N < 2 || o->n_alpha > o->r ||
+        o->n_beta > o->r)
+        return ACSE_ERR_SHAPE;
+    if (o->prec < ACSE_FP64 || o->prec > ACSE_TF32) return ACSE_ERR_ARG;
+    if (o->recon != ACSE_RECON_V) return ACSE_ERR_UNSUPPORTED;
+    if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
+    acse_ctx* c = (acse_ctx*)calloc(1, sizeof(acse_ctx));
+    if (!c) return ACSE_ERR_NOMEM;
+    c->opt = *o;
+    c->r = o->r;
+    c->N = N;
+    c->stream = (cudaStream_t)stream;
+    c->nsplit = o->prec == ACSE_BF16X3 ? 3 : 1;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        free(c);
+        return ACSE_ERR_CUDA;
+    }
+    int s = alloc_work(c);
+    if (s == ACSE_OK && o->prec != ACSE_FP64) s = tc_plan_create(c);
+    if (s != ACSE_OK) {
+        tc_plan_destroy(c);
+        free_work(c);
+        free(c);
+        return s;
+    }
+    const size_t R2 = (size_t)c->r * c->r;
+    const cudaMemcpyKind kh = is_host_ptr(h) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kv = is_host_ptr(V) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(c->w.h, h, R2 * sizeof(double), kh, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->w.V, V, R2 * R2 * sizeof(double), kv, c->stream) != cudaSuccess)
+        s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK) s = launch_build_K(c);
+    if (s == ACSE_OK) {
+        k_set1<<<1, 1, 0, c->stream>>>(c->w.scal + 2, o->eps0 > 0.0 ? o->eps0 : 0.1);
+        if (cudaGetLastError() != cudaSuccess) s = ACSE_ERR_CUDA;
+    }
+    // host sources must stay valid until the copies are done
+    if (s == ACSE_OK && (kh == cudaMemcpyHostToDevice || kv == cudaMemcpyHostToDevice) &&
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        s = ACSE_ERR_CUDA;
+    if (s != ACSE_OK) {
+        tc_plan_destroy(c);
+        free_work(c);
+        free(c);
+        return s;
+    }
+    *out = c;
+    return ACSE_OK;
+}
+
+extern "C" int acse_destroy(acse_ctx* c) {
+    if (!c) return ACSE_ERR_ARG;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2 * ACSE_PROF_MAX; ++i)
+        if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+    tc_plan_destroy(c);
+    free_work(c);
+    free(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------------ contraction pass
+// G(W) for the current D: builds the operands, runs every O(r^6) GEMM of the pass in one
+// grouped launch, assembles B and G.  prep_D = 1 recomputes 1D, M and the ph layout of M.
+static int contract_G(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale,
+                      int mask, double* const out[3], double* norm2_dst, int prep_D) {
+    Work& w = c->w;
+    if (prep_D) ACSE_TRY(launch_gamma_M(c, D));
+    if (c->opt.prec == ACSE_FP64) {
+        if (prep_D) ACSE_TRY(launch_pack_Mph(c));
+        ACSE_TRY(launch_W_intermediates(c, W));
+        const int r = c->r, R2 = r * r, R22 = 2 * R2;
+        GemmF64 g[9];
+        int n = 0;
+        for (int s = 0; s < 3; ++s) {
+            const double f = (s == 1) ? 2.0 : 1.0;   // mixed-spin (rs) sums count both orders
+            g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0};
+            g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0};
+        }
+        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0};
+        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0};
+        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0};
+        ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
+    } else {
+        ACSE_TRY(tc_contract(c, D, W, prep_D));
+    }
+    ACSE_TRY(launch_build_B(c));
+    ACSE_TRY(launch_assemble_G(c, sW, scale, mask, out, norm2_dst));
+    return ACSE_OK;
+}
+
+static int residual_dev(acse_ctx* c, const double* const D[3], double* const A[3], double* norm2_dst) {
+    const double* W[3] = {c->w.Kh[0], c->w.Kh[1], c->w.Kh[2]};
+    return contract_G(c, D, W, +1, 1.0, 1, A, norm2_dst, 1);
+}
+
+// Update for the D whose 1D / M are current: U = 1/2 G(A), A pair-anti-Hermitian (s = -1).
+static int update_dev(acse_ctx* c, const double* const D[3], const double* const A[3], double* const U[3]) {
+    return contract_G(c, D, A, -1, 0.5, 0, U, nullptr, 0);
+}
+
+// ------------------------------------------------------------------------- staging
+struct Staged {
+    const double* in[3];
+    double* out[3];
+    int host_in, host_out;
+};
+
+static int stage_inputs(acse_ctx* c, const double* D0, const double* D1, const double* D2, const double* src[3],
+                        int* host) {
+    const double* Ds[3] = {D0, D1, D2};
+    *host = 0;
+    const size_t b4 = n4_of(c) * sizeof(double);
+    for (int s = 0; s < 3; ++s) {
+        if (!Ds[s]) return ACSE_ERR_ARG;
+        if (is_host_ptr(Ds[s])) {
+            ACSE_CUDA_TRY(cudaMemcpyAsync(c->w.stage_in[s], Ds[s], b4, cudaMemcpyHostToDevice, c->stream));
+            src[s] = c->w.stage_in[s];
+            *host = 1;
+        } else {
+            src[s] = Ds[s];
+        }
+    }
+    return ACSE_OK;
+}
+
+static int check_D(acse_ctx* c, const double* const D[3]) {
+    if (!c->opt.check_inputs) return ACSE_OK;
+    ACSE_TRY(launch_trace_check(c, D));
+    double hv[2];
+    ACSE_CUDA_TRY(cudaMemcpyAsync(hv, c->w.scal + 7, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (hv[1] != 0.0) return ACSE_ERR_NONFINITE;
+    const double want = 0.5 * c->N * (c->N - 1);
+    if (!(fabs(hv[0] - want) <= 1e-8 * want)) return ACSE_ERR_TRACE;
+    return ACSE_OK;
+}
+
+static int put_scalar(acse_ctx* c, double* dst, const double* src_dev, int* need_sync) {
+    if (!dst) return ACSE_OK;
+    if (is_host_ptr(dst)) {
+        ACSE_CUDA_TRY(cudaMemcpyAsync(dst, src_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        *need_sync = 1;
+    } else {
+        ACSE_TRY(launch_copy_scalar(c, dst, src_dev));
+    }
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------------------ energy
+extern "C" int acse_energy(acse_ctx* c, const double* Daa, const double* Dab, const double* Dbb, double* E) {
+    if (!c) return ACSE_ERR_ARG;
+    if (!E) return latch(c, ACSE_ERR_ARG);
+    const double* D[3];
+    int host_in = 0, sync = 0;
+    int s = stage_inputs(c, Daa, Dab, Dbb, D, &host_in);
+    if (s == ACSE_OK) s = launch_energy(c, D, c->w.scal + 1);
+    if (s == ACSE_OK) s = put_scalar(c, E, c->w.scal + 1, &sync);
+    if (s == ACSE_OK && (sync || host_in) && cudaStreamSynchronize(c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+    return latch(c, s);
+}
+
+// ---------------------------------------------------------------------------- residual
+extern "C" int acse_residual(acse_ctx* c, const double* Daa, const double* Dab, const double* Dbb, double* Aaa,
+                             double* Aab, double* Abb, double* norm2) {
+    if (!c) return ACSE_ERR_ARG;
+    const double* D[3];
+    int host_in = 0, sync = 0;
+    int s = stage_inputs(c, Daa, Dab, Dbb, D, &host_in);
+    if (s == ACSE_OK) s = check_D(c, D);
+    double* Aout[3] = {Aaa, Aab, Abb};
+    double* A[3];
+    int host_out[3] = {0, 0, 0};
+    for (int b = 0; b < 3 && s == ACSE_OK; ++b) {
+        if (!Aout[b]) {
+            A[b] = c->w.A[b];
+        } else if (is_host_ptr(Aout[b])) {
+            A[b] = c->w.stage_out[b];
+            host_out[b] = 1;
+        } else {
+            A[b] = Aout[b];
+        }
+    }
+    if (s == ACSE_OK) s = residual_dev(c, D, A, c->w.scal + 0);
+    const size_t b4 = n4_of(c) * sizeof(double);
+    for (int b = 0; b < 3 && s == ACSE_OK; ++b)
+        if (host_out[b]) {
+            if (cudaMemcpyAsync(Aout[b], A[b], b4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+            sync = 1;
+        }
+    if (s == ACSE_OK) s = put_scalar(c, norm2, c->w.scal + 0, &sync);
+    if (s == ACSE_OK && (sync || host_in) && cudaStreamSynchronize(c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+    return latch(c, s);
+}
+
+// -------------------------------------------------------------------------------- step
+extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double eps, double* E_out,
+                         double* norm2_out, double* eps_used) {
+    if (!c) return ACSE_ERR_ARG;
+    Work& w = c->w;
+    const double* Din[3];
+    int host_in = 0, sync = 0;
+    int s = stage_inputs(c, Daa, Dab, Dbb, Din, &host_in);
+    if (s == ACSE_OK) s = check_D(c, Din);
+    double* D[3] = {(double*)Din[0], (double*)Din[1], (double*)Din[2]};
+    const double* Dc[3] = {D[0], D[1], D[2]};
+    // A at D (masked), ||A||^2 before the mask -> scal[0]
+    if (s == ACSE_OK) s = residual_dev(c, Dc, w.A, w.scal + 0);
+    const double* Ac[3] = {w.A[0], w.A[1], w.A[2]};
+    if (s == ACSE_OK) s = update_dev(c, Dc, Ac, w.U);
+    const double* Uc[3] = {w.U[0], w.U[1], w.U[2]};
+    if (s == ACSE_OK) {
+        if (c->opt.line_search) {
+            // f(0) = ||A(D)||^2; f(e0), f(2 e0) from trial residuals at D + t e0 U
+            s = launch_copy_scalar(c, w.scal + 4, w.scal + 0);
+            const double* Dt[3] = {w.Dt[0], w.Dt[1], w.Dt[2]};
+            for (int t = 1; t <= 2 && s == ACSE_OK; ++t) {
+                s = launch_axpy(c, D, Uc, w.scal + 2, (double)t, w.Dt);
+                // the trial residual reuses the X/Y/T buffers; its A goes to the stage_out scratch
+                double* At[3] = {w.stage_out[0], w.stage_out[1], w.stage_out[2]};
+                if (s == ACSE_OK) s = residual_dev(c, Dt, At, w.scal + 4 + t);
+            }
+            if (s == ACSE_OK) s = launch_line_search(c);
+        } else {
+            k_set1<<<1, 1, 0, c->stream>>>(w.scal + 3, eps);
+            c->launches++;
+            if (cudaGetLastError() != cudaSuccess) s = ACSE_ERR_CUDA;
+        }
+    }
+    if (s == ACSE_OK) s = launch_axpy(c, D, Uc, w.scal + 3, 1.0, D);
+    if (s == ACSE_OK) s = launch_energy(c, Dc, w.scal + 1);
+    if (s == ACSE_OK && host_in) {
+        const size_t b4 = n4_of(c) * sizeof(double);
+        double* Dh[3] = {Daa, Dab, Dbb};
+        for (int b = 0; b < 3 && s == ACSE_OK; ++b)
+            if (D[b] == w.stage_in[b] &&
+                cudaMemcpyAsync(Dh[b], D[b], b4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+                s = ACSE_ERR_CUDA;
+        sync = 1;
+    }
+    if (s == ACSE_OK) s = put_scalar(c, E_out, w.scal + 1, &sync);
+    if (s == ACSE_OK) s = put_scalar(c, norm2_out, w.scal + 0, &sync);
+    if (s == ACSE_OK) s = put_scalar(c, eps_used, w.scal + 3, &sync);
+    if (s == ACSE_OK && sync && cudaStreamSynchronize(c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+    return latch(c, s);
+}
+
+extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps, double wE,
+                                      double wN, double* dh, double* dV, double* dDaa, double* dDab, double* dDbb) {
+    (void)D_ckpt; (void)n_steps; (void)eps; (void)wE; (void)wN; (void)dh; (void)dV; (void)dDaa; (void)dDab; (void)dDbb;
+    if (!c) return ACSE_ERR_ARG;
+    return latch(c, ACSE_ERR_UNSUPPORTED);
+}
+
+// ------------------------------------------------------------------------------ profiling
+// Event pairs around every O(r^6) GEMM launch while profiling is on; read back (and summed in
+// a fixed order) by acse_profile_read, which synchronises the stream.
+int prof_begin(acse_ctx* c) {
+    if (!c->prof_on) return ACSE_OK;
+    if (c->prof_n >= ACSE_PROF_MAX) return ACSE_OK;   // ring full: later launches not timed
+    cudaEvent_t* e = &c->prof_ev[2 * c->prof_n];
+    if (!e[0]) {
+        ACSE_CUDA_TRY(cudaEventCreate(&e[0]));
+        ACSE_CUDA_TRY(cudaEventCreate(&e[1]));
+    }
+    ACSE_CUDA_TRY(cudaEventRecord(e[0], c->stream));
+    return ACSE_OK;
+}
+
+int prof_end(acse_ctx* c) {
+    if (!c->prof_on || c->prof_n >= ACSE_PROF_MAX) return ACSE_OK;
+    ACSE_CUDA_TRY(cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream));
+    c->prof_n++;
+    return ACSE_OK;
+}
+
+static int prof_drain(acse_ctx* c) {
+    if (c->prof_n == 0) return ACSE_OK;
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->prof_n; ++i) {
+        float ms = 0.f;
+        ACSE_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+        c->prof_ms += ms;
+        c->prof_count++;
+    }
+    c->prof_n = 0;
+    return ACSE_OK;
+}
+
+extern "C" int acse_profile(acse_ctx* c, int enable) {
+    if (!c) return ACSE_ERR_ARG;
+    int s = prof_drain(c);
+    c->prof_on = enable;
+    c->prof_ms = 0.0;
+    c->prof_count = 0;
+    c->launches = 0;
+    return latch(c, s);
+}
+
+extern "C" int acse_profile_read(acse_ctx* c, double* gemm_ms, long long* gemm_launches, long long* launches) {
+    if (!c) return ACSE_ERR_ARG;
+    int s = prof_drain(c);
+    if (gemm_ms) *gemm_ms = c->prof_ms;
+    if (gemm_launches) *gemm_launches = c->prof_count;
+    if (launches) *launches = c->launches;
+    return latch(c, s);
+}

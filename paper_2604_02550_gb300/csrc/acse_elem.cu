@@ -1,0 +1,543 @@
+// Elementwise, O(r^4) and O(r^5) kernels of the ACSE hot path (FP64).
+//
+// Notation: spin blocks X_aa, X_ab, X_bb in full-square row-major [i][j][k][l]
+// (X_ab = X^{ia jb}_{ka lb}); R2 = r^2.  The O(r^6) work (pair-pair and particle-hole
+// GEMMs) is done elsewhere; this file builds their operands and consumes their outputs.
+//
+// The V-reconstructed three-body sum of Appendix C,
+//     B^{ij}_{kl} = sum_{pqr} W^{kp}_{rq} 3D^{ijp}_{rql},
+// splits (nine M.1D terms, pairs of which coincide by antisymmetry) into
+//     B = (X1 - 2 X2 - X4 + 2 X5 + X7 - 2 X8) / 9,
+//     X^{ij}_{kp} = sum_rs M^{ij}_{rs} W^{kp}_{rs}   (pair GEMM)     X1 = X . 1D over p
+//     w^k_s  = sum_pr W^{kp}_{rs} 1D^p_r                              X2^{ij}_{kl} = sum_s w^k_s M^{ij}_{ls}
+//     Q^k_i  = sum_prs W^{kp}_{rs} M^{ip}_{rs}                        X4 = Q^k_i 1D^j_l,  X7 = Q^k_j 1D^i_l
+//     Z^{kp}_{js} = sum_r W^{kp}_{rs} 1D^j_r                          X5^{ij}_{kl} = sum_ps Z^{kp}_{js} M^{ip}_{ls}
+//     X8 = X5 with i <-> j                                             (particle-hole GEMM)
+// (the E^{ij}_{kl} intermediate of Appendix C is 2 X5 - X4), and the residual of
+// Eq. (residual) with the commutator sign convention becomes
+//     G(W) = 4 (Y - s Y^T) - 12 (B - B_{k<->l}) + 12 s (B^T - B^T_{i<->j}),   Y = D W^T,
+// s = +1 for a pair-Hermitian W (W = K/2: the residual A) and -1 for a pair-anti-Hermitian
+// W (W = A: the update, whose commutator sign flips, Appendix B last remark).
+#include "acse_internal.h"
+
+#define TPB 256
+
+static inline int grid_for(size_t n, int tpb = TPB) {
+    size_t g = (n + tpb - 1) / tpb;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum (deterministic); result valid in thread 0.
+__device__ double block_sum(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+// ---------------------------------------------------------------------------------- K
+// Eq. (2) read as K = 1/2(<pq|rs> - <pq|sr>) + (h_pr d_qs + h_qs d_pr - h_ps d_qr - h_qr d_ps)/(2(N-1)),
+// <pq|rs> = (pr|qs).  Stored halved: the residual's W is K/2 (H = sum (K/2) a+a+aa).
+__global__ void k_build_K(int r, double inv2N1, const double* __restrict__ h, const double* __restrict__ V,
+                          double* __restrict__ Kaa, double* __restrict__ Kab, double* __restrict__ Kbb) {
+    const size_t n = (size_t)r * r * r * r;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e % r), k = (int)((e / r) % r), j = (int)((e / ((size_t)r * r)) % r),
+                  i = (int)(e / ((size_t)r * r * r));
+        const double vd = V[(((size_t)i * r + k) * r + j) * r + l];   // (ik|jl) = <ij|kl>
+        const double vx = V[(((size_t)i * r + l) * r + j) * r + k];   // (il|jk) = <ij|lk>
+        const double hik = h[i * r + k] * (j == l), hjl = h[j * r + l] * (i == k);
+        const double hil = h[i * r + l] * (j == k), hjk = h[j * r + k] * (i == l);
+        const double ks = 0.5 * (vd - vx) + (hik + hjl - hil - hjk) * inv2N1;
+        const double kx = 0.5 * vd + (hik + hjl) * inv2N1;
+        Kaa[e] = 0.5 * ks;
+        Kbb[e] = 0.5 * ks;
+        Kab[e] = 0.5 * kx;
+    }
+}
+
+int launch_build_K(acse_ctx* c) {
+    const int r = c->r;
+    const size_t n = (size_t)r * r * r * r;
+    k_build_K<<<grid_for(n), TPB, 0, c->stream>>>(r, 1.0 / (2.0 * (c->N - 1)), c->w.h, c->w.V, c->w.Kh[0],
+                                                  c->w.Kh[1], c->w.Kh[2]);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------------------ 1D and M
+// 1D^p_r = 2/(N-1) sum_q 2D^{pq}_{rq} over spin orbitals (App. C):
+//   g_a[p][r] = c sum_q (Daa[p][q][r][q] + Dab[p][q][r][q]);  g_b[p][r] = c sum_q (Dbb[p][q][r][q] + Dab[q][p][q][r]).
+__global__ void k_gamma(int r, double cN, const double* __restrict__ Daa, const double* __restrict__ Dab,
+                        const double* __restrict__ Dbb, double* __restrict__ gam) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * r * r) return;
+    const int sp = t / (r * r), p = (t / r) % r, rr = t % r;
+    const size_t r3 = (size_t)r * r * r, r2 = (size_t)r * r;
+    double s = 0.0;
+    if (sp == 0) {
+        for (int q = 0; q < r; ++q) s += Daa[p * r3 + q * r2 + rr * r + q] + Dab[p * r3 + q * r2 + rr * r + q];
+    } else {
+        for (int q = 0; q < r; ++q) s += Dbb[p * r3 + q * r2 + rr * r + q] + Dab[q * r3 + p * r2 + q * r + rr];
+    }
+    gam[t] = cN * s;
+}
+
+// M = 3 2Delta + 1D^1D = 3 2D - 2 (1D^1D), (1D^1D)^{ij}_{kl} = 1/2(g^i_k g^j_l - g^j_k g^i_l) (App. C);
+// the exchange piece vanishes in the ab block (1D is spin diagonal).
+__global__ void k_build_M(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
+                          const double* __restrict__ Dab, const double* __restrict__ Dbb, double* __restrict__ Maa,
+                          double* __restrict__ Mab, double* __restrict__ Mbb) {
+    const size_t n = (size_t)r * r * r * r;
+    const double* ga = gam;
+    const double* gb = gam + r * r;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e % r), k = (int)((e / r) % r), j = (int)((e / ((size_t)r * r)) % r),
+                  i = (int)(e / ((size_t)r * r * r));
+        Maa[e] = 3.0 * Daa[e] - (ga[i * r + k] * ga[j * r + l] - ga[j * r + k] * ga[i * r + l]);
+        Mbb[e] = 3.0 * Dbb[e] - (gb[i * r + k] * gb[j * r + l] - gb[j * r + k] * gb[i * r + l]);
+        Mab[e] = 3.0 * Dab[e] - ga[i * r + k] * gb[j * r + l];
+    }
+}
+
+int launch_gamma_M(acse_ctx* c, const double* const D[3]) {
+    const int r = c->r;
+    k_gamma<<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, 2.0 / (c->N - 1), D[0], D[1], D[2], c->w.gam);
+    ACSE_LAUNCHED(c);
+    const size_t n = (size_t)r * r * r * r;
+    k_build_M<<<grid_for(n), TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], c->w.M[0], c->w.M[1], c->w.M[2]);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------ particle-hole layout of M
+// Diagonal ph sector: rows (sI,i,l), cols (sP,p,s) of M^{i sI, p sP}_{l sI, s sP}:
+//   (a,a) Maa[i][p][l][s]  (a,b) Mab[i][p][l][s]  (b,a) Mab[p][i][s][l]  (b,b) Mbb[i][p][l][s]
+// Spin-flip sectors (both Z and M carry a sign -1 there, which cancels in the product):
+//   F1: (I,L) = (ia, lb), (P,S) = (pb, sa):  Mf1[(i,l)][(p,s)] = Mab[i][p][s][l]
+//   F2: (I,L) = (ib, la), (P,S) = (pa, sb):  Mf2[(i,l)][(p,s)] = Mab[p][i][l][s]
+__global__ void k_pack_Mph(int r, const double* __restrict__ Maa, const double* __restrict__ Mab,
+                           const double* __restrict__ Mbb, double* __restrict__ Md, double* __restrict__ Mf1,
+                           double* __restrict__ Mf2) {
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    const size_t nd = 4 * n4;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < nd) {
+            const size_t row = e / (2 * R2), col = e % (2 * R2);
+            const int sI = (int)(row / R2), sP = (int)(col / R2);
+            const int i = (int)((row % R2) / r), l = (int)(row % r);
+            const int p = (int)((col % R2) / r), s = (int)(col % r);
+            double v;
+            if (sI == 0 && sP == 0) v = Maa[((i * r + p) * (size_t)r + l) * r + s];
+            else if (sI == 0) v = Mab[((i * r + p) * (size_t)r + l) * r + s];
+            else if (sP == 0) v = Mab[((p * r + i) * (size_t)r + s) * r + l];
+            else v = Mbb[((i * r + p) * (size_t)r + l) * r + s];
+            Md[e] = v;
+        } else {
+            const size_t f = e - nd;
+            const int which = (int)(f / n4);
+            const size_t g = f % n4;
+            const int i = (int)(g / (R2 * r)), l = (int)((g / R2) % r), p = (int)((g / r) % r), s = (int)(g % r);
+            if (which == 0) Mf1[g] = Mab[((i * r + p) * (size_t)r + s) * r + l];
+            else Mf2[g] = Mab[((p * r + i) * (size_t)r + l) * r + s];
+        }
+    }
+}
+
+int launch_pack_Mph(acse_ctx* c) {
+    const int r = c->r;
+    const size_t n = (size_t)6 * r * r * r * r;
+    k_pack_Mph<<<grid_for(n), TPB, 0, c->stream>>>(r, c->w.M[0], c->w.M[1], c->w.M[2], c->w.Md, c->w.Mf1, c->w.Mf2);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------- W-dependent intermediates
+// Z^{kp}_{js} = sum_r W^{kp}_{rs} 1D^j_r in the ph layout (rows (sK,k,j), cols (sP,p,s)):
+//   (a,a) sum_r Waa[k][p][r][s] ga[j][r]     (a,b) sum_r Wab[k][p][r][s] ga[j][r]
+//   (b,a) sum_r Wab[p][k][s][r] gb[j][r]     (b,b) sum_r Wbb[k][p][r][s] gb[j][r]
+//   F1:   Zf1[(k,j)][(p,s)] = sum_r Wab[k][p][s][r] gb[j][r]
+//   F2:   Zf2[(k,j)][(p,s)] = sum_r Wab[p][k][r][s] ga[j][r]
+__global__ void k_build_Z(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
+                          const double* __restrict__ Wbb, const double* __restrict__ gam, double* __restrict__ Zd,
+                          double* __restrict__ Zf1, double* __restrict__ Zf2) {
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2, r3 = R2 * r;
+    const size_t nd = 4 * n4;
+    const double* ga = gam;
+    const double* gb = gam + R2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        if (e < nd) {
+            const size_t row = e / (2 * R2), col = e % (2 * R2);
+            const int sK = (int)(row / R2), sP = (int)(col / R2);
+            const int k = (int)((row % R2) / r), j = (int)(row % r);
+            const int p = (int)((col % R2) / r), s = (int)(col % r);
+            if (sK == 0) {
+                const double* W = (sP == 0) ? Waa : Wab;
+                const double* base = W + k * r3 + p * R2 + s;
+                for (int q = 0; q < r; ++q) acc += base[q * r] * ga[j * r + q];
+            } else if (sP == 0) {
+                const double* base = Wab + p * r3 + k * R2 + s * r;
+                for (int q = 0; q < r; ++q) acc += base[q] * gb[j * r + q];
+            } else {
+                const double* base = Wbb + k * r3 + p * R2 + s;
+                for (int q = 0; q < r; ++q) acc += base[q * r] * gb[j * r + q];
+            }
+            Zd[e] = acc;
+        } else {
+            const size_t f = e - nd;
+            const int which = (int)(f / n4);
+            const size_t g = f % n4;
+            const int k = (int)(g / (R2 * r)), j = (int)((g / R2) % r), p = (int)((g / r) % r), s = (int)(g % r);
+            if (which == 0) {
+                const double* base = Wab + k * r3 + p * R2 + s * r;
+                for (int q = 0; q < r; ++q) acc += base[q] * gb[j * r + q];
+                Zf1[g] = acc;
+            } else {
+                const double* base = Wab + p * r3 + k * R2 + s;
+                for (int q = 0; q < r; ++q) acc += base[q * r] * ga[j * r + q];
+                Zf2[g] = acc;
+            }
+        }
+    }
+}
+
+// w^k_s = sum_pr W^{kp}_{rs} 1D^p_r (spin diagonal):
+//   w_a[k][s] = sum Waa[k][p][r][s] ga[p][r] - sum Wab[k][p][s][r] gb[p][r]
+//   w_b[k][s] = sum Wbb[k][p][r][s] gb[p][r] - sum Wab[p][k][r][s] ga[p][r]
+__global__ void k_build_w(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
+                          const double* __restrict__ Wbb, const double* __restrict__ gam, double* __restrict__ wv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * r * r) return;
+    const int sp = t / (r * r), k = (t / r) % r, s = t % r;
+    const size_t R2 = (size_t)r * r, r3 = R2 * r;
+    const double* ga = gam;
+    const double* gb = gam + R2;
+    double acc = 0.0;
+    for (int p = 0; p < r; ++p)
+        for (int q = 0; q < r; ++q) {
+            if (sp == 0)
+                acc += Waa[k * r3 + p * R2 + q * r + s] * ga[p * r + q] - Wab[k * r3 + p * R2 + s * r + q] * gb[p * r + q];
+            else
+                acc += Wbb[k * r3 + p * R2 + q * r + s] * gb[p * r + q] - Wab[p * r3 + k * R2 + q * r + s] * ga[p * r + q];
+        }
+    wv[t] = acc;
+}
+
+// Q^k_i = sum_prs W^{kp}_{rs} M^{ip}_{rs} (spin diagonal; the mixed-spin (rs) sum counts both
+// orders, hence the factor 2):
+//   Q_a[k][i] = sum Waa[k][prs] Maa[i][prs] + 2 sum Wab[k][prs] Mab[i][prs]
+//   Q_b[k][i] = sum Wbb[k][prs] Mbb[i][prs] + 2 sum Wab[p][k][rs] Mab[p][i][rs]
+__global__ void k_build_Q(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
+                          const double* __restrict__ Wbb, const double* __restrict__ Maa,
+                          const double* __restrict__ Mab, const double* __restrict__ Mbb, double* __restrict__ Qv) {
+    const int t = blockIdx.x;
+    const int sp = t / (r * r), k = (t / r) % r, i = t % r;
+    const size_t R2 = (size_t)r * r, r3 = R2 * r;
+    double acc = 0.0;
+    if (sp == 0) {
+        for (size_t e = threadIdx.x; e < r3; e += blockDim.x)
+            acc += Waa[k * r3 + e] * Maa[i * r3 + e] + 2.0 * Wab[k * r3 + e] * Mab[i * r3 + e];
+    } else {
+        for (size_t e = threadIdx.x; e < r3; e += blockDim.x) {
+            const size_t p = e / R2, rs = e % R2;
+            acc += Wbb[k * r3 + e] * Mbb[i * r3 + e] + 2.0 * Wab[p * r3 + k * R2 + rs] * Mab[p * r3 + i * R2 + rs];
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) Qv[t] = acc;
+}
+
+int launch_W_intermediates(acse_ctx* c, const double* const W[3]) {
+    const int r = c->r;
+    const size_t n = (size_t)6 * r * r * r * r;
+    k_build_Z<<<grid_for(n), TPB, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.Zd, c->w.Zf1, c->w.Zf2);
+    ACSE_LAUNCHED(c);
+    k_build_w<<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.w);
+    ACSE_LAUNCHED(c);
+    k_build_Q<<<2 * r * r, TPB, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.M[0], c->w.M[1], c->w.M[2], c->w.Q);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------------- B spin types
+// T0 = B^{ia ja}_{ka la}, T1 = B^{ib jb}_{kb lb}, T2 = B^{ia jb}_{ka lb}, T3 = B^{ia jb}_{kb la}.
+// X5 sources: diag ph output X5d[(sK,k,j)][(sI,i,l)], flips X5f1[(k,j)][(i,l)] (K=ka, J=jb),
+// X5f2[(k,j)][(i,l)] (K=kb, J=ja).
+struct BArgs {
+    int r;
+    const double* X[3];
+    const double* X5d;
+    const double* X5f1;
+    const double* X5f2;
+    const double* M[3];
+    const double* gam;
+    const double* w;
+    const double* Q;
+    double* T[4];
+};
+
+__global__ void k_build_B(const __grid_constant__ BArgs a) {
+    const int r = a.r;
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2, R22 = 2 * R2;
+    const double* ga = a.gam;
+    const double* gb = a.gam + R2;
+    const double* wa = a.w;
+    const double* wb = a.w + R2;
+    const double* Qa = a.Q;
+    const double* Qb = a.Q + R2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 4 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e / n4);
+        const size_t g = e % n4;
+        const int i = (int)(g / (R2 * r)), j = (int)((g / R2) % r), k = (int)((g / r) % r), l = (int)(g % r);
+        const size_t ij = (size_t)i * r + j;
+        double x1 = 0.0, x2 = 0.0, x4 = 0.0, x5, x7 = 0.0, x8;
+        if (t < 2) {
+            const double* X = a.X[t == 0 ? 0 : 2];
+            const double* M = a.M[t == 0 ? 0 : 2];
+            const double* gg = t == 0 ? ga : gb;
+            const double* ww = t == 0 ? wa : wb;
+            const double* QQ = t == 0 ? Qa : Qb;
+            const double* Xr = X + ij * R2 + (size_t)k * r;
+            const double* Mr = M + ij * R2 + (size_t)l * r;
+            for (int p = 0; p < r; ++p) {
+                x1 += Xr[p] * gg[p * r + l];
+                x2 += ww[k * r + p] * Mr[p];
+            }
+            x4 = QQ[k * r + i] * gg[j * r + l];
+            x7 = QQ[k * r + j] * gg[i * r + l];
+            const size_t off = (size_t)t * R2;
+            x5 = a.X5d[(off + (size_t)k * r + j) * R22 + off + (size_t)i * r + l];
+            x8 = a.X5d[(off + (size_t)k * r + i) * R22 + off + (size_t)j * r + l];
+        } else if (t == 2) {
+            // I=ia J=jb K=ka L=lb
+            const double* Xr = a.X[1] + ij * R2 + (size_t)k * r;
+            const double* Mab = a.M[1] + ij * R2;
+            for (int p = 0; p < r; ++p) {
+                x1 += Xr[p] * gb[p * r + l];
+                x2 -= wa[k * r + p] * Mab[(size_t)p * r + l];
+            }
+            x4 = Qa[k * r + i] * gb[j * r + l];
+            x5 = a.X5f1[((size_t)k * r + j) * R2 + (size_t)i * r + l];
+            x8 = a.X5d[((size_t)k * r + i) * R22 + R2 + (size_t)j * r + l];
+        } else {
+            // I=ia J=jb K=kb L=la
+            const double* Xr = a.X[1] + ij * R2 + k;
+            const double* Mr = a.M[1] + ij * R2 + (size_t)l * r;
+            for (int p = 0; p < r; ++p) {
+                x1 -= Xr[(size_t)p * r] * ga[p * r + l];
+                x2 += wb[k * r + p] * Mr[p];
+            }
+            x5 = a.X5d[(R2 + (size_t)k * r + j) * R22 + (size_t)i * r + l];
+            x7 = Qb[k * r + j] * ga[i * r + l];
+            x8 = a.X5f2[((size_t)k * r + i) * R2 + (size_t)j * r + l];
+        }
+        a.T[t][g] = (x1 - 2.0 * x2 - x4 + 2.0 * x5 + x7 - 2.0 * x8) * (1.0 / 9.0);
+    }
+}
+
+int launch_build_B(acse_ctx* c) {
+    BArgs a;
+    a.r = c->r;
+    for (int s = 0; s < 3; ++s) { a.X[s] = c->w.X[s]; a.M[s] = c->w.M[s]; }
+    a.X5d = c->w.X5d; a.X5f1 = c->w.X5f1; a.X5f2 = c->w.X5f2;
+    a.gam = c->w.gam; a.w = c->w.w; a.Q = c->w.Q;
+    for (int t = 0; t < 4; ++t) a.T[t] = c->w.T[t];
+    const size_t n = (size_t)4 * c->r * c->r * c->r * c->r;
+    k_build_B<<<grid_for(n), TPB, 0, c->stream>>>(a);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// --------------------------------------------------------------------------- G assembly
+// G_aa[ij][kl] = 4(Yaa[ij][kl] - s Yaa[kl][ij]) - 12(T0[ij][kl] - T0[ij][lk]) + 12 s (T0[kl][ij] - T0[kl][ji])
+// G_bb likewise with T1;
+// G_ab[ij][kl] = 4(Yab[ij][kl] - s Yab[kl][ij]) - 12(T2[ij][kl] - T3[ij][lk]) + 12 s (T2[kl][ij] - T3[kl][ji]).
+// out = scale * G; norm^2 partials (aa + bb + 4 ab, before the mask) per block.
+struct GArgs {
+    int r;
+    const double* Y[3];
+    const double* T[4];
+    double* out[3];
+    double s, scale;
+    int mask, lo, hi;
+    double* partial;
+};
+
+#define G_GRID (152 * 4)
+
+__global__ void __launch_bounds__(TPB) k_assemble_G(const __grid_constant__ GArgs a) {
+    const int r = a.r;
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    double nrm = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 3 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        const int blk = (int)(e / n4);
+        const size_t g = e % n4;
+        const int i = (int)(g / (R2 * r)), j = (int)((g / R2) % r), k = (int)((g / r) % r), l = (int)(g % r);
+        const size_t ij = (size_t)i * r + j, kl = (size_t)k * r + l, lk = (size_t)l * r + k, ji = (size_t)j * r + i;
+        const double* Y = a.Y[blk];
+        const double* P;
+        const double* Qx;
+        if (blk == 0) { P = a.T[0]; Qx = a.T[0]; }
+        else if (blk == 2) { P = a.T[1]; Qx = a.T[1]; }
+        else { P = a.T[2]; Qx = a.T[3]; }
+        const double v = 4.0 * (Y[ij * R2 + kl] - a.s * Y[kl * R2 + ij])
+                         - 12.0 * (P[ij * R2 + kl] - Qx[ij * R2 + lk])
+                         + 12.0 * a.s * (P[kl * R2 + ij] - Qx[kl * R2 + ji]);
+        double o = a.scale * v;
+        nrm += (blk == 1 ? 4.0 : 1.0) * o * o;
+        if (a.mask && i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo &&
+            l < a.hi)
+            o = 0.0;
+        a.out[blk][g] = o;
+    }
+    nrm = block_sum(nrm);
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = nrm;
+}
+
+// Fixed-order final sum of `n` partials into dst (one block).
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double* __restrict__ dst) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+    v = block_sum(v);
+    if (threadIdx.x == 0) *dst = v;
+}
+
+int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3], double* norm2_dst) {
+    GArgs a;
+    a.r = c->r;
+    for (int s = 0; s < 3; ++s) { a.Y[s] = c->w.Y[s]; a.out[s] = out[s]; }
+    for (int t = 0; t < 4; ++t) a.T[t] = c->w.T[t];
+    a.s = (double)sW;
+    a.scale = scale;
+    a.mask = apply_mask && c->opt.mask_active;
+    a.lo = c->opt.act_lo;
+    a.hi = c->opt.act_hi;
+    a.partial = c->w.partial;
+    k_assemble_G<<<G_GRID, TPB, 0, c->stream>>>(a);
+    ACSE_LAUNCHED(c);
+    if (norm2_dst) {
+        k_sum_partials<<<1, TPB, 0, c->stream>>>(c->w.partial, G_GRID, norm2_dst);
+        ACSE_LAUNCHED(c);
+    }
+    return ACSE_OK;
+}
+
+// ----------------------------------------------------------------------------- energy
+// E = sum K.2D = 2 [sum Kh_aa D_aa + sum Kh_bb D_bb + 4 sum Kh_ab D_ab]   (Kh = K/2)
+__global__ void __launch_bounds__(TPB) k_energy(int r, const double* __restrict__ Kaa, const double* __restrict__ Kab,
+                                                const double* __restrict__ Kbb, const double* __restrict__ Daa,
+                                                const double* __restrict__ Dab, const double* __restrict__ Dbb,
+                                                double* __restrict__ partial) {
+    const size_t n4 = (size_t)r * r * r * r;
+    double s = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x)
+        s += Kaa[e] * Daa[e] + Kbb[e] * Dbb[e] + 4.0 * Kab[e] * Dab[e];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = 2.0 * s;
+}
+
+int launch_energy(acse_ctx* c, const double* const D[3], double* E_dst) {
+    k_energy<<<G_GRID, TPB, 0, c->stream>>>(c->r, c->w.Kh[0], c->w.Kh[1], c->w.Kh[2], D[0], D[1], D[2],
+                                            c->w.partial + G_GRID);
+    ACSE_LAUNCHED(c);
+    k_sum_partials<<<1, TPB, 0, c->stream>>>(c->w.partial + G_GRID, G_GRID, E_dst);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------------------ axpy
+// out = D + (mul * eps) U, eps read from device memory (the line search writes it there).
+__global__ void k_axpy(size_t n, const double* __restrict__ D0, const double* __restrict__ D1,
+                       const double* __restrict__ D2, const double* __restrict__ U0, const double* __restrict__ U1,
+                       const double* __restrict__ U2, const double* __restrict__ eps, double mul, double* O0,
+                       double* O1, double* O2) {
+    const double e = mul * (*eps);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 3 * n; t += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / n);
+        const size_t i = t % n;
+        if (b == 0) O0[i] = D0[i] + e * U0[i];
+        else if (b == 1) O1[i] = D1[i] + e * U1[i];
+        else O2[i] = D2[i] + e * U2[i];
+    }
+}
+
+int launch_axpy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev, double eps_mul,
+                double* const out[3]) {
+    const size_t n = (size_t)c->r * c->r * c->r * c->r;
+    k_axpy<<<grid_for(3 * n), TPB, 0, c->stream>>>(n, D[0], D[1], D[2], U[0], U[1], U[2], eps_dev, eps_mul, out[0],
+                                                   out[1], out[2]);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------------ line search
+// scal[2] = e0 (state), scal[4..6] = f(0), f(e0), f(2 e0)  ->  scal[3] = eps, scal[2] = eps.
+__global__ void k_line_search(double* scal) {
+    const double e0 = scal[2], f0 = scal[4], f1 = scal[5], f2 = scal[6];
+    const double cc = (f2 - 2.0 * f1 + f0) / (2.0 * e0 * e0);
+    double x;
+    if (cc > 0.0) {
+        const double b = (f1 - f0) / e0 - cc * e0;
+        x = -b / (2.0 * cc);
+        x = fmin(fmax(x, 0.25 * e0), 2.0 * e0);
+    } else {
+        x = (f1 <= f2) ? e0 : 2.0 * e0;
+    }
+    scal[3] = x;
+    scal[2] = x;
+}
+
+int launch_line_search(acse_ctx* c) {
+    k_line_search<<<1, 1, 0, c->stream>>>(c->w.scal);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// --------------------------------------------------------------------------- checks
+// scal[7] = spin-orbital trace Tr 2D = Tr aa + Tr bb + 2 Tr ab;  scal[8] = 1 if any entry of D is not finite.
+__global__ void k_trace_check(int r, const double* __restrict__ Daa, const double* __restrict__ Dab,
+                              const double* __restrict__ Dbb, double* scal) {
+    const size_t n4 = (size_t)r * r * r * r, R2 = (size_t)r * r;
+    double tr = 0.0, bad = 0.0;
+    for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
+        const double a = Daa[e], b = Dab[e], c = Dbb[e];
+        if (!isfinite(a) || !isfinite(b) || !isfinite(c)) bad = 1.0;
+        const size_t row = e / R2, col = e % R2;
+        if (row == col) tr += a + c + 2.0 * b;
+    }
+    tr = block_sum(tr);
+    bad = block_sum(bad);
+    if (threadIdx.x == 0) {
+        scal[7] = tr;
+        scal[8] = bad;
+    }
+}
+
+int launch_trace_check(acse_ctx* c, const double* const D[3]) {
+    k_trace_check<<<1, 1024, 0, c->stream>>>(c->r, D[0], D[1], D[2], c->w.scal);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+__global__ void k_copy1(double* dst, const double* src) { *dst = *src; }
+
+int launch_copy_scalar(acse_ctx* c, double* dst, const double* src) {
+    k_copy1<<<1, 1, 0, c->stream>>>(dst, src);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}

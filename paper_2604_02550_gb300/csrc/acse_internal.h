@@ -1,0 +1,146 @@
+// Internal declarations shared by the translation units of libacse.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/acse.h"
+
+#define ACSE_MAX_R 64
+
+// ------------------------------------------------------------------------------------------
+// Dense "NT" GEMM problem: C[m*ldc + n] = alpha * sum_k A[m*lda + k] * B[n*ldb + k] (+ beta*C).
+// Both operands are K-major (row m of A and row n of B hold contiguous k).
+// ------------------------------------------------------------------------------------------
+struct GemmF64 {
+    const double* A;
+    const double* B;
+    double* C;
+    int M, N, K;
+    int lda, ldb, ldc;
+    double alpha, beta;
+};
+
+// Split-precision operand problem for the tensor-core path.  A and B are 16-bit (BF16) or
+// 32-bit (TF32) element arrays with K' = nsplit * K columns (zero padded to a multiple of the
+// K tile).  C is FP32.
+struct GemmTC {
+    const void* A;
+    const void* B;
+    float* C;
+    int M, N, Kp;          // Kp = padded split-K length in elements
+    int lda, ldb, ldc;     // elements
+    float alpha;
+};
+
+// Scratch layout of one context (all device memory, owned by the context).
+struct Work {
+    // K/2 blocks (the W of the residual), r^4 each
+    double* Kh[3];
+    // 1-RDM per spin (r^2 each) and the M blocks (r^4 each)
+    double* gam;          // [2][r][r]
+    double* M[3];
+    // particle-hole layouts of M: diag (2r^2 x 2r^2), flips (r^2 x r^2)
+    double* Md;
+    double* Mf1;
+    double* Mf2;
+    // per-W intermediates
+    double* Zd;
+    double* Zf1;
+    double* Zf2;
+    double* w;            // [2][r][r]
+    double* Q;            // [2][r][r]
+    double* X[3];         // pair GEMM outputs M W^T (r^4 each)
+    double* Y[3];         // pair GEMM outputs D W^T
+    double* X5d;          // 4 r^4
+    double* X5f1;
+    double* X5f2;
+    double* T[4];         // B spin types aaaa, bbbb, abab, abba (r^4 each)
+    // residual, update, trial D for the line search
+    double* A[3];
+    double* U[3];
+    double* Dt[3];
+    // host-argument staging
+    double* stage_in[3];
+    double* stage_out[3];
+    double* h;            // r^2 copy of h
+    double* V;            // r^4 copy of V
+    // scalars: [0] norm2, [1] E, [2] eps0 (line-search state), [3] eps used, [4..6] f0,f1,f2,
+    //          [7] trace, [8] nonfinite flag
+    double* scal;
+    double* partial;      // reduction partials
+    int npartial;
+    // mixed-precision operand copies (bf16 or tf32 bit patterns), allocated when prec != FP64
+    void* tc_pairA[3];    // [M; D] split, (2 r^2) x Kp
+    void* tc_pairB[3];    // W split, r^2 x Kp
+    void* tc_Md;          // (2r^2) x Kp2
+    void* tc_Zd;
+    void* tc_Mf[2];
+    void* tc_Zf[2];
+    float* tc_pairC[3];   // [X; Y] FP32 (2r^2 x r^2)
+    float* tc_X5d;
+    float* tc_X5f[2];
+    int Kp1, Kp2;         // padded split K for r^2 and 2 r^2 contractions
+};
+
+struct acse_ctx {
+    acse_opts opt;
+    int r, N;
+    cudaStream_t stream;
+    int last_error;
+    int device;
+    int nsplit;           // split terms for the tensor-core path (3 for BF16x3, 1 for TF32)
+    Work w;
+    void* tc_plan;        // tensor-core GEMM plan (tensor maps etc.)
+    // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches
+    long long launches;
+    int prof_on;
+    int prof_n;           // recorded event pairs (ring of ACSE_PROF_MAX)
+    cudaEvent_t prof_ev[2 * 256];
+    double prof_ms;       // summed GEMM time of pairs already read back
+    long long prof_count;
+};
+#define ACSE_PROF_MAX 256
+
+// count a kernel launch of context c and check the launch error
+#define ACSE_LAUNCHED(c)                                                      \
+    do {                                                                      \
+        (c)->launches++;                                                      \
+        if (cudaGetLastError() != cudaSuccess) return ACSE_ERR_CUDA;          \
+    } while (0)
+
+int prof_begin(acse_ctx* c);
+int prof_end(acse_ctx* c);
+
+// error helpers ---------------------------------------------------------------------------
+#define ACSE_CUDA_TRY(expr)                                                   \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) return ACSE_ERR_CUDA;                          \
+    } while (0)
+
+#define ACSE_TRY(expr)                                                        \
+    do {                                                                      \
+        int _s = (expr);                                                      \
+        if (_s != ACSE_OK) return _s;                                         \
+    } while (0)
+
+// kernels (acse_elem.cu) -------------------------------------------------------------------
+int launch_build_K(acse_ctx* c);
+int launch_gamma_M(acse_ctx* c, const double* const D[3]);
+int launch_pack_Mph(acse_ctx* c);
+int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
+int launch_build_B(acse_ctx* c);
+int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3],
+                      double* norm2_dst);
+int launch_energy(acse_ctx* c, const double* const D[3], double* E_dst);
+int launch_axpy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev,
+                double eps_mul, double* const out[3]);
+int launch_line_search(acse_ctx* c);
+int launch_trace_check(acse_ctx* c, const double* const D[3]);
+int launch_copy_scalar(acse_ctx* c, double* dst, const double* src);
+
+// GEMM back ends ------------------------------------------------------------------------------
+int gemm_f64_grouped(acse_ctx* c, const GemmF64* probs, int nprob, cudaStream_t s);

@@ -363,3 +363,16 @@ def test_complex_step_matches_central_difference():
     fp = O.objective(p.h + t * dh, p.V + t * dV, p.N, D0 + t * dD, 0.05, 2, 1.0, 0.5)
     fm = O.objective(p.h - t * dh, p.V - t * dV, p.N, D0 - t * dD, 0.05, 2, 1.0, 0.5)
     assert cs == pytest.approx((fp - fm) / (2 * t), rel=1e-7)
+
+
+def test_residual_entries_match_full_residual(sys4):
+    """The entry-wise evaluation (printed Eq. residual, 3D elements on the fly) used for sampled
+    parity at full size agrees with the brute-force-pinned full residual."""
+    s = sys4
+    r = s["r"]
+    Db = O.blocks_from_so(s["D"])
+    A = O.residual(s["K"], s["D"], s["N"])
+    rng = np.random.default_rng(3)
+    ent = [tuple(int(x) for x in rng.integers(0, 2 * r, 4)) for _ in range(12)]
+    e = O.residual_entries(s["h"], s["V"], s["N"], *Db, ent)
+    np.testing.assert_allclose(e, [A[t] for t in ent], atol=1e-14)
