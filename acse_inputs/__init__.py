@@ -65,7 +65,7 @@ def _det_blocks(occ_a, occ_b, r):
     daa = 0.5 * (np.einsum("ik,jl->ijkl", ga, ga) - np.einsum("jk,il->ijkl", ga, ga))
     dbb = 0.5 * (np.einsum("ik,jl->ijkl", gb, gb) - np.einsum("jk,il->ijkl", gb, gb))
     dab = 0.5 * np.einsum("ik,jl->ijkl", ga, gb)
-    return daa, dab, dbb
+    return tuple(np.ascontiguousarray(x) for x in (daa, dab, dbb))
 
 
 def hf_rdm_blocks(r: int, n_alpha: int, n_beta: int):
@@ -179,6 +179,7 @@ def cas_rdm_blocks(h, V, core, active, nelecas, root=0, nroots=None) -> CASResul
     Dab = 0.5 * (np.einsum("ik,jl->ijkl", ta, tb) - np.einsum("ik,jl->ijkl", gaa, gbb))
     ix = np.ix_(act, act, act, act)
     Daa[ix] += daa_act; Dbb[ix] += dbb_act; Dab[ix] += dab_act
+    Daa, Dab, Dbb = (np.ascontiguousarray(x) for x in (Daa, Dab, Dbb))
     # <S^2> = Ms^2 + Ms + N_beta - sum_pq <a+_pa a_qa a+_qb a_pb>; for Ms = 0 (spin-flip term)
     # <a+_pa a_qa a+_qb a_pb> = <E^a_pq E^b_qp>
     ee_ab_pq = np.einsum("qpJB,qpJB->", T_a, T_b)
@@ -226,7 +227,7 @@ def rdm_blocks_from_ci(r, sa, sb, c):
     Daa = 0.5 * (np.einsum("rpJB,qsJB->pqrs", T_a, T_a) - np.einsum("qr,ps->pqrs", dl, ga))
     Dbb = 0.5 * (np.einsum("rpAJ,qsAJ->pqrs", T_b, T_b) - np.einsum("qr,ps->pqrs", dl, gb))
     Dab = 0.5 * np.einsum("rpJB,qsJB->pqrs", T_a, T_b)
-    return Daa, Dab, Dbb
+    return tuple(np.ascontiguousarray(x) for x in (Daa, Dab, Dbb))
 
 
 def random_state_rdm_blocks(r: int, n_alpha: int, n_beta: int, seed: int):

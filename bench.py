@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32"])
     ap.add_argument("--r", type=int, default=48, help="orbitals (48: the CAS(8e,8o) workload)")
-    ap.add_argument("--eps", type=float, default=0.1)
+    ap.add_argument("--eps", type=float, default=1e-3, help="Euler step (the paper's default 1e-3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="measure FP64/TF32/BF16 matmul peaks and exit")

@@ -66,7 +66,7 @@ typedef struct {
     int mask_active;   /* 1: zero A where i,j,k,l all lie in [act_lo, act_hi) (Methods)     */
     int act_lo, act_hi;
     int line_search;   /* 1: acse_step picks eps from ||A(D + e U)||^2 at {0, e0, 2 e0}     */
-    double eps0;       /* initial trial step of the line search (e0); 0 -> 0.1              */
+    double eps0;       /* initial trial step of the line search (e0); 0 -> 1e-3             */
     int check_inputs;  /* 1: acse_residual / acse_step verify Tr 2D and finiteness (syncs)  */
 } acse_opts;
 

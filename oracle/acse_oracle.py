@@ -257,7 +257,7 @@ def line_search_eps(f0, f1, f2, e0):
 
 
 def run_acse(h, V, N, D0, eps, nsteps, line_search=False, mask=None, stop_rule=False,
-             eps0=0.1, log=None):
+             eps0=1e-3, log=None):
     """The Euler-step driver.  Returns dict(D, E[list], norm2[list], eps[list], steps).
 
     E[n], norm2[n] are at D_n (E[0] at the reference).  With stop_rule the loop ends when E

@@ -95,7 +95,7 @@ def current_stream_handle():
     return torch.cuda.current_stream().cuda_stream
 
 
-def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=0.1,
+def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
                 check_inputs=False, stream=None):
     o = AcseOpts()
     o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta

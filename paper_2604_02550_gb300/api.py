@@ -19,7 +19,7 @@ def _dev(x, device):
 class ACSE:
     """One ACSE problem (integrals and options) bound to a CUDA stream."""
 
-    def __init__(self, r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=0.1,
+    def __init__(self, r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
                  check_inputs=False, device="cuda", stream=None):
         self.r, self.n_alpha, self.n_beta = r, n_alpha, n_beta
         self.device = torch.device(device)

@@ -141,7 +141,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         s = ACSE_ERR_CUDA;
     if (s == ACSE_OK) s = launch_build_K(c);
     if (s == ACSE_OK) {
-        k_set1<<<1, 1, 0, c->stream>>>(c->w.scal + 2, o->eps0 > 0.0 ? o->eps0 : 0.1);
+        k_set1<<<1, 1, 0, c->stream>>>(c->w.scal + 2, o->eps0 > 0.0 ? o->eps0 : 1e-3);
         if (cudaGetLastError() != cudaSuccess) s = ACSE_ERR_CUDA;
     }
     // host sources must stay valid until the copies are done

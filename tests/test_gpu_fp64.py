@@ -62,7 +62,7 @@ def test_step_parity(acse, r, na, nb, kind, mask):
     p = _random_problem(r, na, nb, 60 + r, kind)
     ctx = acse.ACSE(r, na, nb, p.h, p.V, "fp64", mask=mask)
     D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
-    eps = 0.05
+    eps = 1e-3
     E, n2, e_used = ctx.step(D, eps)
     torch.cuda.synchronize()
     Dw, Ew, n2w = oracle_step_blocks(p, (p.Daa, p.Dab, p.Dbb), eps, mask)
@@ -89,7 +89,9 @@ def test_mask_residual(acse):
 
 
 def test_config1_trajectory(acse):
-    """r = 8, N = 8, HF reference: one residual and 20 steps at eps = 0.1, E at every step."""
+    """r = 8, N = 8, HF reference: one residual and 20 steps, E at every step.  eps = 1e-3 (the
+    paper's default step); eps = 0.1 diverges to NaN within five steps on these integrals, on the
+    oracle and on the GPU alike."""
     p = I.config_problem(1)
     ctx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64")
     D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
@@ -99,8 +101,8 @@ def test_config1_trajectory(acse):
     K = O.reduced_hamiltonian(p.h, p.V, p.N)
     Do = O.so_from_blocks(p.Daa, p.Dab, p.Dbb)
     for n in range(20):
-        E, _, _ = ctx.step(D, 0.1)
-        Do, _, _ = O.step(K, Do, p.N, 0.1)
+        E, _, _ = ctx.step(D, 1e-3)
+        Do, _, _ = O.step(K, Do, p.N, 1e-3)
         assert float(E) == pytest.approx(O.energy(K, Do), abs=TOL_E), f"step {n}"
     assert maxrel(to_np(D), O.blocks_from_so(Do)) < 1e-11
     ctx.close()
@@ -108,10 +110,10 @@ def test_config1_trajectory(acse):
 
 def test_line_search_steps(acse):
     p = I.make_problem(8, 6, 5, "cas", core=[0], active=[1, 2, 3, 4], nelecas=4)
-    ctx = acse.ACSE(p.r, 3, 3, p.h, p.V, "fp64", line_search=True, eps0=0.1)
+    ctx = acse.ACSE(p.r, 3, 3, p.h, p.V, "fp64", line_search=True, eps0=1e-3)
     D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
     K = O.reduced_hamiltonian(p.h, p.V, p.N)
-    out = O.run_acse(p.h, p.V, p.N, O.so_from_blocks(p.Daa, p.Dab, p.Dbb), None, 4, line_search=True, eps0=0.1)
+    out = O.run_acse(p.h, p.V, p.N, O.so_from_blocks(p.Daa, p.Dab, p.Dbb), None, 4, line_search=True, eps0=1e-3)
     for n in range(4):
         E, n2, e = ctx.step(D)
         assert float(e) == pytest.approx(out["eps"][n], rel=1e-10)
@@ -160,8 +162,8 @@ def test_host_pointer_arguments(acse):
     assert n2[0] == pytest.approx(n2w, rel=1e-12)
     D = [x.copy() for x in (p.Daa, p.Dab, p.Dbb)]
     E = np.zeros(1)
-    _lib.acse_step(ctx, *D, 0.05, E, None, None)
-    Dw, Ew, _ = oracle_step_blocks(p, (p.Daa, p.Dab, p.Dbb), 0.05)
+    _lib.acse_step(ctx, *D, 1e-3, E, None, None)
+    Dw, Ew, _ = oracle_step_blocks(p, (p.Daa, p.Dab, p.Dbb), 1e-3)
     assert maxrel(D, Dw) < TOL_A
     assert E[0] == pytest.approx(Ew, abs=TOL_E)
     _lib.acse_destroy(ctx)
