@@ -194,6 +194,7 @@ static int contract_G(acse_ctx* c, const double* const D[3], const double* const
     } else {
         ACSE_TRY(tc_contract(c, D, W, prep_D));
     }
+    ACSE_TRY(launch_Q(c));
     ACSE_TRY(launch_build_B(c));
     ACSE_TRY(launch_assemble_G(c, sW, scale, mask, out, norm2_dst));
     return ACSE_OK;

@@ -219,47 +219,47 @@ __global__ void k_build_Z(int r, const double* __restrict__ Waa, const double* _
 // w^k_s = sum_pr W^{kp}_{rs} 1D^p_r (spin diagonal):
 //   w_a[k][s] = sum Waa[k][p][r][s] ga[p][r] - sum Wab[k][p][s][r] gb[p][r]
 //   w_b[k][s] = sum Wbb[k][p][r][s] gb[p][r] - sum Wab[p][k][r][s] ga[p][r]
+template <typename T>
 __global__ void k_build_w(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
-                          const double* __restrict__ Wbb, const double* __restrict__ gam, double* __restrict__ wv) {
+                          const double* __restrict__ Wbb, const double* __restrict__ gam, T* __restrict__ wv) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * r * r) return;
     const int sp = t / (r * r), k = (t / r) % r, s = t % r;
     const size_t R2 = (size_t)r * r, r3 = R2 * r;
     const double* ga = gam;
     const double* gb = gam + R2;
-    double acc = 0.0;
+    T acc = 0;
     for (int p = 0; p < r; ++p)
         for (int q = 0; q < r; ++q) {
             if (sp == 0)
-                acc += Waa[k * r3 + p * R2 + q * r + s] * ga[p * r + q] - Wab[k * r3 + p * R2 + s * r + q] * gb[p * r + q];
+                acc += (T)Waa[k * r3 + p * R2 + q * r + s] * (T)ga[p * r + q] -
+                       (T)Wab[k * r3 + p * R2 + s * r + q] * (T)gb[p * r + q];
             else
-                acc += Wbb[k * r3 + p * R2 + q * r + s] * gb[p * r + q] - Wab[p * r3 + k * R2 + q * r + s] * ga[p * r + q];
+                acc += (T)Wbb[k * r3 + p * R2 + q * r + s] * (T)gb[p * r + q] -
+                       (T)Wab[p * r3 + k * R2 + q * r + s] * (T)ga[p * r + q];
         }
     wv[t] = acc;
 }
 
-// Q^k_i = sum_prs W^{kp}_{rs} M^{ip}_{rs} (spin diagonal; the mixed-spin (rs) sum counts both
-// orders, hence the factor 2):
-//   Q_a[k][i] = sum Waa[k][prs] Maa[i][prs] + 2 sum Wab[k][prs] Mab[i][prs]
-//   Q_b[k][i] = sum Wbb[k][prs] Mbb[i][prs] + 2 sum Wab[p][k][rs] Mab[p][i][rs]
-__global__ void k_build_Q(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
-                          const double* __restrict__ Wbb, const double* __restrict__ Maa,
-                          const double* __restrict__ Mab, const double* __restrict__ Mbb, double* __restrict__ Qv) {
-    const int t = blockIdx.x;
+// Q^k_i = sum_prs W^{kp}_{rs} M^{ip}_{rs} is a partial trace of the pair GEMM output
+// X^{ij}_{kp} = sum_rs M^{ij}_{rs} W^{kp}_{rs}:  Q^k_i = sum_P X^{iP}_{kP}, i.e.
+//   Q_a[k][i] = sum_p Xaa[(i,p)][(k,p)] + sum_p Xab[(i,p)][(k,p)]
+//   Q_b[k][i] = sum_p Xbb[(i,p)][(k,p)] + sum_p Xab[(p,i)][(p,k)]
+// (O(r^3) instead of O(r^5); Xab already carries the factor 2 of the mixed-spin (rs) sum).
+template <typename T>
+__global__ void k_Q_from_X(int r, const T* __restrict__ Xaa, const T* __restrict__ Xab, const T* __restrict__ Xbb,
+                           size_t ldx, T* __restrict__ Qv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * r * r) return;
     const int sp = t / (r * r), k = (t / r) % r, i = t % r;
-    const size_t R2 = (size_t)r * r, r3 = R2 * r;
-    double acc = 0.0;
-    if (sp == 0) {
-        for (size_t e = threadIdx.x; e < r3; e += blockDim.x)
-            acc += Waa[k * r3 + e] * Maa[i * r3 + e] + 2.0 * Wab[k * r3 + e] * Mab[i * r3 + e];
-    } else {
-        for (size_t e = threadIdx.x; e < r3; e += blockDim.x) {
-            const size_t p = e / R2, rs = e % R2;
-            acc += Wbb[k * r3 + e] * Mbb[i * r3 + e] + 2.0 * Wab[p * r3 + k * R2 + rs] * Mab[p * r3 + i * R2 + rs];
-        }
+    T acc = 0;
+    for (int p = 0; p < r; ++p) {
+        if (sp == 0)
+            acc += Xaa[(size_t)(i * r + p) * ldx + k * r + p] + Xab[(size_t)(i * r + p) * ldx + k * r + p];
+        else
+            acc += Xbb[(size_t)(i * r + p) * ldx + k * r + p] + Xab[(size_t)(p * r + i) * ldx + p * r + k];
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) Qv[t] = acc;
+    Qv[t] = acc;
 }
 
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]) {
@@ -267,9 +267,28 @@ int launch_W_intermediates(acse_ctx* c, const double* const W[3]) {
     const size_t n = (size_t)6 * r * r * r * r;
     k_build_Z<<<grid_for(n), TPB, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.Zd, c->w.Zf1, c->w.Zf2);
     ACSE_LAUNCHED(c);
-    k_build_w<<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.w);
+    k_build_w<double><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.w);
     ACSE_LAUNCHED(c);
-    k_build_Q<<<2 * r * r, TPB, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.M[0], c->w.M[1], c->w.M[2], c->w.Q);
+    return ACSE_OK;
+}
+
+int launch_w_mixed(acse_ctx* c, const double* const W[3]) {
+    const int r = c->r;
+    k_build_w<float><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.w32);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+int launch_Q(acse_ctx* c) {
+    const int r = c->r;
+    const size_t R2 = (size_t)r * r;
+    if (c->opt.prec == ACSE_FP64) {
+        k_Q_from_X<double><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, c->w.X[0], c->w.X[1], c->w.X[2], R2,
+                                                                          c->w.Q);
+    } else {
+        k_Q_from_X<float><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, c->w.tc_pairC[0], c->w.tc_pairC[1],
+                                                                         c->w.tc_pairC[2], R2, c->w.Q32);
+    }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
@@ -278,42 +297,44 @@ int launch_W_intermediates(acse_ctx* c, const double* const W[3]) {
 // T0 = B^{ia ja}_{ka la}, T1 = B^{ib jb}_{kb lb}, T2 = B^{ia jb}_{ka lb}, T3 = B^{ia jb}_{kb la}.
 // X5 sources: diag ph output X5d[(sK,k,j)][(sI,i,l)], flips X5f1[(k,j)][(i,l)] (K=ka, J=jb),
 // X5f2[(k,j)][(i,l)] (K=kb, J=ja).
+template <typename T>
 struct BArgs {
     int r;
-    const double* X[3];
-    const double* X5d;
-    const double* X5f1;
-    const double* X5f2;
-    const double* M[3];
-    const double* gam;
-    const double* w;
-    const double* Q;
-    double* T[4];
+    const T* X[3];       // X^{ij}_{kp} per sector, row stride R2
+    const T* X5d;
+    const T* X5f1;
+    const T* X5f2;
+    const T* M[3];
+    const T* gam;
+    const T* w;
+    const T* Q;
+    T* T_[4];
 };
 
-__global__ void k_build_B(const __grid_constant__ BArgs a) {
+template <typename T>
+__global__ void k_build_B(const __grid_constant__ BArgs<T> a) {
     const int r = a.r;
     const size_t R2 = (size_t)r * r, n4 = R2 * R2, R22 = 2 * R2;
-    const double* ga = a.gam;
-    const double* gb = a.gam + R2;
-    const double* wa = a.w;
-    const double* wb = a.w + R2;
-    const double* Qa = a.Q;
-    const double* Qb = a.Q + R2;
+    const T* ga = a.gam;
+    const T* gb = a.gam + R2;
+    const T* wa = a.w;
+    const T* wb = a.w + R2;
+    const T* Qa = a.Q;
+    const T* Qb = a.Q + R2;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 4 * n4; e += (size_t)gridDim.x * blockDim.x) {
         const int t = (int)(e / n4);
         const size_t g = e % n4;
         const int i = (int)(g / (R2 * r)), j = (int)((g / R2) % r), k = (int)((g / r) % r), l = (int)(g % r);
         const size_t ij = (size_t)i * r + j;
-        double x1 = 0.0, x2 = 0.0, x4 = 0.0, x5, x7 = 0.0, x8;
+        T x1 = 0, x2 = 0, x4 = 0, x5, x7 = 0, x8;
         if (t < 2) {
-            const double* X = a.X[t == 0 ? 0 : 2];
-            const double* M = a.M[t == 0 ? 0 : 2];
-            const double* gg = t == 0 ? ga : gb;
-            const double* ww = t == 0 ? wa : wb;
-            const double* QQ = t == 0 ? Qa : Qb;
-            const double* Xr = X + ij * R2 + (size_t)k * r;
-            const double* Mr = M + ij * R2 + (size_t)l * r;
+            const T* X = a.X[t == 0 ? 0 : 2];
+            const T* M = a.M[t == 0 ? 0 : 2];
+            const T* gg = t == 0 ? ga : gb;
+            const T* ww = t == 0 ? wa : wb;
+            const T* QQ = t == 0 ? Qa : Qb;
+            const T* Xr = X + ij * R2 + (size_t)k * r;
+            const T* Mr = M + ij * R2 + (size_t)l * r;
             for (int p = 0; p < r; ++p) {
                 x1 += Xr[p] * gg[p * r + l];
                 x2 += ww[k * r + p] * Mr[p];
@@ -325,8 +346,8 @@ __global__ void k_build_B(const __grid_constant__ BArgs a) {
             x8 = a.X5d[(off + (size_t)k * r + i) * R22 + off + (size_t)j * r + l];
         } else if (t == 2) {
             // I=ia J=jb K=ka L=lb
-            const double* Xr = a.X[1] + ij * R2 + (size_t)k * r;
-            const double* Mab = a.M[1] + ij * R2;
+            const T* Xr = a.X[1] + ij * R2 + (size_t)k * r;
+            const T* Mab = a.M[1] + ij * R2;
             for (int p = 0; p < r; ++p) {
                 x1 += Xr[p] * gb[p * r + l];
                 x2 -= wa[k * r + p] * Mab[(size_t)p * r + l];
@@ -336,8 +357,8 @@ __global__ void k_build_B(const __grid_constant__ BArgs a) {
             x8 = a.X5d[((size_t)k * r + i) * R22 + R2 + (size_t)j * r + l];
         } else {
             // I=ia J=jb K=kb L=la
-            const double* Xr = a.X[1] + ij * R2 + k;
-            const double* Mr = a.M[1] + ij * R2 + (size_t)l * r;
+            const T* Xr = a.X[1] + ij * R2 + k;
+            const T* Mr = a.M[1] + ij * R2 + (size_t)l * r;
             for (int p = 0; p < r; ++p) {
                 x1 -= Xr[(size_t)p * r] * ga[p * r + l];
                 x2 += wb[k * r + p] * Mr[p];
@@ -346,19 +367,31 @@ __global__ void k_build_B(const __grid_constant__ BArgs a) {
             x7 = Qb[k * r + j] * ga[i * r + l];
             x8 = a.X5f2[((size_t)k * r + i) * R2 + (size_t)j * r + l];
         }
-        a.T[t][g] = (x1 - 2.0 * x2 - x4 + 2.0 * x5 + x7 - 2.0 * x8) * (1.0 / 9.0);
+        a.T_[t][g] = (x1 - (T)2 * x2 - x4 + (T)2 * x5 + x7 - (T)2 * x8) * (T)(1.0 / 9.0);
     }
 }
 
 int launch_build_B(acse_ctx* c) {
-    BArgs a;
-    a.r = c->r;
-    for (int s = 0; s < 3; ++s) { a.X[s] = c->w.X[s]; a.M[s] = c->w.M[s]; }
-    a.X5d = c->w.X5d; a.X5f1 = c->w.X5f1; a.X5f2 = c->w.X5f2;
-    a.gam = c->w.gam; a.w = c->w.w; a.Q = c->w.Q;
-    for (int t = 0; t < 4; ++t) a.T[t] = c->w.T[t];
     const size_t n = (size_t)4 * c->r * c->r * c->r * c->r;
-    k_build_B<<<grid_for(n), TPB, 0, c->stream>>>(a);
+    const size_t R2 = (size_t)c->r * c->r;
+    if (c->opt.prec == ACSE_FP64) {
+        BArgs<double> a;
+        a.r = c->r;
+        for (int s = 0; s < 3; ++s) { a.X[s] = c->w.X[s]; a.M[s] = c->w.M[s]; }
+        a.X5d = c->w.X5d; a.X5f1 = c->w.X5f1; a.X5f2 = c->w.X5f2;
+        a.gam = c->w.gam; a.w = c->w.w; a.Q = c->w.Q;
+        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T[t];
+        k_build_B<double><<<grid_for(n), TPB, 0, c->stream>>>(a);
+    } else {
+        BArgs<float> a;
+        a.r = c->r;
+        for (int s = 0; s < 3; ++s) { a.X[s] = c->w.tc_pairC[s]; a.M[s] = c->w.M32[s]; }
+        a.X5d = c->w.tc_X5d; a.X5f1 = c->w.tc_X5f[0]; a.X5f2 = c->w.tc_X5f[1];
+        a.gam = c->w.gam32; a.w = c->w.w32; a.Q = c->w.Q32;
+        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T32[t];
+        (void)R2;
+        k_build_B<float><<<grid_for(n), TPB, 0, c->stream>>>(a);
+    }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
@@ -368,19 +401,21 @@ int launch_build_B(acse_ctx* c) {
 // G_bb likewise with T1;
 // G_ab[ij][kl] = 4(Yab[ij][kl] - s Yab[kl][ij]) - 12(T2[ij][kl] - T3[ij][lk]) + 12 s (T2[kl][ij] - T3[kl][ji]).
 // out = scale * G; norm^2 partials (aa + bb + 4 ab, before the mask) per block.
+template <typename T>
 struct GArgs {
     int r;
-    const double* Y[3];
-    const double* T[4];
+    const T* Y[3];       // Y^{ij}_{kl} per sector, row stride R2
+    const T* T_[4];
     double* out[3];
-    double s, scale;
+    T s, scale;
     int mask, lo, hi;
     double* partial;
 };
 
 #define G_GRID (152 * 4)
 
-__global__ void __launch_bounds__(TPB) k_assemble_G(const __grid_constant__ GArgs a) {
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_assemble_G(const __grid_constant__ GArgs<T> a) {
     const int r = a.r;
     const size_t R2 = (size_t)r * r, n4 = R2 * R2;
     double nrm = 0.0;
@@ -389,16 +424,16 @@ __global__ void __launch_bounds__(TPB) k_assemble_G(const __grid_constant__ GArg
         const size_t g = e % n4;
         const int i = (int)(g / (R2 * r)), j = (int)((g / R2) % r), k = (int)((g / r) % r), l = (int)(g % r);
         const size_t ij = (size_t)i * r + j, kl = (size_t)k * r + l, lk = (size_t)l * r + k, ji = (size_t)j * r + i;
-        const double* Y = a.Y[blk];
-        const double* P;
-        const double* Qx;
-        if (blk == 0) { P = a.T[0]; Qx = a.T[0]; }
-        else if (blk == 2) { P = a.T[1]; Qx = a.T[1]; }
-        else { P = a.T[2]; Qx = a.T[3]; }
-        const double v = 4.0 * (Y[ij * R2 + kl] - a.s * Y[kl * R2 + ij])
-                         - 12.0 * (P[ij * R2 + kl] - Qx[ij * R2 + lk])
-                         + 12.0 * a.s * (P[kl * R2 + ij] - Qx[kl * R2 + ji]);
-        double o = a.scale * v;
+        const T* Y = a.Y[blk];
+        const T* P;
+        const T* Qx;
+        if (blk == 0) { P = a.T_[0]; Qx = a.T_[0]; }
+        else if (blk == 2) { P = a.T_[1]; Qx = a.T_[1]; }
+        else { P = a.T_[2]; Qx = a.T_[3]; }
+        const T v = (T)4 * (Y[ij * R2 + kl] - a.s * Y[kl * R2 + ij])
+                    - (T)12 * (P[ij * R2 + kl] - Qx[ij * R2 + lk])
+                    + (T)12 * a.s * (P[kl * R2 + ij] - Qx[kl * R2 + ji]);
+        double o = (double)(a.scale * v);
         nrm += (blk == 1 ? 4.0 : 1.0) * o * o;
         if (a.mask && i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo &&
             l < a.hi)
@@ -417,18 +452,33 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
     if (threadIdx.x == 0) *dst = v;
 }
 
-int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3], double* norm2_dst) {
-    GArgs a;
+template <typename T>
+static void fill_G(acse_ctx* c, GArgs<T>& a, int sW, double scale, int apply_mask, double* const out[3]) {
     a.r = c->r;
-    for (int s = 0; s < 3; ++s) { a.Y[s] = c->w.Y[s]; a.out[s] = out[s]; }
-    for (int t = 0; t < 4; ++t) a.T[t] = c->w.T[t];
-    a.s = (double)sW;
-    a.scale = scale;
+    for (int s = 0; s < 3; ++s) a.out[s] = out[s];
+    a.s = (T)sW;
+    a.scale = (T)scale;
     a.mask = apply_mask && c->opt.mask_active;
     a.lo = c->opt.act_lo;
     a.hi = c->opt.act_hi;
     a.partial = c->w.partial;
-    k_assemble_G<<<G_GRID, TPB, 0, c->stream>>>(a);
+}
+
+int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3], double* norm2_dst) {
+    const size_t R2 = (size_t)c->r * c->r;
+    if (c->opt.prec == ACSE_FP64) {
+        GArgs<double> a;
+        fill_G(c, a, sW, scale, apply_mask, out);
+        for (int s = 0; s < 3; ++s) a.Y[s] = c->w.Y[s];
+        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T[t];
+        k_assemble_G<double><<<G_GRID, TPB, 0, c->stream>>>(a);
+    } else {
+        GArgs<float> a;
+        fill_G(c, a, sW, scale, apply_mask, out);
+        for (int s = 0; s < 3; ++s) a.Y[s] = c->w.tc_pairC[s] + R2 * R2;   // rows r^2.. of [X; Y]
+        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T32[t];
+        k_assemble_G<float><<<G_GRID, TPB, 0, c->stream>>>(a);
+    }
     ACSE_LAUNCHED(c);
     if (norm2_dst) {
         k_sum_partials<<<1, TPB, 0, c->stream>>>(c->w.partial, G_GRID, norm2_dst);

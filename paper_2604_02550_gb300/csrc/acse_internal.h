@@ -82,7 +82,14 @@ struct Work {
     float* tc_pairC[3];   // [X; Y] FP32 (2r^2 x r^2)
     float* tc_X5d;
     float* tc_X5f[2];
-    int Kp1, Kp2;         // padded split K for r^2 and 2 r^2 contractions
+    int Kp1, Kp2;         // padded K (per split term) for r^2 and 2 r^2 contractions
+    // FP32 intermediates of the split-precision path
+    float* M32[3];
+    float* gam32;         // [2][r][r]
+    float* w32;
+    float* Q32;
+    float* T32[4];
+    int* tc_err;          // device flag: a bounded wait inside the tensor-core GEMM ran out
 };
 
 struct acse_ctx {
@@ -133,6 +140,8 @@ int launch_gamma_M(acse_ctx* c, const double* const D[3]);
 int launch_pack_Mph(acse_ctx* c);
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
 int launch_build_B(acse_ctx* c);
+int launch_w_mixed(acse_ctx* c, const double* const W[3]);
+int launch_Q(acse_ctx* c);
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3],
                       double* norm2_dst);
 int launch_energy(acse_ctx* c, const double* const D[3], double* E_dst);

@@ -1,9 +1,427 @@
-// Tensor-core (tcgen05) split-precision contraction path.
+// Split-precision O(r^6) contractions on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// C[m][n] = alpha * sum_k A'[m][k] B'[n][k] in FP32, where A' and B' are K-major operand copies
+// written by the pack kernels of acse_mixed.cu:
+//   BF16x3: A' = [hi(A) | hi(A) | lo(A)], B' = [hi(B) | lo(B) | hi(B)] (bf16, kind::f16), so the
+//           single K-concatenated product is hi.hi + hi.lo + lo.hi with FP32 accumulation;
+//   TF32:   A' = tf32(A), B' = tf32(B) (kind::tf32), one product.
+// Each K segment is zero padded to a multiple of the 128-byte K block.
+//
+// Kernel: one 128 x BN output tile per CTA, 6 warps.  Warp 0 lane 0 issues TMA loads (128B
+// swizzle) into a STAGES-deep shared-memory ring; warp 1 owns the TMEM accumulator (128 lanes x BN
+// fp32 columns) and its lane 0 issues tcgen05.mma (M=128, N=BN, K=16/8 per instruction, 4 per
+// K block) and tcgen05.commit to release stages; warps 2-5 read TMEM with tcgen05.ld and store
+// FP32 rows.  Every mbarrier wait is bounded: on expiry the kernel raises the device error flag,
+// lets the in-flight copies and MMAs land (again bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
 #include "acse_internal.h"
 
-int tc_plan_create(acse_ctx* c) { (void)c; return ACSE_ERR_UNSUPPORTED; }
-void tc_plan_destroy(acse_ctx* c) { (void)c; }
+#define TC_MAXP 12
+#define TC_BM 128
+#define TC_THREADS 192
+#define TC_DRAIN_NS 2000000000ull      // bound of the clean-up waits (2 s)
+#define TC_WAIT_NS 4000000000ull       // default bound of the pipeline waits (4 s)
+
+struct TcProb {
+    float* C;
+    int M, N, kblocks, ldc;
+    float alpha;
+    int tiles_n;
+    int tile_start;
+};
+
+struct __align__(64) TcBatch {
+    CUtensorMap tmA[TC_MAXP];
+    CUtensorMap tmB[TC_MAXP];
+    TcProb p[TC_MAXP];
+    int nprob;
+    int total_tiles;
+    int* err;
+    unsigned long long wait_ns;
+};
+
+// ------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `parity` to complete, at most `limit_ns` (and at most 2^30 polls).
+// Returns false on expiry or when `abort` is raised by another thread of the CTA.
+__device__ bool bounded_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns, volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 1; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 0) {
+            if (abort && *abort) return false;
+            if (global_ns() - t0 > limit_ns) return false;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)map) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint32_t a = smem_u32(p);
+    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: D = F32, A/B = BF16 (KIND 0) or TF32 (KIND 1), both K-major, M = 128.
+template <int KIND, int BN>
+__device__ __forceinline__ uint32_t make_idesc() {
+    const uint32_t fmt = KIND == 0 ? 1u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    if (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void raise_abort(int* err, volatile int* abort_flag) {
+    atomicExch(err, 1);
+    *abort_flag = 1;
+}
+
+// ------------------------------------------------------------------------------ kernel
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant__ TcBatch b) {
+    constexpr int A_BYTES = TC_BM * 128;
+    constexpr int B_BYTES = BN * 128;
+    constexpr int KELEM = KIND == 0 ? 64 : 32;      // elements per 128-byte K block
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x;
+    int pi = 0;
+    while (pi + 1 < b.nprob && b.p[pi + 1].tile_start <= t) ++pi;
+    const TcProb& P = b.p[pi];
+    const int local = t - P.tile_start;
+    const int m0 = (local / P.tiles_n) * TC_BM;
+    const int n0 = (local % P.tiles_n) * BN;
+    const int nk = P.kblocks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch(&b.tmA[pi]);
+            tma_prefetch(&b.tmB[pi]);
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES &&
+                    !bounded_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, b.wait_ns, abort_flag)) {
+                    raise_abort(b.err, abort_flag);
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                tma_load_2d(sA + s * A_BYTES, &b.tmA[pi], kb * KELEM, m0, &full[s]);
+                tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], kb * KELEM, n0, &full[s]);
+                ++issued;
+            }
+            // every issued copy must have landed before the CTA may exit
+            for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+                if (!bounded_wait(&full[kb % STAGES], (kb / STAGES) & 1, TC_DRAIN_NS, nullptr))
+                    raise_abort(b.err, abort_flag);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc<KIND, BN>();
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (!bounded_wait(&full[s], (kb / STAGES) & 1, b.wait_ns, abort_flag)) {
+                    raise_abort(b.err, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t da = smem_desc(sA + s * A_BYTES);
+                const uint64_t db = smem_desc(sB + s * B_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) umma<KIND>(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                umma_commit(&empty[s]);
+            }
+            umma_commit(accf);   // arrives when every MMA issued above has completed (also after an abort)
+        }
+    } else {
+        const int q = warp & 3;   // TMEM lane quadrant this warp may access
+        const bool ok = bounded_wait(accf, 0, b.wait_ns + TC_DRAIN_NS, nullptr);
+        if (!ok) raise_abort(b.err, abort_flag);
+        tc_fence_after();
+        const bool store = ok && !*abort_flag && nk > 0;
+        const int row = m0 + q * 32 + lane;
+        float* Crow = P.C + (size_t)row * P.ldc;
+        const bool vec = (P.ldc & 3) == 0;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t v[32];
+            __syncwarp();
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);   // warp-collective
+            const int col0 = n0 + c * 32;
+            if (store && row < P.M && col0 < P.N) {
+                if (vec && col0 + 32 <= P.N) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        float4 o = make_float4(P.alpha * __uint_as_float(v[j]), P.alpha * __uint_as_float(v[j + 1]),
+                                               P.alpha * __uint_as_float(v[j + 2]),
+                                               P.alpha * __uint_as_float(v[j + 3]));
+                        *reinterpret_cast<float4*>(Crow + col0 + j) = o;
+                    }
+                } else {
+                    for (int j = 0; j < 32 && col0 + j < P.N; ++j) Crow[col0 + j] = P.alpha * __uint_as_float(v[j]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+// --------------------------------------------------------------------------- host plan
+struct TcPlan {
+    PFN_cuTensorMapEncodeTiled_v12000 encode;
+    TcBatch batch;
+    int kind;        // 0 = bf16 (kind::f16), 1 = tf32
+    int bn;
+    int stages;
+    size_t smem;
+};
+
+static int stages_for(int bn) { return bn == 256 ? 4 : 6; }
+
+static size_t smem_for(int bn, int stages) { return (size_t)stages * (TC_BM + bn) * 128 + 1024 + 256; }
+
+template <int KIND, int BN>
+static int set_attr() {
+    const int st = stages_for(BN);
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<KIND, BN, BN == 256 ? 4 : 6>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(BN, st)));
+    return ACSE_OK;
+}
+
+static int encode_map(TcPlan* pl, CUtensorMap* m, const void* base, int rows, int inner_elems, int box_rows) {
+    const CUtensorMapDataType dt = pl->kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const int es = pl->kind == 0 ? 2 : 4;
+    cuuint64_t gdim[2] = {(cuuint64_t)inner_elems, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)inner_elems * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = pl->encode(m, dt, 2, const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ACSE_OK : ACSE_ERR_CUDA;
+}
+
+int tc_mixed_alloc(acse_ctx* c);
+void tc_mixed_free(acse_ctx* c);
+int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]);
+int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]);
+
+int tc_plan_create(acse_ctx* c) {
+    TcPlan* pl = (TcPlan*)calloc(1, sizeof(TcPlan));
+    if (!pl) return ACSE_ERR_NOMEM;
+    c->tc_plan = pl;
+    pl->kind = c->opt.prec == ACSE_TF32 ? 1 : 0;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return ACSE_ERR_CUDA;
+    }
+    pl->encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    ACSE_TRY(tc_mixed_alloc(c));
+    const int r = c->r, R2 = r * r, R22 = 2 * R2;
+    pl->bn = R2 >= 256 ? 256 : 128;
+    pl->stages = stages_for(pl->bn);
+    pl->smem = smem_for(pl->bn, pl->stages);
+    if (pl->kind == 0) {
+        ACSE_TRY(pl->bn == 256 ? (set_attr<0, 256>()) : (set_attr<0, 128>()));
+    } else {
+        ACSE_TRY(pl->bn == 256 ? (set_attr<1, 256>()) : (set_attr<1, 128>()));
+    }
+    Work& w = c->w;
+    const int ns = c->nsplit;
+    const int L1 = ns * w.Kp1, L2 = ns * w.Kp2;      // operand row lengths (elements)
+    const int kel = pl->kind == 0 ? 64 : 32;
+    TcBatch& b = pl->batch;
+    memset(&b, 0, sizeof(b));
+    int n = 0;
+    auto add = [&](const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) -> int {
+        ACSE_TRY(encode_map(pl, &b.tmA[n], A, M, L, TC_BM));
+        ACSE_TRY(encode_map(pl, &b.tmB[n], B, N, L, pl->bn));
+        TcProb& p = b.p[n];
+        p.C = C;
+        p.M = M;
+        p.N = N;
+        p.kblocks = L / kel;
+        p.ldc = ldc;
+        p.alpha = alpha;
+        p.tiles_n = (N + pl->bn - 1) / pl->bn;
+        p.tile_start = b.total_tiles;
+        b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
+        ++n;
+        return ACSE_OK;
+    };
+    // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
+    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f));
+    for (int s = 0; s < 3; ++s)
+        ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f));
+    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
+    b.nprob = n;
+    b.err = w.tc_err;
+    b.wait_ns = TC_WAIT_NS;
+    return ACSE_OK;
+}
+
+void tc_plan_destroy(acse_ctx* c) {
+    if (!c->tc_plan) return;
+    tc_mixed_free(c);
+    free(c->tc_plan);
+    c->tc_plan = nullptr;
+}
+
+int tc_set_wait_ns(acse_ctx* c, unsigned long long ns) {
+    if (!c->tc_plan) return ACSE_ERR_UNSUPPORTED;
+    ((TcPlan*)c->tc_plan)->batch.wait_ns = ns ? ns : TC_WAIT_NS;
+    return ACSE_OK;
+}
+
+int tc_gemm_launch(acse_ctx* c) {
+    TcPlan* pl = (TcPlan*)c->tc_plan;
+    const TcBatch& b = pl->batch;
+    ACSE_TRY(prof_begin(c));
+    if (pl->kind == 0) {
+        if (pl->bn == 256) k_gemm_tc<0, 256, 4><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
+        else k_gemm_tc<0, 128, 6><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
+    } else {
+        if (pl->bn == 256) k_gemm_tc<1, 256, 4><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
+        else k_gemm_tc<1, 128, 6><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
+    }
+    ACSE_LAUNCHED(c);
+    ACSE_TRY(prof_end(c));
+    return ACSE_OK;
+}
+
 int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D) {
-    (void)c; (void)D; (void)W; (void)prep_D;
-    return ACSE_ERR_UNSUPPORTED;
+    if (prep_D) ACSE_TRY(tc_mixed_prep_D(c, D));
+    ACSE_TRY(tc_mixed_prep_W(c, W));
+    ACSE_TRY(tc_gemm_launch(c));
+    return ACSE_OK;
 }
