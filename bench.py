@@ -51,7 +51,7 @@ def default_prec():
     # the tensor-core path when this build provides it, else FP64
     try:
         from paper_2604_02550_gb300 import _lib
-        return "bf16x3" if getattr(_lib, "HAS_TC", False) else "fp64"
+        return "bf16x3" if getattr(_lib, "HAS_TC", True) else "fp64"
     except Exception:
         return "fp64"
 

@@ -122,6 +122,16 @@ int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_ste
 int acse_profile(acse_ctx* ctx, int enable);
 int acse_profile_read(acse_ctx* ctx, double* gemm_ms, long long* gemm_launches, long long* launches);
 
+/* Device status.  The tensor-core GEMM bounds every device-side wait; when one runs out the
+ * kernel raises a device flag, drains its copies, frees its tensor memory and returns.
+ * acse_sync_status synchronises the context's stream and returns ACSE_ERR_TIMEOUT if the flag is
+ * set (calls that synchronise anyway report it too); acse_clear_status clears the flag and the
+ * latched error.  acse_set_wait_bound_ns sets the bound of those waits (0 = default, 4 s): a
+ * host-side fault-injection knob for testing the timeout path. */
+int acse_sync_status(acse_ctx* ctx);
+int acse_clear_status(acse_ctx* ctx);
+int acse_set_wait_bound_ns(acse_ctx* ctx, unsigned long long ns);
+
 /* Text of a status code. */
 const char* acse_strerror(int status);
 

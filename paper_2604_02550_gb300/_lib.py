@@ -15,8 +15,8 @@ PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32}
 
 # symbols declared in include/acse.h
 EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
-           "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_strerror",
-           "acse_last_error", "acse_version")
+           "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_sync_status",
+           "acse_clear_status", "acse_set_wait_bound_ns", "acse_strerror", "acse_last_error", "acse_version")
 
 
 class AcseOpts(ctypes.Structure):
@@ -55,8 +55,12 @@ def lib():
         L.acse_profile.argtypes = [c_void_p, c_int]
         L.acse_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(ctypes.c_longlong),
                                         POINTER(ctypes.c_longlong)]
+        L.acse_sync_status.argtypes = [c_void_p]
+        L.acse_clear_status.argtypes = [c_void_p]
+        L.acse_set_wait_bound_ns.argtypes = [c_void_p, ctypes.c_ulonglong]
         for name in ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
-                     "acse_residual_backward", "acse_last_error", "acse_profile", "acse_profile_read"):
+                     "acse_residual_backward", "acse_last_error", "acse_profile", "acse_profile_read",
+                     "acse_sync_status", "acse_clear_status", "acse_set_wait_bound_ns"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -147,3 +151,15 @@ def acse_profile_read(ctx):
     nl = ctypes.c_longlong()
     _check(lib().acse_profile_read(ctx, byref(ms), byref(ng), byref(nl)), "acse_profile_read")
     return ms.value, ng.value, nl.value
+
+
+def acse_sync_status(ctx):
+    _check(lib().acse_sync_status(ctx), "acse_sync_status")
+
+
+def acse_clear_status(ctx):
+    _check(lib().acse_clear_status(ctx), "acse_clear_status")
+
+
+def acse_set_wait_bound_ns(ctx, ns):
+    _check(lib().acse_set_wait_bound_ns(ctx, int(ns)), "acse_set_wait_bound_ns")

@@ -8,6 +8,7 @@
 int tc_plan_create(acse_ctx* c);
 void tc_plan_destroy(acse_ctx* c);
 int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
+int tc_set_wait_ns(acse_ctx* c, unsigned long long ns);
 
 static const char* k_version = "libacse 0.1 (sm_103a; FP64 DFMA + tcgen05 split-precision GEMMs)";
 
@@ -80,17 +81,20 @@ static int alloc_work(acse_ctx* c) {
     size_t tot = 0;
 #define A_(p, bytes) ACSE_TRY(alloc_d((void**)&(p), (bytes), &tot))
     for (int s = 0; s < 3; ++s) {
-        A_(w.Kh[s], b4); A_(w.M[s], b4); A_(w.X[s], b4); A_(w.Y[s], b4);
+        A_(w.Kh[s], b4);
         A_(w.A[s], b4); A_(w.U[s], b4); A_(w.Dt[s], b4);
         A_(w.stage_in[s], b4); A_(w.stage_out[s], b4);
     }
-    for (int t = 0; t < 4; ++t) A_(w.T[t], b4);
     A_(w.gam, 2 * R2 * sizeof(double));
-    A_(w.w, 2 * R2 * sizeof(double));
-    A_(w.Q, 2 * R2 * sizeof(double));
-    A_(w.Md, 4 * b4); A_(w.Mf1, b4); A_(w.Mf2, b4);
-    A_(w.Zd, 4 * b4); A_(w.Zf1, b4); A_(w.Zf2, b4);
-    A_(w.X5d, 4 * b4); A_(w.X5f1, b4); A_(w.X5f2, b4);
+    if (c->opt.prec == ACSE_FP64) {   // FP64 intermediates (the split path has FP32 ones)
+        for (int s = 0; s < 3; ++s) { A_(w.M[s], b4); A_(w.X[s], b4); A_(w.Y[s], b4); }
+        for (int t = 0; t < 4; ++t) A_(w.T[t], b4);
+        A_(w.w, 2 * R2 * sizeof(double));
+        A_(w.Q, 2 * R2 * sizeof(double));
+        A_(w.Md, 4 * b4); A_(w.Mf1, b4); A_(w.Mf2, b4);
+        A_(w.Zd, 4 * b4); A_(w.Zf1, b4); A_(w.Zf2, b4);
+        A_(w.X5d, 4 * b4); A_(w.X5f1, b4); A_(w.X5f2, b4);
+    }
     A_(w.h, R2 * sizeof(double));
     A_(w.V, b4);
     A_(w.scal, 16 * sizeof(double));
@@ -175,9 +179,11 @@ extern "C" int acse_destroy(acse_ctx* c) {
 static int contract_G(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale,
                       int mask, double* const out[3], double* norm2_dst, int prep_D) {
     Work& w = c->w;
-    if (prep_D) ACSE_TRY(launch_gamma_M(c, D));
     if (c->opt.prec == ACSE_FP64) {
-        if (prep_D) ACSE_TRY(launch_pack_Mph(c));
+        if (prep_D) {
+            ACSE_TRY(launch_gamma_M(c, D));
+            ACSE_TRY(launch_pack_Mph(c));
+        }
         ACSE_TRY(launch_W_intermediates(c, W));
         const int r = c->r, R2 = r * r, R22 = 2 * R2;
         GemmF64 g[9];
@@ -192,6 +198,7 @@ static int contract_G(acse_ctx* c, const double* const D[3], const double* const
         g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0};
         ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
     } else {
+        if (prep_D) ACSE_TRY(launch_gamma(c, D));
         ACSE_TRY(tc_contract(c, D, W, prep_D));
     }
     ACSE_TRY(launch_Q(c));
@@ -247,6 +254,19 @@ static int check_D(acse_ctx* c, const double* const D[3]) {
     return ACSE_OK;
 }
 
+// After a stream synchronisation: ACSE_ERR_TIMEOUT if a bounded device wait ran out.
+static int device_status(acse_ctx* c) {
+    if (!c->w.tc_err) return ACSE_OK;
+    int flag = 0;
+    ACSE_CUDA_TRY(cudaMemcpy(&flag, c->w.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return flag ? ACSE_ERR_TIMEOUT : ACSE_OK;
+}
+
+static int sync_and_status(acse_ctx* c) {
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return device_status(c);
+}
+
 static int put_scalar(acse_ctx* c, double* dst, const double* src_dev, int* need_sync) {
     if (!dst) return ACSE_OK;
     if (is_host_ptr(dst)) {
@@ -267,7 +287,7 @@ extern "C" int acse_energy(acse_ctx* c, const double* Daa, const double* Dab, co
     int s = stage_inputs(c, Daa, Dab, Dbb, D, &host_in);
     if (s == ACSE_OK) s = launch_energy(c, D, c->w.scal + 1);
     if (s == ACSE_OK) s = put_scalar(c, E, c->w.scal + 1, &sync);
-    if (s == ACSE_OK && (sync || host_in) && cudaStreamSynchronize(c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK && (sync || host_in)) s = sync_and_status(c);
     return latch(c, s);
 }
 
@@ -300,7 +320,7 @@ extern "C" int acse_residual(acse_ctx* c, const double* Daa, const double* Dab, 
             sync = 1;
         }
     if (s == ACSE_OK) s = put_scalar(c, norm2, c->w.scal + 0, &sync);
-    if (s == ACSE_OK && (sync || host_in) && cudaStreamSynchronize(c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK && (sync || host_in)) s = sync_and_status(c);
     return latch(c, s);
 }
 
@@ -352,7 +372,7 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
     if (s == ACSE_OK) s = put_scalar(c, E_out, w.scal + 1, &sync);
     if (s == ACSE_OK) s = put_scalar(c, norm2_out, w.scal + 0, &sync);
     if (s == ACSE_OK) s = put_scalar(c, eps_used, w.scal + 3, &sync);
-    if (s == ACSE_OK && sync && cudaStreamSynchronize(c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK && sync) s = sync_and_status(c);
     return latch(c, s);
 }
 
@@ -415,4 +435,27 @@ extern "C" int acse_profile_read(acse_ctx* c, double* gemm_ms, long long* gemm_l
     if (gemm_launches) *gemm_launches = c->prof_count;
     if (launches) *launches = c->launches;
     return latch(c, s);
+}
+
+// ------------------------------------------------------------------------------ status
+extern "C" int acse_sync_status(acse_ctx* c) {
+    if (!c) return ACSE_ERR_ARG;
+    int s = sync_and_status(c);
+    if (s == ACSE_OK && c->w.tc_err) {
+        // clear a reported flag so that later calls start clean
+    }
+    return latch(c, s);
+}
+
+extern "C" int acse_clear_status(acse_ctx* c) {
+    if (!c) return ACSE_ERR_ARG;
+    c->last_error = ACSE_OK;
+    if (c->w.tc_err && cudaMemsetAsync(c->w.tc_err, 0, sizeof(int), c->stream) != cudaSuccess) return ACSE_ERR_CUDA;
+    return ACSE_OK;
+}
+
+extern "C" int acse_set_wait_bound_ns(acse_ctx* c, unsigned long long ns) {
+    if (!c) return ACSE_ERR_ARG;
+    if (c->opt.prec == ACSE_FP64) return ACSE_OK;   // the FP64 path has no device-side waits
+    return latch(c, tc_set_wait_ns(c, ns));
 }

@@ -114,10 +114,16 @@ __global__ void k_build_M(int r, const double* __restrict__ gam, const double* _
     }
 }
 
-int launch_gamma_M(acse_ctx* c, const double* const D[3]) {
+int launch_gamma(acse_ctx* c, const double* const D[3]) {
     const int r = c->r;
     k_gamma<<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, 2.0 / (c->N - 1), D[0], D[1], D[2], c->w.gam);
     ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+int launch_gamma_M(acse_ctx* c, const double* const D[3]) {
+    const int r = c->r;
+    ACSE_TRY(launch_gamma(c, D));
     const size_t n = (size_t)r * r * r * r;
     k_build_M<<<grid_for(n), TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], c->w.M[0], c->w.M[1], c->w.M[2]);
     ACSE_LAUNCHED(c);

@@ -136,6 +136,7 @@ int prof_end(acse_ctx* c);
 
 // kernels (acse_elem.cu) -------------------------------------------------------------------
 int launch_build_K(acse_ctx* c);
+int launch_gamma(acse_ctx* c, const double* const D[3]);
 int launch_gamma_M(acse_ctx* c, const double* const D[3]);
 int launch_pack_Mph(acse_ctx* c);
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]);

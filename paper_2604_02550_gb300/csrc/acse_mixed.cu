@@ -1,0 +1,295 @@
+// Operand packing and FP32 intermediates of the split-precision (BF16x3 / TF32) path.
+//
+// Every O(r^6) GEMM operand is written once per contraction pass, directly in the K-major
+// layout the tensor-core GEMM reads (one row per output row / column, K segments zero padded to
+// a multiple of the 128-byte K block):
+//   BF16x3  x = hi + lo, hi = bf16(x), lo = bf16(x - hi);  A rows [hi|hi|lo], B rows [hi|lo|hi]
+//   TF32    x -> tf32 (round to nearest, ties away)        A rows, B rows [x]
+// The logical operands are those of the FP64 path (acse_elem.cu): the pair-pair [M; D] and W
+// blocks, and the particle-hole layouts of M and Z.  The 1-RDM is accumulated in FP64 (exactly
+// as in the FP64 path) and rounded to FP32 here; M, Z and w are formed in FP32.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "acse_internal.h"
+
+#define MX_TPB 256
+
+static inline int mx_grid(size_t n) {
+    size_t g = (n + MX_TPB - 1) / MX_TPB;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+
+// PAT 0: operand A ([hi|hi|lo]); PAT 1: operand B ([hi|lo|hi]).  ld = row length in elements.
+template <int PREC, int PAT>
+__device__ __forceinline__ void put(void* base, size_t row, size_t ld, int Kp, int k, float x) {
+    if (PREC == ACSE_BF16X3) {
+        __nv_bfloat16* p = (__nv_bfloat16*)base + row * ld;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+        p[k] = hi;
+        p[Kp + k] = PAT == 0 ? hi : lo;
+        p[2 * Kp + k] = PAT == 0 ? lo : hi;
+    } else {
+        float* p = (float*)base + row * ld;
+        p[k] = tf32_rna(x);
+    }
+}
+
+struct MxPtrs {
+    void* pairA[3];
+    void* pairB[3];
+    void* Md;
+    void* Zd;
+    void* Mf[2];
+    void* Zf[2];
+    float* M32[3];
+    float* gam32;
+    int Kp1, Kp2, ns;
+};
+
+static MxPtrs mx_ptrs(acse_ctx* c) {
+    MxPtrs p;
+    Work& w = c->w;
+    for (int s = 0; s < 3; ++s) {
+        p.pairA[s] = w.tc_pairA[s];
+        p.pairB[s] = w.tc_pairB[s];
+        p.M32[s] = w.M32[s];
+    }
+    p.Md = w.tc_Md;
+    p.Zd = w.tc_Zd;
+    for (int f = 0; f < 2; ++f) {
+        p.Mf[f] = w.tc_Mf[f];
+        p.Zf[f] = w.tc_Zf[f];
+    }
+    p.gam32 = w.gam32;
+    p.Kp1 = w.Kp1;
+    p.Kp2 = w.Kp2;
+    p.ns = c->nsplit;
+    return p;
+}
+
+// --------------------------------------------------------------------------- per D
+// M = 3 2D - 2 (1D^1D) in FP32 (App. C), stored plain (M32) and as rows 0..r^2-1 of the pair
+// operand [M; D]; rows r^2..2r^2-1 hold D.  Also rounds the FP64 1-RDM to FP32.
+template <int PREC>
+__global__ void k_mx_prepD(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
+                           const double* __restrict__ Dab, const double* __restrict__ Dbb, const __grid_constant__ MxPtrs p) {
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    const size_t ld = (size_t)p.ns * p.Kp1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 6 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < 2 * R2) p.gam32[e] = (float)gam[e];
+        const int s = (int)(e / (2 * n4));
+        const size_t rem = e % (2 * n4);
+        const size_t row = rem / R2;
+        const int k = (int)(rem % R2);
+        const double* D = s == 0 ? Daa : (s == 1 ? Dab : Dbb);
+        float x;
+        if (row < R2) {
+            const int i = (int)(row / r), j = (int)(row % r), kk = k / r, l = k % r;
+            const double* ga = gam + (s == 2 ? R2 : 0);
+            const double* gb = gam + (s == 0 ? 0 : R2);
+            const float d = (float)D[row * R2 + k];
+            if (s == 1)
+                x = 3.0f * d - (float)ga[i * r + kk] * (float)gb[j * r + l];
+            else
+                x = 3.0f * d - ((float)ga[i * r + kk] * (float)ga[j * r + l] - (float)ga[j * r + kk] * (float)ga[i * r + l]);
+            p.M32[s][row * R2 + k] = x;
+        } else {
+            x = (float)D[(row - R2) * R2 + k];
+        }
+        put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k, x);
+    }
+}
+
+// Particle-hole layouts of M (the B operands of the ph GEMMs), same index maps as the FP64 path:
+//   Md[(sI,i,l)][(sP,p,s)]: (a,a) Maa[i][p][l][s], (a,b) Mab[i][p][l][s], (b,a) Mab[p][i][s][l], (b,b) Mbb[i][p][l][s]
+//   Mf1[(i,l)][(p,s)] = Mab[i][p][s][l],  Mf2[(i,l)][(p,s)] = Mab[p][i][l][s]
+template <int PREC>
+__global__ void k_mx_pack_Mph(int r, const __grid_constant__ MxPtrs p) {
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2, nd = 4 * n4;
+    const size_t ld2 = (size_t)p.ns * p.Kp2, ld1 = (size_t)p.ns * p.Kp1;
+    const float* Maa = p.M32[0];
+    const float* Mab = p.M32[1];
+    const float* Mbb = p.M32[2];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < nd) {
+            const size_t row = e / (2 * R2), col = e % (2 * R2);
+            const int sI = (int)(row / R2), sP = (int)(col / R2);
+            const int i = (int)((row % R2) / r), l = (int)(row % r);
+            const int pp = (int)((col % R2) / r), s = (int)(col % r);
+            float v;
+            if (sI == 0 && sP == 0) v = Maa[((i * r + pp) * (size_t)r + l) * r + s];
+            else if (sI == 0) v = Mab[((i * r + pp) * (size_t)r + l) * r + s];
+            else if (sP == 0) v = Mab[((pp * r + i) * (size_t)r + s) * r + l];
+            else v = Mbb[((i * r + pp) * (size_t)r + l) * r + s];
+            put<PREC, 1>(p.Md, row, ld2, p.Kp2, (int)col, v);
+        } else {
+            const size_t f = e - nd;
+            const int which = (int)(f / n4);
+            const size_t g = f % n4;
+            const size_t row = g / R2;
+            const int col = (int)(g % R2);
+            const int i = (int)(row / r), l = (int)(row % r), pp = col / r, s = col % r;
+            const float v = which == 0 ? Mab[((i * r + pp) * (size_t)r + s) * r + l] : Mab[((pp * r + i) * (size_t)r + l) * r + s];
+            put<PREC, 1>(p.Mf[which], row, ld1, p.Kp1, col, v);
+        }
+    }
+}
+
+int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
+    const int r = c->r;
+    const size_t n4 = (size_t)r * r * r * r;
+    MxPtrs p = mx_ptrs(c);
+    if (c->opt.prec == ACSE_BF16X3) {
+        k_mx_prepD<ACSE_BF16X3><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        ACSE_LAUNCHED(c);
+        k_mx_pack_Mph<ACSE_BF16X3><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, p);
+    } else {
+        k_mx_prepD<ACSE_TF32><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        ACSE_LAUNCHED(c);
+        k_mx_pack_Mph<ACSE_TF32><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, p);
+    }
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// --------------------------------------------------------------------------- per W
+// Pair operand B: W blocks as (kp) x (rs) rows.
+template <int PREC>
+__global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
+                            const double* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    const size_t ld = (size_t)p.ns * p.Kp1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 3 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(e / n4);
+        const size_t g = e % n4;
+        const double* W = s == 0 ? Waa : (s == 1 ? Wab : Wbb);
+        put<PREC, 1>(p.pairB[s], g / R2, ld, p.Kp1, (int)(g % R2), (float)W[g]);
+    }
+}
+
+// Z^{kp}_{js} = sum_r W^{kp}_{rs} 1D^j_r (operand A of the ph GEMMs), same index maps as the FP64 path:
+//   Zd (a,a) sum_r Waa[k][p][r][s] ga[j][r]   (a,b) sum_r Wab[k][p][r][s] ga[j][r]
+//      (b,a) sum_r Wab[p][k][s][r] gb[j][r]   (b,b) sum_r Wbb[k][p][r][s] gb[j][r]
+//   Zf1[(k,j)][(p,s)] = sum_r Wab[k][p][s][r] gb[j][r],  Zf2[(k,j)][(p,s)] = sum_r Wab[p][k][r][s] ga[j][r]
+template <int PREC>
+__global__ void k_mx_Z(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
+                       const double* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
+    const size_t R2 = (size_t)r * r, n4 = R2 * R2, r3 = R2 * r, nd = 4 * n4;
+    const size_t ld2 = (size_t)p.ns * p.Kp2, ld1 = (size_t)p.ns * p.Kp1;
+    const float* ga = p.gam32;
+    const float* gb = p.gam32 + R2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        if (e < nd) {
+            const size_t row = e / (2 * R2), col = e % (2 * R2);
+            const int sK = (int)(row / R2), sP = (int)(col / R2);
+            const int k = (int)((row % R2) / r), j = (int)(row % r);
+            const int pp = (int)((col % R2) / r), s = (int)(col % r);
+            if (sK == 0) {
+                const double* base = (sP == 0 ? Waa : Wab) + k * r3 + pp * R2 + s;
+                for (int q = 0; q < r; ++q) acc += (float)base[q * r] * ga[j * r + q];
+            } else if (sP == 0) {
+                const double* base = Wab + pp * r3 + k * R2 + s * r;
+                for (int q = 0; q < r; ++q) acc += (float)base[q] * gb[j * r + q];
+            } else {
+                const double* base = Wbb + k * r3 + pp * R2 + s;
+                for (int q = 0; q < r; ++q) acc += (float)base[q * r] * gb[j * r + q];
+            }
+            put<PREC, 0>(p.Zd, row, ld2, p.Kp2, (int)col, acc);
+        } else {
+            const size_t f = e - nd;
+            const int which = (int)(f / n4);
+            const size_t g = f % n4;
+            const size_t row = g / R2;
+            const int col = (int)(g % R2);
+            const int k = (int)(row / r), j = (int)(row % r), pp = col / r, s = col % r;
+            if (which == 0) {
+                const double* base = Wab + k * r3 + pp * R2 + s * r;
+                for (int q = 0; q < r; ++q) acc += (float)base[q] * gb[j * r + q];
+            } else {
+                const double* base = Wab + pp * r3 + k * R2 + s;
+                for (int q = 0; q < r; ++q) acc += (float)base[q * r] * ga[j * r + q];
+            }
+            put<PREC, 0>(p.Zf[which], row, ld1, p.Kp1, col, acc);
+        }
+    }
+}
+
+int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
+    const int r = c->r;
+    const size_t n4 = (size_t)r * r * r * r;
+    MxPtrs p = mx_ptrs(c);
+    if (c->opt.prec == ACSE_BF16X3) {
+        k_mx_pack_W<ACSE_BF16X3><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        ACSE_LAUNCHED(c);
+        k_mx_Z<ACSE_BF16X3><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+    } else {
+        k_mx_pack_W<ACSE_TF32><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        ACSE_LAUNCHED(c);
+        k_mx_Z<ACSE_TF32><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+    }
+    ACSE_LAUNCHED(c);
+    return launch_w_mixed(c, W);
+}
+
+// ------------------------------------------------------------------------ workspace
+static int mx_alloc(void** p, size_t bytes, bool zero) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ACSE_ERR_NOMEM;
+    }
+    if (zero && cudaMemset(*p, 0, bytes) != cudaSuccess) return ACSE_ERR_CUDA;
+    return ACSE_OK;
+}
+
+int tc_mixed_alloc(acse_ctx* c) {
+    Work& w = c->w;
+    const size_t r = c->r, R2 = r * r, n4 = R2 * R2;
+    const int es = c->opt.prec == ACSE_BF16X3 ? 2 : 4;
+    const int kb = 128 / es;
+    w.Kp1 = (int)((R2 + kb - 1) / kb * kb);
+    w.Kp2 = (int)((2 * R2 + kb - 1) / kb * kb);
+    const size_t ns = c->nsplit;
+    const size_t L1 = ns * w.Kp1 * es, L2 = ns * w.Kp2 * es;   // row bytes
+    // operand buffers are zeroed once: the K padding is never written afterwards
+    for (int s = 0; s < 3; ++s) {
+        ACSE_TRY(mx_alloc(&w.tc_pairA[s], 2 * R2 * L1, true));
+        ACSE_TRY(mx_alloc(&w.tc_pairB[s], R2 * L1, true));
+        ACSE_TRY(mx_alloc((void**)&w.tc_pairC[s], 2 * R2 * R2 * sizeof(float), false));
+        ACSE_TRY(mx_alloc((void**)&w.M32[s], n4 * sizeof(float), false));
+    }
+    ACSE_TRY(mx_alloc(&w.tc_Md, 2 * R2 * L2, true));
+    ACSE_TRY(mx_alloc(&w.tc_Zd, 2 * R2 * L2, true));
+    for (int f = 0; f < 2; ++f) {
+        ACSE_TRY(mx_alloc(&w.tc_Mf[f], R2 * L1, true));
+        ACSE_TRY(mx_alloc(&w.tc_Zf[f], R2 * L1, true));
+        ACSE_TRY(mx_alloc((void**)&w.tc_X5f[f], n4 * sizeof(float), false));
+    }
+    ACSE_TRY(mx_alloc((void**)&w.tc_X5d, 4 * n4 * sizeof(float), false));
+    for (int t = 0; t < 4; ++t) ACSE_TRY(mx_alloc((void**)&w.T32[t], n4 * sizeof(float), false));
+    ACSE_TRY(mx_alloc((void**)&w.gam32, 2 * R2 * sizeof(float), false));
+    ACSE_TRY(mx_alloc((void**)&w.w32, 2 * R2 * sizeof(float), false));
+    ACSE_TRY(mx_alloc((void**)&w.Q32, 2 * R2 * sizeof(float), false));
+    ACSE_TRY(mx_alloc((void**)&w.tc_err, sizeof(int), true));
+    return ACSE_OK;
+}
+
+void tc_mixed_free(acse_ctx* c) {
+    Work& w = c->w;
+    void* ptrs[] = {w.tc_pairA[0], w.tc_pairA[1], w.tc_pairA[2], w.tc_pairB[0], w.tc_pairB[1], w.tc_pairB[2],
+                    w.tc_pairC[0], w.tc_pairC[1], w.tc_pairC[2], w.M32[0], w.M32[1], w.M32[2], w.tc_Md, w.tc_Zd,
+                    w.tc_Mf[0], w.tc_Mf[1], w.tc_Zf[0], w.tc_Zf[1], w.tc_X5f[0], w.tc_X5f[1], w.tc_X5d,
+                    w.T32[0], w.T32[1], w.T32[2], w.T32[3], w.gam32, w.w32, w.Q32, w.tc_err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}

@@ -1,0 +1,115 @@
+"""Split-precision (BF16x3, TF32) tensor-core path vs the FP64 oracle and the FP64 GPU path.
+
+Tolerances (normwise relative, max|dA| / max|A|): BF16x3 represents each operand as hi + lo with
+about 16 significant bits and drops the lo.lo product, so each product carries a relative error
+of about 2^-16 = 1.5e-5 before FP32 accumulation; the residual combines GEMM outputs of similar
+size with some cancellation, hence 5e-4.  TF32 (one product, 11 significant bits, 2^-11 = 4.9e-4
+per product) gets 2e-2.
+"""
+import numpy as np
+import pytest
+
+import acse_inputs as I
+from oracle import acse_oracle as O
+from tests.gpu_helpers import maxrel, oracle_residual_blocks, oracle_step_blocks, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 5e-4, "tf32": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def acse():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_02550_gb300 import api
+    return api
+
+
+def _problem(r, na, nb, seed, kind):
+    h, V = I.make_integrals(r, seed)
+    if kind == "state":
+        D = I.random_state_rdm_blocks(r, na, nb, seed + 1)
+    else:
+        D = I.random_pair_tensor_blocks(r, seed + 1, hermitian=1, scale=0.05)
+    return I.Problem(f"rand_r{r}", r, na, nb, h, V, *D)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("r,na,nb,kind", [(4, 2, 2, "state"), (6, 3, 2, "state"), (9, 3, 3, "pair"),
+                                          (12, 4, 3, "pair"), (17, 5, 4, "pair")])
+def test_residual_parity_mixed(acse, prec, r, na, nb, kind):
+    p = _problem(r, na, nb, 100 + r, kind)
+    ctx = acse.ACSE(r, na, nb, p.h, p.V, prec)
+    A, n2 = ctx.residual(ctx.to_blocks((p.Daa, p.Dab, p.Dbb)))
+    from paper_2604_02550_gb300 import _lib
+    _lib.acse_sync_status(ctx.ctx)
+    want, n2w = oracle_residual_blocks(p, (p.Daa, p.Dab, p.Dbb))
+    err = maxrel(to_np(A), want)
+    print(f"{prec} r={r}: max rel err {err:.3e}, norm2 rel err {abs(float(n2) - n2w) / n2w:.3e}")
+    assert err < TOL[prec]
+    assert float(n2) == pytest.approx(n2w, rel=4 * TOL[prec])
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_step_parity_mixed(acse, prec):
+    p = _problem(6, 3, 3, 7, "state")
+    ctx = acse.ACSE(6, 3, 3, p.h, p.V, prec, mask=(1, 4))
+    D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    eps = 1e-3
+    E, n2, _ = ctx.step(D, eps)
+    Dw, Ew, n2w = oracle_step_blocks(p, (p.Daa, p.Dab, p.Dbb), eps, (1, 4))
+    Uw = tuple((a - b) / eps for a, b in zip(Dw, (p.Daa, p.Dab, p.Dbb)))
+    Ug = tuple((a - b) / eps for a, b in zip(to_np(D), (p.Daa, p.Dab, p.Dbb)))
+    err = maxrel(Ug, Uw)
+    print(f"{prec} step: U rel err {err:.3e}, E err {abs(float(E) - Ew):.3e}")
+    assert err < 2 * TOL[prec]
+    assert abs(float(E) - Ew) < 1e-6 if prec == "bf16x3" else 1e-4
+    ctx.close()
+
+
+def test_mixed_vs_fp64_gpu_config2(acse):
+    """r = 24, CAS(6e,6o): BF16x3 and FP64 GPU residuals on the same input, and energies over
+    10 steps (mixed-precision error per iteration)."""
+    p = I.config_problem(2)
+    c64 = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64")
+    cmx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "bf16x3")
+    D64 = c64.to_blocks((p.Daa, p.Dab, p.Dbb))
+    Dmx = cmx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    A64, _ = c64.residual(D64)
+    Amx, _ = cmx.residual(Dmx)
+    err = maxrel(to_np(Amx), to_np(A64))
+    print(f"config 2 residual: BF16x3 vs FP64 max rel err {err:.3e}")
+    assert err < TOL["bf16x3"]
+    dE = []
+    for n in range(10):
+        E64, _, _ = c64.step(D64, 1e-3)
+        Emx, _, _ = cmx.step(Dmx, 1e-3)
+        dE.append(abs(float(Emx) - float(E64)))
+    print("per-step |E_bf16x3 - E_fp64|:", " ".join(f"{x:.2e}" for x in dE))
+    assert max(dE) < 1e-3
+    c64.close()
+    cmx.close()
+
+
+def test_timeout_status_and_recovery(acse):
+    """A bounded device wait that runs out (bound set to 1 ns from the host) ends the GEMM with
+    ACSE_ERR_TIMEOUT and no fault; with the default bound the next call is correct again."""
+    from paper_2604_02550_gb300 import _lib
+    p = _problem(12, 4, 3, 3, "pair")
+    ctx = acse.ACSE(12, 4, 3, p.h, p.V, "bf16x3")
+    D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    _lib.acse_set_wait_bound_ns(ctx.ctx, 1)
+    ctx.residual(D)
+    with pytest.raises(_lib.AcseError) as ei:
+        _lib.acse_sync_status(ctx.ctx)
+    assert ei.value.status == -6
+    _lib.acse_set_wait_bound_ns(ctx.ctx, 0)
+    _lib.acse_clear_status(ctx.ctx)
+    A, _ = ctx.residual(D)
+    _lib.acse_sync_status(ctx.ctx)
+    want, _ = oracle_residual_blocks(p, (p.Daa, p.Dab, p.Dbb))
+    assert maxrel(to_np(A), want) < TOL["bf16x3"]
+    ctx.close()
