@@ -8,7 +8,7 @@
 int tc_plan_create(acse_ctx* c);
 void tc_plan_destroy(acse_ctx* c);
 int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
-int tc_set_wait_ns(acse_ctx* c, unsigned long long ns);
+int tc_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall);
 
 static const char* k_version = "libacse 0.1 (sm_103a; FP64 DFMA + tcgen05 split-precision GEMMs)";
 
@@ -440,11 +440,7 @@ extern "C" int acse_profile_read(acse_ctx* c, double* gemm_ms, long long* gemm_l
 // ------------------------------------------------------------------------------ status
 extern "C" int acse_sync_status(acse_ctx* c) {
     if (!c) return ACSE_ERR_ARG;
-    int s = sync_and_status(c);
-    if (s == ACSE_OK && c->w.tc_err) {
-        // clear a reported flag so that later calls start clean
-    }
-    return latch(c, s);
+    return latch(c, sync_and_status(c));
 }
 
 extern "C" int acse_clear_status(acse_ctx* c) {
@@ -454,8 +450,8 @@ extern "C" int acse_clear_status(acse_ctx* c) {
     return ACSE_OK;
 }
 
-extern "C" int acse_set_wait_bound_ns(acse_ctx* c, unsigned long long ns) {
+extern "C" int acse_set_wait_bound_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
     if (!c) return ACSE_ERR_ARG;
-    if (c->opt.prec == ACSE_FP64) return ACSE_OK;   // the FP64 path has no device-side waits
-    return latch(c, tc_set_wait_ns(c, ns));
+    if (c->opt.prec == ACSE_FP64) return inject_stall ? latch(c, ACSE_ERR_UNSUPPORTED) : ACSE_OK;
+    return latch(c, tc_set_wait_ns(c, ns, inject_stall));
 }

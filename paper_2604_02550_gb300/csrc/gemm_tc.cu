@@ -41,6 +41,7 @@ struct __align__(64) TcBatch {
     int total_tiles;
     int* err;
     unsigned long long wait_ns;
+    int inject_stall;     // test knob: the MMA thread first waits on a barrier nothing signals
 };
 
 // ------------------------------------------------------------------------- PTX helpers
@@ -186,7 +187,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
     uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* accf = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+    uint64_t* never = accf + 1;                     // signalled by nobody (fault-injection knob)
+    uint32_t* tmem_slot = (uint32_t*)(never + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
+        mbar_init(never, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = make_idesc<KIND, BN>();
-            for (int kb = 0; kb < nk; ++kb) {
+            if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
+            for (int kb = 0; kb < nk && !*abort_flag; ++kb) {
                 const int s = kb % STAGES;
                 if (!bounded_wait(&full[s], (kb / STAGES) & 1, b.wait_ns, abort_flag)) {
                     raise_abort(b.err, abort_flag);
@@ -397,9 +401,10 @@ void tc_plan_destroy(acse_ctx* c) {
     c->tc_plan = nullptr;
 }
 
-int tc_set_wait_ns(acse_ctx* c, unsigned long long ns) {
+int tc_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
     if (!c->tc_plan) return ACSE_ERR_UNSUPPORTED;
     ((TcPlan*)c->tc_plan)->batch.wait_ns = ns ? ns : TC_WAIT_NS;
+    ((TcPlan*)c->tc_plan)->batch.inject_stall = inject_stall;
     return ACSE_OK;
 }
 

@@ -95,18 +95,19 @@ def test_mixed_vs_fp64_gpu_config2(acse):
 
 
 def test_timeout_status_and_recovery(acse):
-    """A bounded device wait that runs out (bound set to 1 ns from the host) ends the GEMM with
-    ACSE_ERR_TIMEOUT and no fault; with the default bound the next call is correct again."""
+    """A bounded device wait that runs out (the MMA thread waits on a barrier that nothing
+    signals, with a 1 ms bound set from the host) ends the GEMM with ACSE_ERR_TIMEOUT and no
+    fault; with the knob off the next call is correct again."""
     from paper_2604_02550_gb300 import _lib
     p = _problem(12, 4, 3, 3, "pair")
     ctx = acse.ACSE(12, 4, 3, p.h, p.V, "bf16x3")
     D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
-    _lib.acse_set_wait_bound_ns(ctx.ctx, 1)
+    _lib.acse_set_wait_bound_ns(ctx.ctx, 1_000_000, inject_stall=True)
     ctx.residual(D)
     with pytest.raises(_lib.AcseError) as ei:
         _lib.acse_sync_status(ctx.ctx)
     assert ei.value.status == -6
-    _lib.acse_set_wait_bound_ns(ctx.ctx, 0)
+    _lib.acse_set_wait_bound_ns(ctx.ctx, 0, inject_stall=False)
     _lib.acse_clear_status(ctx.ctx)
     A, _ = ctx.residual(D)
     _lib.acse_sync_status(ctx.ctx)
