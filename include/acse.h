@@ -51,7 +51,8 @@ typedef enum {
     ACSE_ERR_CUDA = -5,       /* a CUDA runtime / driver call failed                   */
     ACSE_ERR_TIMEOUT = -6,    /* a bounded device-side wait ran out                    */
     ACSE_ERR_NOMEM = -7,      /* device allocation failed at context creation          */
-    ACSE_ERR_UNSUPPORTED = -8 /* option not built (e.g. a reconstruction not available) */
+    ACSE_ERR_UNSUPPORTED = -8, /* option not built (e.g. a reconstruction not available) */
+    ACSE_ERR_TOO_LARGE = -9    /* r above the static scratch of acse_energy_noalloc (64)  */
 } acse_status;
 
 typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2 } acse_prec;
@@ -126,11 +127,38 @@ int acse_profile_read(acse_ctx* ctx, double* gemm_ms, long long* gemm_launches, 
  * kernel raises a device flag, drains its copies, frees its tensor memory and returns.
  * acse_sync_status synchronises the context's stream and returns ACSE_ERR_TIMEOUT if the flag is
  * set (calls that synchronise anyway report it too); acse_clear_status clears the flag and the
- * latched error.  acse_set_wait_bound_ns sets the bound of those waits (0 = default, 4 s): a
- * host-side fault-injection knob for testing the timeout path. */
+ * latched error.  acse_set_wait_bound_ns sets the bound of those waits (0 = default, 4 s);
+ * with inject_stall = 1 the GEMM's MMA-issuing thread first waits on a barrier that nothing
+ * signals, so every tile runs into the bound and the call ends with ACSE_ERR_TIMEOUT (a
+ * host-side fault-injection knob for testing the timeout path; no fault, no hang).  Tensor-core
+ * precisions only (ACSE_ERR_UNSUPPORTED for inject_stall on FP64). */
 int acse_sync_status(acse_ctx* ctx);
 int acse_clear_status(acse_ctx* ctx);
-int acse_set_wait_bound_ns(acse_ctx* ctx, unsigned long long ns);
+int acse_set_wait_bound_ns(acse_ctx* ctx, unsigned long long ns, int inject_stall);
+
+/* Allocation-free energy trace.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory when they need an energy -- code running under a
+ * framework or memory manager that owns the whole device heap, code on a latency-critical path
+ * that must not risk the implicit device synchronisation of cudaMalloc/cudaFree, or callers that
+ * hold only integrals and a 2-RDM and no context.  It computes the same E = sum K.2D as
+ * acse_energy (K formed element by element inside the kernel from h and V, so no K buffer) and
+ * allocates nothing: its only scratch is a file-scope static device array of 64 x 64 doubles
+ * (32 KiB, held by every GPU that loads the library until the process exits), one FP64 partial
+ * sum per (i, j).
+ *   r, n_alpha, n_beta: as in acse_opts (N = n_alpha + n_beta >= 2); r <= 64, larger r returns
+ *     ACSE_ERR_TOO_LARGE.
+ *   h (r*r), V (r^4, chemist's (pq|rs)), Daa, Dab, Dbb (r^4 each), E (one double): DEVICE
+ *     pointers only (a host pointer returns ACSE_ERR_ARG); the caller owns all of them.
+ *   cuda_stream: the cudaStream_t the two kernels are launched on; the call is asynchronous.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current and caches it; make that first call before any stream capture.  Every
+ * call shares the one array and it keeps the last call's contents; nothing in it needs to start
+ * at zero (each call writes every slot it reads before reading it), but calls whose kernels
+ * overlap on the GPU (other streams, other threads) race on it and must be ordered by the
+ * caller. */
+int acse_energy_noalloc(int r, int n_alpha, int n_beta, const double* h, const double* V,
+                        const double* Daa, const double* Dab, const double* Dbb, double* E,
+                        void* cuda_stream);
 
 /* Text of a status code. */
 const char* acse_strerror(int status);

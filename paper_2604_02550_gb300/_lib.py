@@ -16,7 +16,8 @@ PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32}
 # symbols declared in include/acse.h
 EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
            "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_sync_status",
-           "acse_clear_status", "acse_set_wait_bound_ns", "acse_strerror", "acse_last_error", "acse_version")
+           "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_strerror",
+           "acse_last_error", "acse_version")
 
 
 class AcseOpts(ctypes.Structure):
@@ -55,9 +56,11 @@ def lib():
         L.acse_profile.argtypes = [c_void_p, c_int]
         L.acse_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(ctypes.c_longlong),
                                         POINTER(ctypes.c_longlong)]
+        L.acse_energy_noalloc.argtypes = [c_int, c_int, c_int] + [c_void_p] * 7
+        L.acse_energy_noalloc.restype = c_int
         L.acse_sync_status.argtypes = [c_void_p]
         L.acse_clear_status.argtypes = [c_void_p]
-        L.acse_set_wait_bound_ns.argtypes = [c_void_p, ctypes.c_ulonglong]
+        L.acse_set_wait_bound_ns.argtypes = [c_void_p, ctypes.c_ulonglong, c_int]
         for name in ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
                      "acse_residual_backward", "acse_last_error", "acse_profile", "acse_profile_read",
                      "acse_sync_status", "acse_clear_status", "acse_set_wait_bound_ns"):
@@ -161,5 +164,12 @@ def acse_clear_status(ctx):
     _check(lib().acse_clear_status(ctx), "acse_clear_status")
 
 
-def acse_set_wait_bound_ns(ctx, ns):
-    _check(lib().acse_set_wait_bound_ns(ctx, int(ns)), "acse_set_wait_bound_ns")
+def acse_set_wait_bound_ns(ctx, ns, inject_stall=False):
+    _check(lib().acse_set_wait_bound_ns(ctx, int(ns), int(bool(inject_stall))), "acse_set_wait_bound_ns")
+
+
+def acse_energy_noalloc(r, n_alpha, n_beta, h, V, Daa, Dab, Dbb, E, stream=None):
+    """Energy through the allocation-free entry point (device tensors only)."""
+    st = current_stream_handle() if stream is None else stream
+    _check(lib().acse_energy_noalloc(int(r), int(n_alpha), int(n_beta), ptr(h), ptr(V), ptr(Daa), ptr(Dab),
+                                     ptr(Dbb), ptr(E), st), "acse_energy_noalloc")

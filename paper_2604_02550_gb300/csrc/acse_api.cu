@@ -25,6 +25,7 @@ extern "C" const char* acse_strerror(int s) {
         case ACSE_ERR_TIMEOUT: return "device-side wait timed out";
         case ACSE_ERR_NOMEM: return "device allocation failed";
         case ACSE_ERR_UNSUPPORTED: return "option not supported by this build";
+        case ACSE_ERR_TOO_LARGE: return "r exceeds the static scratch of acse_energy_noalloc (r <= 64)";
         default: return "unknown status";
     }
 }

@@ -30,6 +30,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     assert not missing, missing
     assert set(_declared()) == set(_lib.EXPORTS)
     assert "sm_103a" in _lib.version()
+    assert _lib.strerror(-9).startswith("r exceeds")
 
 
 def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
