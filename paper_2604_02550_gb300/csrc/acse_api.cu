@@ -130,7 +130,8 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         free(c);
         return ACSE_ERR_CUDA;
     }
-    int s = alloc_work(c);
+    int s = tiled_set_attrs();
+    if (s == ACSE_OK) s = alloc_work(c);
     if (s == ACSE_OK && o->prec != ACSE_FP64) s = tc_plan_create(c);
     if (s != ACSE_OK) {
         tc_plan_destroy(c);

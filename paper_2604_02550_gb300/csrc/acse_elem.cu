@@ -173,79 +173,7 @@ int launch_pack_Mph(acse_ctx* c) {
 }
 
 // ------------------------------------------------------------------- W-dependent intermediates
-// Z^{kp}_{js} = sum_r W^{kp}_{rs} 1D^j_r in the ph layout (rows (sK,k,j), cols (sP,p,s)):
-//   (a,a) sum_r Waa[k][p][r][s] ga[j][r]     (a,b) sum_r Wab[k][p][r][s] ga[j][r]
-//   (b,a) sum_r Wab[p][k][s][r] gb[j][r]     (b,b) sum_r Wbb[k][p][r][s] gb[j][r]
-//   F1:   Zf1[(k,j)][(p,s)] = sum_r Wab[k][p][s][r] gb[j][r]
-//   F2:   Zf2[(k,j)][(p,s)] = sum_r Wab[p][k][r][s] ga[j][r]
-__global__ void k_build_Z(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
-                          const double* __restrict__ Wbb, const double* __restrict__ gam, double* __restrict__ Zd,
-                          double* __restrict__ Zf1, double* __restrict__ Zf2) {
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2, r3 = R2 * r;
-    const size_t nd = 4 * n4;
-    const double* ga = gam;
-    const double* gb = gam + R2;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        if (e < nd) {
-            const size_t row = e / (2 * R2), col = e % (2 * R2);
-            const int sK = (int)(row / R2), sP = (int)(col / R2);
-            const int k = (int)((row % R2) / r), j = (int)(row % r);
-            const int p = (int)((col % R2) / r), s = (int)(col % r);
-            if (sK == 0) {
-                const double* W = (sP == 0) ? Waa : Wab;
-                const double* base = W + k * r3 + p * R2 + s;
-                for (int q = 0; q < r; ++q) acc += base[q * r] * ga[j * r + q];
-            } else if (sP == 0) {
-                const double* base = Wab + p * r3 + k * R2 + s * r;
-                for (int q = 0; q < r; ++q) acc += base[q] * gb[j * r + q];
-            } else {
-                const double* base = Wbb + k * r3 + p * R2 + s;
-                for (int q = 0; q < r; ++q) acc += base[q * r] * gb[j * r + q];
-            }
-            Zd[e] = acc;
-        } else {
-            const size_t f = e - nd;
-            const int which = (int)(f / n4);
-            const size_t g = f % n4;
-            const int k = (int)(g / (R2 * r)), j = (int)((g / R2) % r), p = (int)((g / r) % r), s = (int)(g % r);
-            if (which == 0) {
-                const double* base = Wab + k * r3 + p * R2 + s * r;
-                for (int q = 0; q < r; ++q) acc += base[q] * gb[j * r + q];
-                Zf1[g] = acc;
-            } else {
-                const double* base = Wab + p * r3 + k * R2 + s;
-                for (int q = 0; q < r; ++q) acc += base[q * r] * ga[j * r + q];
-                Zf2[g] = acc;
-            }
-        }
-    }
-}
-
-// w^k_s = sum_pr W^{kp}_{rs} 1D^p_r (spin diagonal):
-//   w_a[k][s] = sum Waa[k][p][r][s] ga[p][r] - sum Wab[k][p][s][r] gb[p][r]
-//   w_b[k][s] = sum Wbb[k][p][r][s] gb[p][r] - sum Wab[p][k][r][s] ga[p][r]
-template <typename T>
-__global__ void k_build_w(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
-                          const double* __restrict__ Wbb, const double* __restrict__ gam, T* __restrict__ wv) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * r * r) return;
-    const int sp = t / (r * r), k = (t / r) % r, s = t % r;
-    const size_t R2 = (size_t)r * r, r3 = R2 * r;
-    const double* ga = gam;
-    const double* gb = gam + R2;
-    T acc = 0;
-    for (int p = 0; p < r; ++p)
-        for (int q = 0; q < r; ++q) {
-            if (sp == 0)
-                acc += (T)Waa[k * r3 + p * R2 + q * r + s] * (T)ga[p * r + q] -
-                       (T)Wab[k * r3 + p * R2 + s * r + q] * (T)gb[p * r + q];
-            else
-                acc += (T)Wbb[k * r3 + p * R2 + q * r + s] * (T)gb[p * r + q] -
-                       (T)Wab[p * r3 + k * R2 + q * r + s] * (T)ga[p * r + q];
-        }
-    wv[t] = acc;
-}
+// Z, w (acse_tiled.cu) and Q (a partial trace of the pair GEMM output X).
 
 // Q^k_i = sum_prs W^{kp}_{rs} M^{ip}_{rs} is a partial trace of the pair GEMM output
 // X^{ij}_{kp} = sum_rs M^{ij}_{rs} W^{kp}_{rs}:  Q^k_i = sum_P X^{iP}_{kP}, i.e.
@@ -269,20 +197,8 @@ __global__ void k_Q_from_X(int r, const T* __restrict__ Xaa, const T* __restrict
 }
 
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]) {
-    const int r = c->r;
-    const size_t n = (size_t)6 * r * r * r * r;
-    k_build_Z<<<grid_for(n), TPB, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.Zd, c->w.Zf1, c->w.Zf2);
-    ACSE_LAUNCHED(c);
-    k_build_w<double><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.w);
-    ACSE_LAUNCHED(c);
-    return ACSE_OK;
-}
-
-int launch_w_mixed(acse_ctx* c, const double* const W[3]) {
-    const int r = c->r;
-    k_build_w<float><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, W[0], W[1], W[2], c->w.gam, c->w.w32);
-    ACSE_LAUNCHED(c);
-    return ACSE_OK;
+    ACSE_TRY(launch_Z_tiled(c, W));
+    return launch_w_tiled(c, W);
 }
 
 int launch_Q(acse_ctx* c) {
@@ -300,107 +216,16 @@ int launch_Q(acse_ctx* c) {
 }
 
 // ------------------------------------------------------------------------- B spin types
-// T0 = B^{ia ja}_{ka la}, T1 = B^{ib jb}_{kb lb}, T2 = B^{ia jb}_{ka lb}, T3 = B^{ia jb}_{kb la}.
-// X5 sources: diag ph output X5d[(sK,k,j)][(sI,i,l)], flips X5f1[(k,j)][(i,l)] (K=ka, J=jb),
-// X5f2[(k,j)][(i,l)] (K=kb, J=ja).
-template <typename T>
-struct BArgs {
-    int r;
-    const T* X[3];       // X^{ij}_{kp} per sector, row stride R2
-    const T* X5d;
-    const T* X5f1;
-    const T* X5f2;
-    const T* M[3];
-    const T* gam;
-    const T* w;
-    const T* Q;
-    T* T_[4];
-};
-
-template <typename T>
-__global__ void k_build_B(const __grid_constant__ BArgs<T> a) {
-    const int r = a.r;
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2, R22 = 2 * R2;
-    const T* ga = a.gam;
-    const T* gb = a.gam + R2;
-    const T* wa = a.w;
-    const T* wb = a.w + R2;
-    const T* Qa = a.Q;
-    const T* Qb = a.Q + R2;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 4 * n4; e += (size_t)gridDim.x * blockDim.x) {
-        const int t = (int)(e / n4);
-        const size_t g = e % n4;
-        const int i = (int)(g / (R2 * r)), j = (int)((g / R2) % r), k = (int)((g / r) % r), l = (int)(g % r);
-        const size_t ij = (size_t)i * r + j;
-        T x1 = 0, x2 = 0, x4 = 0, x5, x7 = 0, x8;
-        if (t < 2) {
-            const T* X = a.X[t == 0 ? 0 : 2];
-            const T* M = a.M[t == 0 ? 0 : 2];
-            const T* gg = t == 0 ? ga : gb;
-            const T* ww = t == 0 ? wa : wb;
-            const T* QQ = t == 0 ? Qa : Qb;
-            const T* Xr = X + ij * R2 + (size_t)k * r;
-            const T* Mr = M + ij * R2 + (size_t)l * r;
-            for (int p = 0; p < r; ++p) {
-                x1 += Xr[p] * gg[p * r + l];
-                x2 += ww[k * r + p] * Mr[p];
-            }
-            x4 = QQ[k * r + i] * gg[j * r + l];
-            x7 = QQ[k * r + j] * gg[i * r + l];
-            const size_t off = (size_t)t * R2;
-            x5 = a.X5d[(off + (size_t)k * r + j) * R22 + off + (size_t)i * r + l];
-            x8 = a.X5d[(off + (size_t)k * r + i) * R22 + off + (size_t)j * r + l];
-        } else if (t == 2) {
-            // I=ia J=jb K=ka L=lb
-            const T* Xr = a.X[1] + ij * R2 + (size_t)k * r;
-            const T* Mab = a.M[1] + ij * R2;
-            for (int p = 0; p < r; ++p) {
-                x1 += Xr[p] * gb[p * r + l];
-                x2 -= wa[k * r + p] * Mab[(size_t)p * r + l];
-            }
-            x4 = Qa[k * r + i] * gb[j * r + l];
-            x5 = a.X5f1[((size_t)k * r + j) * R2 + (size_t)i * r + l];
-            x8 = a.X5d[((size_t)k * r + i) * R22 + R2 + (size_t)j * r + l];
-        } else {
-            // I=ia J=jb K=kb L=la
-            const T* Xr = a.X[1] + ij * R2 + k;
-            const T* Mr = a.M[1] + ij * R2 + (size_t)l * r;
-            for (int p = 0; p < r; ++p) {
-                x1 -= Xr[(size_t)p * r] * ga[p * r + l];
-                x2 += wb[k * r + p] * Mr[p];
-            }
-            x5 = a.X5d[(R2 + (size_t)k * r + j) * R22 + (size_t)i * r + l];
-            x7 = Qb[k * r + j] * ga[i * r + l];
-            x8 = a.X5f2[((size_t)k * r + i) * R2 + (size_t)j * r + l];
-        }
-        a.T_[t][g] = (x1 - (T)2 * x2 - x4 + (T)2 * x5 + x7 - (T)2 * x8) * (T)(1.0 / 9.0);
-    }
-}
-
-int launch_build_B(acse_ctx* c) {
-    const size_t n = (size_t)4 * c->r * c->r * c->r * c->r;
-    const size_t R2 = (size_t)c->r * c->r;
-    if (c->opt.prec == ACSE_FP64) {
-        BArgs<double> a;
-        a.r = c->r;
-        for (int s = 0; s < 3; ++s) { a.X[s] = c->w.X[s]; a.M[s] = c->w.M[s]; }
-        a.X5d = c->w.X5d; a.X5f1 = c->w.X5f1; a.X5f2 = c->w.X5f2;
-        a.gam = c->w.gam; a.w = c->w.w; a.Q = c->w.Q;
-        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T[t];
-        k_build_B<double><<<grid_for(n), TPB, 0, c->stream>>>(a);
-    } else {
-        BArgs<float> a;
-        a.r = c->r;
-        for (int s = 0; s < 3; ++s) { a.X[s] = c->w.tc_pairC[s]; a.M[s] = c->w.M32[s]; }
-        a.X5d = c->w.tc_X5d; a.X5f1 = c->w.tc_X5f[0]; a.X5f2 = c->w.tc_X5f[1];
-        a.gam = c->w.gam32; a.w = c->w.w32; a.Q = c->w.Q32;
-        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T32[t];
-        (void)R2;
-        k_build_B<float><<<grid_for(n), TPB, 0, c->stream>>>(a);
-    }
-    ACSE_LAUNCHED(c);
-    return ACSE_OK;
-}
+// T0 = B^{ia ja}_{ka la}, T1 = B^{ib jb}_{kb lb}, T2 = B^{ia jb}_{ka lb}, T3 = B^{ia jb}_{kb la}
+// (acse_tiled.cu, one block per pair (i, j)):
+//   T0: x1 = sum_p Xaa[ij][kp] ga[p][l], x2 = sum_p wa[k][p] Maa[ij][l][p], x4 = Qa[k][i] ga[j][l],
+//       x7 = Qa[k][j] ga[i][l], x5 = X5d[(a,k,j)][(a,i,l)], x8 = X5d[(a,k,i)][(a,j,l)];  T1 the same in b
+//   T2: x1 = sum_p Xab[ij][kp] gb[p][l], x2 = -sum_p wa[k][p] Mab[ij][p][l], x4 = Qa[k][i] gb[j][l],
+//       x5 = X5f1[(k,j)][(i,l)], x8 = X5d[(a,k,i)][(b,j,l)], x7 = 0
+//   T3: x1 = -sum_p Xab[ij][pk] ga[p][l], x2 = sum_p wb[k][p] Mab[ij][l][p], x5 = X5d[(b,k,j)][(a,i,l)],
+//       x7 = Qb[k][j] ga[i][l], x8 = X5f2[(k,i)][(j,l)], x4 = 0
+//   B = (x1 - 2 x2 - x4 + 2 x5 + x7 - 2 x8) / 9.
+int launch_build_B(acse_ctx* c) { return launch_B_tiled(c); }
 
 // --------------------------------------------------------------------------- G assembly
 // G_aa[ij][kl] = 4(Yaa[ij][kl] - s Yaa[kl][ij]) - 12(T0[ij][kl] - T0[ij][lk]) + 12 s (T0[kl][ij] - T0[kl][ji])

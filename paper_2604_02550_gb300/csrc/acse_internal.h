@@ -141,7 +141,10 @@ int launch_gamma_M(acse_ctx* c, const double* const D[3]);
 int launch_pack_Mph(acse_ctx* c);
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
 int launch_build_B(acse_ctx* c);
-int launch_w_mixed(acse_ctx* c, const double* const W[3]);
+int launch_Z_tiled(acse_ctx* c, const double* const W[3]);
+int launch_w_tiled(acse_ctx* c, const double* const W[3]);
+int launch_B_tiled(acse_ctx* c);
+int tiled_set_attrs();
 int launch_Q(acse_ctx* c);
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3],
                       double* norm2_dst);

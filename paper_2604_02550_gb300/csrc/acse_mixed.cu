@@ -176,69 +176,17 @@ __global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double*
     }
 }
 
-// Z^{kp}_{js} = sum_r W^{kp}_{rs} 1D^j_r (operand A of the ph GEMMs), same index maps as the FP64 path:
-//   Zd (a,a) sum_r Waa[k][p][r][s] ga[j][r]   (a,b) sum_r Wab[k][p][r][s] ga[j][r]
-//      (b,a) sum_r Wab[p][k][s][r] gb[j][r]   (b,b) sum_r Wbb[k][p][r][s] gb[j][r]
-//   Zf1[(k,j)][(p,s)] = sum_r Wab[k][p][s][r] gb[j][r],  Zf2[(k,j)][(p,s)] = sum_r Wab[p][k][r][s] ga[j][r]
-template <int PREC>
-__global__ void k_mx_Z(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
-                       const double* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2, r3 = R2 * r, nd = 4 * n4;
-    const size_t ld2 = (size_t)p.ns * p.Kp2, ld1 = (size_t)p.ns * p.Kp1;
-    const float* ga = p.gam32;
-    const float* gb = p.gam32 + R2;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
-        float acc = 0.f;
-        if (e < nd) {
-            const size_t row = e / (2 * R2), col = e % (2 * R2);
-            const int sK = (int)(row / R2), sP = (int)(col / R2);
-            const int k = (int)((row % R2) / r), j = (int)(row % r);
-            const int pp = (int)((col % R2) / r), s = (int)(col % r);
-            if (sK == 0) {
-                const double* base = (sP == 0 ? Waa : Wab) + k * r3 + pp * R2 + s;
-                for (int q = 0; q < r; ++q) acc += (float)base[q * r] * ga[j * r + q];
-            } else if (sP == 0) {
-                const double* base = Wab + pp * r3 + k * R2 + s * r;
-                for (int q = 0; q < r; ++q) acc += (float)base[q] * gb[j * r + q];
-            } else {
-                const double* base = Wbb + k * r3 + pp * R2 + s;
-                for (int q = 0; q < r; ++q) acc += (float)base[q * r] * gb[j * r + q];
-            }
-            put<PREC, 0>(p.Zd, row, ld2, p.Kp2, (int)col, acc);
-        } else {
-            const size_t f = e - nd;
-            const int which = (int)(f / n4);
-            const size_t g = f % n4;
-            const size_t row = g / R2;
-            const int col = (int)(g % R2);
-            const int k = (int)(row / r), j = (int)(row % r), pp = col / r, s = col % r;
-            if (which == 0) {
-                const double* base = Wab + k * r3 + pp * R2 + s * r;
-                for (int q = 0; q < r; ++q) acc += (float)base[q] * gb[j * r + q];
-            } else {
-                const double* base = Wab + pp * r3 + k * R2 + s;
-                for (int q = 0; q < r; ++q) acc += (float)base[q * r] * ga[j * r + q];
-            }
-            put<PREC, 0>(p.Zf[which], row, ld1, p.Kp1, col, acc);
-        }
-    }
-}
-
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const int r = c->r;
     const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
-    if (c->opt.prec == ACSE_BF16X3) {
+    if (c->opt.prec == ACSE_BF16X3)
         k_mx_pack_W<ACSE_BF16X3><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
-        ACSE_LAUNCHED(c);
-        k_mx_Z<ACSE_BF16X3><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
-    } else {
+    else
         k_mx_pack_W<ACSE_TF32><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
-        ACSE_LAUNCHED(c);
-        k_mx_Z<ACSE_TF32><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
-    }
     ACSE_LAUNCHED(c);
-    return launch_w_mixed(c, W);
+    ACSE_TRY(launch_Z_tiled(c, W));
+    return launch_w_tiled(c, W);
 }
 
 // ------------------------------------------------------------------------ workspace
