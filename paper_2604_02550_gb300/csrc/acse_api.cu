@@ -66,7 +66,7 @@ static void free_work(acse_ctx* c) {
     Work& w = c->w;
     void* ptrs[] = {w.Kh[0], w.Kh[1], w.Kh[2], w.gam, w.M[0], w.M[1], w.M[2], w.Md, w.Mf1, w.Mf2, w.Zd, w.Zf1,
                     w.Zf2, w.w, w.Q, w.X[0], w.X[1], w.X[2], w.Y[0], w.Y[1], w.Y[2], w.X5d, w.X5f1, w.X5f2,
-                    w.T[0], w.T[1], w.T[2], w.T[3], w.A[0], w.A[1], w.A[2], w.U[0], w.U[1], w.U[2], w.Dt[0],
+                    w.H[0], w.H[1], w.H[2], w.zdiag, w.A[0], w.A[1], w.A[2], w.U[0], w.U[1], w.U[2], w.Dt[0],
                     w.Dt[1], w.Dt[2], w.stage_in[0], w.stage_in[1], w.stage_in[2], w.stage_out[0],
                     w.stage_out[1], w.stage_out[2], w.h, w.V, w.scal, w.partial};
     for (void* p : ptrs)
@@ -89,7 +89,8 @@ static int alloc_work(acse_ctx* c) {
     A_(w.gam, 2 * R2 * sizeof(double));
     if (c->opt.prec == ACSE_FP64) {   // FP64 intermediates (the split path has FP32 ones)
         for (int s = 0; s < 3; ++s) { A_(w.M[s], b4); A_(w.X[s], b4); A_(w.Y[s], b4); }
-        for (int t = 0; t < 4; ++t) A_(w.T[t], b4);
+        for (int t = 0; t < 3; ++t) A_(w.H[t], b4);
+        A_(w.zdiag, 4 * R2 * (size_t)c->r * sizeof(double));
         A_(w.w, 2 * R2 * sizeof(double));
         A_(w.Q, 2 * R2 * sizeof(double));
         A_(w.Md, 4 * b4); A_(w.Mf1, b4); A_(w.Mf2, b4);

@@ -196,10 +196,7 @@ __global__ void k_Q_from_X(int r, const T* __restrict__ Xaa, const T* __restrict
     Qv[t] = acc;
 }
 
-int launch_W_intermediates(acse_ctx* c, const double* const W[3]) {
-    ACSE_TRY(launch_Z_tiled(c, W));
-    return launch_w_tiled(c, W);
-}
+int launch_W_intermediates(acse_ctx* c, const double* const W[3]) { return launch_Z_tiled(c, W); }
 
 int launch_Q(acse_ctx* c) {
     const int r = c->r;
@@ -228,15 +225,15 @@ int launch_Q(acse_ctx* c) {
 int launch_build_B(acse_ctx* c) { return launch_B_tiled(c); }
 
 // --------------------------------------------------------------------------- G assembly
-// G_aa[ij][kl] = 4(Yaa[ij][kl] - s Yaa[kl][ij]) - 12(T0[ij][kl] - T0[ij][lk]) + 12 s (T0[kl][ij] - T0[kl][ji])
-// G_bb likewise with T1;
-// G_ab[ij][kl] = 4(Yab[ij][kl] - s Yab[kl][ij]) - 12(T2[ij][kl] - T3[ij][lk]) + 12 s (T2[kl][ij] - T3[kl][ji]).
-// out = scale * G; norm^2 partials (aa + bb + 4 ab, before the mask) per block.
+// The B kernel (acse_tiled.cu) leaves H_b = 4 Y_b - 12 (P - P'_{k<->l}) per block b, so that
+//   G_b[ij][kl] = H_b[ij][kl] - s H_b[kl][ij]
+// (= 4(Y - sY^T) - 12(B - B_{k<->l}) + 12 s (B^T - B^T_{i<->j}) of Appendix B).  out = scale * G,
+// transposed reads through 32 x 32 shared-memory tiles; ||.||^2 partials (aa + bb + 4 ab, before
+// the mask) per block, in a fixed order.
 template <typename T>
 struct GArgs {
     int r;
-    const T* Y[3];       // Y^{ij}_{kl} per sector, row stride R2
-    const T* T_[4];
+    const T* H[3];
     double* out[3];
     T s, scale;
     int mask, lo, hi;
@@ -246,30 +243,37 @@ struct GArgs {
 #define G_GRID (152 * 4)
 
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_assemble_G(const __grid_constant__ GArgs<T> a) {
+__global__ void __launch_bounds__(256) k_assemble_G(const __grid_constant__ GArgs<T> a) {
+    __shared__ T tile[32][33];
     const int r = a.r;
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    const int R2 = r * r;
+    const int nT = (R2 + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     double nrm = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 3 * n4; e += (size_t)gridDim.x * blockDim.x) {
-        const int blk = (int)(e / n4);
-        const size_t g = e % n4;
-        const int i = (int)(g / (R2 * r)), j = (int)((g / R2) % r), k = (int)((g / r) % r), l = (int)(g % r);
-        const size_t ij = (size_t)i * r + j, kl = (size_t)k * r + l, lk = (size_t)l * r + k, ji = (size_t)j * r + i;
-        const T* Y = a.Y[blk];
-        const T* P;
-        const T* Qx;
-        if (blk == 0) { P = a.T_[0]; Qx = a.T_[0]; }
-        else if (blk == 2) { P = a.T_[1]; Qx = a.T_[1]; }
-        else { P = a.T_[2]; Qx = a.T_[3]; }
-        const T v = (T)4 * (Y[ij * R2 + kl] - a.s * Y[kl * R2 + ij])
-                    - (T)12 * (P[ij * R2 + kl] - Qx[ij * R2 + lk])
-                    + (T)12 * a.s * (P[kl * R2 + ij] - Qx[kl * R2 + ji]);
-        double o = (double)(a.scale * v);
-        nrm += (blk == 1 ? 4.0 : 1.0) * o * o;
-        if (a.mask && i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo &&
-            l < a.hi)
-            o = 0.0;
-        a.out[blk][g] = o;
+    for (int tid = blockIdx.x; tid < 3 * nT * nT; tid += gridDim.x) {
+        const int blk = tid / (nT * nT);
+        const int ti = (tid / nT) % nT, tj = tid % nT;
+        const T* H = a.H[blk];
+        // tile[y][x] = H[(tj*32 + y)][(ti*32 + x)]   (rows kl, columns ij)
+        for (int y = ty; y < 32; y += 8) {
+            const int kl = tj * 32 + y, ij = ti * 32 + tx;
+            tile[y][tx] = (kl < R2 && ij < R2) ? H[(size_t)kl * R2 + ij] : (T)0;
+        }
+        __syncthreads();
+        for (int y = ty; y < 32; y += 8) {
+            const int ij = ti * 32 + y, kl = tj * 32 + tx;
+            if (ij < R2 && kl < R2) {
+                const T v = a.scale * (H[(size_t)ij * R2 + kl] - a.s * tile[tx][y]);
+                double o = (double)v;
+                nrm += (blk == 1 ? 4.0 : 1.0) * o * o;
+                const int i = ij / r, j = ij % r, k = kl / r, l = kl % r;
+                if (a.mask && i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi &&
+                    l >= a.lo && l < a.hi)
+                    o = 0.0;
+                a.out[blk][(size_t)ij * R2 + kl] = o;
+            }
+        }
+        __syncthreads();
     }
     nrm = block_sum(nrm);
     if (threadIdx.x == 0) a.partial[blockIdx.x] = nrm;
@@ -296,19 +300,16 @@ static void fill_G(acse_ctx* c, GArgs<T>& a, int sW, double scale, int apply_mas
 }
 
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3], double* norm2_dst) {
-    const size_t R2 = (size_t)c->r * c->r;
     if (c->opt.prec == ACSE_FP64) {
         GArgs<double> a;
         fill_G(c, a, sW, scale, apply_mask, out);
-        for (int s = 0; s < 3; ++s) a.Y[s] = c->w.Y[s];
-        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T[t];
-        k_assemble_G<double><<<G_GRID, TPB, 0, c->stream>>>(a);
+        for (int s = 0; s < 3; ++s) a.H[s] = c->w.H[s];
+        k_assemble_G<double><<<G_GRID, 256, 0, c->stream>>>(a);
     } else {
         GArgs<float> a;
         fill_G(c, a, sW, scale, apply_mask, out);
-        for (int s = 0; s < 3; ++s) a.Y[s] = c->w.tc_pairC[s] + R2 * R2;   // rows r^2.. of [X; Y]
-        for (int t = 0; t < 4; ++t) a.T_[t] = c->w.T32[t];
-        k_assemble_G<float><<<G_GRID, TPB, 0, c->stream>>>(a);
+        for (int s = 0; s < 3; ++s) a.H[s] = c->w.H32[s];
+        k_assemble_G<float><<<G_GRID, 256, 0, c->stream>>>(a);
     }
     ACSE_LAUNCHED(c);
     if (norm2_dst) {

@@ -57,7 +57,8 @@ struct Work {
     double* X5d;          // 4 r^4
     double* X5f1;
     double* X5f2;
-    double* T[4];         // B spin types aaaa, bbbb, abab, abba (r^4 each)
+    double* H[3];         // H_b = 4 Y_b - 12 (P - P'_{k<->l}) per block (r^4 each); G_b = H_b - s H_b^T
+    double* zdiag;        // [4][r][r][r]: diagonal rows j = p of Z (for w)
     // residual, update, trial D for the line search
     double* A[3];
     double* U[3];
@@ -88,7 +89,8 @@ struct Work {
     float* gam32;         // [2][r][r]
     float* w32;
     float* Q32;
-    float* T32[4];
+    float* H32[3];
+    float* zdiag32;
     int* tc_err;          // device flag: a bounded wait inside the tensor-core GEMM ran out
 };
 
@@ -142,7 +144,6 @@ int launch_pack_Mph(acse_ctx* c);
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
 int launch_build_B(acse_ctx* c);
 int launch_Z_tiled(acse_ctx* c, const double* const W[3]);
-int launch_w_tiled(acse_ctx* c, const double* const W[3]);
 int launch_B_tiled(acse_ctx* c);
 int tiled_set_attrs();
 int launch_Q(acse_ctx* c);

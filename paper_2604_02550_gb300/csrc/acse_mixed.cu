@@ -185,8 +185,7 @@ int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     else
         k_mx_pack_W<ACSE_TF32><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     ACSE_LAUNCHED(c);
-    ACSE_TRY(launch_Z_tiled(c, W));
-    return launch_w_tiled(c, W);
+    return launch_Z_tiled(c, W);   // Z packs and w (the diagonal of Z)
 }
 
 // ------------------------------------------------------------------------ workspace
@@ -224,7 +223,8 @@ int tc_mixed_alloc(acse_ctx* c) {
         ACSE_TRY(mx_alloc((void**)&w.tc_X5f[f], n4 * sizeof(float), false));
     }
     ACSE_TRY(mx_alloc((void**)&w.tc_X5d, 4 * n4 * sizeof(float), false));
-    for (int t = 0; t < 4; ++t) ACSE_TRY(mx_alloc((void**)&w.T32[t], n4 * sizeof(float), false));
+    for (int t = 0; t < 3; ++t) ACSE_TRY(mx_alloc((void**)&w.H32[t], n4 * sizeof(float), false));
+    ACSE_TRY(mx_alloc((void**)&w.zdiag32, 4 * R2 * r * sizeof(float), false));
     ACSE_TRY(mx_alloc((void**)&w.gam32, 2 * R2 * sizeof(float), false));
     ACSE_TRY(mx_alloc((void**)&w.w32, 2 * R2 * sizeof(float), false));
     ACSE_TRY(mx_alloc((void**)&w.Q32, 2 * R2 * sizeof(float), false));
@@ -237,7 +237,7 @@ void tc_mixed_free(acse_ctx* c) {
     void* ptrs[] = {w.tc_pairA[0], w.tc_pairA[1], w.tc_pairA[2], w.tc_pairB[0], w.tc_pairB[1], w.tc_pairB[2],
                     w.tc_pairC[0], w.tc_pairC[1], w.tc_pairC[2], w.M32[0], w.M32[1], w.M32[2], w.tc_Md, w.tc_Zd,
                     w.tc_Mf[0], w.tc_Mf[1], w.tc_Zf[0], w.tc_Zf[1], w.tc_X5f[0], w.tc_X5f[1], w.tc_X5d,
-                    w.T32[0], w.T32[1], w.T32[2], w.T32[3], w.gam32, w.w32, w.Q32, w.tc_err};
+                    w.H32[0], w.H32[1], w.H32[2], w.zdiag32, w.gam32, w.w32, w.Q32, w.tc_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
