@@ -100,7 +100,7 @@ static int alloc_work(acse_ctx* c) {
     A_(w.h, R2 * sizeof(double));
     A_(w.V, b4);
     A_(w.scal, 16 * sizeof(double));
-    w.npartial = 4096;
+    w.npartial = 8192;
     A_(w.partial, (size_t)w.npartial * sizeof(double));
 #undef A_
     ACSE_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), c->stream));
@@ -193,12 +193,13 @@ static int contract_G(acse_ctx* c, const double* const D[3], const double* const
         int n = 0;
         for (int s = 0; s < 3; ++s) {
             const double f = (s == 1) ? 2.0 : 1.0;   // mixed-spin (rs) sums count both orders
-            g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0};
-            g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0};
+            g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0};
+            g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0};
         }
-        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0};
-        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0};
-        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0};
+        // particle-hole outputs stored permuted: X5p[sK*nsb + sI][(i,j)][(k,l)]
+        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, r};
+        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, r};
+        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, r};
         ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
     } else {
         if (prep_D) ACSE_TRY(launch_gamma(c, D));

@@ -240,7 +240,7 @@ struct GArgs {
     double* partial;
 };
 
-#define G_GRID (152 * 4)
+#define G_GRID (152 * 16)
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_assemble_G(const __grid_constant__ GArgs<T> a) {

@@ -21,6 +21,7 @@ struct GemmF64 {
     int M, N, K;
     int lda, ldb, ldc;
     double alpha, beta;
+    int perm_r;   // 0: C row-major; r: particle-hole output stored permuted (see gemm_tc.cu)
 };
 
 // Split-precision operand problem for the tensor-core path.  A and B are 16-bit (BF16) or

@@ -43,6 +43,30 @@ __device__ __forceinline__ void put(void* base, size_t row, size_t ld, int Kp, i
     }
 }
 
+// Four consecutive K positions k..k+3 of one row at once (8-byte stores for BF16, 16-byte for TF32);
+// requires k % 4 == 0 and a row length that keeps 8/16-byte alignment (true when r is even).
+template <int PREC, int PAT>
+__device__ __forceinline__ void put4(void* base, size_t row, size_t ld, int Kp, int k, const float (&x)[4]) {
+    if (PREC == ACSE_BF16X3) {
+        __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            hi[u] = __float2bfloat16_rn(x[u]);
+            lo[u] = __float2bfloat16_rn(x[u] - __bfloat162float(hi[u]));
+        }
+        __nv_bfloat16* p = (__nv_bfloat16*)base + row * ld + k;
+        uint2 H, L;
+        memcpy(&H, hi, 8);
+        memcpy(&L, lo, 8);
+        *reinterpret_cast<uint2*>(p) = H;
+        *reinterpret_cast<uint2*>(p + Kp) = PAT == 0 ? H : L;
+        *reinterpret_cast<uint2*>(p + 2 * Kp) = PAT == 0 ? L : H;
+    } else {
+        float4 v = make_float4(tf32_rna(x[0]), tf32_rna(x[1]), tf32_rna(x[2]), tf32_rna(x[3]));
+        *reinterpret_cast<float4*>((float*)base + row * ld + k) = v;
+    }
+}
+
 struct MxPtrs {
     void* pairA[3];
     void* pairB[3];
@@ -78,69 +102,86 @@ static MxPtrs mx_ptrs(acse_ctx* c) {
 
 // --------------------------------------------------------------------------- per D
 // M = 3 2D - 2 (1D^1D) in FP32 (App. C), stored plain (M32) and as rows 0..r^2-1 of the pair
-// operand [M; D]; rows r^2..2r^2-1 hold D.  Also rounds the FP64 1-RDM to FP32.
+// operand [M; D]; rows r^2..2r^2-1 hold D.  Also rounds the FP64 1-RDM to FP32.  Each thread
+// handles four consecutive columns (vector stores when r is even).
 template <int PREC>
 __global__ void k_mx_prepD(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
                            const double* __restrict__ Dab, const double* __restrict__ Dbb, const __grid_constant__ MxPtrs p) {
     const size_t R2 = (size_t)r * r, n4 = R2 * R2;
     const size_t ld = (size_t)p.ns * p.Kp1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 6 * n4; e += (size_t)gridDim.x * blockDim.x) {
+    const int c4 = (int)((R2 + 3) / 4);
+    const bool vec = (r & 1) == 0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 6 * R2 * c4; e += (size_t)gridDim.x * blockDim.x) {
         if (e < 2 * R2) p.gam32[e] = (float)gam[e];
-        const int s = (int)(e / (2 * n4));
-        const size_t rem = e % (2 * n4);
-        const size_t row = rem / R2;
-        const int k = (int)(rem % R2);
+        const int s = (int)(e / (2 * R2 * c4));
+        const size_t rem = e % (2 * R2 * c4);
+        const size_t row = rem / c4;
+        const int k0 = (int)(rem % c4) * 4;
         const double* D = s == 0 ? Daa : (s == 1 ? Dab : Dbb);
-        float x;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        const int nk = (int)(R2 - k0) < 4 ? (int)(R2 - k0) : 4;
         if (row < R2) {
-            const int i = (int)(row / r), j = (int)(row % r), kk = k / r, l = k % r;
+            const int i = (int)(row / r), j = (int)(row % r);
             const double* ga = gam + (s == 2 ? R2 : 0);
             const double* gb = gam + (s == 0 ? 0 : R2);
-            const float d = (float)D[row * R2 + k];
-            if (s == 1)
-                x = 3.0f * d - (float)ga[i * r + kk] * (float)gb[j * r + l];
-            else
-                x = 3.0f * d - ((float)ga[i * r + kk] * (float)ga[j * r + l] - (float)ga[j * r + kk] * (float)ga[i * r + l]);
-            p.M32[s][row * R2 + k] = x;
+            for (int u = 0; u < nk; ++u) {
+                const int k = k0 + u, kk = k / r, l = k % r;
+                const float d = (float)D[row * R2 + k];
+                x[u] = s == 1 ? 3.0f * d - (float)ga[i * r + kk] * (float)gb[j * r + l]
+                              : 3.0f * d - ((float)ga[i * r + kk] * (float)ga[j * r + l] -
+                                            (float)ga[j * r + kk] * (float)ga[i * r + l]);
+                p.M32[s][row * R2 + k] = x[u];
+            }
         } else {
-            x = (float)D[(row - R2) * R2 + k];
+            for (int u = 0; u < nk; ++u) x[u] = (float)D[(row - R2) * R2 + k0 + u];
         }
-        put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k, x);
+        if (vec && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
+        else
+            for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
     }
 }
 
-// Particle-hole layouts of M (the B operands of the ph GEMMs), same index maps as the FP64 path:
-//   Md[(sI,i,l)][(sP,p,s)]: (a,a) Maa[i][p][l][s], (a,b) Mab[i][p][l][s], (b,a) Mab[p][i][s][l], (b,b) Mbb[i][p][l][s]
-//   Mf1[(i,l)][(p,s)] = Mab[i][p][s][l],  Mf2[(i,l)][(p,s)] = Mab[p][i][l][s]
+// Particle-hole layouts of M (the B operands of the ph GEMMs), copied as r x r blocks per (t, i, p):
+//   t=0 Md(a,a) rows (a,i,l) cols (a,p,s) <- Maa[i][p][l][s]      t=1 Md(a,b) <- Mab[i][p][l][s]
+//   t=2 Md(b,a) rows (b,i,l) cols (a,p,s) <- Mab[p][i][s][l]      t=3 Md(b,b) <- Mbb[i][p][l][s]
+//   t=4 Mf1[(i,l)][(p,s)] <- Mab[i][p][s][l]                        t=5 Mf2[(i,l)][(p,s)] <- Mab[p][i][l][s]
+// (transposed source blocks go through shared memory so that reads and writes stay coalesced).
 template <int PREC>
-__global__ void k_mx_pack_Mph(int r, const __grid_constant__ MxPtrs p) {
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2, nd = 4 * n4;
-    const size_t ld2 = (size_t)p.ns * p.Kp2, ld1 = (size_t)p.ns * p.Kp1;
-    const float* Maa = p.M32[0];
-    const float* Mab = p.M32[1];
-    const float* Mbb = p.M32[2];
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd + 2 * n4; e += (size_t)gridDim.x * blockDim.x) {
-        if (e < nd) {
-            const size_t row = e / (2 * R2), col = e % (2 * R2);
-            const int sI = (int)(row / R2), sP = (int)(col / R2);
-            const int i = (int)((row % R2) / r), l = (int)(row % r);
-            const int pp = (int)((col % R2) / r), s = (int)(col % r);
-            float v;
-            if (sI == 0 && sP == 0) v = Maa[((i * r + pp) * (size_t)r + l) * r + s];
-            else if (sI == 0) v = Mab[((i * r + pp) * (size_t)r + l) * r + s];
-            else if (sP == 0) v = Mab[((pp * r + i) * (size_t)r + s) * r + l];
-            else v = Mbb[((i * r + pp) * (size_t)r + l) * r + s];
-            put<PREC, 1>(p.Md, row, ld2, p.Kp2, (int)col, v);
-        } else {
-            const size_t f = e - nd;
-            const int which = (int)(f / n4);
-            const size_t g = f % n4;
-            const size_t row = g / R2;
-            const int col = (int)(g % R2);
-            const int i = (int)(row / r), l = (int)(row % r), pp = col / r, s = col % r;
-            const float v = which == 0 ? Mab[((i * r + pp) * (size_t)r + s) * r + l] : Mab[((pp * r + i) * (size_t)r + l) * r + s];
-            put<PREC, 1>(p.Mf[which], row, ld1, p.Kp1, col, v);
-        }
+__global__ void __launch_bounds__(256) k_mx_pack_Mph(int r, const __grid_constant__ MxPtrs p) {
+    __shared__ float tile[ACSE_MAX_R][ACSE_MAX_R + 1];
+    const int R2 = r * r;
+    const int t = blockIdx.x / R2, ip = blockIdx.x % R2;
+    const int i = ip / r, pp = ip % r;
+    const size_t r3 = (size_t)R2 * r;
+    const float* src;
+    bool tr;
+    switch (t) {
+        case 0: src = p.M32[0] + i * r3 + (size_t)pp * R2; tr = false; break;
+        case 1: src = p.M32[1] + i * r3 + (size_t)pp * R2; tr = false; break;
+        case 2: src = p.M32[1] + pp * r3 + (size_t)i * R2; tr = true; break;
+        case 3: src = p.M32[2] + i * r3 + (size_t)pp * R2; tr = false; break;
+        case 4: src = p.M32[1] + i * r3 + (size_t)pp * R2; tr = true; break;
+        default: src = p.M32[1] + pp * r3 + (size_t)i * R2; tr = false; break;
+    }
+    for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+        const int u = e / r, v = e % r;
+        if (tr) tile[v][u] = src[e];
+        else tile[u][v] = src[e];
+    }
+    __syncthreads();
+    void* dst;
+    size_t ld;
+    int Kp, rowbase, colbase;
+    if (t < 4) {
+        dst = p.Md; ld = (size_t)p.ns * p.Kp2; Kp = p.Kp2;
+        rowbase = (t >> 1) * R2 + i * r; colbase = (t & 1) * R2 + pp * r;
+    } else {
+        dst = p.Mf[t - 4]; ld = (size_t)p.ns * p.Kp1; Kp = p.Kp1;
+        rowbase = i * r; colbase = pp * r;
+    }
+    for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+        const int l = e / r, s2 = e % r;
+        put<PREC, 1>(dst, (size_t)rowbase + l, ld, Kp, colbase + s2, tile[l][s2]);
     }
 }
 
@@ -148,14 +189,15 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
     const int r = c->r;
     const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
+    const int R2 = r * r;
     if (c->opt.prec == ACSE_BF16X3) {
-        k_mx_prepD<ACSE_BF16X3><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_BF16X3><<<mx_grid(6 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_BF16X3><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, p);
+        k_mx_pack_Mph<ACSE_BF16X3><<<6 * R2, 256, 0, c->stream>>>(r, p);
     } else {
-        k_mx_prepD<ACSE_TF32><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_TF32><<<mx_grid(6 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_TF32><<<mx_grid(6 * n4), MX_TPB, 0, c->stream>>>(r, p);
+        k_mx_pack_Mph<ACSE_TF32><<<6 * R2, 256, 0, c->stream>>>(r, p);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -168,12 +210,22 @@ __global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double*
                             const double* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
     const size_t R2 = (size_t)r * r, n4 = R2 * R2;
     const size_t ld = (size_t)p.ns * p.Kp1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 3 * n4; e += (size_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e / n4);
-        const size_t g = e % n4;
-        const double* W = s == 0 ? Waa : (s == 1 ? Wab : Wbb);
-        put<PREC, 1>(p.pairB[s], g / R2, ld, p.Kp1, (int)(g % R2), (float)W[g]);
+    const int c4 = (int)((R2 + 3) / 4);
+    const bool vec = (r & 1) == 0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 3 * R2 * c4; e += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(e / (R2 * c4));
+        const size_t rem = e % (R2 * c4);
+        const size_t row = rem / c4;
+        const int k0 = (int)(rem % c4) * 4;
+        const double* W = (s == 0 ? Waa : (s == 1 ? Wab : Wbb)) + row * R2;
+        const int nk = (int)(R2 - k0) < 4 ? (int)(R2 - k0) : 4;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int u = 0; u < nk; ++u) x[u] = (float)W[k0 + u];
+        if (vec && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
+        else
+            for (int u = 0; u < nk; ++u) put<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0 + u, x[u]);
     }
+    (void)n4;
 }
 
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
@@ -181,9 +233,9 @@ int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
     if (c->opt.prec == ACSE_BF16X3)
-        k_mx_pack_W<ACSE_BF16X3><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_BF16X3><<<mx_grid(3 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     else
-        k_mx_pack_W<ACSE_TF32><<<mx_grid(3 * n4), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_TF32><<<mx_grid(3 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     ACSE_LAUNCHED(c);
     return launch_Z_tiled(c, W);   // Z packs and w (the diagonal of Z)
 }

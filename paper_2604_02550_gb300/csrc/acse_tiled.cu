@@ -165,8 +165,8 @@ struct BTiledArgs {
     int r;
     const T* X[3];      // pair GEMM outputs X^{ij}_{kp}, row stride r^2
     const T* Y[3];      // pair GEMM outputs Y^{ij}_{kl}
-    const T* X5d;       // (2r^2) x (2r^2)
-    const T* X5f1;
+    const T* X5d;       // permuted: [4][(i,j)][(k,l)] for (sK,sI) = aa, ab, ba, bb
+    const T* X5f1;      // permuted: [(i,j)][(k,l)]
     const T* X5f2;
     const T* M[3];
     const T* gam;
@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
     const int r = a.r;
     const int rp = pad4(r);
     const int R2 = r * r;
-    const size_t R22 = 2 * (size_t)R2;
     T* XT = (T*)tl_smem;      // [p][k]
     T* G1 = XT + rp * rp;     // [p][l]
     T* WT = G1 + rp * rp;     // [p][k]
@@ -227,6 +226,17 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             }
             __syncthreads();
             T* Bt = Bs + (size_t)tt * R2;
+            // X5 rows of the permuted particle-hole outputs (contiguous over (k, l)):
+            //   T0: X5d[aa][(i,j)], X5d[aa][(j,i)]   T1: X5d[bb][(i,j)], X5d[bb][(j,i)]
+            //   T2: X5f1[(i,j)],    X5d[ab][(j,i)]   T3: X5d[ba][(i,j)], X5f2[(j,i)]
+            const size_t sq = (size_t)R2 * R2;
+            const size_t rij = ((size_t)i * r + j) * R2, rji = ((size_t)j * r + i) * R2;
+            const T* X5row;
+            const T* X8row;
+            if (t == 0) { X5row = a.X5d + rij; X8row = a.X5d + rji; }
+            else if (t == 1) { X5row = a.X5d + 3 * sq + rij; X8row = a.X5d + 3 * sq + rji; }
+            else if (t == 2) { X5row = a.X5f1 + rij; X8row = a.X5d + 1 * sq + rji; }
+            else { X5row = a.X5d + 2 * sq + rij; X8row = a.X5f2 + rji; }
             for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
                 const int k0 = (tile / nt) * 4, l0 = (tile % nt) * 4;
                 T x1[4][4], x2[4][4];
@@ -244,23 +254,18 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                     for (int v = 0; v < 4; ++v) {
                         const int l = l0 + v;
                         if (l >= r) continue;
-                        T x4 = 0, x5, x7 = 0, x8;
+                        T x4 = 0, x7 = 0;
+                        const size_t kl = (size_t)k * r + l;
+                        const T x5 = X5row[kl], x8 = X8row[kl];
                         if (t < 2) {
                             const T* gg = t == 0 ? ga : gb;
                             const T* QQ = t == 0 ? Qa : Qb;
                             x4 = QQ[k * r + i] * gg[j * r + l];
                             x7 = QQ[k * r + j] * gg[i * r + l];
-                            const size_t off = (size_t)t * R2;
-                            x5 = a.X5d[(off + (size_t)k * r + j) * R22 + off + (size_t)i * r + l];
-                            x8 = a.X5d[(off + (size_t)k * r + i) * R22 + off + (size_t)j * r + l];
                         } else if (t == 2) {
                             x4 = Qa[k * r + i] * gb[j * r + l];
-                            x5 = a.X5f1[((size_t)k * r + j) * R2 + (size_t)i * r + l];
-                            x8 = a.X5d[((size_t)k * r + i) * R22 + R2 + (size_t)j * r + l];
                         } else {
-                            x5 = a.X5d[(R2 + (size_t)k * r + j) * R22 + (size_t)i * r + l];
                             x7 = Qb[k * r + j] * ga[i * r + l];
-                            x8 = a.X5f2[((size_t)k * r + i) * R2 + (size_t)j * r + l];
                         }
                         Bt[k * r + l] = (sgn1 * x1[u][v] - (T)2 * sgn2 * x2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
                                         (T)(1.0 / 9.0);

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ GemmF6
         __syncthreads();
     }
     const double alpha = P.alpha, beta = P.beta;
+    const int pr = P.perm_r, pR2 = pr * pr;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int m = m0 + ty + 16 * i;
@@ -82,9 +83,19 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ GemmF6
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
+            size_t dst;
+            if (pr) {   // row (sK, k, j), column (sI, i, l) -> Cp[sK * nsb + sI][(i, j)][(k, l)]
+                const int nsb = N / pR2;
+                const int sK = m / pR2, kk = (m % pR2) / pr, jj = m % pr;
+                const int sI = n / pR2, ii = (n % pR2) / pr, ll = n % pr;
+                dst = ((size_t)(sK * nsb + sI) * pR2 + (size_t)ii * pr + jj) * pR2 + (size_t)kk * pr + ll;
+            } else {
+                dst = (size_t)m * P.ldc + n;
+            }
             double v = alpha * acc[i][j];
-            if (beta != 0.0) v += beta * Crow[n];
-            Crow[n] = v;
+            if (beta != 0.0) v += beta * P.C[dst];
+            P.C[dst] = v;
+            (void)Crow;
         }
     }
 }

@@ -31,6 +31,8 @@ struct TcProb {
     float alpha;
     int tiles_n;
     int tile_start;
+    int perm_r;   // 0: C row-major.  r: particle-hole output C[(sK,k,j)][(sI,i,l)] stored as
+                  // Cp[sK * nsb + sI][(i,j)][(k,l)] (nsb = N / r^2), the row order the B kernel reads
 };
 
 struct __align__(64) TcBatch {
@@ -266,7 +268,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
         const bool store = ok && !*abort_flag && nk > 0;
         const int row = m0 + q * 32 + lane;
         float* Crow = P.C + (size_t)row * P.ldc;
-        const bool vec = (P.ldc & 3) == 0;
+        const bool vec = (P.ldc & 3) == 0 && P.perm_r == 0;
+        // permuted particle-hole store: row (sK, kk, jj) fixed per thread, columns (sI, i, l)
+        const int pr = P.perm_r, pR2 = pr * pr;
+        int sK = 0, kk = 0, jj = 0, nsb = 1;
+        if (pr) {
+            sK = row / pR2;
+            kk = (row % pR2) / pr;
+            jj = row % pr;
+            nsb = P.N / pR2;
+        }
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t v[32];
@@ -274,7 +285,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
             tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);   // warp-collective
             const int col0 = n0 + c * 32;
             if (store && row < P.M && col0 < P.N) {
-                if (vec && col0 + 32 <= P.N) {
+                if (pr) {
+                    int sI = col0 / pR2, ii = (col0 % pR2) / pr, ll = col0 % pr;
+                    for (int j = 0; j < 32 && col0 + j < P.N; ++j) {
+                        const size_t dst = ((size_t)(sK * nsb + sI) * pR2 + (size_t)ii * pr + jj) * pR2 + (size_t)kk * pr + ll;
+                        P.C[dst] = P.alpha * __uint_as_float(v[j]);
+                        if (++ll == pr) {
+                            ll = 0;
+                            if (++ii == pr) { ii = 0; ++sI; }
+                        }
+                    }
+                } else if (vec && col0 + 32 <= P.N) {
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
                         float4 o = make_float4(P.alpha * __uint_as_float(v[j]), P.alpha * __uint_as_float(v[j + 1]),
@@ -367,7 +388,8 @@ int tc_plan_create(acse_ctx* c) {
     TcBatch& b = pl->batch;
     memset(&b, 0, sizeof(b));
     int n = 0;
-    auto add = [&](const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) -> int {
+    auto add = [&](const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha,
+                   int perm_r) -> int {
         ACSE_TRY(encode_map(pl, &b.tmA[n], A, M, L, TC_BM));
         ACSE_TRY(encode_map(pl, &b.tmB[n], B, N, L, pl->bn));
         TcProb& p = b.p[n];
@@ -379,15 +401,16 @@ int tc_plan_create(acse_ctx* c) {
         p.alpha = alpha;
         p.tiles_n = (N + pl->bn - 1) / pl->bn;
         p.tile_start = b.total_tiles;
+        p.perm_r = perm_r;
         b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
         ++n;
         return ACSE_OK;
     };
     // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
-    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f));
+    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f, r));
     for (int s = 0; s < 3; ++s)
-        ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f));
-    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
+        ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f, 0));
+    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f, r));
     b.nprob = n;
     b.err = w.tc_err;
     b.wait_ns = TC_WAIT_NS;
