@@ -196,10 +196,9 @@ static int contract_G(acse_ctx* c, const double* const D[3], const double* const
             g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0};
             g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0};
         }
-        // particle-hole outputs stored permuted: X5p[sK*nsb + sI][(i,j)][(k,l)]
-        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, r};
-        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, r};
-        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, r};
+        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, 0};
+        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0};
+        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0};
         ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
     } else {
         if (prep_D) ACSE_TRY(launch_gamma(c, D));

@@ -165,8 +165,8 @@ struct BTiledArgs {
     int r;
     const T* X[3];      // pair GEMM outputs X^{ij}_{kp}, row stride r^2
     const T* Y[3];      // pair GEMM outputs Y^{ij}_{kl}
-    const T* X5d;       // permuted: [4][(i,j)][(k,l)] for (sK,sI) = aa, ab, ba, bb
-    const T* X5f1;      // permuted: [(i,j)][(k,l)]
+    const T* X5d;       // (2r^2) x (2r^2), rows (sK,k,j), columns (sI,i,l)
+    const T* X5f1;      // r^2 x r^2
     const T* X5f2;
     const T* M[3];
     const T* gam;
@@ -226,17 +226,16 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             }
             __syncthreads();
             T* Bt = Bs + (size_t)tt * R2;
-            // X5 rows of the permuted particle-hole outputs (contiguous over (k, l)):
-            //   T0: X5d[aa][(i,j)], X5d[aa][(j,i)]   T1: X5d[bb][(i,j)], X5d[bb][(j,i)]
-            //   T2: X5f1[(i,j)],    X5d[ab][(j,i)]   T3: X5d[ba][(i,j)], X5f2[(j,i)]
-            const size_t sq = (size_t)R2 * R2;
-            const size_t rij = ((size_t)i * r + j) * R2, rji = ((size_t)j * r + i) * R2;
-            const T* X5row;
-            const T* X8row;
-            if (t == 0) { X5row = a.X5d + rij; X8row = a.X5d + rji; }
-            else if (t == 1) { X5row = a.X5d + 3 * sq + rij; X8row = a.X5d + 3 * sq + rji; }
-            else if (t == 2) { X5row = a.X5f1 + rij; X8row = a.X5d + 1 * sq + rji; }
-            else { X5row = a.X5d + 2 * sq + rij; X8row = a.X5f2 + rji; }
+            // particle-hole sources: x5 at row (k, j), column (i, l); x8 at row (k, i), column (j, l):
+            //   T0: X5d(a,a) both   T1: X5d(b,b) both   T2: X5f1, X5d(a,b)   T3: X5d(b,a), X5f2
+            const size_t R22 = 2 * (size_t)R2;
+            const T* X5b;
+            const T* X8b;
+            size_t ld5, ld8;
+            if (t == 0) { X5b = a.X5d; X8b = a.X5d; ld5 = ld8 = R22; }
+            else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
+            else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
+            else { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
             for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
                 const int k0 = (tile / nt) * 4, l0 = (tile % nt) * 4;
                 T x1[4][4], x2[4][4];
@@ -255,8 +254,8 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                         const int l = l0 + v;
                         if (l >= r) continue;
                         T x4 = 0, x7 = 0;
-                        const size_t kl = (size_t)k * r + l;
-                        const T x5 = X5row[kl], x8 = X8row[kl];
+                        const T x5 = X5b[((size_t)k * r + j) * ld5 + (size_t)i * r + l];
+                        const T x8 = X8b[((size_t)k * r + i) * ld8 + (size_t)j * r + l];
                         if (t < 2) {
                             const T* gg = t == 0 ? ga : gb;
                             const T* QQ = t == 0 ? Qa : Qb;

@@ -407,10 +407,10 @@ int tc_plan_create(acse_ctx* c) {
         return ACSE_OK;
     };
     // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
-    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f, r));
+    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f, 0));
     for (int s = 0; s < 3; ++s)
         ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f, 0));
-    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f, r));
+    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f, 0));
     b.nprob = n;
     b.err = w.tc_err;
     b.wait_ns = TC_WAIT_NS;
