@@ -71,6 +71,20 @@ def workload(r, seed=0):
                           name=f"cas44_r{r}")
 
 
+def gemm_traffic(prec):
+    """DRAM bytes of one GEMM launch from profiles/gemm_tc_traffic.txt (an ncu capture), or None when
+    the kernel source has changed since that capture or the precision differs."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "gemm_tc_traffic.txt")
+    if prec != "bf16x3" or not os.path.exists(path):
+        return None
+    kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
+    src = os.path.join(ROOT, "paper_2604_02550_gb300", "csrc", "gemm_tc.cu")
+    if hashlib.sha1(open(src, "rb").read()).hexdigest() != kv.get("gemm_tc_sha1"):
+        return None
+    return float(kv["traffic_bytes"])
+
+
 def flops_per_pass(r):
     """2 M N K over the O(r^6) GEMMs of one contraction pass G(W):
     pair-pair: 3 spin sectors x ([M; D] (2 r^2 rows) x r^2 x r^2); particle-hole: one
@@ -276,7 +290,8 @@ def main():
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": TF32_PEAK_TFLOPS,
                 "peak_source": "measured cuBLAS TF32 8192^3 on this pool (bench.py --peaks)"}
         ach = fl / gemm_avg_s / 1e12
-    roof.update({"achieved": ach, "frac": ach / roof["peak"], "traffic": None, "kernel": "grouped O(r^6) GEMM",
+    roof.update({"achieved": ach, "frac": ach / roof["peak"], "traffic": gemm_traffic(prec) if p.r == 48 else None,
+                 "kernel": "grouped O(r^6) GEMM",
                  "flops_per_launch": split * fl, "launch_ms": 1e3 * gemm_avg_s,
                  "gemm_share_of_step": (gemm_ms / args.steps) / per_step})
     line = {"metric": "acse_residual_evals_per_s", "value": value, "unit": "residual evals/s", "n_gpus": world,
