@@ -9,6 +9,10 @@ int tc_plan_create(acse_ctx* c);
 void tc_plan_destroy(acse_ctx* c);
 int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
 int tc_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall);
+void adj_free(acse_ctx* c);
+extern "C" int acse_residual_backward_impl(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps,
+                                            double wE, double wN, double* dh, double* dV, double* dDaa,
+                                            double* dDab, double* dDbb);
 
 static const char* k_version = "libacse 0.1 (sm_103a; FP64 DFMA + tcgen05 split-precision GEMMs)";
 
@@ -170,6 +174,7 @@ extern "C" int acse_destroy(acse_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 2 * ACSE_PROF_MAX; ++i)
         if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+    adj_free(c);
     tc_plan_destroy(c);
     free_work(c);
     free(c);
@@ -179,8 +184,8 @@ extern "C" int acse_destroy(acse_ctx* c) {
 // ------------------------------------------------------------------------ contraction pass
 // G(W) for the current D: builds the operands, runs every O(r^6) GEMM of the pass in one
 // grouped launch, assembles B and G.  prep_D = 1 recomputes 1D, M and the ph layout of M.
-static int contract_G(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale,
-                      int mask, double* const out[3], double* norm2_dst, int prep_D) {
+int acse_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale, int mask,
+                  double* const out[3], double* norm2_dst, int prep_D) {
     Work& w = c->w;
     if (c->opt.prec == ACSE_FP64) {
         if (prep_D) {
@@ -193,12 +198,12 @@ static int contract_G(acse_ctx* c, const double* const D[3], const double* const
         int n = 0;
         for (int s = 0; s < 3; ++s) {
             const double f = (s == 1) ? 2.0 : 1.0;   // mixed-spin (rs) sums count both orders
-            g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0};
-            g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0};
+            g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0, 0, 0};
+            g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0, 0, 0};
         }
-        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, 0};
-        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0};
-        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0};
+        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, 0, 0, 0};
+        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 0, 0};
+        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 0, 0};
         ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
     } else {
         if (prep_D) ACSE_TRY(launch_gamma(c, D));
@@ -212,12 +217,12 @@ static int contract_G(acse_ctx* c, const double* const D[3], const double* const
 
 static int residual_dev(acse_ctx* c, const double* const D[3], double* const A[3], double* norm2_dst) {
     const double* W[3] = {c->w.Kh[0], c->w.Kh[1], c->w.Kh[2]};
-    return contract_G(c, D, W, +1, 1.0, 1, A, norm2_dst, 1);
+    return acse_contract(c, D, W, +1, 1.0, 1, A, norm2_dst, 1);
 }
 
 // Update for the D whose 1D / M are current: U = 1/2 G(A), A pair-anti-Hermitian (s = -1).
 static int update_dev(acse_ctx* c, const double* const D[3], const double* const A[3], double* const U[3]) {
-    return contract_G(c, D, A, -1, 0.5, 0, U, nullptr, 0);
+    return acse_contract(c, D, A, -1, 0.5, 0, U, nullptr, 0);
 }
 
 // ------------------------------------------------------------------------- staging
@@ -381,9 +386,8 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
 
 extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps, double wE,
                                       double wN, double* dh, double* dV, double* dDaa, double* dDab, double* dDbb) {
-    (void)D_ckpt; (void)n_steps; (void)eps; (void)wE; (void)wN; (void)dh; (void)dV; (void)dDaa; (void)dDab; (void)dDbb;
     if (!c) return ACSE_ERR_ARG;
-    return latch(c, ACSE_ERR_UNSUPPORTED);
+    return latch(c, acse_residual_backward_impl(c, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
 }
 
 // ------------------------------------------------------------------------------ profiling

@@ -11,8 +11,9 @@
 #define ACSE_MAX_R 64
 
 // ------------------------------------------------------------------------------------------
-// Dense "NT" GEMM problem: C[m*ldc + n] = alpha * sum_k A[m*lda + k] * B[n*ldb + k] (+ beta*C).
-// Both operands are K-major (row m of A and row n of B hold contiguous k).
+// Dense GEMM problem: C[m*ldc + n] = alpha * sum_k A(m,k) B(n,k) (+ beta*C), with
+//   A(m,k) = A[m*lda + k] (transA = 0, K-major) or A[k*lda + m] (transA = 1),
+//   B(n,k) = B[n*ldb + k] (transB = 0, K-major) or B[k*ldb + n] (transB = 1).
 // ------------------------------------------------------------------------------------------
 struct GemmF64 {
     const double* A;
@@ -22,6 +23,7 @@ struct GemmF64 {
     int lda, ldb, ldc;
     double alpha, beta;
     int perm_r;   // 0: C row-major; r: particle-hole output stored permuted (see gemm_tc.cu)
+    int transA, transB;
 };
 
 // Split-precision operand problem for the tensor-core path.  A and B are 16-bit (BF16) or
@@ -104,6 +106,7 @@ struct acse_ctx {
     int nsplit;           // split terms for the tensor-core path (3 for BF16x3, 1 for TF32)
     Work w;
     void* tc_plan;        // tensor-core GEMM plan (tensor maps etc.)
+    void* adj;            // adjoint workspace (allocated by the first acse_residual_backward call)
     // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches
     long long launches;
     int prof_on;

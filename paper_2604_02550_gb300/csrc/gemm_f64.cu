@@ -47,15 +47,18 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ GemmF6
     const double* __restrict__ B = P.B;
     const bool arow_ok = (m0 + lrow) < M;
     const bool brow_ok = (n0 + lrow) < N;
-    const double* Arow = A + (size_t)(m0 + lrow) * P.lda;
-    const double* Brow = B + (size_t)(n0 + lrow) * P.ldb;
+    // element (row, k) of each operand: row-major (K-major) or transposed storage
+    const size_t a_rs = P.transA ? 1 : (size_t)P.lda, a_ks = P.transA ? (size_t)P.lda : 1;
+    const size_t b_rs = P.transB ? 1 : (size_t)P.ldb, b_ks = P.transB ? (size_t)P.ldb : 1;
+    const double* Arow = A + (size_t)(m0 + lrow) * a_rs;
+    const double* Brow = B + (size_t)(n0 + lrow) * b_rs;
 
     for (int k0 = 0; k0 < K; k0 += GF_BK) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = k0 + lk + q;
-            As[lk + q][lrow] = (arow_ok && k < K) ? Arow[k] : 0.0;
-            Bs[lk + q][lrow] = (brow_ok && k < K) ? Brow[k] : 0.0;
+            As[lk + q][lrow] = (arow_ok && k < K) ? Arow[(size_t)k * a_ks] : 0.0;
+            Bs[lk + q][lrow] = (brow_ok && k < K) ? Brow[(size_t)k * b_ks] : 0.0;
         }
         __syncthreads();
 #pragma unroll
