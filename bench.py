@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="measure FP64/TF32/BF16 matmul peaks and exit")
+    ap.add_argument("--batch", action="store_true",
+                    help="time the 16-instance batch (r = 12..40, CAS(4e,4o) ground + excited) instead")
     return ap.parse_args()
 
 
@@ -222,6 +224,44 @@ def measure_peaks():
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args, rank, world):
+    """The 16-instance batch: graph-replayed steps, one grouped GEMM launch per pass."""
+    import numpy as np
+    import torch
+    import acse_inputs as I
+    from paper_2604_02550_gb300 import _lib
+    prec = args.prec or default_prec()
+    probs = I.batch_problems(seed=100 * rank)
+    eps = args.eps if args.eps is not None else 1e-4
+    b = _lib.acse_batch_create(probs, prec)
+    for i, p in enumerate(probs):
+        _lib.acse_batch_set_D(b, i, p.Daa, p.Dab, p.Dbb, eps)
+    _lib.acse_batch_run(b, len(probs), args.warmup, stop_rule=False)
+    for i, p in enumerate(probs):
+        _lib.acse_batch_set_D(b, i, p.Daa, p.Dab, p.Dbb, eps)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    E, N2, S, R = _lib.acse_batch_run(b, len(probs), args.steps, stop_rule=False)
+    dt = time.perf_counter() - t0
+    clocks = sampler.stop()
+    tune, split, launches = _lib.acse_batch_info(b)
+    _lib.acse_batch_destroy(b)
+    fl = sum(2 * flops_per_pass(p.r) for p in probs)
+    line = {"metric": "acse_residual_evals_per_s", "value": world * len(probs) * args.steps / dt,
+            "unit": "residual evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else prec, "data": "synthetic",
+            "config": {"workload": "batch16_r12-40_cas44", "instances": len(probs), "prec": prec, "eps": eps,
+                       "step": "one graph replay: every instance's residual + update + axpy + energy",
+                       "tile_choice": tune, "split_r2": split},
+            "tflops": world * fl * args.steps / dt / 1e12, "clocks": clocks,
+            "energies_finite": bool(np.all(np.isfinite(E)))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -234,6 +274,9 @@ def main():
         measure_peaks()
         return
     torch.cuda.set_device(local)
+    if args.batch:
+        run_batch(args, rank, world)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

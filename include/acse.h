@@ -115,6 +115,32 @@ int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_ste
                            double wE, double wN, double* dh, double* dV,
                            double* dDaa, double* dDab, double* dDbb);
 
+/* Batched propagation: n independent instances (electronic states, or molecules with different r)
+ * advanced together.  Each Euler step runs one grouped GEMM launch per contraction pass over all
+ * instances, spin sectors and tiles, with the per-instance elementwise work on forked streams; the
+ * step is captured once as a CUDA graph and replayed.  The Methods-section stopping rule runs on the
+ * device per instance: when E or ||A|| increases the previous D is restored and the instance is
+ * frozen; when |dE| < 1e-6 Eh it is frozen at the new D.  Tile widths of the grouped tensor-core
+ * launch are chosen on the first run by timing candidate partitions on the real operands (cached per
+ * process by the multiset of r and the precision).
+ *   opts, h, V: arrays of n (all instances share opts[0].prec; line search and input checks are off).
+ *   acse_batch_set_D: instance i's 2-RDM (device or host pointers, copied) and its step eps; resets
+ *     its trajectory state.  acse_batch_get_D copies the current blocks out.
+ *   acse_batch_run: nsteps graph replays; per instance (host arrays of n, each may be NULL): E and
+ *     ||A||^2 at the current D, accepted steps, stop reason (0 running, 1 E or ||A|| rose, 2 converged).
+ *   acse_batch_info: the tile choice (0 all 256 wide, 1 all 128 wide, 2 split at r^2 = split_r2) and
+ *     the kernels launched so far.  n <= 64. */
+typedef struct acse_batch acse_batch;
+int acse_batch_create(acse_batch** batch, int n, const acse_opts* opts, const double* const* h,
+                      const double* const* V, void* cuda_stream);
+int acse_batch_destroy(acse_batch* batch);
+int acse_batch_set_D(acse_batch* batch, int i, const double* Daa, const double* Dab, const double* Dbb,
+                     double eps);
+int acse_batch_get_D(acse_batch* batch, int i, double* Daa, double* Dab, double* Dbb);
+int acse_batch_run(acse_batch* batch, int nsteps, int stop_rule, double* E_out, double* norm2_out,
+                   int* steps_out, int* reason_out);
+int acse_batch_info(const acse_batch* batch, int* tune_choice, int* split_r2, long long* launches);
+
 /* Profiling (not part of the method).  acse_profile(ctx, 1) resets the counters and starts
  * recording a CUDA-event pair around every O(r^6) GEMM launch of this context (up to 256
  * launches between reads); acse_profile(ctx, 0) stops.  acse_profile_read synchronises the

@@ -16,8 +16,9 @@ PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32}
 # symbols declared in include/acse.h
 EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
            "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_sync_status",
-           "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_strerror",
-           "acse_last_error", "acse_version")
+           "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_batch_create",
+           "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D", "acse_batch_run", "acse_batch_info",
+           "acse_strerror", "acse_last_error", "acse_version")
 
 
 class AcseOpts(ctypes.Structure):
@@ -58,6 +59,16 @@ def lib():
                                         POINTER(ctypes.c_longlong)]
         L.acse_energy_noalloc.argtypes = [c_int, c_int, c_int] + [c_void_p] * 7
         L.acse_energy_noalloc.restype = c_int
+        L.acse_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(AcseOpts), POINTER(c_void_p),
+                                        POINTER(c_void_p), c_void_p]
+        L.acse_batch_destroy.argtypes = [c_void_p]
+        L.acse_batch_set_D.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]
+        L.acse_batch_get_D.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+        L.acse_batch_run.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.acse_batch_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_longlong)]
+        for name in ("acse_batch_create", "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D",
+                     "acse_batch_run", "acse_batch_info"):
+            getattr(L, name).restype = c_int
         L.acse_sync_status.argtypes = [c_void_p]
         L.acse_clear_status.argtypes = [c_void_p]
         L.acse_set_wait_bound_ns.argtypes = [c_void_p, ctypes.c_ulonglong, c_int]
@@ -173,3 +184,59 @@ def acse_energy_noalloc(r, n_alpha, n_beta, h, V, Daa, Dab, Dbb, E, stream=None)
     st = current_stream_handle() if stream is None else stream
     _check(lib().acse_energy_noalloc(int(r), int(n_alpha), int(n_beta), ptr(h), ptr(V), ptr(Daa), ptr(Dab),
                                      ptr(Dbb), ptr(E), st), "acse_energy_noalloc")
+
+
+def _opts(r, n_alpha, n_beta, prec="fp64", mask=None):
+    o = AcseOpts()
+    o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    if mask is not None:
+        o.mask_active, o.act_lo, o.act_hi = 1, int(mask[0]), int(mask[1])
+    o.eps0 = 1e-3
+    return o
+
+
+def acse_batch_create(problems, prec="bf16x3", masks=None, stream=None):
+    """problems: sequence of objects with r, n_alpha, n_beta, h, V (numpy or tensors)."""
+    n = len(problems)
+    arr = (AcseOpts * n)()
+    for i, p in enumerate(problems):
+        arr[i] = _opts(p.r, p.n_alpha, p.n_beta, prec, None if masks is None else masks[i])
+    hs = (c_void_p * n)(*[ptr(p.h) for p in problems])
+    Vs = (c_void_p * n)(*[ptr(p.V) for p in problems])
+    h_ = c_void_p()
+    st = current_stream_handle() if stream is None else stream
+    _check(lib().acse_batch_create(byref(h_), n, arr, hs, Vs, st), "acse_batch_create")
+    return h_
+
+
+def acse_batch_destroy(b):
+    _check(lib().acse_batch_destroy(b), "acse_batch_destroy")
+
+
+def acse_batch_set_D(b, i, Daa, Dab, Dbb, eps):
+    _check(lib().acse_batch_set_D(b, int(i), ptr(Daa), ptr(Dab), ptr(Dbb), float(eps)), "acse_batch_set_D")
+
+
+def acse_batch_get_D(b, i, Daa, Dab, Dbb):
+    _check(lib().acse_batch_get_D(b, int(i), ptr(Daa), ptr(Dab), ptr(Dbb)), "acse_batch_get_D")
+
+
+def acse_batch_run(b, n, nsteps, stop_rule=True):
+    """Returns (E, norm2, steps, reason) as numpy arrays of length n."""
+    import numpy as np
+    E = np.zeros(n)
+    N2 = np.zeros(n)
+    S = np.zeros(n, dtype=np.int32)
+    R = np.zeros(n, dtype=np.int32)
+    _check(lib().acse_batch_run(b, int(nsteps), int(bool(stop_rule)), E.ctypes.data, N2.ctypes.data,
+                                S.ctypes.data, R.ctypes.data), "acse_batch_run")
+    return E, N2, S, R
+
+
+def acse_batch_info(b):
+    t = c_int()
+    sp = c_int()
+    nl = ctypes.c_longlong()
+    _check(lib().acse_batch_info(b, byref(t), byref(sp), byref(nl)), "acse_batch_info")
+    return t.value, sp.value, nl.value

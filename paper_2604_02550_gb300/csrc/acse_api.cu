@@ -8,6 +8,8 @@
 int tc_plan_create(acse_ctx* c);
 void tc_plan_destroy(acse_ctx* c);
 int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
+int tc_contract_pre(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
+int tc_gemm_launch(acse_ctx* c);
 int tc_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall);
 void adj_free(acse_ctx* c);
 extern "C" int acse_residual_backward_impl(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps,
@@ -184,35 +186,62 @@ extern "C" int acse_destroy(acse_ctx* c) {
 // ------------------------------------------------------------------------ contraction pass
 // G(W) for the current D: builds the operands, runs every O(r^6) GEMM of the pass in one
 // grouped launch, assembles B and G.  prep_D = 1 recomputes 1D, M and the ph layout of M.
-int acse_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale, int mask,
-                  double* const out[3], double* norm2_dst, int prep_D) {
-    Work& w = c->w;
+int acse_contract_pre(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D) {
+    for (int s = 0; s < 3; ++s) {
+        c->cur_D[s] = D[s];
+        c->cur_W[s] = W[s];
+    }
     if (c->opt.prec == ACSE_FP64) {
         if (prep_D) {
             ACSE_TRY(launch_gamma_M(c, D));
             ACSE_TRY(launch_pack_Mph(c));
         }
-        ACSE_TRY(launch_W_intermediates(c, W));
-        const int r = c->r, R2 = r * r, R22 = 2 * R2;
+        return launch_W_intermediates(c, W);
+    }
+    if (prep_D) ACSE_TRY(launch_gamma(c, D));
+    return tc_contract_pre(c, D, W, prep_D);
+}
+
+// The nine FP64 GEMMs of the pass whose operands acse_contract_pre prepared.
+int acse_gemm_list_f64(acse_ctx* c, GemmF64* g, int* n) {
+    Work& w = c->w;
+    const int r = c->r, R2 = r * r, R22 = 2 * R2;
+    int k = 0;
+    for (int s = 0; s < 3; ++s) {
+        const double f = (s == 1) ? 2.0 : 1.0;   // mixed-spin (rs) sums count both orders
+        g[k++] = GemmF64{w.M[s], c->cur_W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0, 0, 0};
+        g[k++] = GemmF64{c->cur_D[s], c->cur_W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0, 0, 0};
+    }
+    g[k++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, 0, 0, 0};
+    g[k++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 0, 0};
+    g[k++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 0, 0};
+    *n = k;
+    return ACSE_OK;
+}
+
+int acse_contract_gemm(acse_ctx* c) {
+    if (c->opt.prec == ACSE_FP64) {
         GemmF64 g[9];
         int n = 0;
-        for (int s = 0; s < 3; ++s) {
-            const double f = (s == 1) ? 2.0 : 1.0;   // mixed-spin (rs) sums count both orders
-            g[n++] = GemmF64{w.M[s], W[s], w.X[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0, 0, 0};
-            g[n++] = GemmF64{D[s], W[s], w.Y[s], R2, R2, R2, R2, R2, R2, f, 0.0, 0, 0, 0};
-        }
-        g[n++] = GemmF64{w.Zd, w.Md, w.X5d, R22, R22, R22, R22, R22, R22, 1.0, 0.0, 0, 0, 0};
-        g[n++] = GemmF64{w.Zf1, w.Mf1, w.X5f1, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 0, 0};
-        g[n++] = GemmF64{w.Zf2, w.Mf2, w.X5f2, R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 0, 0};
-        ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
-    } else {
-        if (prep_D) ACSE_TRY(launch_gamma(c, D));
-        ACSE_TRY(tc_contract(c, D, W, prep_D));
+        ACSE_TRY(acse_gemm_list_f64(c, g, &n));
+        return gemm_f64_grouped(c, g, n, c->stream);
     }
+    return tc_gemm_launch(c);
+}
+
+int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* const out[3], double* norm2_dst) {
     ACSE_TRY(launch_Q(c));
     ACSE_TRY(launch_build_B(c));
-    ACSE_TRY(launch_assemble_G(c, sW, scale, mask, out, norm2_dst));
-    return ACSE_OK;
+    return launch_assemble_G(c, sW, scale, mask, out, norm2_dst);
+}
+
+// G(W) for the current D: operands, every O(r^6) GEMM of the pass in one grouped launch, assembly.
+// prep_D = 1 recomputes 1D, M and the particle-hole layout of M.
+int acse_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale, int mask,
+                  double* const out[3], double* norm2_dst, int prep_D) {
+    ACSE_TRY(acse_contract_pre(c, D, W, prep_D));
+    ACSE_TRY(acse_contract_gemm(c));
+    return acse_contract_post(c, sW, scale, mask, out, norm2_dst);
 }
 
 static int residual_dev(acse_ctx* c, const double* const D[3], double* const A[3], double* norm2_dst) {

@@ -38,6 +38,22 @@ struct GemmTC {
     float alpha;
 };
 
+// Problem table of one grouped tensor-core GEMM launch (gemm_tc.cu); TcBatch lives in device memory.
+struct TcBatch;
+struct TcTable {
+    TcBatch* dev;
+    TcBatch* host;
+    int kind;        // 0 = bf16 (kind::f16), 1 = tf32
+    int bn;          // tile width
+    int stages;
+    size_t smem;
+};
+int tc_table_init(TcTable* t, int kind, int bn);
+void tc_table_free(TcTable* t);
+int tc_table_upload(TcTable* t);
+int tc_table_append(TcTable* t, struct acse_ctx* c);
+int tc_table_launch(const TcTable* t, cudaStream_t st);
+
 // Scratch layout of one context (all device memory, owned by the context).
 struct Work {
     // K/2 blocks (the W of the residual), r^4 each
@@ -107,6 +123,8 @@ struct acse_ctx {
     Work w;
     void* tc_plan;        // tensor-core GEMM plan (tensor maps etc.)
     void* adj;            // adjoint workspace (allocated by the first acse_residual_backward call)
+    const double* cur_D[3];   // operands of the contraction pass in flight (FP64 GEMM list)
+    const double* cur_W[3];
     // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches
     long long launches;
     int prof_on;
@@ -162,3 +180,11 @@ int launch_copy_scalar(acse_ctx* c, double* dst, const double* src);
 
 // GEMM back ends ------------------------------------------------------------------------------
 int gemm_f64_grouped(acse_ctx* c, const GemmF64* probs, int nprob, cudaStream_t s);
+
+// contraction pass in three phases (acse_api.cu): operands, the O(r^6) GEMMs, assembly
+int acse_contract_pre(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);
+int acse_contract_gemm(acse_ctx* c);
+int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* const out[3], double* norm2_dst);
+int acse_gemm_list_f64(acse_ctx* c, GemmF64* g, int* n);
+int acse_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale, int mask,
+                  double* const out[3], double* norm2_dst, int prep_D);

@@ -19,7 +19,7 @@
 
 #include "acse_internal.h"
 
-#define TC_MAXP 12
+#define TC_MAXP 160          // problems of one grouped launch (16 instances x 9 GEMMs fit)
 #define TC_BM 128
 #define TC_THREADS 192
 #define TC_DRAIN_NS 2000000000ull      // bound of the clean-up waits (2 s)
@@ -178,7 +178,8 @@ __device__ __forceinline__ void raise_abort(int* err, volatile int* abort_flag) 
 
 // ------------------------------------------------------------------------------ kernel
 template <int KIND, int BN, int STAGES>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant__ TcBatch b) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const TcBatch* __restrict__ bp) {
+    const TcBatch& b = *bp;   // problem table in device memory (tensor maps written by the host)
     constexpr int A_BYTES = TC_BM * 128;
     constexpr int B_BYTES = BN * 128;
     constexpr int KELEM = KIND == 0 ? 64 : 32;      // elements per 128-byte K block
@@ -195,8 +196,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x;
-    int pi = 0;
-    while (pi + 1 < b.nprob && b.p[pi + 1].tile_start <= t) ++pi;
+    int lo = 0, hi = b.nprob - 1;   // last problem with tile_start <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.p[mid].tile_start <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int pi = lo;
     const TcProb& P = b.p[pi];
     const int local = t - P.tile_start;
     const int m0 = (local / P.tiles_n) * TC_BM;
@@ -319,13 +325,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const __grid_constant
 }
 
 // --------------------------------------------------------------------------- host plan
+// A table (TcTable, acse_internal.h) holds the problems of one grouped launch; its TcBatch lives in
+// device memory (the tensor maps are written by the host before any launch reads them).
 struct TcPlan {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
-    TcBatch batch;
-    int kind;        // 0 = bf16 (kind::f16), 1 = tf32
-    int bn;
-    int stages;
-    size_t smem;
+    TcTable tab;
 };
 
 static int stages_for(int bn) { return bn == 256 ? 4 : 6; }
@@ -334,24 +338,124 @@ static size_t smem_for(int bn, int stages) { return (size_t)stages * (TC_BM + bn
 
 template <int KIND, int BN>
 static int set_attr() {
-    const int st = stages_for(BN);
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<KIND, BN, BN == 256 ? 4 : 6>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(BN, st)));
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_for(BN, stages_for(BN))));
     return ACSE_OK;
 }
 
-static int encode_map(TcPlan* pl, CUtensorMap* m, const void* base, int rows, int inner_elems, int box_rows) {
-    const CUtensorMapDataType dt = pl->kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const int es = pl->kind == 0 ? 2 : 4;
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return ACSE_ERR_CUDA;
+        }
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    *out = g_encode;
+    return ACSE_OK;
+}
+
+static int encode_map(int kind, CUtensorMap* m, const void* base, int rows, int inner_elems, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc;
+    ACSE_TRY(get_encode(&enc));
+    const CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const int es = kind == 0 ? 2 : 4;
     cuuint64_t gdim[2] = {(cuuint64_t)inner_elems, (cuuint64_t)rows};
     cuuint64_t gstride[1] = {(cuuint64_t)inner_elems * es};
     cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = pl->encode(m, dt, 2, const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, dt, 2, const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? ACSE_OK : ACSE_ERR_CUDA;
 }
+
+int tc_table_init(TcTable* t, int kind, int bn) {
+    memset(t, 0, sizeof(*t));
+    t->kind = kind;
+    t->bn = bn;
+    t->stages = stages_for(bn);
+    t->smem = smem_for(bn, t->stages);
+    if (kind == 0) ACSE_TRY(bn == 256 ? (set_attr<0, 256>()) : (set_attr<0, 128>()));
+    else ACSE_TRY(bn == 256 ? (set_attr<1, 256>()) : (set_attr<1, 128>()));
+    t->host = (TcBatch*)calloc(1, sizeof(TcBatch));
+    if (!t->host) return ACSE_ERR_NOMEM;
+    t->host->wait_ns = TC_WAIT_NS;
+    if (cudaMalloc((void**)&t->dev, sizeof(TcBatch)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACSE_ERR_NOMEM;
+    }
+    return ACSE_OK;
+}
+
+void tc_table_free(TcTable* t) {
+    if (t->dev) cudaFree(t->dev);
+    free(t->host);
+    memset(t, 0, sizeof(*t));
+}
+
+int tc_table_upload(TcTable* t) {
+    ACSE_CUDA_TRY(cudaMemcpy(t->dev, t->host, sizeof(TcBatch), cudaMemcpyHostToDevice));
+    return ACSE_OK;
+}
+
+// Append the nine GEMMs of one contraction pass of context c to table t (tile width t->bn).
+int tc_table_append(TcTable* t, acse_ctx* c) {
+    TcBatch& b = *t->host;
+    Work& w = c->w;
+    const int r = c->r, R2 = r * r, R22 = 2 * R2;
+    const int ns = c->nsplit;
+    const int L1 = ns * w.Kp1, L2 = ns * w.Kp2;      // operand row lengths (elements)
+    const int kel = t->kind == 0 ? 64 : 32;
+    if (b.nprob + 6 > TC_MAXP) return ACSE_ERR_SHAPE;
+    auto add = [&](const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) -> int {
+        const int n = b.nprob;
+        ACSE_TRY(encode_map(t->kind, &b.tmA[n], A, M, L, TC_BM));
+        ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->bn));
+        TcProb& p = b.p[n];
+        p.C = C;
+        p.M = M;
+        p.N = N;
+        p.kblocks = L / kel;
+        p.ldc = ldc;
+        p.alpha = alpha;
+        p.tiles_n = (N + t->bn - 1) / t->bn;
+        p.tile_start = b.total_tiles;
+        p.perm_r = 0;
+        b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
+        b.nprob = n + 1;
+        return ACSE_OK;
+    };
+    // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
+    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f));
+    for (int s = 0; s < 3; ++s)
+        ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f));
+    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
+    b.err = w.tc_err;
+    return ACSE_OK;
+}
+
+int tc_table_launch(const TcTable* t, cudaStream_t st) {
+    const int tiles = t->host->total_tiles;
+    if (tiles == 0) return ACSE_OK;
+    if (t->kind == 0) {
+        if (t->bn == 256) k_gemm_tc<0, 256, 4><<<tiles, TC_THREADS, t->smem, st>>>(t->dev);
+        else k_gemm_tc<0, 128, 6><<<tiles, TC_THREADS, t->smem, st>>>(t->dev);
+    } else {
+        if (t->bn == 256) k_gemm_tc<1, 256, 4><<<tiles, TC_THREADS, t->smem, st>>>(t->dev);
+        else k_gemm_tc<1, 128, 6><<<tiles, TC_THREADS, t->smem, st>>>(t->dev);
+    }
+    ACSE_CUDA_TRY(cudaGetLastError());
+    return ACSE_OK;
+}
+
+int tc_default_bn(int r) { return r * r >= 256 ? 256 : 128; }
 
 int tc_mixed_alloc(acse_ctx* c);
 void tc_mixed_free(acse_ctx* c);
@@ -362,63 +466,16 @@ int tc_plan_create(acse_ctx* c) {
     TcPlan* pl = (TcPlan*)calloc(1, sizeof(TcPlan));
     if (!pl) return ACSE_ERR_NOMEM;
     c->tc_plan = pl;
-    pl->kind = c->opt.prec == ACSE_TF32 ? 1 : 0;
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        return ACSE_ERR_CUDA;
-    }
-    pl->encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    ACSE_TRY(get_encode(&pl->encode));
     ACSE_TRY(tc_mixed_alloc(c));
-    const int r = c->r, R2 = r * r, R22 = 2 * R2;
-    pl->bn = R2 >= 256 ? 256 : 128;
-    pl->stages = stages_for(pl->bn);
-    pl->smem = smem_for(pl->bn, pl->stages);
-    if (pl->kind == 0) {
-        ACSE_TRY(pl->bn == 256 ? (set_attr<0, 256>()) : (set_attr<0, 128>()));
-    } else {
-        ACSE_TRY(pl->bn == 256 ? (set_attr<1, 256>()) : (set_attr<1, 128>()));
-    }
-    Work& w = c->w;
-    const int ns = c->nsplit;
-    const int L1 = ns * w.Kp1, L2 = ns * w.Kp2;      // operand row lengths (elements)
-    const int kel = pl->kind == 0 ? 64 : 32;
-    TcBatch& b = pl->batch;
-    memset(&b, 0, sizeof(b));
-    int n = 0;
-    auto add = [&](const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha,
-                   int perm_r) -> int {
-        ACSE_TRY(encode_map(pl, &b.tmA[n], A, M, L, TC_BM));
-        ACSE_TRY(encode_map(pl, &b.tmB[n], B, N, L, pl->bn));
-        TcProb& p = b.p[n];
-        p.C = C;
-        p.M = M;
-        p.N = N;
-        p.kblocks = L / kel;
-        p.ldc = ldc;
-        p.alpha = alpha;
-        p.tiles_n = (N + pl->bn - 1) / pl->bn;
-        p.tile_start = b.total_tiles;
-        p.perm_r = perm_r;
-        b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
-        ++n;
-        return ACSE_OK;
-    };
-    // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
-    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f, 0));
-    for (int s = 0; s < 3; ++s)
-        ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f, 0));
-    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f, 0));
-    b.nprob = n;
-    b.err = w.tc_err;
-    b.wait_ns = TC_WAIT_NS;
-    return ACSE_OK;
+    ACSE_TRY(tc_table_init(&pl->tab, c->opt.prec == ACSE_TF32 ? 1 : 0, tc_default_bn(c->r)));
+    ACSE_TRY(tc_table_append(&pl->tab, c));
+    return tc_table_upload(&pl->tab);
 }
 
 void tc_plan_destroy(acse_ctx* c) {
     if (!c->tc_plan) return;
+    tc_table_free(&((TcPlan*)c->tc_plan)->tab);
     tc_mixed_free(c);
     free(c->tc_plan);
     c->tc_plan = nullptr;
@@ -426,30 +483,28 @@ void tc_plan_destroy(acse_ctx* c) {
 
 int tc_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
     if (!c->tc_plan) return ACSE_ERR_UNSUPPORTED;
-    ((TcPlan*)c->tc_plan)->batch.wait_ns = ns ? ns : TC_WAIT_NS;
-    ((TcPlan*)c->tc_plan)->batch.inject_stall = inject_stall;
-    return ACSE_OK;
+    TcTable& t = ((TcPlan*)c->tc_plan)->tab;
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    t.host->wait_ns = ns ? ns : TC_WAIT_NS;
+    t.host->inject_stall = inject_stall;
+    return tc_table_upload(&t);
 }
 
 int tc_gemm_launch(acse_ctx* c) {
     TcPlan* pl = (TcPlan*)c->tc_plan;
-    const TcBatch& b = pl->batch;
     ACSE_TRY(prof_begin(c));
-    if (pl->kind == 0) {
-        if (pl->bn == 256) k_gemm_tc<0, 256, 4><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
-        else k_gemm_tc<0, 128, 6><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
-    } else {
-        if (pl->bn == 256) k_gemm_tc<1, 256, 4><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
-        else k_gemm_tc<1, 128, 6><<<b.total_tiles, TC_THREADS, pl->smem, c->stream>>>(b);
-    }
-    ACSE_LAUNCHED(c);
+    ACSE_TRY(tc_table_launch(&pl->tab, c->stream));
+    c->launches++;
     ACSE_TRY(prof_end(c));
     return ACSE_OK;
 }
 
-int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D) {
+int tc_contract_pre(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D) {
     if (prep_D) ACSE_TRY(tc_mixed_prep_D(c, D));
-    ACSE_TRY(tc_mixed_prep_W(c, W));
-    ACSE_TRY(tc_gemm_launch(c));
-    return ACSE_OK;
+    return tc_mixed_prep_W(c, W);
+}
+
+int tc_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D) {
+    ACSE_TRY(tc_contract_pre(c, D, W, prep_D));
+    return tc_gemm_launch(c);
 }

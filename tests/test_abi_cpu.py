@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "acse.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(acse_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(acse_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_hot_path_calls():
