@@ -32,7 +32,8 @@ struct acse_batch {
     int n;
     int prec;
     acse_ctx** ctx;
-    cudaStream_t stream;
+    cudaStream_t stream;       // the batch's own capture stream (non-blocking)
+    cudaStream_t user;         // the caller's stream: a run starts after its pending work
     cudaStream_t* sub;
     cudaEvent_t fork;
     cudaEvent_t* join;
@@ -262,7 +263,7 @@ static int autotune(acse_batch* B) {
 // ------------------------------------------------------------------------------ ABI
 extern "C" int acse_batch_destroy(acse_batch* B) {
     if (!B) return ACSE_ERR_ARG;
-    cudaStreamSynchronize(B->stream);
+    if (B->stream) cudaStreamSynchronize(B->stream);
     if (B->graph_ready) cudaGraphExecDestroy(B->graph);
     for (int t = 0; t < B->ntab; ++t) tc_table_free(&B->tab[t]);
     for (int i = 0; i < B->n; ++i) {
@@ -275,6 +276,7 @@ extern "C" int acse_batch_destroy(acse_batch* B) {
         }
     }
     if (B->fork) cudaEventDestroy(B->fork);
+    if (B->stream) cudaStreamDestroy(B->stream);
     free(B->ctx);
     free(B->sub);
     free(B->join);
@@ -292,13 +294,15 @@ extern "C" int acse_batch_create(acse_batch** out, int n, const acse_opts* opts,
     if (!B) return ACSE_ERR_NOMEM;
     B->n = n;
     B->prec = opts[0].prec;
-    B->stream = (cudaStream_t)stream;
+    B->user = (cudaStream_t)stream;
     B->stop_rule = 1;
     B->ctx = (acse_ctx**)calloc(n, sizeof(acse_ctx*));
     B->sub = (cudaStream_t*)calloc(n, sizeof(cudaStream_t));
     B->join = (cudaEvent_t*)calloc(n, sizeof(cudaEvent_t));
     int s = (B->ctx && B->sub && B->join) ? ACSE_OK : ACSE_ERR_NOMEM;
-    if (s == ACSE_OK && cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK && (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess))
+        s = ACSE_ERR_CUDA;
     for (int i = 0; i < n && s == ACSE_OK; ++i) {
         if (cudaStreamCreateWithFlags(&B->sub[i], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) != cudaSuccess) {
@@ -363,6 +367,9 @@ extern "C" int acse_batch_get_D(acse_batch* B, int i, double* Daa, double* Dab, 
 extern "C" int acse_batch_run(acse_batch* B, int nsteps, int stop_rule, double* E_out, double* norm2_out,
                               int* steps_out, int* reason_out) {
     if (!B || nsteps < 0) return ACSE_ERR_ARG;
+    // order after the caller's pending work
+    ACSE_CUDA_TRY(cudaEventRecord(B->fork, B->user));
+    ACSE_CUDA_TRY(cudaStreamWaitEvent(B->stream, B->fork, 0));
     if (B->ntab == 0 && B->prec != ACSE_FP64) ACSE_TRY(autotune(B));
     if (B->stop_rule != stop_rule && B->graph_ready) {
         cudaGraphExecDestroy(B->graph);
