@@ -343,26 +343,42 @@ int launch_energy(acse_ctx* c, const double* const D[3], double* E_dst) {
 }
 
 // ------------------------------------------------------------------------------ axpy
-// out = D + (mul * eps) U, eps read from device memory (the line search writes it there).
-__global__ void k_axpy(size_t n, const double* __restrict__ D0, const double* __restrict__ D1,
+// out = D + (mul * eps) U, eps read from device memory (the line search writes it there); grid y
+// selects the block.  double2 accesses when every pointer is 16-byte aligned, with a scalar tail.
+__global__ void k_axpy(int n, int vec, const double* __restrict__ D0, const double* __restrict__ D1,
                        const double* __restrict__ D2, const double* __restrict__ U0, const double* __restrict__ U1,
                        const double* __restrict__ U2, const double* __restrict__ eps, double mul, double* O0,
                        double* O1, double* O2) {
     const double e = mul * (*eps);
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 3 * n; t += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(t / n);
-        const size_t i = t % n;
-        if (b == 0) O0[i] = D0[i] + e * U0[i];
-        else if (b == 1) O1[i] = D1[i] + e * U1[i];
-        else O2[i] = D2[i] + e * U2[i];
+    const int b = blockIdx.y;
+    const double* D = b == 0 ? D0 : b == 1 ? D1 : D2;
+    const double* U = b == 0 ? U0 : b == 1 ? U1 : U2;
+    double* O = b == 0 ? O0 : b == 1 ? O1 : O2;
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        const int n2 = n >> 1;
+        const double2* D2v = reinterpret_cast<const double2*>(D);
+        const double2* U2v = reinterpret_cast<const double2*>(U);
+        double2* O2v = reinterpret_cast<double2*>(O);
+        for (int i = t0; i < n2; i += stride) {
+            const double2 d = D2v[i], u = U2v[i];
+            O2v[i] = make_double2(d.x + e * u.x, d.y + e * u.y);
+        }
+        if ((n & 1) && t0 == 0) O[n - 1] = D[n - 1] + e * U[n - 1];
+    } else {
+        for (int i = t0; i < n; i += stride) O[i] = D[i] + e * U[i];
     }
 }
 
 int launch_axpy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev, double eps_mul,
                 double* const out[3]) {
-    const size_t n = (size_t)c->r * c->r * c->r * c->r;
-    k_axpy<<<grid_for(3 * n), TPB, 0, c->stream>>>(n, D[0], D[1], D[2], U[0], U[1], U[2], eps_dev, eps_mul, out[0],
-                                                   out[1], out[2]);
+    const int n = c->r * c->r * c->r * c->r;
+    uintptr_t bits = 0;
+    for (int b = 0; b < 3; ++b) bits |= (uintptr_t)D[b] | (uintptr_t)U[b] | (uintptr_t)out[b];
+    const int vec = (bits & 15) == 0;
+    k_axpy<<<dim3(grid_for((size_t)n) / 2 + 1, 3), TPB, 0, c->stream>>>(n, vec, D[0], D[1], D[2], U[0], U[1], U[2],
+                                                                      eps_dev, eps_mul, out[0], out[1], out[2]);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }

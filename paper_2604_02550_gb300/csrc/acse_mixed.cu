@@ -107,38 +107,41 @@ static MxPtrs mx_ptrs(acse_ctx* c) {
 template <int PREC>
 __global__ void k_mx_prepD(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
                            const double* __restrict__ Dab, const double* __restrict__ Dbb, const __grid_constant__ MxPtrs p) {
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    // grid: x over groups of four columns, y over (sector, row of [M; D])
+    const int R2 = r * r;
+    const int c4 = (R2 + 3) >> 2;
+    const int q4 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y / (2 * R2);
+    const int row = blockIdx.y - s * 2 * R2;
+    if (blockIdx.x == 0 && blockIdx.y == 0)
+        for (int e = threadIdx.x; e < 2 * R2; e += blockDim.x) p.gam32[e] = (float)gam[e];
+    if (q4 >= c4) return;
     const size_t ld = (size_t)p.ns * p.Kp1;
-    const int c4 = (int)((R2 + 3) / 4);
-    const bool vec = (r & 1) == 0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 6 * R2 * c4; e += (size_t)gridDim.x * blockDim.x) {
-        if (e < 2 * R2) p.gam32[e] = (float)gam[e];
-        const int s = (int)(e / (2 * R2 * c4));
-        const size_t rem = e % (2 * R2 * c4);
-        const size_t row = rem / c4;
-        const int k0 = (int)(rem % c4) * 4;
-        const double* D = s == 0 ? Daa : (s == 1 ? Dab : Dbb);
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        const int nk = (int)(R2 - k0) < 4 ? (int)(R2 - k0) : 4;
-        if (row < R2) {
-            const int i = (int)(row / r), j = (int)(row % r);
-            const double* ga = gam + (s == 2 ? R2 : 0);
-            const double* gb = gam + (s == 0 ? 0 : R2);
-            for (int u = 0; u < nk; ++u) {
-                const int k = k0 + u, kk = k / r, l = k % r;
-                const float d = (float)D[row * R2 + k];
-                x[u] = s == 1 ? 3.0f * d - (float)ga[i * r + kk] * (float)gb[j * r + l]
-                              : 3.0f * d - ((float)ga[i * r + kk] * (float)ga[j * r + l] -
-                                            (float)ga[j * r + kk] * (float)ga[i * r + l]);
-                p.M32[s][row * R2 + k] = x[u];
-            }
-        } else {
-            for (int u = 0; u < nk; ++u) x[u] = (float)D[(row - R2) * R2 + k0 + u];
+    const int k0 = q4 * 4;
+    const double* D = s == 0 ? Daa : (s == 1 ? Dab : Dbb);
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
+    if (row < R2) {
+        const int i = row / r, j = row - i * r;
+        const double* ga = gam + (s == 2 ? R2 : 0);
+        const double* gb = gam + (s == 0 ? 0 : R2);
+        const double* Drow = D + (size_t)row * R2;
+        float* Mrow = p.M32[s] + (size_t)row * R2;
+        for (int u = 0; u < nk; ++u) {
+            const int k = k0 + u, kk = k / r, l = k - kk * r;
+            const float d = (float)Drow[k];
+            x[u] = s == 1 ? 3.0f * d - (float)ga[i * r + kk] * (float)gb[j * r + l]
+                          : 3.0f * d - ((float)ga[i * r + kk] * (float)ga[j * r + l] -
+                                        (float)ga[j * r + kk] * (float)ga[i * r + l]);
+            Mrow[k] = x[u];
         }
-        if (vec && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
-        else
-            for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
+    } else {
+        const double* Drow = D + (size_t)(row - R2) * R2;
+        for (int u = 0; u < nk; ++u) x[u] = (float)Drow[k0 + u];
     }
+    if ((r & 1) == 0 && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
+    else
+        for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
 }
 
 // Particle-hole layouts of M (the B operands of the ph GEMMs), copied as r x r blocks per (t, i, p):
@@ -191,11 +194,11 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
     MxPtrs p = mx_ptrs(c);
     const int R2 = r * r;
     if (c->opt.prec == ACSE_BF16X3) {
-        k_mx_prepD<ACSE_BF16X3><<<mx_grid(6 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_BF16X3><<<dim3((R2 / 4 + 128) / 128, 6 * R2), 128, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
         k_mx_pack_Mph<ACSE_BF16X3><<<6 * R2, 256, 0, c->stream>>>(r, p);
     } else {
-        k_mx_prepD<ACSE_TF32><<<mx_grid(6 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_TF32><<<dim3((R2 / 4 + 128) / 128, 6 * R2), 128, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
         k_mx_pack_Mph<ACSE_TF32><<<6 * R2, 256, 0, c->stream>>>(r, p);
     }
@@ -208,24 +211,22 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
 template <int PREC>
 __global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
                             const double* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
-    const size_t R2 = (size_t)r * r, n4 = R2 * R2;
+    // grid: x over groups of four columns, y over (sector, row)
+    const int R2 = r * r;
+    const int c4 = (R2 + 3) >> 2;
+    const int q4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q4 >= c4) return;
+    const int s = blockIdx.y / R2;
+    const int row = blockIdx.y - s * R2;
     const size_t ld = (size_t)p.ns * p.Kp1;
-    const int c4 = (int)((R2 + 3) / 4);
-    const bool vec = (r & 1) == 0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 3 * R2 * c4; e += (size_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e / (R2 * c4));
-        const size_t rem = e % (R2 * c4);
-        const size_t row = rem / c4;
-        const int k0 = (int)(rem % c4) * 4;
-        const double* W = (s == 0 ? Waa : (s == 1 ? Wab : Wbb)) + row * R2;
-        const int nk = (int)(R2 - k0) < 4 ? (int)(R2 - k0) : 4;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int u = 0; u < nk; ++u) x[u] = (float)W[k0 + u];
-        if (vec && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
-        else
-            for (int u = 0; u < nk; ++u) put<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0 + u, x[u]);
-    }
-    (void)n4;
+    const double* W = (s == 0 ? Waa : (s == 1 ? Wab : Wbb)) + (size_t)row * R2;
+    const int k0 = q4 * 4;
+    const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int u = 0; u < nk; ++u) x[u] = (float)W[k0 + u];
+    if ((r & 1) == 0 && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
+    else
+        for (int u = 0; u < nk; ++u) put<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0 + u, x[u]);
 }
 
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
@@ -233,9 +234,9 @@ int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
     if (c->opt.prec == ACSE_BF16X3)
-        k_mx_pack_W<ACSE_BF16X3><<<mx_grid(3 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_BF16X3><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     else
-        k_mx_pack_W<ACSE_TF32><<<mx_grid(3 * n4 / 4 + 1), MX_TPB, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_TF32><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     ACSE_LAUNCHED(c);
     return launch_Z_tiled(c, W);   // Z packs and w (the diagonal of Z)
 }

@@ -25,16 +25,25 @@ __device__ __forceinline__ float tl_tf32(float x) {
 
 __host__ __device__ __forceinline__ int pad4(int r) { return (r + 3) & ~3; }
 
+// 4 consecutive elements of a shared array (16-byte aligned: offsets are multiples of 4 elements).
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    const double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
 // acc[a][b] += sum_q A[q][i0 + a] * B[q][j0 + b]  (A, B: [rp][rp] shared arrays, rp % 4 == 0)
 template <typename T>
 __device__ __forceinline__ void mma4x4(T (&acc)[4][4], const T* A, const T* B, int rp, int n, int i0, int j0) {
+#pragma unroll 4
     for (int q = 0; q < n; ++q) {
         T a[4], b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            a[u] = A[q * rp + i0 + u];
-            b[u] = B[q * rp + j0 + u];
-        }
+        ld4(A + q * rp + i0, a);
+        ld4(B + q * rp + j0, b);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -72,11 +81,29 @@ __device__ __forceinline__ void z_store(const ZOut& o, int which, size_t row, in
     }
 }
 
-// Block (t, k, p), t = 0..5:
+#define Z_PCH 8          // p values per block
+#define Z_PREF 16        // slice elements prefetched per thread (r^2 <= 4096 = 16 x 256)
+
+// Block (t, k, p0..p0+Z_PCH-1), t = 0..5:
 //   t=0 Zd(a,a): W_kp[q][s] = Waa[k][p][q][s], ga      t=1 Zd(a,b): Wab[k][p][q][s], ga
 //   t=2 Zd(b,a): W_kp[q][s] = Wab[p][k][s][q], gb      t=3 Zd(b,b): Wbb[k][p][q][s], gb
 //   t=4 Zf1:     W_kp[q][s] = Wab[k][p][s][q], gb      t=5 Zf2:     Wab[p][k][q][s], ga
-// (the spin-flip sectors drop a sign -1 that their M operand drops too).
+// (the spin-flip sectors drop a sign -1 that their M operand drops too).  The 1D is staged once per
+// block; the W slice of the next p is loaded into registers while the current one is multiplied.
+template <typename T>
+__device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, const double* Waa, const double* Wab,
+                                                const double* Wbb, bool& tr) {
+    const size_t R2 = (size_t)r * r, r3 = R2 * r;
+    switch (t) {
+        case 0: tr = false; return Waa + k * r3 + p * R2;
+        case 1: tr = false; return Wab + k * r3 + p * R2;
+        case 2: tr = true; return Wab + p * r3 + k * R2;
+        case 3: tr = false; return Wbb + k * r3 + p * R2;
+        case 4: tr = true; return Wab + k * r3 + p * R2;
+        default: tr = false; return Wab + p * r3 + k * R2;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TL_TPB) k_Z_tiled(int r, const double* __restrict__ Waa,
                                                     const double* __restrict__ Wab,
@@ -87,58 +114,76 @@ __global__ void __launch_bounds__(TL_TPB) k_Z_tiled(int r, const double* __restr
     T* Ws = (T*)tl_smem;          // [q][s]
     T* gT = Ws + rp * rp;         // [q][j] = 1D[j][q]
     const int R2 = r * r;
-    const int t = blockIdx.x / R2;
-    const int kp = blockIdx.x % R2;
-    const int k = kp / r, p = kp % r;
-    const size_t r3 = (size_t)R2 * r;
+    const int nchunk = (r + Z_PCH - 1) / Z_PCH;
+    const int t = blockIdx.x / (r * nchunk);
+    const int k = (blockIdx.x / nchunk) % r;
+    const int p0 = (blockIdx.x % nchunk) * Z_PCH;
+    const int p1 = min(p0 + Z_PCH, r);
     const double* g = gam + ((t == 2 || t == 3 || t == 4) ? R2 : 0);
-    const double* src;
-    bool transposed;
-    switch (t) {
-        case 0: src = Waa + k * r3 + (size_t)p * R2; transposed = false; break;
-        case 1: src = Wab + k * r3 + (size_t)p * R2; transposed = false; break;
-        case 2: src = Wab + p * r3 + (size_t)k * R2; transposed = true; break;
-        case 3: src = Wbb + k * r3 + (size_t)p * R2; transposed = false; break;
-        case 4: src = Wab + k * r3 + (size_t)p * R2; transposed = true; break;
-        default: src = Wab + p * r3 + (size_t)k * R2; transposed = false; break;
-    }
     for (int e = threadIdx.x; e < rp * rp; e += blockDim.x) {
         Ws[e] = (T)0;
         gT[e] = (T)0;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-        const int u = e / r, v = e % r;
-        const T x = (T)src[e];
-        if (transposed) Ws[v * rp + u] = x;   // src[s][q] -> Ws[q][s]
-        else Ws[u * rp + v] = x;
-        gT[v * rp + u] = (T)g[e];              // g[j][q] -> gT[q][j]
+        const int u = e / r, v = e - u * r;
+        gT[v * rp + u] = (T)g[e];                // g[j][q] -> gT[q][j]
     }
-    __syncthreads();
     int which, sK, sP, dslot;
     if (t < 4) { which = -1; sK = t >> 1; sP = t & 1; }
     else { which = t - 4; sK = 0; sP = 0; }
     dslot = t == 0 ? 0 : t == 3 ? 1 : t == 4 ? 2 : t == 5 ? 3 : -1;
     const int nt = rp / 4;
-    for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
-        const int j0 = (tile / nt) * 4, s0 = (tile % nt) * 4;
-        T acc[4][4];
+    bool tr;
+    T pre[Z_PREF];
+    {
+        const double* src = z_slice<T>(t, k, p0, r, Waa, Wab, Wbb, tr);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < Z_PREF; ++u) {
+            const int e = threadIdx.x + u * TL_TPB;
+            pre[u] = e < R2 ? (T)src[e] : (T)0;
+        }
+    }
+    for (int p = p0; p < p1; ++p) {
+        __syncthreads();   // previous slice consumed
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0;
-        mma4x4<T>(acc, gT, Ws, rp, r, j0, s0);
+        for (int u = 0; u < Z_PREF; ++u) {
+            const int e = threadIdx.x + u * TL_TPB;
+            if (e < R2) {
+                const int a = e / r, b = e - a * r;
+                if (tr) Ws[b * rp + a] = pre[u];   // src[s][q] -> Ws[q][s]
+                else Ws[a * rp + b] = pre[u];
+            }
+        }
+        __syncthreads();
+        if (p + 1 < p1) {
+            const double* src = z_slice<T>(t, k, p + 1, r, Waa, Wab, Wbb, tr);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int j = j0 + u;
-            if (j >= r) continue;
-            const size_t row = (size_t)sK * R2 + (size_t)k * r + j;
+            for (int u = 0; u < Z_PREF; ++u) {
+                const int e = threadIdx.x + u * TL_TPB;
+                pre[u] = e < R2 ? (T)src[e] : (T)0;
+            }
+        }
+        for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
+            const int j0 = (tile / nt) * 4, s0 = (tile % nt) * 4;
+            T acc[4][4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int s = s0 + v;
-                if (s >= r) continue;
-                z_store<T>(o, which, row, sP * R2 + p * r + s, acc[u][v]);
-                if (dslot >= 0 && j == p) ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s] = acc[u][v];
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+            mma4x4<T>(acc, gT, Ws, rp, r, j0, s0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                if (j >= r) continue;
+                const size_t row = (size_t)sK * R2 + (size_t)k * r + j;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int s = s0 + v;
+                    if (s >= r) continue;
+                    z_store<T>(o, which, row, sP * R2 + p * r + s, acc[u][v]);
+                    if (dslot >= 0 && j == p) ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s] = acc[u][v];
+                }
             }
         }
     }
@@ -294,14 +339,16 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
     if (c->opt.prec == ACSE_FP64) {
         o.Zd = w.Zd; o.Zf[0] = w.Zf1; o.Zf[1] = w.Zf2;
         o.mode = 0; o.ldd = 2 * R2; o.ldf = R2; o.Kp1 = o.Kp2 = 0; o.diag = w.zdiag;
-        k_Z_tiled<double><<<6 * R2, TL_TPB, 2 * rp * rp * sizeof(double), c->stream>>>(r, W[0], W[1], W[2], w.gam, o);
+        k_Z_tiled<double><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 2 * rp * rp * sizeof(double), c->stream>>>(
+            r, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
         k_w_from_diag<double><<<(2 * R2 + 127) / 128, 128, 0, c->stream>>>(r, w.zdiag, w.w);
     } else {
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
         o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : 2;
         o.ldd = c->nsplit * w.Kp2; o.ldf = c->nsplit * w.Kp1; o.Kp1 = w.Kp1; o.Kp2 = w.Kp2; o.diag = w.zdiag32;
-        k_Z_tiled<float><<<6 * R2, TL_TPB, 2 * rp * rp * sizeof(float), c->stream>>>(r, W[0], W[1], W[2], w.gam, o);
+        k_Z_tiled<float><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 2 * rp * rp * sizeof(float), c->stream>>>(
+            r, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
         k_w_from_diag<float><<<(2 * R2 + 127) / 128, 128, 0, c->stream>>>(r, w.zdiag32, w.w32);
     }
