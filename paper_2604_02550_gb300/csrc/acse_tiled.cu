@@ -84,6 +84,27 @@ __device__ __forceinline__ void z_store(const ZOut& o, int which, size_t row, in
 #define Z_PCH 8          // p values per block
 #define Z_PREF 16        // slice elements prefetched per thread (r^2 <= 4096 = 16 x 256)
 
+// Two consecutive columns col, col + 1 of one output row (col even, row length even).
+template <typename T>
+__device__ __forceinline__ void z_store2(const ZOut& o, int which, size_t row, int col, T v0, T v1) {
+    void* base = which < 0 ? o.Zd : o.Zf[which];
+    const size_t ld = which < 0 ? (size_t)o.ldd : (size_t)o.ldf;
+    const int Kp = which < 0 ? o.Kp2 : o.Kp1;
+    if (o.mode == 0) {
+        *reinterpret_cast<double2*>((double*)base + row * ld + col) = make_double2((double)v0, (double)v1);
+    } else if (o.mode == 1) {
+        __nv_bfloat16* p = (__nv_bfloat16*)base + row * ld + col;
+        const float x0 = (float)v0, x1 = (float)v1;
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(x0, x1);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(x0 - __low2float(hi), x1 - __high2float(hi));
+        *reinterpret_cast<__nv_bfloat162*>(p) = hi;
+        *reinterpret_cast<__nv_bfloat162*>(p + Kp) = hi;
+        *reinterpret_cast<__nv_bfloat162*>(p + 2 * Kp) = lo;
+    } else {
+        *reinterpret_cast<float2*>((float*)base + row * ld + col) = make_float2(tl_tf32((float)v0), tl_tf32((float)v1));
+    }
+}
+
 // Block (t, k, p0..p0+Z_PCH-1), t = 0..5:
 //   t=0 Zd(a,a): W_kp[q][s] = Waa[k][p][q][s], ga      t=1 Zd(a,b): Wab[k][p][q][s], ga
 //   t=2 Zd(b,a): W_kp[q][s] = Wab[p][k][s][q], gb      t=3 Zd(b,b): Wbb[k][p][q][s], gb
@@ -144,8 +165,9 @@ __global__ void __launch_bounds__(TL_TPB) k_Z_tiled(int r, const double* __restr
             pre[u] = e < R2 ? (T)src[e] : (T)0;
         }
     }
+    T* Os = gT + rp * rp;         // [j][s] output block of the current p
     for (int p = p0; p < p1; ++p) {
-        __syncthreads();   // previous slice consumed
+        __syncthreads();   // previous slice and output block consumed
 #pragma unroll
         for (int u = 0; u < Z_PREF; ++u) {
             const int e = threadIdx.x + u * TL_TPB;
@@ -173,19 +195,29 @@ __global__ void __launch_bounds__(TL_TPB) k_Z_tiled(int r, const double* __restr
                 for (int v = 0; v < 4; ++v) acc[u][v] = 0;
             mma4x4<T>(acc, gT, Ws, rp, r, j0, s0);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = j0 + u;
-                if (j >= r) continue;
-                const size_t row = (size_t)sK * R2 + (size_t)k * r + j;
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int s = s0 + v;
-                    if (s >= r) continue;
-                    z_store<T>(o, which, row, sP * R2 + p * r + s, acc[u][v]);
-                    if (dslot >= 0 && j == p) ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s] = acc[u][v];
-                }
+                for (int v = 0; v < 4; ++v) Os[(j0 + u) * rp + s0 + v] = acc[u][v];
+        }
+        __syncthreads();
+        // rows (sK, k, j), columns (sP, p, s): r contiguous values per row, stored in pairs
+        const int colbase = sP * R2 + p * r;
+        if ((r & 1) == 0) {
+            const int hr = r >> 1;
+            for (int e = threadIdx.x; e < r * hr; e += blockDim.x) {
+                const int j = e / hr, s2 = (e - j * hr) * 2;
+                z_store2<T>(o, which, (size_t)sK * R2 + (size_t)k * r + j, colbase + s2, Os[j * rp + s2],
+                            Os[j * rp + s2 + 1]);
+            }
+        } else {
+            for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+                const int j = e / r, s2 = e - j * r;
+                z_store<T>(o, which, (size_t)sK * R2 + (size_t)k * r + j, colbase + s2, Os[j * rp + s2]);
             }
         }
+        if (dslot >= 0)
+            for (int s2 = threadIdx.x; s2 < r; s2 += blockDim.x)
+                ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s2] = Os[p * rp + s2];
     }
 }
 
@@ -226,7 +258,9 @@ struct BTiledArgs {
 // B rows are kept in shared memory (Bs[t][k][l]) and combined into
 //   H_aa = 4 Y_aa - 12 (B0 - B0_{k<->l}),  H_bb = 4 Y_bb - 12 (B1 - B1_{k<->l}),
 //   H_ab = 4 Y_ab - 12 (B2 - B3_{k<->l}).
-template <typename T>
+// STAGE: the particle-hole rows (x5, x8) and the Q / 1D vectors of (x4, x7) are staged in shared
+// memory with coalesced loads before the products (off when shared memory would not fit).
+template <typename T, bool STAGE>
 __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTiledArgs<T> a) {
     extern __shared__ __align__(16) unsigned char tl_smem[];
     const int r = a.r;
@@ -237,6 +271,9 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
     T* WT = G1 + rp * rp;     // [p][k]
     T* MT = WT + rp * rp;     // [p][l]
     T* Bs = MT + rp * rp;     // [2][r][r]: current pair of B types
+    T* X5s = Bs + 2 * R2;     // [k][l] (STAGE)
+    T* X8s = X5s + R2;
+    T* vq = X8s + R2;         // 4 vectors of r: Q column, 1D row, Q column, 1D row (x4, x7)
     const int i = blockIdx.x / r, j = blockIdx.x % r;
     const size_t ij = (size_t)blockIdx.x;
     const T* ga = a.gam;
@@ -244,8 +281,8 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
     const T* Qa = a.Q;
     const T* Qb = a.Q + R2;
     const int nt = rp / 4;
+    const size_t R22 = 2 * (size_t)R2;
     for (int e = threadIdx.x; e < 4 * rp * rp; e += blockDim.x) XT[e] = (T)0;   // zero padding once
-    // three rounds: (t0 = 0 -> H_aa), (t0 = 1 -> H_bb), (types 2 and 3 -> H_ab)
     for (int round = 0; round < 3; ++round) {
         const int ntypes = round < 2 ? 1 : 2;
         for (int tt = 0; tt < ntypes; ++tt) {
@@ -260,20 +297,8 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             else if (t == 1) { Xrow = a.X[2] + ij * R2; g1 = gb; wv = a.w + R2; Mrow = a.M[2] + ij * R2; }
             else if (t == 2) { Xrow = a.X[1] + ij * R2; g1 = gb; wv = a.w; Mrow = a.M[1] + ij * R2; mT = false; sgn2 = -1; }
             else { Xrow = a.X[1] + ij * R2; g1 = ga; wv = a.w + R2; Mrow = a.M[1] + ij * R2; xT = true; sgn1 = -1; }
-            __syncthreads();
-            for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-                const int u = e / r, v = e % r;
-                // XT[p][k] = X[(k,p)] (types 0-2) or X[(p,k)] (type 3)
-                XT[xT ? u * rp + v : v * rp + u] = Xrow[e];
-                G1[u * rp + v] = g1[e];
-                WT[v * rp + u] = wv[e];                      // w[k][p] -> WT[p][k]
-                MT[mT ? v * rp + u : u * rp + v] = Mrow[e];  // M[(l,p)] -> MT[p][l]  or  M[(p,l)]
-            }
-            __syncthreads();
-            T* Bt = Bs + (size_t)tt * R2;
             // particle-hole sources: x5 at row (k, j), column (i, l); x8 at row (k, i), column (j, l):
             //   T0: X5d(a,a) both   T1: X5d(b,b) both   T2: X5f1, X5d(a,b)   T3: X5d(b,a), X5f2
-            const size_t R22 = 2 * (size_t)R2;
             const T* X5b;
             const T* X8b;
             size_t ld5, ld8;
@@ -281,6 +306,32 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
             else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
             else { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
+            // x4 = Q4[k] g4[l], x7 = Q7[k] g7[l] (zero vectors where a type has no such term)
+            const T* Q4 = t == 0 ? Qa : t == 1 ? Qb : t == 2 ? Qa : nullptr;
+            const T* g4 = t == 0 ? ga : t == 1 ? gb : t == 2 ? gb : nullptr;
+            const T* Q7 = t == 0 ? Qa : t == 1 ? Qb : t == 3 ? Qb : nullptr;
+            const T* g7 = t == 0 ? ga : t == 1 ? gb : t == 3 ? ga : nullptr;
+            __syncthreads();
+            for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+                const int u = e / r, v = e - u * r;
+                XT[xT ? u * rp + v : v * rp + u] = Xrow[e];   // T3 uses Xab[ij][p][k]
+                G1[u * rp + v] = g1[e];
+                WT[v * rp + u] = wv[e];                      // w[k][p] -> WT[p][k]
+                MT[mT ? v * rp + u : u * rp + v] = Mrow[e];  // M[(l,p)] -> MT[p][l]  or  M[(p,l)]
+                if (STAGE) {
+                    X5s[e] = X5b[((size_t)u * r + j) * ld5 + (size_t)i * r + v];   // (k, l) = (u, v)
+                    X8s[e] = X8b[((size_t)u * r + i) * ld8 + (size_t)j * r + v];
+                }
+            }
+            if (STAGE)
+                for (int e = threadIdx.x; e < r; e += blockDim.x) {
+                    vq[e] = Q4 ? Q4[e * r + i] : (T)0;            // Q[k][i]
+                    vq[r + e] = g4 ? g4[j * r + e] : (T)0;        // g[j][l]
+                    vq[2 * r + e] = Q7 ? Q7[e * r + j] : (T)0;    // Q[k][j]
+                    vq[3 * r + e] = g7 ? g7[i * r + e] : (T)0;    // g[i][l]
+                }
+            __syncthreads();
+            T* Bt = Bs + (size_t)tt * R2;
             for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
                 const int k0 = (tile / nt) * 4, l0 = (tile % nt) * 4;
                 T x1[4][4], x2[4][4];
@@ -298,18 +349,17 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                     for (int v = 0; v < 4; ++v) {
                         const int l = l0 + v;
                         if (l >= r) continue;
-                        T x4 = 0, x7 = 0;
-                        const T x5 = X5b[((size_t)k * r + j) * ld5 + (size_t)i * r + l];
-                        const T x8 = X8b[((size_t)k * r + i) * ld8 + (size_t)j * r + l];
-                        if (t < 2) {
-                            const T* gg = t == 0 ? ga : gb;
-                            const T* QQ = t == 0 ? Qa : Qb;
-                            x4 = QQ[k * r + i] * gg[j * r + l];
-                            x7 = QQ[k * r + j] * gg[i * r + l];
-                        } else if (t == 2) {
-                            x4 = Qa[k * r + i] * gb[j * r + l];
+                        T x4, x5, x7, x8;
+                        if (STAGE) {
+                            x4 = vq[k] * vq[r + l];
+                            x7 = vq[2 * r + k] * vq[3 * r + l];
+                            x5 = X5s[k * r + l];
+                            x8 = X8s[k * r + l];
                         } else {
-                            x7 = Qb[k * r + j] * ga[i * r + l];
+                            x4 = Q4 ? Q4[k * r + i] * g4[j * r + l] : (T)0;
+                            x7 = Q7 ? Q7[k * r + j] * g7[i * r + l] : (T)0;
+                            x5 = X5b[((size_t)k * r + j) * ld5 + (size_t)i * r + l];
+                            x8 = X8b[((size_t)k * r + i) * ld8 + (size_t)j * r + l];
                         }
                         Bt[k * r + l] = (sgn1 * x1[u][v] - (T)2 * sgn2 * x2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
                                         (T)(1.0 / 9.0);
@@ -324,7 +374,7 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
         const T* Yrow = a.Y[b] + ij * R2;
         T* Hrow = a.H[b] + ij * R2;
         for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-            const int k = e / r, l = e % r;
+            const int k = e / r, l = e - k * r;
             Hrow[e] = (T)4 * Yrow[e] - (T)12 * (P[e] - Px[l * r + k]);
         }
     }
@@ -339,7 +389,7 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
     if (c->opt.prec == ACSE_FP64) {
         o.Zd = w.Zd; o.Zf[0] = w.Zf1; o.Zf[1] = w.Zf2;
         o.mode = 0; o.ldd = 2 * R2; o.ldf = R2; o.Kp1 = o.Kp2 = 0; o.diag = w.zdiag;
-        k_Z_tiled<double><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 2 * rp * rp * sizeof(double), c->stream>>>(
+        k_Z_tiled<double><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 3 * rp * rp * sizeof(double), c->stream>>>(
             r, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
         k_w_from_diag<double><<<(2 * R2 + 127) / 128, 128, 0, c->stream>>>(r, w.zdiag, w.w);
@@ -347,7 +397,7 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
         o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : 2;
         o.ldd = c->nsplit * w.Kp2; o.ldf = c->nsplit * w.Kp1; o.Kp1 = w.Kp1; o.Kp2 = w.Kp2; o.diag = w.zdiag32;
-        k_Z_tiled<float><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 2 * rp * rp * sizeof(float), c->stream>>>(
+        k_Z_tiled<float><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 3 * rp * rp * sizeof(float), c->stream>>>(
             r, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
         k_w_from_diag<float><<<(2 * R2 + 127) / 128, 128, 0, c->stream>>>(r, w.zdiag32, w.w32);
@@ -356,7 +406,10 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
     return ACSE_OK;
 }
 
-static size_t b_smem(int r, size_t es) { return (4 * (size_t)pad4(r) * pad4(r) + 2 * (size_t)r * r) * es; }
+static size_t b_smem(int r, size_t es, bool stage) {
+    return (4 * (size_t)pad4(r) * pad4(r) + (stage ? 4 : 2) * (size_t)r * r + (stage ? 4 * (size_t)r : 0)) * es;
+}
+static const size_t k_smem_cap = 227 * 1024;
 
 int launch_B_tiled(acse_ctx* c) {
     const int r = c->r;
@@ -368,7 +421,10 @@ int launch_B_tiled(acse_ctx* c) {
         for (int s = 0; s < 3; ++s) { a.X[s] = w.X[s]; a.Y[s] = w.Y[s]; a.M[s] = w.M[s]; a.H[s] = w.H[s]; }
         a.X5d = w.X5d; a.X5f1 = w.X5f1; a.X5f2 = w.X5f2;
         a.gam = w.gam; a.w = w.w; a.Q = w.Q;
-        k_B_tiled<double><<<R2, TL_TPB, b_smem(r, sizeof(double)), c->stream>>>(a);
+        if (b_smem(r, sizeof(double), true) <= k_smem_cap)
+            k_B_tiled<double, true><<<R2, TL_TPB, b_smem(r, sizeof(double), true), c->stream>>>(a);
+        else
+            k_B_tiled<double, false><<<R2, TL_TPB, b_smem(r, sizeof(double), false), c->stream>>>(a);
     } else {
         BTiledArgs<float> a;
         a.r = r;
@@ -380,18 +436,22 @@ int launch_B_tiled(acse_ctx* c) {
         }
         a.X5d = w.tc_X5d; a.X5f1 = w.tc_X5f[0]; a.X5f2 = w.tc_X5f[1];
         a.gam = w.gam32; a.w = w.w32; a.Q = w.Q32;
-        k_B_tiled<float><<<R2, TL_TPB, b_smem(r, sizeof(float)), c->stream>>>(a);
+        k_B_tiled<float, true><<<R2, TL_TPB, b_smem(r, sizeof(float), true), c->stream>>>(a);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
 
 int tiled_set_attrs() {
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)b_smem(ACSE_MAX_R, sizeof(double))));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)b_smem(ACSE_MAX_R, sizeof(float))));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k_smem_cap));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)b_smem(ACSE_MAX_R, sizeof(float), true)));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       2 * ACSE_MAX_R * ACSE_MAX_R * (int)sizeof(double)));
+                                       3 * ACSE_MAX_R * ACSE_MAX_R * (int)sizeof(double)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       3 * ACSE_MAX_R * ACSE_MAX_R * (int)sizeof(float)));
     return ACSE_OK;
 }
