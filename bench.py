@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32"])
+    ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32", "tf32x3"])
     ap.add_argument("--r", type=int, default=48, help="orbitals (48: the CAS(8e,8o) workload)")
     ap.add_argument("--eps", type=float, default=None,
                     help="Euler step; default 1e-4 for r >= 32 (1e-3 diverges there), else the paper's 1e-3")
@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--peaks", action="store_true", help="measure FP64/TF32/BF16 matmul peaks and exit")
     ap.add_argument("--batch", action="store_true",
                     help="time the 16-instance batch (r = 12..40, CAS(4e,4o) ground + excited) instead")
+    ap.add_argument("--time-to-e", action="store_true",
+                    help="time-to-E on the r = 48 workload: BF16x3 vs FP64, Methods stopping rule, step cap")
+    ap.add_argument("--cap", type=int, default=100, help="step cap of --time-to-e")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="adjoint cost relative to the forward steps (FP64, r = 24 CAS(6e,6o), 4 steps)")
     return ap.parse_args()
 
 
@@ -150,6 +155,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist=None, device="cuda"):
+    """The slowest rank's timed-region length (ms): an all-reduce MAX when a process group is up."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    return float(t)
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units per second over all ranks (weak scaling: every rank processes units_per_rank)."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def dist_init(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -171,25 +191,75 @@ def cpu_oracle_timing(p, n_evals=1):
     return n_evals / dt, dt, os.cpu_count()
 
 
+REF_BUDGET_S = 150.0   # host time the reference arm may spend on its warm-up + timed steps
+
+
+def truncated_problem(p, rs):
+    """The workload restricted to its first rs orbitals (h, V and the D blocks sliced; N unchanged).
+    Every occupied and active orbital of the CAS workloads lies below rs >= act_hi, so the 2-RDM keeps
+    all of its nonzero entries."""
+    import numpy as np
+    s = slice(0, rs)
+    cut = lambda x: np.ascontiguousarray(x[(s,) * x.ndim])
+    return type(p)(f"{p.name}[:{rs}]", rs, p.n_alpha, p.n_beta, cut(p.h), cut(p.V), cut(p.Daa), cut(p.Dab),
+                   cut(p.Dbb), p.act_lo, p.act_hi, None)
+
+
+def reference_sample_size(p, nsteps):
+    """Largest orbital count rs (a multiple of 4, >= the occupied + active orbitals, <= r) for which
+    nsteps oracle residual evaluations of the truncated problem fit REF_BUDGET_S; the cost is predicted
+    from one timed evaluation at 16 orbitals scaled by rs^6 (an over-estimate: the oracle's BLAS
+    contractions run more efficiently at larger sizes)."""
+    from oracle import acse_oracle as O
+    r0 = max(16, p.act_hi)
+    q = truncated_problem(p, r0)
+    K = O.reduced_hamiltonian(q.h, q.V, q.N)
+    D = O.so_from_blocks(q.Daa, q.Dab, q.Dbb)
+    t0 = time.perf_counter()
+    O.residual(K, D, q.N)
+    t16 = time.perf_counter() - t0
+    best = r0
+    for rs in range(r0, p.r + 1, 4):
+        if nsteps * t16 * (rs / r0) ** 6 <= REF_BUDGET_S:
+            best = rs
+    return best
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores, each step one oracle residual evaluation of a bounded sample
+    of the workload: the problem truncated to its first rs orbitals, rs chosen so that the warm-up and
+    timed steps fit a few minutes; the rate is scaled to evaluations of the full workload by the
+    O(r^6) contraction count, (rs / r)^6."""
     if rank != 0:
         return
+    from oracle import acse_oracle as O
     p = workload(args.r)
-    for _ in range(min(args.warmup, 1)):
-        pass   # numpy has nothing to warm up; the first timed evaluation includes no compilation
+    rs = reference_sample_size(p, args.steps + args.warmup)
+    q = truncated_problem(p, rs) if rs < p.r else p
+    K = O.reduced_hamiltonian(q.h, q.V, q.N)
+    D = O.so_from_blocks(q.Daa, q.Dab, q.Dbb)
+    for _ in range(args.warmup):
+        O.residual(K, D, q.N)
     times = []
     for _ in range(args.steps):
-        v, dt, cores = cpu_oracle_timing(p, 1)
-        times.append(dt)
+        t0 = time.perf_counter()
+        A = O.residual(K, D, q.N)
+        times.append(time.perf_counter() - t0)
+        del A
     total = sum(times)
-    val = args.steps / total
+    scale = (rs / p.r) ** 6
+    val = scale * args.steps / total
+    sample = (f"per step one FP64 oracle residual evaluation of {p.name} truncated to its first {rs} of {p.r} "
+              f"orbitals ({total / args.steps:.3f} s), rate scaled by (rs/r)^6 = {scale:.3g} to evaluations of "
+              f"the full workload" if rs < p.r else f"per step one FP64 oracle residual evaluation of {p.name}")
     line = {"metric": "acse_residual_evals_per_s", "value": val, "unit": "residual evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": "fp64 (numpy oracle, spin-orbital basis)"},
+            "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": "fp64 (numpy oracle, spin-orbital basis)",
+                       "sample_r": rs},
             "cpu_baseline": {"kind": "oracle", "value": val, "unit": "residual evals/s", "cores": os.cpu_count(),
-                             "sample": f"one full oracle residual evaluation of {p.name} per step"},
+                             "sample": sample},
             "e2e": {"value": val, "unit": "residual evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -262,6 +332,88 @@ def run_batch(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_time_to_e(args):
+    """Wall time from the initial D until the stopping rule of the Methods section fires (E or ||A|| rises,
+    or |dE| < 1e-6 Eh), capped at args.cap steps, for BF16x3 and FP64 on the same workload: one batch of
+    one instance, one graph-replayed step per call so that E is logged at every iteration."""
+    import numpy as np
+    from paper_2604_02550_gb300 import _lib
+    p = workload(args.r)
+    eps = args.eps if args.eps is not None else (1e-4 if p.r >= 32 else 1e-3)
+    out = {"metric": "time_to_E", "workload": p.name, "eps": eps, "cap": args.cap, "runs": {}}
+    logs = {}
+    for prec in ("bf16x3", "fp64"):
+        b = _lib.acse_batch_create([p], prec)
+        _lib.acse_batch_set_D(b, 0, p.Daa, p.Dab, p.Dbb, eps)
+        _lib.acse_batch_run(b, 1, 0, stop_rule=True)       # capture + autotune, no step
+        Es, n2s = [], []
+        t0 = time.perf_counter()
+        steps, reason = 0, 0
+        for _ in range(args.cap):
+            E, N2, S, R = _lib.acse_batch_run(b, 1, 1, stop_rule=True)
+            Es.append(float(E[0]))
+            n2s.append(float(N2[0]))
+            steps, reason = int(S[0]), int(R[0])
+            if reason:
+                break
+        dt = time.perf_counter() - t0
+        _lib.acse_batch_destroy(b)
+        logs[prec] = Es
+        out["runs"][prec] = {"seconds": dt, "steps": steps, "stop_reason": reason, "E_final": Es[-1],
+                             "norm2_final": n2s[-1], "E_first": Es[0]}
+    m = min(len(logs["bf16x3"]), len(logs["fp64"]))
+    dE = np.abs(np.array(logs["bf16x3"][:m]) - np.array(logs["fp64"][:m]))
+    out["max_abs_dE_per_iteration"] = float(dE.max())
+    out["abs_dE_final"] = float(abs(logs["bf16x3"][-1] - logs["fp64"][-1]))
+    out["dE_every_10"] = [float(x) for x in dE[::10]]
+    out["speedup_bf16x3_vs_fp64"] = out["runs"]["fp64"]["seconds"] / out["runs"]["bf16x3"]["seconds"]
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint_cost(args):
+    """Adjoint cost relative to forward: n FP64 Euler steps through acse_step vs one
+    acse_residual_backward over the same n steps with every checkpoint given."""
+    import torch
+    from paper_2604_02550_gb300 import api
+    p = workload(24)
+    n, eps = 4, 1e-3
+    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64")
+    D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    ck = [tuple(x.clone() for x in D)]
+    for _ in range(n):
+        ctx.step(D, eps)
+        ck.append(tuple(x.clone() for x in D))
+    ctx.backward(ck, n, eps, 1.0, 0.5)                    # warm-up (allocates the adjoint workspace)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=3):
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def fwd():
+        Dw = tuple(x.clone() for x in ck[0])
+        for _ in range(n):
+            ctx.step(Dw, eps)
+
+    t_f = timed(fwd)
+    t_b = timed(lambda: ctx.backward(ck, n, eps, 1.0, 0.5))
+    ck_sparse = [ck[0]] + [None] * n                       # only D_0: every D_k recomputed
+    t_b0 = timed(lambda: ctx.backward(ck_sparse, n, eps, 1.0, 0.5))
+    ctx.close()
+    print(json.dumps({"metric": "adjoint_cost_ratio", "workload": p.name, "prec": "fp64", "steps": n, "eps": eps,
+                      "forward_ms": t_f, "backward_ms_all_checkpoints": t_b, "ratio_all_checkpoints": t_b / t_f,
+                      "backward_ms_only_D0": t_b0, "ratio_only_D0": t_b0 / t_f,
+                      "objective": "E(D_n) + 0.5 ||A(D_n)||^2"}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -276,6 +428,12 @@ def main():
     torch.cuda.set_device(local)
     if args.batch:
         run_batch(args, rank, world)
+        return
+    if args.time_to_e:
+        run_time_to_e(args)
+        return
+    if args.adjoint:
+        run_adjoint_cost(args)
         return
     dist = None
     if world > 1:
@@ -316,15 +474,11 @@ def main():
     _lib.acse_profile(ctx.ctx, 0)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    ms_max = float(t)
+    ms_max = max_over_ranks(ms, dist)
     per_step = ms_max / args.steps
-    value = world * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(args.steps, world, ms_max)
     fl = flops_per_pass(p.r)
-    split = 3 if prec == "bf16x3" else 1
+    split = 3 if prec in ("bf16x3", "tf32x3") else 1
     # dominant kernel: the grouped O(r^6) GEMM launch (one per contraction pass)
     gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1e3
     peaks = {}
@@ -341,7 +495,7 @@ def main():
     else:
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": TF32_PEAK_TFLOPS,
                 "peak_source": "measured cuBLAS TF32 8192^3 on this pool (bench.py --peaks)"}
-        ach = fl / gemm_avg_s / 1e12
+        ach = split * fl / gemm_avg_s / 1e12
     roof.update({"achieved": ach, "frac": ach / roof["peak"], "traffic": gemm_traffic(prec) if p.r == 48 else None,
                  "kernel": "grouped O(r^6) GEMM",
                  "flops_per_launch": split * fl, "launch_ms": 1e3 * gemm_avg_s,
@@ -349,7 +503,7 @@ def main():
                  "timed_launches": gemm_n})
     line = {"metric": "acse_residual_evals_per_s", "value": value, "unit": "residual evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16x3 (f32 accumulate)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else f"{prec} (f32 accumulate)",
             "data": "synthetic",
             "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "eps": args.eps,
                        "step": "acse_step: residual + update + axpy + energy",

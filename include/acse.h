@@ -55,7 +55,15 @@ typedef enum {
     ACSE_ERR_TOO_LARGE = -9    /* r above the static scratch of acse_energy_noalloc (64)  */
 } acse_status;
 
-typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2 } acse_prec;
+/* Arithmetic of the O(r^6) contractions (everything else, the 1-RDM, norms, energy, axpy and line search,
+ * stays FP64; the r^5 and r^4 intermediates run in FP32 in the split modes):
+ *   ACSE_FP64    FP64 FMA throughout;
+ *   ACSE_BF16X3  x = hi + lo (two bf16), products hi.hi + hi.lo + lo.hi, FP32 accumulation (about 2^-16
+ *                relative per product);
+ *   ACSE_TF32    one tf32 product, FP32 accumulation (about 2^-11);
+ *   ACSE_TF32X3  x = hi + lo (two tf32), products hi.hi + hi.lo + lo.hi, FP32 accumulation (about 2^-21;
+ *                limited by the FP32 intermediates). */
+typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2, ACSE_TF32X3 = 3 } acse_prec;
 typedef enum { ACSE_RECON_V = 0 } acse_recon;
 
 typedef struct {

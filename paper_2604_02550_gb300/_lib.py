@@ -10,8 +10,8 @@ from ctypes import POINTER, byref, c_double, c_int, c_void_p
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libacse.so")
 
-ACSE_FP64, ACSE_BF16X3, ACSE_TF32 = 0, 1, 2
-PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32}
+ACSE_FP64, ACSE_BF16X3, ACSE_TF32, ACSE_TF32X3 = 0, 1, 2, 3
+PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32, "tf32x3": ACSE_TF32X3}
 
 # symbols declared in include/acse.h
 EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",

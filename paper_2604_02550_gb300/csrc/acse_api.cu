@@ -122,7 +122,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     if (o->r < 2 || o->r > ACSE_MAX_R || o->n_alpha < 0 || o->n_beta < 0 || N < 2 || o->n_alpha > o->r ||
         o->n_beta > o->r)
         return ACSE_ERR_SHAPE;
-    if (o->prec < ACSE_FP64 || o->prec > ACSE_TF32) return ACSE_ERR_ARG;
+    if (o->prec < ACSE_FP64 || o->prec > ACSE_TF32X3) return ACSE_ERR_ARG;
     if (o->recon != ACSE_RECON_V) return ACSE_ERR_UNSUPPORTED;
     if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
     acse_ctx* c = (acse_ctx*)calloc(1, sizeof(acse_ctx));
@@ -131,7 +131,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     c->r = o->r;
     c->N = N;
     c->stream = (cudaStream_t)stream;
-    c->nsplit = o->prec == ACSE_BF16X3 ? 3 : 1;
+    c->nsplit = (o->prec == ACSE_BF16X3 || o->prec == ACSE_TF32X3) ? 3 : 1;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         free(c);
@@ -395,8 +395,7 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
             if (cudaGetLastError() != cudaSuccess) s = ACSE_ERR_CUDA;
         }
     }
-    if (s == ACSE_OK) s = launch_axpy(c, D, Uc, w.scal + 3, 1.0, D);
-    if (s == ACSE_OK) s = launch_energy(c, Dc, w.scal + 1);
+    if (s == ACSE_OK) s = launch_axpy_energy(c, D, Uc, w.scal + 3, w.scal + 1);
     if (s == ACSE_OK && host_in) {
         const size_t b4 = n4_of(c) * sizeof(double);
         double* Dh[3] = {Daa, Dab, Dbb};

@@ -23,6 +23,8 @@
 int launch_axpy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev, double eps_mul,
                 double* const out[3]);
 int launch_energy(acse_ctx* c, const double* const D[3], double* E_dst);
+int launch_axpy_energy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev,
+                       double* E_dst);
 
 // scalar slots of each instance's device scalar block (acse_ctx::w.scal, 16 doubles)
 enum { S_N2 = 0, S_E = 1, S_EPS_USED = 3, S_EPREV = 9, S_N2PREV = 10, S_FROZEN = 11, S_STEPS = 12, S_EPS = 13,
@@ -176,9 +178,7 @@ static int batch_step(acse_batch* B) {
         ACSE_LAUNCHED(c);
         double* Dm[3] = {B->D[3 * i], B->D[3 * i + 1], B->D[3 * i + 2]};
         const double* Uc[3] = {w.U[0], w.U[1], w.U[2]};
-        ACSE_TRY(launch_axpy(c, Dm, Uc, w.scal + S_EPS_USED, 1.0, Dm));
-        const double* Dc[3] = {Dm[0], Dm[1], Dm[2]};
-        ACSE_TRY(launch_energy(c, Dc, w.scal + S_E));
+        ACSE_TRY(launch_axpy_energy(c, Dm, Uc, w.scal + S_EPS_USED, w.scal + S_E));
     }
     return join_all(B);
 }
@@ -190,7 +190,7 @@ static std::map<std::vector<int>, std::pair<int, int>> g_tune_cache;   // key: p
 static int build_tables(acse_batch* B, int choice, int split_r2) {
     for (int t = 0; t < B->ntab; ++t) tc_table_free(&B->tab[t]);
     B->ntab = 0;
-    const int kind = B->prec == ACSE_TF32 ? 1 : 0;
+    const int kind = (B->prec == ACSE_TF32 || B->prec == ACSE_TF32X3) ? 1 : 0;
     int bns[2];
     if (choice == 0) { bns[0] = 256; B->ntab = 1; }
     else if (choice == 1) { bns[0] = 128; B->ntab = 1; }

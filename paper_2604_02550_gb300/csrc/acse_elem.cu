@@ -82,19 +82,23 @@ int launch_build_K(acse_ctx* c) {
 // ------------------------------------------------------------------------------ 1D and M
 // 1D^p_r = 2/(N-1) sum_q 2D^{pq}_{rq} over spin orbitals (App. C):
 //   g_a[p][r] = c sum_q (Daa[p][q][r][q] + Dab[p][q][r][q]);  g_b[p][r] = c sum_q (Dbb[p][q][r][q] + Dab[q][p][q][r]).
-__global__ void k_gamma(int r, double cN, const double* __restrict__ Daa, const double* __restrict__ Dab,
-                        const double* __restrict__ Dbb, double* __restrict__ gam) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per output element (lanes over q, fixed-order warp reduction).
+__global__ void __launch_bounds__(256) k_gamma(int r, double cN, const double* __restrict__ Daa,
+                                               const double* __restrict__ Dab, const double* __restrict__ Dbb,
+                                               double* __restrict__ gam) {
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (t >= 2 * r * r) return;
     const int sp = t / (r * r), p = (t / r) % r, rr = t % r;
     const size_t r3 = (size_t)r * r * r, r2 = (size_t)r * r;
     double s = 0.0;
     if (sp == 0) {
-        for (int q = 0; q < r; ++q) s += Daa[p * r3 + q * r2 + rr * r + q] + Dab[p * r3 + q * r2 + rr * r + q];
+        for (int q = lane; q < r; q += 32) s += Daa[p * r3 + q * r2 + rr * r + q] + Dab[p * r3 + q * r2 + rr * r + q];
     } else {
-        for (int q = 0; q < r; ++q) s += Dbb[p * r3 + q * r2 + rr * r + q] + Dab[q * r3 + p * r2 + q * r + rr];
+        for (int q = lane; q < r; q += 32) s += Dbb[p * r3 + q * r2 + rr * r + q] + Dab[q * r3 + p * r2 + q * r + rr];
     }
-    gam[t] = cN * s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) gam[t] = cN * s;
 }
 
 // M = 3 2Delta + 1D^1D = 3 2D - 2 (1D^1D), (1D^1D)^{ij}_{kl} = 1/2(g^i_k g^j_l - g^j_k g^i_l) (App. C);
@@ -116,7 +120,7 @@ __global__ void k_build_M(int r, const double* __restrict__ gam, const double* _
 
 int launch_gamma(acse_ctx* c, const double* const D[3]) {
     const int r = c->r;
-    k_gamma<<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, 2.0 / (c->N - 1), D[0], D[1], D[2], c->w.gam);
+    k_gamma<<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(r, 2.0 / (c->N - 1), D[0], D[1], D[2], c->w.gam);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
@@ -181,19 +185,22 @@ int launch_pack_Mph(acse_ctx* c) {
 //   Q_b[k][i] = sum_p Xbb[(i,p)][(k,p)] + sum_p Xab[(p,i)][(p,k)]
 // (O(r^3) instead of O(r^5); Xab already carries the factor 2 of the mixed-spin (rs) sum).
 template <typename T>
-__global__ void k_Q_from_X(int r, const T* __restrict__ Xaa, const T* __restrict__ Xab, const T* __restrict__ Xbb,
-                           size_t ldx, T* __restrict__ Qv) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_Q_from_X(int r, const T* __restrict__ Xaa, const T* __restrict__ Xab,
+                                                  const T* __restrict__ Xbb, size_t ldx, T* __restrict__ Qv) {
+    // one warp per output element, lanes over p, fixed-order warp reduction
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (t >= 2 * r * r) return;
     const int sp = t / (r * r), k = (t / r) % r, i = t % r;
     T acc = 0;
-    for (int p = 0; p < r; ++p) {
+    for (int p = lane; p < r; p += 32) {
         if (sp == 0)
             acc += Xaa[(size_t)(i * r + p) * ldx + k * r + p] + Xab[(size_t)(i * r + p) * ldx + k * r + p];
         else
             acc += Xbb[(size_t)(i * r + p) * ldx + k * r + p] + Xab[(size_t)(p * r + i) * ldx + p * r + k];
     }
-    Qv[t] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) Qv[t] = acc;
 }
 
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]) { return launch_Z_tiled(c, W); }
@@ -202,10 +209,10 @@ int launch_Q(acse_ctx* c) {
     const int r = c->r;
     const size_t R2 = (size_t)r * r;
     if (c->opt.prec == ACSE_FP64) {
-        k_Q_from_X<double><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, c->w.X[0], c->w.X[1], c->w.X[2], R2,
+        k_Q_from_X<double><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(r, c->w.X[0], c->w.X[1], c->w.X[2], R2,
                                                                           c->w.Q);
     } else {
-        k_Q_from_X<float><<<(2 * r * r + 127) / 128, 128, 0, c->stream>>>(r, c->w.tc_pairC[0], c->w.tc_pairC[1],
+        k_Q_from_X<float><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(r, c->w.tc_pairC[0], c->w.tc_pairC[1],
                                                                          c->w.tc_pairC[2], R2, c->w.Q32);
     }
     ACSE_LAUNCHED(c);
@@ -242,41 +249,82 @@ struct GArgs {
 
 #define G_GRID (152 * 16)
 
+// Per-thread accumulator of the norm: FP64 on the FP64 path; on the FP32 path a double-float pair
+// (hi, lo) fed with exact products (v*v and its FMA residual) through Knuth's TwoSum, so that the
+// sum keeps about 48 significant bits without FP64 arithmetic (slow on this GPU).
+template <typename T>
+struct NormAcc;
+template <>
+struct NormAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v, double m) { s += m * v * v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct NormAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v, float m) {   // m = 1 or 4 (exact scaling)
+        const float mv = m * v;
+        const float p = __fmul_rn(mv, v);  // never contracted into an FMA
+        const float e = fmaf(mv, v, -p);   // p + e = m v^2 exactly
+        const float s = hi + p;            // TwoSum(hi, p)
+        const float bb = s - hi;
+        const float t = (hi - (s - bb)) + (p - bb);
+        hi = s;
+        lo += t + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename T>
+__device__ __forceinline__ void g_put(const GArgs<T>& a, int blk, int r, int R2, int ij, int kl, T v, NormAcc<T>& nrm) {
+    nrm.add(v, blk == 1 ? (T)4 : (T)1);
+    double o = (double)v;
+    if (a.mask) {
+        const int i = ij / r, j = ij - i * r, k = kl / r, l = kl - k * r;
+        if (i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo && l < a.hi) o = 0.0;
+    }
+    a.out[blk][(size_t)ij * R2 + kl] = o;
+}
+
+// G_b = scale (H_b - s H_b^T) (pair transpose), the masked result in FP64 and the unmasked norm
+// partials.  Work items are pairs of 32 x 32 tiles (ti <= tj): the tiles P = H[ti rows][tj cols] and
+// Q = H[tj rows][ti cols] are read once and give both output tiles, since
+//   G[ij][kl] = scale (P[ij][kl] - s Q[kl][ij]),   G[kl][ij] = scale (Q[kl][ij] - s P[ij][kl]).
 template <typename T>
 __global__ void __launch_bounds__(256) k_assemble_G(const __grid_constant__ GArgs<T> a) {
-    __shared__ T tile[32][33];
+    __shared__ T P[32][33];
+    __shared__ T Q[32][33];
     const int r = a.r;
     const int R2 = r * r;
     const int nT = (R2 + 31) / 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    double nrm = 0.0;
-    for (int tid = blockIdx.x; tid < 3 * nT * nT; tid += gridDim.x) {
-        const int blk = tid / (nT * nT);
-        const int ti = (tid / nT) % nT, tj = tid % nT;
+    NormAcc<T> nrm;
+    for (int w = blockIdx.x; w < 3 * nT * nT; w += gridDim.x) {
+        const int blk = w / (nT * nT);
+        const int ti = (w / nT) % nT, tj = w % nT;
+        if (ti > tj) continue;                              // block-uniform
         const T* H = a.H[blk];
-        // tile[y][x] = H[(tj*32 + y)][(ti*32 + x)]   (rows kl, columns ij)
         for (int y = ty; y < 32; y += 8) {
-            const int kl = tj * 32 + y, ij = ti * 32 + tx;
-            tile[y][tx] = (kl < R2 && ij < R2) ? H[(size_t)kl * R2 + ij] : (T)0;
+            const int pr = ti * 32 + y, pc = tj * 32 + tx;
+            P[y][tx] = (pr < R2 && pc < R2) ? H[(size_t)pr * R2 + pc] : (T)0;
+            const int qr = tj * 32 + y, qc = ti * 32 + tx;
+            Q[y][tx] = (qr < R2 && qc < R2) ? H[(size_t)qr * R2 + qc] : (T)0;
         }
         __syncthreads();
         for (int y = ty; y < 32; y += 8) {
             const int ij = ti * 32 + y, kl = tj * 32 + tx;
-            if (ij < R2 && kl < R2) {
-                const T v = a.scale * (H[(size_t)ij * R2 + kl] - a.s * tile[tx][y]);
-                double o = (double)v;
-                nrm += (blk == 1 ? 4.0 : 1.0) * o * o;
-                const int i = ij / r, j = ij % r, k = kl / r, l = kl % r;
-                if (a.mask && i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi &&
-                    l >= a.lo && l < a.hi)
-                    o = 0.0;
-                a.out[blk][(size_t)ij * R2 + kl] = o;
-            }
+            if (ij < R2 && kl < R2) g_put(a, blk, r, R2, ij, kl, a.scale * (P[y][tx] - a.s * Q[tx][y]), nrm);
         }
+        if (ti != tj)
+            for (int y = ty; y < 32; y += 8) {
+                const int kl = tj * 32 + y, ij = ti * 32 + tx;
+                if (ij < R2 && kl < R2) g_put(a, blk, r, R2, kl, ij, a.scale * (Q[y][tx] - a.s * P[tx][y]), nrm);
+            }
         __syncthreads();
     }
-    nrm = block_sum(nrm);
-    if (threadIdx.x == 0) a.partial[blockIdx.x] = nrm;
+    const double tot = block_sum(nrm.value());
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = tot;
 }
 
 // Fixed-order final sum of `n` partials into dst (one block).
@@ -379,6 +427,65 @@ int launch_axpy(acse_ctx* c, double* const D[3], const double* const U[3], const
     const int vec = (bits & 15) == 0;
     k_axpy<<<dim3(grid_for((size_t)n) / 2 + 1, 3), TPB, 0, c->stream>>>(n, vec, D[0], D[1], D[2], U[0], U[1], U[2],
                                                                       eps_dev, eps_mul, out[0], out[1], out[2]);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+// D <- D + eps U fused with the energy of the new D: E = 2 [sum Kh_aa D_aa + sum Kh_bb D_bb
+// + 4 sum Kh_ab D_ab].  Grid (AXE_X, 3): block row y handles spin block y; block partials
+// (partial[y * AXE_X + x]) are summed in a fixed order by k_sum_partials.
+#define AXE_X (152 * 4)
+__global__ void __launch_bounds__(TPB) k_axpy_energy(int n, int vec, double* D0, double* D1, double* D2,
+                                                     const double* __restrict__ U0, const double* __restrict__ U1,
+                                                     const double* __restrict__ U2, const double* __restrict__ K0,
+                                                     const double* __restrict__ K1, const double* __restrict__ K2,
+                                                     const double* __restrict__ eps, double* __restrict__ partial) {
+    const double e = *eps;
+    const int b = blockIdx.y;
+    double* D = b == 0 ? D0 : b == 1 ? D1 : D2;
+    const double* U = b == 0 ? U0 : b == 1 ? U1 : U2;
+    const double* K = b == 0 ? K0 : b == 1 ? K1 : K2;
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (vec) {
+        const int n2 = n >> 1;
+        double2* Dv = reinterpret_cast<double2*>(D);
+        const double2* Uv = reinterpret_cast<const double2*>(U);
+        const double2* Kv = reinterpret_cast<const double2*>(K);
+        for (int i = t0; i < n2; i += stride) {
+            const double2 d = Dv[i], u = Uv[i], k = Kv[i];
+            const double2 o = make_double2(d.x + e * u.x, d.y + e * u.y);
+            Dv[i] = o;
+            acc += k.x * o.x + k.y * o.y;
+        }
+        if ((n & 1) && t0 == 0) {
+            const double o = D[n - 1] + e * U[n - 1];
+            D[n - 1] = o;
+            acc += K[n - 1] * o;
+        }
+    } else {
+        for (int i = t0; i < n; i += stride) {
+            const double o = D[i] + e * U[i];
+            D[i] = o;
+            acc += K[i] * o;
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[b * gridDim.x + blockIdx.x] = (b == 1 ? 8.0 : 2.0) * acc;
+}
+
+int launch_axpy_energy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev,
+                       double* E_dst) {
+    const int n = c->r * c->r * c->r * c->r;
+    uintptr_t bits = 0;
+    for (int b = 0; b < 3; ++b) bits |= (uintptr_t)D[b] | (uintptr_t)U[b] | (uintptr_t)c->w.Kh[b];
+    const int vec = (bits & 15) == 0;
+    double* part = c->w.partial + 2 * G_GRID;
+    k_axpy_energy<<<dim3(AXE_X, 3), TPB, 0, c->stream>>>(n, vec, D[0], D[1], D[2], U[0], U[1], U[2], c->w.Kh[0],
+                                                          c->w.Kh[1], c->w.Kh[2], eps_dev, part);
+    ACSE_LAUNCHED(c);
+    k_sum_partials<<<1, TPB, 0, c->stream>>>(part, 3 * AXE_X, E_dst);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }

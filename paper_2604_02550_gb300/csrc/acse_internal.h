@@ -172,6 +172,8 @@ int launch_Q(acse_ctx* c);
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3],
                       double* norm2_dst);
 int launch_energy(acse_ctx* c, const double* const D[3], double* E_dst);
+int launch_axpy_energy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev,
+                       double* E_dst);
 int launch_axpy(acse_ctx* c, double* const D[3], const double* const U[3], const double* eps_dev,
                 double eps_mul, double* const out[3]);
 int launch_line_search(acse_ctx* c);

@@ -5,6 +5,7 @@
 // a multiple of the 128-byte K block):
 //   BF16x3  x = hi + lo, hi = bf16(x), lo = bf16(x - hi);  A rows [hi|hi|lo], B rows [hi|lo|hi]
 //   TF32    x -> tf32 (round to nearest, ties away)        A rows, B rows [x]
+//   TF32x3  x = hi + lo, hi = tf32(x), lo = tf32(x - hi);  A rows [hi|hi|lo], B rows [hi|lo|hi]
 // The logical operands are those of the FP64 path (acse_elem.cu): the pair-pair [M; D] and W
 // blocks, and the particle-hole layouts of M and Z.  The 1-RDM is accumulated in FP64 (exactly
 // as in the FP64 path) and rounded to FP32 here; M, Z and w are formed in FP32.
@@ -37,6 +38,13 @@ __device__ __forceinline__ void put(void* base, size_t row, size_t ld, int Kp, i
         p[k] = hi;
         p[Kp + k] = PAT == 0 ? hi : lo;
         p[2 * Kp + k] = PAT == 0 ? lo : hi;
+    } else if (PREC == ACSE_TF32X3) {
+        float* p = (float*)base + row * ld;
+        const float hi = tf32_rna(x);
+        const float lo = tf32_rna(x - hi);
+        p[k] = hi;
+        p[Kp + k] = PAT == 0 ? hi : lo;
+        p[2 * Kp + k] = PAT == 0 ? lo : hi;
     } else {
         float* p = (float*)base + row * ld;
         p[k] = tf32_rna(x);
@@ -61,6 +69,19 @@ __device__ __forceinline__ void put4(void* base, size_t row, size_t ld, int Kp, 
         *reinterpret_cast<uint2*>(p) = H;
         *reinterpret_cast<uint2*>(p + Kp) = PAT == 0 ? H : L;
         *reinterpret_cast<uint2*>(p + 2 * Kp) = PAT == 0 ? L : H;
+    } else if (PREC == ACSE_TF32X3) {
+        float hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            hi[u] = tf32_rna(x[u]);
+            lo[u] = tf32_rna(x[u] - hi[u]);
+        }
+        float* p = (float*)base + row * ld + k;
+        const float4 H = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        const float4 L = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<float4*>(p) = H;
+        *reinterpret_cast<float4*>(p + Kp) = PAT == 0 ? H : L;
+        *reinterpret_cast<float4*>(p + 2 * Kp) = PAT == 0 ? L : H;
     } else {
         float4 v = make_float4(tf32_rna(x[0]), tf32_rna(x[1]), tf32_rna(x[2]), tf32_rna(x[3]));
         *reinterpret_cast<float4*>((float*)base + row * ld + k) = v;
@@ -102,46 +123,64 @@ static MxPtrs mx_ptrs(acse_ctx* c) {
 
 // --------------------------------------------------------------------------- per D
 // M = 3 2D - 2 (1D^1D) in FP32 (App. C), stored plain (M32) and as rows 0..r^2-1 of the pair
-// operand [M; D]; rows r^2..2r^2-1 hold D.  Also rounds the FP64 1-RDM to FP32.  Each thread
-// handles four consecutive columns (vector stores when r is even).
+// operand [M; D]; rows r^2..2r^2-1 hold D.  Also rounds the FP64 1-RDM to FP32.  One block per
+// (sector, row of [M; D]); each thread handles groups of four consecutive columns (16-byte loads
+// and vector stores when r is even); the two 1-RDM rows a row needs are staged in shared memory.
 template <int PREC>
-__global__ void k_mx_prepD(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
-                           const double* __restrict__ Dab, const double* __restrict__ Dbb, const __grid_constant__ MxPtrs p) {
-    // grid: x over groups of four columns, y over (sector, row of [M; D])
+__global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
+                                                  const double* __restrict__ Dab, const double* __restrict__ Dbb,
+                                                  const __grid_constant__ MxPtrs p) {
+    __shared__ float g1[ACSE_MAX_R], g2[ACSE_MAX_R];
     const int R2 = r * r;
     const int c4 = (R2 + 3) >> 2;
-    const int q4 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y / (2 * R2);
-    const int row = blockIdx.y - s * 2 * R2;
-    if (blockIdx.x == 0 && blockIdx.y == 0)
+    const int s = blockIdx.x / (2 * R2);
+    const int row = blockIdx.x - s * 2 * R2;
+    if (blockIdx.x == 0)
         for (int e = threadIdx.x; e < 2 * R2; e += blockDim.x) p.gam32[e] = (float)gam[e];
-    if (q4 >= c4) return;
-    const size_t ld = (size_t)p.ns * p.Kp1;
-    const int k0 = q4 * 4;
-    const double* D = s == 0 ? Daa : (s == 1 ? Dab : Dbb);
-    float x[4] = {0.f, 0.f, 0.f, 0.f};
-    const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
-    if (row < R2) {
-        const int i = row / r, j = row - i * r;
-        const double* ga = gam + (s == 2 ? R2 : 0);
-        const double* gb = gam + (s == 0 ? 0 : R2);
-        const double* Drow = D + (size_t)row * R2;
-        float* Mrow = p.M32[s] + (size_t)row * R2;
-        for (int u = 0; u < nk; ++u) {
-            const int k = k0 + u, kk = k / r, l = k - kk * r;
-            const float d = (float)Drow[k];
-            x[u] = s == 1 ? 3.0f * d - (float)ga[i * r + kk] * (float)gb[j * r + l]
-                          : 3.0f * d - ((float)ga[i * r + kk] * (float)ga[j * r + l] -
-                                        (float)ga[j * r + kk] * (float)ga[i * r + l]);
-            Mrow[k] = x[u];
+    const bool mrow = row < R2;
+    const int i = mrow ? row / r : 0, j = mrow ? row - (row / r) * r : 0;
+    if (mrow) {
+        // s = 0: rows i, j of 1D_a; s = 2: of 1D_b; s = 1: row i of 1D_a and row j of 1D_b
+        const double* G1 = gam + (s == 2 ? R2 : 0) + (size_t)i * r;
+        const double* G2 = gam + (s == 0 ? 0 : R2) + (size_t)j * r;
+        for (int e = threadIdx.x; e < r; e += blockDim.x) {
+            g1[e] = (float)G1[e];
+            g2[e] = (float)G2[e];
         }
-    } else {
-        const double* Drow = D + (size_t)(row - R2) * R2;
-        for (int u = 0; u < nk; ++u) x[u] = (float)Drow[k0 + u];
     }
-    if ((r & 1) == 0 && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
-    else
-        for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
+    __syncthreads();
+    const size_t ld = (size_t)p.ns * p.Kp1;
+    const double* D = (s == 0 ? Daa : (s == 1 ? Dab : Dbb)) + (size_t)(mrow ? row : row - R2) * R2;
+    float* Mrow = p.M32[s] + (size_t)row * R2;
+    const bool vec = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(s == 0 ? Daa : (s == 1 ? Dab : Dbb)) & 15) == 0);
+    for (int q4 = threadIdx.x; q4 < c4; q4 += blockDim.x) {
+        const int k0 = q4 * 4;
+        const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (vec && nk == 4) {
+            const double2 d01 = *reinterpret_cast<const double2*>(D + k0);
+            const double2 d23 = *reinterpret_cast<const double2*>(D + k0 + 2);
+            x[0] = (float)d01.x; x[1] = (float)d01.y; x[2] = (float)d23.x; x[3] = (float)d23.y;
+        } else {
+            for (int u = 0; u < nk; ++u) x[u] = (float)D[k0 + u];
+        }
+        if (mrow) {
+            int kk = k0 / r, l = k0 - kk * r;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < nk) {
+                    x[u] = s == 1 ? 3.0f * x[u] - g1[kk] * g2[l] : 3.0f * x[u] - (g1[kk] * g2[l] - g2[kk] * g1[l]);
+                }
+                if (++l == r) { l = 0; ++kk; }
+            }
+            if (vec && nk == 4) *reinterpret_cast<float4*>(Mrow + k0) = make_float4(x[0], x[1], x[2], x[3]);
+            else
+                for (int u = 0; u < nk; ++u) Mrow[k0 + u] = x[u];
+        }
+        if (vec && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
+        else
+            for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
+    }
 }
 
 // Particle-hole layouts of M (the B operands of the ph GEMMs), copied as r x r blocks per (t, i, p):
@@ -166,10 +205,23 @@ __global__ void __launch_bounds__(256) k_mx_pack_Mph(int r, const __grid_constan
         case 4: src = p.M32[1] + i * r3 + (size_t)pp * R2; tr = true; break;
         default: src = p.M32[1] + pp * r3 + (size_t)i * R2; tr = false; break;
     }
-    for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-        const int u = e / r, v = e % r;
-        if (tr) tile[v][u] = src[e];
-        else tile[u][v] = src[e];
+    if ((r & 1) == 0) {   // r^2 % 4 == 0 and every source block starts on a 16-byte boundary
+        for (int e4 = threadIdx.x; e4 < R2 / 4; e4 += blockDim.x) {
+            const float4 q = reinterpret_cast<const float4*>(src)[e4];
+            const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = 4 * e4 + c, u = e / r, v = e - u * r;
+                if (tr) tile[v][u] = qv[c];
+                else tile[u][v] = qv[c];
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+            const int u = e / r, v = e % r;
+            if (tr) tile[v][u] = src[e];
+            else tile[u][v] = src[e];
+        }
     }
     __syncthreads();
     void* dst;
@@ -182,9 +234,17 @@ __global__ void __launch_bounds__(256) k_mx_pack_Mph(int r, const __grid_constan
         dst = p.Mf[t - 4]; ld = (size_t)p.ns * p.Kp1; Kp = p.Kp1;
         rowbase = i * r; colbase = pp * r;
     }
-    for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-        const int l = e / r, s2 = e % r;
-        put<PREC, 1>(dst, (size_t)rowbase + l, ld, Kp, colbase + s2, tile[l][s2]);
+    if ((r & 3) == 0) {   // four consecutive columns of one row per thread, vector stores
+        for (int g = threadIdx.x; g < R2 / 4; g += blockDim.x) {
+            const int l = (4 * g) / r, s0 = 4 * g - l * r;
+            const float x[4] = {tile[l][s0], tile[l][s0 + 1], tile[l][s0 + 2], tile[l][s0 + 3]};
+            put4<PREC, 1>(dst, (size_t)rowbase + l, ld, Kp, colbase + s0, x);
+        }
+    } else {
+        for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+            const int l = e / r, s2 = e % r;
+            put<PREC, 1>(dst, (size_t)rowbase + l, ld, Kp, colbase + s2, tile[l][s2]);
+        }
     }
 }
 
@@ -194,11 +254,15 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
     MxPtrs p = mx_ptrs(c);
     const int R2 = r * r;
     if (c->opt.prec == ACSE_BF16X3) {
-        k_mx_prepD<ACSE_BF16X3><<<dim3((R2 / 4 + 128) / 128, 6 * R2), 128, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_BF16X3><<<6 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
         k_mx_pack_Mph<ACSE_BF16X3><<<6 * R2, 256, 0, c->stream>>>(r, p);
+    } else if (c->opt.prec == ACSE_TF32X3) {
+        k_mx_prepD<ACSE_TF32X3><<<6 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        ACSE_LAUNCHED(c);
+        k_mx_pack_Mph<ACSE_TF32X3><<<6 * R2, 256, 0, c->stream>>>(r, p);
     } else {
-        k_mx_prepD<ACSE_TF32><<<dim3((R2 / 4 + 128) / 128, 6 * R2), 128, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_TF32><<<6 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
         k_mx_pack_Mph<ACSE_TF32><<<6 * R2, 256, 0, c->stream>>>(r, p);
     }
@@ -235,6 +299,8 @@ int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     MxPtrs p = mx_ptrs(c);
     if (c->opt.prec == ACSE_BF16X3)
         k_mx_pack_W<ACSE_BF16X3><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+    else if (c->opt.prec == ACSE_TF32X3)
+        k_mx_pack_W<ACSE_TF32X3><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     else
         k_mx_pack_W<ACSE_TF32><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     ACSE_LAUNCHED(c);

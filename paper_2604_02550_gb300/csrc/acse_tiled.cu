@@ -12,10 +12,12 @@
 // Thread micro-tiles are 4 x 4 outputs over r padded to a multiple of 4; operands sit in shared
 // memory laid out so that each thread reads 4-vectors.
 #include <cuda_bf16.h>
+#include <type_traits>
 
 #include "acse_internal.h"
 
 #define TL_TPB 256
+#define ZP_MAX_THREADS 288
 
 __device__ __forceinline__ float tl_tf32(float x) {
     uint32_t u;
@@ -55,7 +57,7 @@ __device__ __forceinline__ void mma4x4(T (&acc)[4][4], const T* A, const T* B, i
 struct ZOut {
     void* Zd;      // (2 r^2) rows
     void* Zf[2];   // r^2 rows
-    int mode;      // 0 = FP64, 1 = BF16x3 (A pattern [hi|hi|lo]), 2 = TF32
+    int mode;      // 0 = FP64, 1 = BF16x3 (A pattern [hi|hi|lo]), 2 = TF32, 3 = TF32x3 ([hi|hi|lo])
     int ldd, ldf;  // row length in elements
     int Kp1, Kp2;  // K segment length (split modes)
     void* diag;    // [4][r][r][r]: rows j = p of Zd(a,a), Zd(b,b), Zf1, Zf2
@@ -76,164 +78,223 @@ __device__ __forceinline__ void z_store(const ZOut& o, int which, size_t row, in
         p[col] = hi;
         p[Kp + col] = hi;
         p[2 * Kp + col] = lo;
+    } else if (o.mode == 3) {
+        float* p = (float*)base + row * ld;
+        const float hi = tl_tf32((float)v);
+        const float lo = tl_tf32((float)v - hi);
+        p[col] = hi;
+        p[Kp + col] = hi;
+        p[2 * Kp + col] = lo;
     } else {
         ((float*)base + row * ld)[col] = tl_tf32((float)v);
     }
 }
 
-#define Z_PCH 8          // p values per block
-#define Z_PREF 16        // slice elements prefetched per thread (r^2 <= 4096 = 16 x 256)
-
-// Two consecutive columns col, col + 1 of one output row (col even, row length even).
-template <typename T>
-__device__ __forceinline__ void z_store2(const ZOut& o, int which, size_t row, int col, T v0, T v1) {
+// Four consecutive columns col..col+3 of one output row (requires row * ld + col % 4 == 0); MODE is
+// the ZOut mode.
+template <int MODE, typename T>
+__device__ __forceinline__ void z_store4(const ZOut& o, int which, size_t row, int col, const T (&v)[4]) {
     void* base = which < 0 ? o.Zd : o.Zf[which];
     const size_t ld = which < 0 ? (size_t)o.ldd : (size_t)o.ldf;
     const int Kp = which < 0 ? o.Kp2 : o.Kp1;
-    if (o.mode == 0) {
-        *reinterpret_cast<double2*>((double*)base + row * ld + col) = make_double2((double)v0, (double)v1);
-    } else if (o.mode == 1) {
-        __nv_bfloat16* p = (__nv_bfloat16*)base + row * ld + col;
-        const float x0 = (float)v0, x1 = (float)v1;
-        const __nv_bfloat162 hi = __floats2bfloat162_rn(x0, x1);
-        const __nv_bfloat162 lo = __floats2bfloat162_rn(x0 - __low2float(hi), x1 - __high2float(hi));
-        *reinterpret_cast<__nv_bfloat162*>(p) = hi;
-        *reinterpret_cast<__nv_bfloat162*>(p + Kp) = hi;
-        *reinterpret_cast<__nv_bfloat162*>(p + 2 * Kp) = lo;
+    if (MODE == 0) {
+        double* q = (double*)base + row * ld + col;
+        *reinterpret_cast<double2*>(q) = make_double2((double)v[0], (double)v[1]);
+        *reinterpret_cast<double2*>(q + 2) = make_double2((double)v[2], (double)v[3]);
+    } else if (MODE == 1) {
+        __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            hi[u] = __float2bfloat16_rn((float)v[u]);
+            lo[u] = __float2bfloat16_rn((float)v[u] - __bfloat162float(hi[u]));
+        }
+        uint2 H, L;
+        memcpy(&H, hi, 8);
+        memcpy(&L, lo, 8);
+        __nv_bfloat16* q = (__nv_bfloat16*)base + row * ld + col;
+        *reinterpret_cast<uint2*>(q) = H;
+        *reinterpret_cast<uint2*>(q + Kp) = H;
+        *reinterpret_cast<uint2*>(q + 2 * Kp) = L;
+    } else if (MODE == 3) {
+        float hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            hi[u] = tl_tf32((float)v[u]);
+            lo[u] = tl_tf32((float)v[u] - hi[u]);
+        }
+        float* q = (float*)base + row * ld + col;
+        *reinterpret_cast<float4*>(q) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(q + Kp) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(q + 2 * Kp) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     } else {
-        *reinterpret_cast<float2*>((float*)base + row * ld + col) = make_float2(tl_tf32((float)v0), tl_tf32((float)v1));
+        float* q = (float*)base + row * ld + col;
+        *reinterpret_cast<float4*>(q) =
+            make_float4(tl_tf32((float)v[0]), tl_tf32((float)v[1]), tl_tf32((float)v[2]), tl_tf32((float)v[3]));
     }
 }
 
-// Block (t, k, p0..p0+Z_PCH-1), t = 0..5:
+// Asynchronous global -> shared copies (cp.async, completion tracked per thread by commit groups).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The r x r slice W_kp[q][s] of spin type t (t = 0..5, see k_Z_pipe) and whether it is stored [s][q].
+__device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, const double* Waa, const double* Wab,
+                                                 const double* Wbb, bool& transposed) {
+    const size_t r3 = (size_t)r * r * r, R2 = (size_t)r * r;
+    switch (t) {
+        case 0: transposed = false; return Waa + k * r3 + p * R2;
+        case 1: transposed = false; return Wab + k * r3 + p * R2;
+        case 2: transposed = true; return Wab + p * r3 + k * R2;
+        case 3: transposed = false; return Wbb + k * r3 + p * R2;
+        case 4: transposed = true; return Wab + k * r3 + p * R2;
+        default: transposed = false; return Wab + p * r3 + k * R2;
+    }
+}
+
+// Z_kp = 1D . W_kp for spin type t and all p of a chunk, one block per (t, k, p-chunk):
 //   t=0 Zd(a,a): W_kp[q][s] = Waa[k][p][q][s], ga      t=1 Zd(a,b): Wab[k][p][q][s], ga
 //   t=2 Zd(b,a): W_kp[q][s] = Wab[p][k][s][q], gb      t=3 Zd(b,b): Wbb[k][p][q][s], gb
 //   t=4 Zf1:     W_kp[q][s] = Wab[k][p][s][q], gb      t=5 Zf2:     Wab[p][k][q][s], ga
-// (the spin-flip sectors drop a sign -1 that their M operand drops too).  The 1D is staged once per
-// block; the W slice of the next p is loaded into registers while the current one is multiplied.
-template <typename T>
-__device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, const double* Waa, const double* Wab,
-                                                const double* Wbb, bool& tr) {
-    const size_t R2 = (size_t)r * r, r3 = R2 * r;
-    switch (t) {
-        case 0: tr = false; return Waa + k * r3 + p * R2;
-        case 1: tr = false; return Wab + k * r3 + p * R2;
-        case 2: tr = true; return Wab + p * r3 + k * R2;
-        case 3: tr = false; return Wbb + k * r3 + p * R2;
-        case 4: tr = true; return Wab + k * r3 + p * R2;
-        default: tr = false; return Wab + p * r3 + k * R2;
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(TL_TPB) k_Z_tiled(int r, const double* __restrict__ Waa,
-                                                    const double* __restrict__ Wab,
-                                                    const double* __restrict__ Wbb,
-                                                    const double* __restrict__ gam, const __grid_constant__ ZOut o) {
+// (the spin-flip sectors drop a sign -1 that their M operand drops too).  The FP64 slices of the
+// next ipb values of p are copied into shared memory (cp.async) while the current ipb slices are
+// multiplied; each thread owns one 4 x 4 output tile of one slice (ipb * (rp/4)^2 threads).
+template <int MODE>
+__global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(int r, int ipb, int pchunk, const double* __restrict__ Waa,
+                                                         const double* __restrict__ Wab,
+                                                         const double* __restrict__ Wbb,
+                                                         const double* __restrict__ gam, const __grid_constant__ ZOut o) {
+    using T = typename std::conditional<MODE == 0, double, float>::type;
     extern __shared__ __align__(16) unsigned char tl_smem[];
-    const int rp = pad4(r);
-    T* Ws = (T*)tl_smem;          // [q][s]
-    T* gT = Ws + rp * rp;         // [q][j] = 1D[j][q]
-    const int R2 = r * r;
-    const int nchunk = (r + Z_PCH - 1) / Z_PCH;
+    const int rp = pad4(r), ldw = rp + 4, R2 = r * r, R2e = (R2 + 1) & ~1;
+    const int nt = rp / 4, nt2 = nt * nt;
+    double* stage = (double*)tl_smem;                    // [ipb][R2e] raw FP64 slices
+    T* gT = (T*)(stage + (size_t)ipb * R2e);             // [q][j] = 1D[j][q], row pitch ldw
+    T* Ws = gT + (size_t)rp * ldw;                       // [ipb][q][s], row pitch ldw
+    const int nchunk = (r + pchunk - 1) / pchunk;
     const int t = blockIdx.x / (r * nchunk);
-    const int k = (blockIdx.x / nchunk) % r;
-    const int p0 = (blockIdx.x % nchunk) * Z_PCH;
-    const int p1 = min(p0 + Z_PCH, r);
+    const int rem = blockIdx.x - t * r * nchunk;
+    const int k = rem / nchunk;
+    const int pb = (rem - k * nchunk) * pchunk;
+    const int pe = min(r, pb + pchunk);
     const double* g = gam + ((t == 2 || t == 3 || t == 4) ? R2 : 0);
-    for (int e = threadIdx.x; e < rp * rp; e += blockDim.x) {
-        Ws[e] = (T)0;
-        gT[e] = (T)0;
-    }
+    const bool vec_ld = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(Waa) | reinterpret_cast<uintptr_t>(Wab) |
+                                          reinterpret_cast<uintptr_t>(Wbb)) & 15) == 0;
+    for (int e = threadIdx.x; e < (1 + ipb) * rp * ldw; e += blockDim.x) gT[e] = (T)0;
     __syncthreads();
     for (int e = threadIdx.x; e < R2; e += blockDim.x) {
         const int u = e / r, v = e - u * r;
-        gT[v * rp + u] = (T)g[e];                // g[j][q] -> gT[q][j]
+        gT[v * ldw + u] = (T)g[e];                       // g[j][q] -> gT[q][j]
     }
-    int which, sK, sP, dslot;
+    auto issue = [&](int p0) {
+        const int n = min(ipb, pe - p0);
+        for (int it = 0; it < n; ++it) {
+            bool tr;
+            const double* src = z_slice(t, k, p0 + it, r, Waa, Wab, Wbb, tr);
+            double* dst = stage + (size_t)it * R2e;
+            if (vec_ld)
+                for (int e = threadIdx.x; e < R2 / 2; e += blockDim.x) cp_async16(dst + 2 * e, src + 2 * e);
+            else
+                for (int e = threadIdx.x; e < R2; e += blockDim.x) cp_async8(dst + e, src + e);
+        }
+        cp_async_commit();
+    };
+    issue(pb);
+    int which, sK, sP;
     if (t < 4) { which = -1; sK = t >> 1; sP = t & 1; }
     else { which = t - 4; sK = 0; sP = 0; }
-    dslot = t == 0 ? 0 : t == 3 ? 1 : t == 4 ? 2 : t == 5 ? 3 : -1;
-    const int nt = rp / 4;
-    bool tr;
-    T pre[Z_PREF];
-    {
-        const double* src = z_slice<T>(t, k, p0, r, Waa, Wab, Wbb, tr);
-#pragma unroll
-        for (int u = 0; u < Z_PREF; ++u) {
-            const int e = threadIdx.x + u * TL_TPB;
-            pre[u] = e < R2 ? (T)src[e] : (T)0;
-        }
-    }
-    T* Os = gT + rp * rp;         // [j][s] output block of the current p
-    for (int p = p0; p < p1; ++p) {
-        __syncthreads();   // previous slice and output block consumed
-#pragma unroll
-        for (int u = 0; u < Z_PREF; ++u) {
-            const int e = threadIdx.x + u * TL_TPB;
-            if (e < R2) {
-                const int a = e / r, b = e - a * r;
-                if (tr) Ws[b * rp + a] = pre[u];   // src[s][q] -> Ws[q][s]
-                else Ws[a * rp + b] = pre[u];
-            }
-        }
-        __syncthreads();
-        if (p + 1 < p1) {
-            const double* src = z_slice<T>(t, k, p + 1, r, Waa, Wab, Wbb, tr);
-#pragma unroll
-            for (int u = 0; u < Z_PREF; ++u) {
-                const int e = threadIdx.x + u * TL_TPB;
-                pre[u] = e < R2 ? (T)src[e] : (T)0;
-            }
-        }
-        for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
-            const int j0 = (tile / nt) * 4, s0 = (tile % nt) * 4;
-            T acc[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = 0;
-            mma4x4<T>(acc, gT, Ws, rp, r, j0, s0);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) Os[(j0 + u) * rp + s0 + v] = acc[u][v];
-        }
-        __syncthreads();
-        // rows (sK, k, j), columns (sP, p, s): r contiguous values per row, stored in pairs
-        const int colbase = sP * R2 + p * r;
-        if ((r & 1) == 0) {
-            const int hr = r >> 1;
-            for (int e = threadIdx.x; e < r * hr; e += blockDim.x) {
-                const int j = e / hr, s2 = (e - j * hr) * 2;
-                z_store2<T>(o, which, (size_t)sK * R2 + (size_t)k * r + j, colbase + s2, Os[j * rp + s2],
-                            Os[j * rp + s2 + 1]);
-            }
-        } else {
+    const int dslot = t == 0 ? 0 : t == 3 ? 1 : t == 4 ? 2 : t == 5 ? 3 : -1;
+    const int it_me = threadIdx.x / nt2, tile = threadIdx.x - it_me * nt2;
+    const int j0 = (tile / nt) * 4, s0 = (tile % nt) * 4;
+    const size_t ld = which < 0 ? (size_t)o.ldd : (size_t)o.ldf;
+    for (int p0 = pb; p0 < pe; p0 += ipb) {
+        const int n = min(ipb, pe - p0);
+        cp_async_wait_all();
+        __syncthreads();                                 // slices landed; previous products done with Ws
+        for (int it = 0; it < n; ++it) {
+            bool tr;
+            z_slice(t, k, p0 + it, r, Waa, Wab, Wbb, tr);
+            const double* st = stage + (size_t)it * R2e;
+            T* W = Ws + (size_t)it * rp * ldw;
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-                const int j = e / r, s2 = e - j * r;
-                z_store<T>(o, which, (size_t)sK * R2 + (size_t)k * r + j, colbase + s2, Os[j * rp + s2]);
+                const int u = e / r, v = e - u * r;
+                const T x = (T)st[e];
+                if (tr) W[v * ldw + u] = x;                // src[s][q] -> W[q][s]
+                else W[u * ldw + v] = x;
             }
         }
-        if (dslot >= 0)
-            for (int s2 = threadIdx.x; s2 < r; s2 += blockDim.x)
-                ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s2] = Os[p * rp + s2];
+        __syncthreads();                                 // Ws ready, stage free
+        if (p0 + ipb < pe) issue(p0 + ipb);              // the next slices load during the products
+        if (it_me >= n) continue;
+        const int p = p0 + it_me;
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+        const T* W = Ws + (size_t)it_me * rp * ldw;
+#pragma unroll 4
+        for (int q = 0; q < r; ++q) {
+            T a[4], b[4];
+            ld4(gT + q * ldw + j0, a);
+            ld4(W + q * ldw + s0, b);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        const int col0 = sP * R2 + p * r + s0;
+        const bool vec_st = s0 + 3 < r && ((size_t)col0 & 3) == 0 && (ld & 3) == 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            if (j >= r) continue;
+            const size_t row = (size_t)sK * R2 + (size_t)k * r + j;
+            if (vec_st) z_store4<MODE, T>(o, which, row, col0, acc[u]);
+            else
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (s0 + v < r) z_store<T>(o, which, row, col0 + v, acc[u][v]);
+            if (dslot >= 0 && j == p)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (s0 + v < r) ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s0 + v] = acc[u][v];
+        }
     }
+    cp_async_wait_all();
 }
 
 // w_a[k][s] = sum_p (Zd(a,a)[(k,p)][(p,s)] - Zf1[(k,p)][(p,s)]),  w_b likewise with Zd(b,b), Zf2
 // (= sum_pq Waa[k][p][q][s] ga[p][q] - sum_pq Wab[k][p][s][q] gb[p][q], and the b analogue).
+// One block per (spin, k): warp w sums p = w, w + 8, ...; lanes over s; the 8 partials are added
+// in a fixed order.
 template <typename T>
-__global__ void k_w_from_diag(int r, const T* __restrict__ diag, T* __restrict__ wout) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_w_from_diag(int r, const T* __restrict__ diag, T* __restrict__ wout) {
+    __shared__ T part[8][ACSE_MAX_R];
     const int R2 = r * r;
-    if (e >= 2 * R2) return;
-    const int sp = e / R2, k = (e / r) % r, s = e % r;
+    const int sp = blockIdx.x / r, k = blockIdx.x % r;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const T* d0 = diag + (size_t)(sp == 0 ? 0 : 1) * R2 * r;
     const T* d1 = diag + (size_t)(sp == 0 ? 2 : 3) * R2 * r;
-    T acc = 0;
-    for (int p = 0; p < r; ++p) acc += d0[((size_t)k * r + p) * r + s] - d1[((size_t)k * r + p) * r + s];
-    wout[e] = acc;
+    for (int s = lane; s < r; s += 32) {
+        T acc = 0;
+        for (int p = w; p < r; p += 8) acc += d0[((size_t)k * r + p) * r + s] - d1[((size_t)k * r + p) * r + s];
+        part[w][s] = acc;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < r; s += blockDim.x) {
+        T acc = 0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) acc += part[g][s];
+        wout[(size_t)sp * R2 + (size_t)k * r + s] = acc;
+    }
 }
 
 // ------------------------------------------------------------------------- B -> H
@@ -380,27 +441,348 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
     }
 }
 
+// ------------------------------------------------------------- B -> H, split-precision path
+// Persistent variant for FP32: each block walks pairs (i, j) with a stride of the grid and, per pair,
+// three rounds (aa: type 0, bb: type 1, ab: types 2 and 3).  A round's X and M rows are copied into
+// shared memory (cp.async) while the previous round is computed.  1D (as [p][l]) and w (as w^T[p][k])
+// of both spins are loaded once per block.  Within a type, the warps of group 1 (threads [0, S),
+// S = nt^2 rounded up to a warp) own 4 x 4 tiles of x1 and the warps of group 2 (threads
+// [S, S + nt^2)) own tiles of x2, so no warp runs both products; each product uses the tile
+// ownership that makes all of its shared loads 16-byte vectors without bank conflicts:
+//   RR (A as [k][q], B as [q][l]): rows k = kb + nt a, columns l = 4 lb + b, four q per step
+//   CR (A as [q][k], B as [q][l]): k = 4 kb + a, l = 4 lb + b, one q per step
+//   CC (A as [q][k], B as [l][q]): k = 4 kb + a, l = lb + nt b, four q per step
+// x2 threads also gather x4, x5, x7, x8 (loads issued before their product) and store
+// (-2 sgn2 x2 - x4 + 2 x5 + x7 - 2 x8) / 9 into Bs; after a barrier x1 threads add sgn1 x1 / 9.
+// Each thread's share of the Y row of the round is loaded into registers at the start of the round
+// and used when H is formed at its end.
+#define BP_MAX_THREADS 512   // r = 64: S = 256, 256 + 256 threads
+
+template <int KIND>
+__device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, const float* B, int ld, int r, int rp,
+                                           int nt, int kb, int lb) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    if (KIND == 0) {   // RR
+        for (int q = 0; q < rp; q += 4) {
+            float av[4][4], bv[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) ld4(A + (kb + nt * a) * ld + q, av[a]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ld4(B + (q + u) * ld + 4 * lb, bv[u]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += av[a][u] * bv[u][b];
+        }
+    } else if (KIND == 1) {   // CR
+#pragma unroll 4
+        for (int q = 0; q < r; ++q) {
+            float av[4], bv[4];
+            ld4(A + q * ld + 4 * kb, av);
+            ld4(B + q * ld + 4 * lb, bv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+    } else {   // CC
+        for (int q = 0; q < rp; q += 4) {
+            float av[4][4], bv[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ld4(A + (q + u) * ld + 4 * kb, av[u]);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ld4(B + (lb + nt * b) * ld + q, bv[b]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += av[u][a] * bv[b][u];
+        }
+    }
+}
+
+// Output coordinates of element (a, b) of a thread's tile for ownership KIND.
+__device__ __forceinline__ int bp_k(int kind, int kb, int nt, int a) { return kind == 0 ? kb + nt * a : 4 * kb + a; }
+__device__ __forceinline__ int bp_l(int kind, int lb, int nt, int b) { return kind == 2 ? lb + nt * b : 4 * lb + b; }
+
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ BTiledArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    const int r = a.r, rp = pad4(r), ld = rp + 4, R2 = r * r, bpitch = r + 1;
+    const int nt = rp / 4, nt2 = nt * nt, S = (nt2 + 31) & ~31;
+    const size_t tile = (size_t)rp * ld;
+    float* gA = (float*)tl_smem;          // 1D_a [p][l]
+    float* gB = gA + tile;                // 1D_b
+    float* wAT = gB + tile;               // w_a^T [p][k]
+    float* wBT = wAT + tile;              // w_b^T
+    float* buf = wBT + tile;              // [2][X, M] operand tiles, element (u, v) of a row at u * ld + v
+    float* Bs = buf + 4 * tile;           // [2][r][r + 1]
+    const size_t R22 = 2 * (size_t)R2;
+    for (int e = threadIdx.x; e < 8 * (int)tile; e += blockDim.x) gA[e] = 0.f;
+    __syncthreads();
+    for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+        const int u = e / r, v = e - u * r;
+        gA[u * ld + v] = a.gam[e];
+        gB[u * ld + v] = a.gam[R2 + e];
+        wAT[v * ld + u] = a.w[e];          // w[k][p] -> w^T[p][k]
+        wBT[v * ld + u] = a.w[R2 + e];
+    }
+    const bool vec = (r & 3) == 0;
+    const bool yvec = (r & 1) == 0;
+    const int npairs_me = blockIdx.x < R2 ? (R2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int nsteps = 3 * npairs_me;
+    // operands of step s = 3 n + round (pair blockIdx.x + n gridDim.x): X and M rows of sector
+    // round 0 -> aa (0), round 1 -> bb (2), round 2 -> ab (1)
+    auto issue = [&](int step, int slot) {
+        const int n = step / 3, round = step - 3 * n;
+        const size_t ij = (size_t)blockIdx.x + (size_t)n * gridDim.x;
+        const int sec = round == 0 ? 0 : round == 1 ? 2 : 1;
+        const float* src[2] = {a.X[sec] + ij * R2, a.M[sec] + ij * R2};
+        for (int h = 0; h < 2; ++h) {
+            float* dst = buf + (size_t)(2 * slot + h) * tile;
+            if (vec) {
+                const int c4 = r / 4;
+                for (int e = threadIdx.x; e < r * c4; e += blockDim.x) {
+                    const int u = e / c4, v = (e - u * c4) * 4;
+                    cp_async16(dst + u * ld + v, src[h] + u * r + v);
+                }
+            } else {
+                for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+                    const int u = e / r, v = e - u * r;
+                    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + u * ld + v);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src[h] + e) : "memory");
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    if (nsteps > 0) issue(0, 0);
+    const int grp = threadIdx.x < S ? 0 : (threadIdx.x < S + nt2 ? 1 : 2);   // x1, x2, idle
+    const int idx = grp == 0 ? threadIdx.x : threadIdx.x - S;
+    const bool active = grp == 0 ? idx < nt2 : grp == 1;
+    const int kb = idx / nt, lb = idx - (idx / nt) * nt;
+    constexpr int YPT = 2;                         // float4 groups of the Y row held per thread
+    for (int step = 0; step < nsteps; ++step) {
+        const int n = step / 3, round = step - 3 * n;
+        const int ij = blockIdx.x + n * gridDim.x;
+        const int i = ij / r, j = ij - (ij / r) * r;
+        const int cur = step & 1;
+        const int b = round == 0 ? 0 : round == 1 ? 2 : 1;
+        cp_async_wait_all();
+        __syncthreads();                                    // operands landed; Bs and the other buffer free
+        if (step + 1 < nsteps) issue(step + 1, cur ^ 1);
+        // this thread's part of the Y row (used when H is formed at the end of the round)
+        const float* Yrow = a.Y[b] + (size_t)ij * R2;
+        float4 yv[YPT];
+        if (yvec) {
+#pragma unroll
+            for (int u = 0; u < YPT; ++u) {
+                const int g = threadIdx.x + u * blockDim.x;
+                yv[u] = g < R2 / 4 ? reinterpret_cast<const float4*>(Yrow)[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        const float* Xs = buf + (size_t)(2 * cur) * tile;
+        const float* Ms = Xs + tile;
+        const int ntypes = round < 2 ? 1 : 2;
+        for (int tt = 0; tt < ntypes; ++tt) {
+            const int t = round < 2 ? round : 2 + tt;
+            float* Bt = Bs + (size_t)tt * r * bpitch;
+            float x1[4][4];
+            if (grp == 1) {
+                // x2 = sum_p w[k][p] M(l, p) (types 0, 1, 3: M row holds M[l][p]; type 2: M[p][l]),
+                // plus the gathered terms of B
+                const int kind = t == 2 ? 1 : 2;
+                const float* X5b;
+                const float* X8b;
+                size_t ld5, ld8;
+                if (t == 0) { X5b = X8b = a.X5d; ld5 = ld8 = R22; }
+                else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
+                else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
+                else { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
+                const float* ga = a.gam;
+                const float* gb = a.gam + R2;
+                const float* Qa = a.Q;
+                const float* Qb = a.Q + R2;
+                const float* Q4 = t == 0 ? Qa : t == 1 ? Qb : t == 2 ? Qa : nullptr;
+                const float* g4 = t == 0 ? ga : t == 1 ? gb : t == 2 ? gb : nullptr;
+                const float* Q7 = t == 0 ? Qa : t == 1 ? Qb : t == 3 ? Qb : nullptr;
+                const float* g7 = t == 0 ? ga : t == 1 ? gb : t == 3 ? ga : nullptr;
+                float rest[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = bp_k(kind, kb, nt, u);
+                    const int kc = k < r ? k : r - 1;
+                    const float q4 = Q4 ? Q4[kc * r + i] : 0.f;
+                    const float q7 = Q7 ? Q7[kc * r + j] : 0.f;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int l = bp_l(kind, lb, nt, v);
+                        const int lc = l < r ? l : r - 1;
+                        const float x4 = Q4 ? q4 * g4[j * r + lc] : 0.f;
+                        const float x7 = Q7 ? q7 * g7[i * r + lc] : 0.f;
+                        const float x5 = X5b[((size_t)kc * r + j) * ld5 + (size_t)i * r + lc];
+                        const float x8 = X8b[((size_t)kc * r + i) * ld8 + (size_t)j * r + lc];
+                        rest[u][v] = -x4 + 2.f * x5 + x7 - 2.f * x8;
+                    }
+                }
+                float acc[4][4];
+                const float* wT = (t == 0 || t == 2) ? wAT : wBT;
+                if (kind == 1) bp_product<1>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                else bp_product<2>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                const float c2 = t == 2 ? 2.f : -2.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = bp_k(kind, kb, nt, u);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int l = bp_l(kind, lb, nt, v);
+                        if (k < r && l < r) Bt[k * bpitch + l] = (c2 * acc[u][v] + rest[u][v]) * (1.f / 9.f);
+                    }
+                }
+            } else if (grp == 0 && active) {
+                const float* g1 = (t == 0 || t == 3) ? gA : gB;
+                if (t == 3) bp_product<1>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                else bp_product<0>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+            }
+            __syncthreads();                                // x2 and gathered parts in Bt
+            if (grp == 0 && active) {
+                const int kind1 = t == 3 ? 1 : 0;
+                const float s1 = (t == 3 ? -1.f : 1.f) / 9.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = bp_k(kind1, kb, nt, u);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int l = 4 * lb + v;
+                        if (k < r && l < r) Bt[k * bpitch + l] += s1 * x1[u][v];
+                    }
+                }
+            }
+        }
+        __syncthreads();                                    // B types of this round complete
+        const float* P = Bs;
+        const float* Px = round < 2 ? Bs : Bs + (size_t)r * bpitch;
+        float* Hrow = a.H[b] + (size_t)ij * R2;
+        if (yvec) {
+#pragma unroll
+            for (int u = 0; u < YPT; ++u) {
+                const int g = threadIdx.x + u * blockDim.x;
+                if (g < R2 / 4) {
+                    const float yy[4] = {yv[u].x, yv[u].y, yv[u].z, yv[u].w};
+                    float hh[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int e = 4 * g + c, k = e / r, l = e - k * r;
+                        hh[c] = 4.f * yy[c] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                    }
+                    reinterpret_cast<float4*>(Hrow)[g] = make_float4(hh[0], hh[1], hh[2], hh[3]);
+                }
+            }
+            for (int g = threadIdx.x + YPT * blockDim.x; g < R2 / 4; g += blockDim.x) {   // rows beyond the prefetch
+                const float4 y4 = reinterpret_cast<const float4*>(Yrow)[g];
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+                float hh[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int e = 4 * g + c, k = e / r, l = e - k * r;
+                    hh[c] = 4.f * yy[c] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                }
+                reinterpret_cast<float4*>(Hrow)[g] = make_float4(hh[0], hh[1], hh[2], hh[3]);
+            }
+        } else {
+            for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+                const int k = e / r, l = e - k * r;
+                Hrow[e] = 4.f * Yrow[e] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+static size_t bp_smem(int r) {
+    const size_t rp = pad4(r), tile = rp * (rp + 4);
+    return (8 * tile + 2 * (size_t)r * (r + 1)) * sizeof(float);
+}
+
 // ------------------------------------------------------------------------------- launch
+// Launch shape of k_Z_pipe: ipb slices per round (ipb * (rp/4)^2 <= ZP_MAX_THREADS threads, at most 4) and
+// the p-chunk per block, chosen to balance the waves over the SMs (a block's first slices are not
+// overlapped, hence the +1 round per block).
+struct ZPlan {
+    int ipb, threads, pchunk, blocks;
+    size_t smem;
+};
+static ZPlan z_plan_compute(int r, size_t es, const void* kern) {
+    ZPlan z;
+    const int rp = pad4(r), nt = rp / 4, nt2 = nt * nt;
+    z.ipb = ZP_MAX_THREADS / nt2;
+    if (z.ipb > 4) z.ipb = 4;
+    if (z.ipb < 1) z.ipb = 1;
+    z.threads = (z.ipb * nt2 + 31) / 32 * 32;
+    const int R2e = (r * r + 1) & ~1;
+    z.smem = (size_t)z.ipb * R2e * sizeof(double) + (size_t)(1 + z.ipb) * rp * (rp + 4) * es;
+    int per_sm = 1, nsm = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, z.threads, z.smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long slots = (long)nsm * per_sm;
+    double best = 1e30;
+    z.pchunk = r;
+    for (int pc = z.ipb; pc <= r; pc += z.ipb) {
+        const long blocks = 6L * r * ((r + pc - 1) / pc);
+        const double cost = (double)((blocks + slots - 1) / slots) * ((pc + z.ipb - 1) / z.ipb + 1);
+        if (cost < best - 1e-9) { best = cost; z.pchunk = pc; }
+    }
+    z.blocks = 6 * r * ((r + z.pchunk - 1) / z.pchunk);
+    return z;
+}
+
+// cached per host thread, output mode and r (the occupancy query is not free)
+static ZPlan z_plan(int r, int mode, size_t es, const void* kern) {
+    static thread_local int cached_r[4] = {-1, -1, -1, -1};
+    static thread_local ZPlan cached[4];
+    if (cached_r[mode] != r) {
+        cached[mode] = z_plan_compute(r, es, kern);
+        cached_r[mode] = r;
+    }
+    return cached[mode];
+}
+
 int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
-    const int r = c->r, rp = pad4(r);
+    const int r = c->r;
     ZOut o;
     Work& w = c->w;
     const int R2 = r * r;
     if (c->opt.prec == ACSE_FP64) {
         o.Zd = w.Zd; o.Zf[0] = w.Zf1; o.Zf[1] = w.Zf2;
         o.mode = 0; o.ldd = 2 * R2; o.ldf = R2; o.Kp1 = o.Kp2 = 0; o.diag = w.zdiag;
-        k_Z_tiled<double><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 3 * rp * rp * sizeof(double), c->stream>>>(
-            r, W[0], W[1], W[2], w.gam, o);
+        const ZPlan zp = z_plan(r, 0, sizeof(double), (const void*)k_Z_pipe<0>);
+        k_Z_pipe<0><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
-        k_w_from_diag<double><<<(2 * R2 + 127) / 128, 128, 0, c->stream>>>(r, w.zdiag, w.w);
+        k_w_from_diag<double><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag, w.w);
     } else {
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
-        o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : 2;
+        o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : (c->opt.prec == ACSE_TF32X3 ? 3 : 2);
         o.ldd = c->nsplit * w.Kp2; o.ldf = c->nsplit * w.Kp1; o.Kp1 = w.Kp1; o.Kp2 = w.Kp2; o.diag = w.zdiag32;
-        k_Z_tiled<float><<<6 * r * ((r + Z_PCH - 1) / Z_PCH), TL_TPB, 3 * rp * rp * sizeof(float), c->stream>>>(
-            r, W[0], W[1], W[2], w.gam, o);
+        const void* kern = o.mode == 1 ? (const void*)k_Z_pipe<1> : o.mode == 3 ? (const void*)k_Z_pipe<3>
+                                                                                : (const void*)k_Z_pipe<2>;
+        const ZPlan zp = z_plan(r, o.mode, sizeof(float), kern);
+        if (o.mode == 1)
+            k_Z_pipe<1><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        else if (o.mode == 3)
+            k_Z_pipe<3><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        else
+            k_Z_pipe<2><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
-        k_w_from_diag<float><<<(2 * R2 + 127) / 128, 128, 0, c->stream>>>(r, w.zdiag32, w.w32);
+        k_w_from_diag<float><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag32, w.w32);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -436,7 +818,24 @@ int launch_B_tiled(acse_ctx* c) {
         }
         a.X5d = w.tc_X5d; a.X5f1 = w.tc_X5f[0]; a.X5f2 = w.tc_X5f[1];
         a.gam = w.gam32; a.w = w.w32; a.Q = w.Q32;
-        k_B_tiled<float, true><<<R2, TL_TPB, b_smem(r, sizeof(float), true), c->stream>>>(a);
+        static thread_local int cached_r = -1, cached_grid = 0;
+        const int nt2 = (pad4(r) / 4) * (pad4(r) / 4);
+        const int threads = (((nt2 + 31) & ~31) + nt2 + 31) / 32 * 32;
+        const bool small = threads <= 320;
+        const void* kern = small ? (const void*)k_B_pipe<320, 2> : (const void*)k_B_pipe<BP_MAX_THREADS, 1>;
+        if (cached_r != r) {
+            int per_sm = 1, nsm = 152, dev = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, bp_smem(r)) != cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            cached_grid = nsm * per_sm < R2 ? nsm * per_sm : R2;
+            cached_r = r;
+        }
+        if (small) k_B_pipe<320, 2><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
+        else k_B_pipe<BP_MAX_THREADS, 1><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -447,11 +846,13 @@ int tiled_set_attrs() {
                                        (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)b_smem(ACSE_MAX_R, sizeof(float), true)));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       3 * ACSE_MAX_R * ACSE_MAX_R * (int)sizeof(double)));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       3 * ACSE_MAX_R * ACSE_MAX_R * (int)sizeof(float)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bp_smem(48)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<BP_MAX_THREADS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bp_smem(ACSE_MAX_R)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     return ACSE_OK;
 }

@@ -468,7 +468,7 @@ int tc_plan_create(acse_ctx* c) {
     c->tc_plan = pl;
     ACSE_TRY(get_encode(&pl->encode));
     ACSE_TRY(tc_mixed_alloc(c));
-    ACSE_TRY(tc_table_init(&pl->tab, c->opt.prec == ACSE_TF32 ? 1 : 0, tc_default_bn(c->r)));
+    ACSE_TRY(tc_table_init(&pl->tab, (c->opt.prec == ACSE_TF32 || c->opt.prec == ACSE_TF32X3) ? 1 : 0, tc_default_bn(c->r)));
     ACSE_TRY(tc_table_append(&pl->tab, c));
     return tc_table_upload(&pl->tab);
 }
