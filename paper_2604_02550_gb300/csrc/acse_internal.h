@@ -47,6 +47,8 @@ struct TcTable {
     int bn;          // tile width
     int stages;
     size_t smem;
+    int pers;        // 1: persistent kernel (one CTA per SM, double-buffered TMEM accumulators)
+    int nsm;         // multiprocessors of the device (grid of the persistent kernel)
 };
 int tc_table_init(TcTable* t, int kind, int bn);
 void tc_table_free(TcTable* t);
@@ -123,6 +125,7 @@ struct acse_ctx {
     Work w;
     void* tc_plan;        // tensor-core GEMM plan (tensor maps etc.)
     void* adj;            // adjoint workspace (allocated by the first acse_residual_backward call)
+    struct acse_ctx* shadow;   // FP64 companion of a split-precision context (its adjoint), or null
     const double* cur_D[3];   // operands of the contraction pass in flight (FP64 GEMM list)
     const double* cur_W[3];
     // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches

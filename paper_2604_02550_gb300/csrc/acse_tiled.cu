@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
     const int pb = (rem - k * nchunk) * pchunk;
     const int pe = min(r, pb + pchunk);
     const double* g = gam + ((t == 2 || t == 3 || t == 4) ? R2 : 0);
+    // (int)((e + 1/2) / r) = e / r for e < r^2: the fraction stays at least 1/(2r) from an integer
+    const float invr = 1.f / (float)r;
     const bool vec_ld = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(Waa) | reinterpret_cast<uintptr_t>(Wab) |
                                           reinterpret_cast<uintptr_t>(Wbb)) & 15) == 0;
     for (int e = threadIdx.x; e < (1 + ipb) * rp * ldw; e += blockDim.x) gT[e] = (T)0;
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
             const double* st = stage + (size_t)it * R2e;
             T* W = Ws + (size_t)it * rp * ldw;
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-                const int u = e / r, v = e - u * r;
+                const int u = (int)(((float)e + 0.5f) * invr), v = e - u * r;   // e / r, see invr
                 const T x = (T)st[e];
                 if (tr) W[v * ldw + u] = x;                // src[s][q] -> W[q][s]
                 else W[u * ldw + v] = x;
@@ -452,8 +454,9 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
 //   RR (A as [k][q], B as [q][l]): rows k = kb + nt a, columns l = 4 lb + b, four q per step
 //   CR (A as [q][k], B as [q][l]): k = 4 kb + a, l = 4 lb + b, one q per step
 //   CC (A as [q][k], B as [l][q]): k = 4 kb + a, l = lb + nt b, four q per step
-// x2 threads also gather x4, x5, x7, x8 (loads issued before their product) and store
-// (-2 sgn2 x2 - x4 + 2 x5 + x7 - 2 x8) / 9 into Bs; after a barrier x1 threads add sgn1 x1 / 9.
+// x2 threads also gather x5, x8 (loads issued before their product) and store
+// (-2 sgn2 x2 + 2 x5 - 2 x8) / 9 into Bs; x1 threads form x7 - x4 before their product and, after a
+// barrier, add (sgn1 x1 - x4 + x7) / 9.
 // Each thread's share of the Y row of the round is loaded into registers at the start of the round
 // and used when H is formed at its end.
 #define BP_MAX_THREADS 512   // r = 64: S = 256, 256 + 256 threads
@@ -535,6 +538,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
     }
     const bool vec = (r & 3) == 0;
     const bool yvec = (r & 1) == 0;
+    // row index of a flat index e < r^2 as (int)((e + 1/2) / r): the fraction stays at least 1/(2r)
+    // away from an integer, far above the float rounding of the product for r <= 64
+    const float invr = 1.f / (float)r;
     const int npairs_me = blockIdx.x < R2 ? (R2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int nsteps = 3 * npairs_me;
     // operands of step s = 3 n + round (pair blockIdx.x + n gridDim.x): X and M rows of sector
@@ -548,8 +554,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             float* dst = buf + (size_t)(2 * slot + h) * tile;
             if (vec) {
                 const int c4 = r / 4;
+                const float inv_c4 = 4.f / (float)r;
                 for (int e = threadIdx.x; e < r * c4; e += blockDim.x) {
-                    const int u = e / c4, v = (e - u * c4) * 4;
+                    const int u = (int)(((float)e + 0.5f) * inv_c4), v = (e - u * c4) * 4;
                     cp_async16(dst + u * ld + v, src[h] + u * r + v);
                 }
             } else {
@@ -605,30 +612,18 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
                 else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
                 else { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
-                const float* ga = a.gam;
-                const float* gb = a.gam + R2;
-                const float* Qa = a.Q;
-                const float* Qb = a.Q + R2;
-                const float* Q4 = t == 0 ? Qa : t == 1 ? Qb : t == 2 ? Qa : nullptr;
-                const float* g4 = t == 0 ? ga : t == 1 ? gb : t == 2 ? gb : nullptr;
-                const float* Q7 = t == 0 ? Qa : t == 1 ? Qb : t == 3 ? Qb : nullptr;
-                const float* g7 = t == 0 ? ga : t == 1 ? gb : t == 3 ? ga : nullptr;
                 float rest[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = bp_k(kind, kb, nt, u);
                     const int kc = k < r ? k : r - 1;
-                    const float q4 = Q4 ? Q4[kc * r + i] : 0.f;
-                    const float q7 = Q7 ? Q7[kc * r + j] : 0.f;
+                    const float* x5r = X5b + ((size_t)kc * r + j) * ld5 + (size_t)i * r;
+                    const float* x8r = X8b + ((size_t)kc * r + i) * ld8 + (size_t)j * r;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int l = bp_l(kind, lb, nt, v);
                         const int lc = l < r ? l : r - 1;
-                        const float x4 = Q4 ? q4 * g4[j * r + lc] : 0.f;
-                        const float x7 = Q7 ? q7 * g7[i * r + lc] : 0.f;
-                        const float x5 = X5b[((size_t)kc * r + j) * ld5 + (size_t)i * r + lc];
-                        const float x8 = X8b[((size_t)kc * r + i) * ld8 + (size_t)j * r + lc];
-                        rest[u][v] = -x4 + 2.f * x5 + x7 - 2.f * x8;
+                        rest[u][v] = 2.f * (x5r[lc] - x8r[lc]);
                     }
                 }
                 float acc[4][4];
@@ -653,14 +648,27 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             __syncthreads();                                // x2 and gathered parts in Bt
             if (grp == 0 && active) {
                 const int kind1 = t == 3 ? 1 : 0;
-                const float s1 = (t == 3 ? -1.f : 1.f) / 9.f;
+                const float s1 = t == 3 ? -1.f : 1.f;
+                // x7 - x4 = Q7[k][j] g7[i][l] - Q4[k][i] g4[j][l] (zero where a type has no such term)
+                const float* ga = a.gam;
+                const float* gb = a.gam + R2;
+                const float* Q4 = t == 0 ? a.Q : t == 1 ? a.Q + R2 : t == 2 ? a.Q : nullptr;
+                const float* g4 = t == 0 ? ga : t == 1 ? gb : t == 2 ? gb : nullptr;
+                const float* Q7 = t == 0 ? a.Q : t == 1 ? a.Q + R2 : t == 3 ? a.Q + R2 : nullptr;
+                const float* g7 = t == 0 ? ga : t == 1 ? gb : t == 3 ? ga : nullptr;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = bp_k(kind1, kb, nt, u);
+                    if (k >= r) continue;
+                    const float q4 = Q4 ? Q4[k * r + i] : 0.f;
+                    const float q7 = Q7 ? Q7[k * r + j] : 0.f;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int l = 4 * lb + v;
-                        if (k < r && l < r) Bt[k * bpitch + l] += s1 * x1[u][v];
+                        if (l < r) {
+                            const float x47 = (Q7 ? q7 * g7[i * r + l] : 0.f) - (Q4 ? q4 * g4[j * r + l] : 0.f);
+                            Bt[k * bpitch + l] += (s1 * x1[u][v] + x47) * (1.f / 9.f);
+                        }
                     }
                 }
             }
@@ -676,10 +684,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 if (g < R2 / 4) {
                     const float yy[4] = {yv[u].x, yv[u].y, yv[u].z, yv[u].w};
                     float hh[4];
+                    int k = (int)(((float)(4 * g) + 0.5f) * invr), l = 4 * g - k * r;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const int e = 4 * g + c, k = e / r, l = e - k * r;
                         hh[c] = 4.f * yy[c] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                        if (++l == r) { l = 0; ++k; }
                     }
                     reinterpret_cast<float4*>(Hrow)[g] = make_float4(hh[0], hh[1], hh[2], hh[3]);
                 }
@@ -688,10 +697,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 const float4 y4 = reinterpret_cast<const float4*>(Yrow)[g];
                 const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
                 float hh[4];
+                int k = (int)(((float)(4 * g) + 0.5f) * invr), l = 4 * g - k * r;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int e = 4 * g + c, k = e / r, l = e - k * r;
                     hh[c] = 4.f * yy[c] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                    if (++l == r) { l = 0; ++k; }
                 }
                 reinterpret_cast<float4*>(Hrow)[g] = make_float4(hh[0], hh[1], hh[2], hh[3]);
             }

@@ -324,6 +324,187 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const TcBatch* __rest
     }
 }
 
+// ------------------------------------------------------------------ persistent variant
+// One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (the table lists the
+// largest-K problem first).  The shared-memory ring runs on across tiles (a global K-block counter
+// gives stage and phase), and the accumulator is double-buffered in TMEM (2 x BN columns): the MMA
+// thread fills buffer (tile & 1) while warps 2-5 drain the other one, so a tile's epilogue and the
+// next tile's first loads and MMAs overlap.  Barriers: full/empty per stage, accf[2] (MMA -> epilogue,
+// one commit per tile), acce[2] (epilogue -> MMA, one arrival per epilogue warp).  All waits are
+// bounded as in k_gemm_tc; at the end the MMA thread commits to drainb and waits for it, so no MMA is
+// in flight when TMEM is freed.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ int tc_find_problem(const TcBatch& b, int t) {
+    int lo = 0, hi = b.nprob - 1;   // last problem with tile_start <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.p[mid].tile_start <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* __restrict__ bp) {
+    const TcBatch& b = *bp;
+    constexpr int A_BYTES = TC_BM * 128;
+    constexpr int B_BYTES = BN * 128;
+    constexpr int KELEM = KIND == 0 ? 64 : 32;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;   // [2]
+    uint64_t* acce = accf + 2;         // [2]
+    uint64_t* never = acce + 2;
+    uint64_t* drainb = never + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drainb + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = b.total_tiles;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], 4);
+        }
+        mbar_init(never, 1);
+        mbar_init(drainb, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                const int pi = tc_find_problem(b, t);
+                const TcProb& P = b.p[pi];
+                const int local = t - P.tile_start;
+                const int m0 = (local / P.tiles_n) * TC_BM;
+                const int n0 = (local % P.tiles_n) * BN;
+                for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !bounded_wait(&empty[s], ((it / STAGES) & 1) ^ 1, b.wait_ns, abort_flag)) {
+                        raise_abort(b.err, abort_flag);
+                        stop = true;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                    tma_load_2d(sA + s * A_BYTES, &b.tmA[pi], kb * KELEM, m0, &full[s]);
+                    tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], kb * KELEM, n0, &full[s]);
+                }
+            }
+            // every issued copy must have landed before the CTA may exit
+            for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k)
+                if (!bounded_wait(&full[k % STAGES], (k / STAGES) & 1, TC_DRAIN_NS, nullptr))
+                    raise_abort(b.err, abort_flag);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc<KIND, BN>();
+            if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
+            int it = 0, lt = 0;
+            for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x, ++lt) {
+                const int pi = tc_find_problem(b, t);
+                const int nk = b.p[pi].kblocks;
+                const int ab = lt & 1, use = lt >> 1;
+                if (use >= 1 && !bounded_wait(&acce[ab], (use - 1) & 1, b.wait_ns + TC_DRAIN_NS, abort_flag)) {
+                    raise_abort(b.err, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(ab * BN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!bounded_wait(&full[s], (it / STAGES) & 1, b.wait_ns, abort_flag)) {
+                        raise_abort(b.err, abort_flag);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = smem_desc(sA + s * A_BYTES);
+                    const uint64_t db = smem_desc(sB + s * B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) umma<KIND>(acc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(&accf[ab]);   // the epilogue of this tile may start when these MMAs are done
+            }
+            umma_commit(drainb);
+            if (!bounded_wait(drainb, 0, TC_DRAIN_NS, nullptr)) raise_abort(b.err, abort_flag);
+        }
+    } else {
+        const int q = warp & 3;   // TMEM lane quadrant this warp may access
+        int lt = 0;
+        for (int t = blockIdx.x; t < T; t += gridDim.x, ++lt) {
+            const int ab = lt & 1, use = lt >> 1;
+            // lane 0 waits and the warp follows its verdict (tcgen05.ld below is warp-collective)
+            int go = 0;
+            if (lane == 0) {
+                const bool ok = bounded_wait(&accf[ab], use & 1, b.wait_ns + TC_DRAIN_NS, abort_flag);
+                if (!ok) raise_abort(b.err, abort_flag);
+                go = ok && !*abort_flag;
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) break;
+            tc_fence_after();
+            const int pi = tc_find_problem(b, t);
+            const TcProb& P = b.p[pi];
+            const int local = t - P.tile_start;
+            const int m0 = (local / P.tiles_n) * TC_BM;
+            const int n0 = (local % P.tiles_n) * BN;
+            const int row = m0 + q * 32 + lane;
+            float* Crow = P.C + (size_t)row * P.ldc;
+            const bool vec = (P.ldc & 3) == 0;
+            const bool store = P.kblocks > 0;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                __syncwarp();
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);   // warp-collective
+                const int col0 = n0 + c * 32;
+                if (store && row < P.M && col0 < P.N) {
+                    if (vec && col0 + 32 <= P.N) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            float4 o = make_float4(P.alpha * __uint_as_float(v[j]), P.alpha * __uint_as_float(v[j + 1]),
+                                                   P.alpha * __uint_as_float(v[j + 2]),
+                                                   P.alpha * __uint_as_float(v[j + 3]));
+                            *reinterpret_cast<float4*>(Crow + col0 + j) = o;
+                        }
+                    } else {
+                        for (int j = 0; j < 32 && col0 + j < P.N; ++j) Crow[col0 + j] = P.alpha * __uint_as_float(v[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[ab]);   // this warp's quarter of the buffer is free
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
 // --------------------------------------------------------------------------- host plan
 // A table (TcTable, acse_internal.h) holds the problems of one grouped launch; its TcBatch lives in
 // device memory (the tensor maps are written by the host before any launch reads them).
@@ -339,6 +520,9 @@ static size_t smem_for(int bn, int stages) { return (size_t)stages * (TC_BM + bn
 template <int KIND, int BN>
 static int set_attr() {
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<KIND, BN, BN == 256 ? 4 : 6>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_for(BN, stages_for(BN))));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_pers<KIND, BN, BN == 256 ? 4 : 6>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_for(BN, stages_for(BN))));
     return ACSE_OK;
@@ -384,6 +568,14 @@ int tc_table_init(TcTable* t, int kind, int bn) {
     t->smem = smem_for(bn, t->stages);
     if (kind == 0) ACSE_TRY(bn == 256 ? (set_attr<0, 256>()) : (set_attr<0, 128>()));
     else ACSE_TRY(bn == 256 ? (set_attr<1, 256>()) : (set_attr<1, 128>()));
+    t->pers = 1;
+    t->nsm = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        t->nsm = 152;
+    }
     t->host = (TcBatch*)calloc(1, sizeof(TcBatch));
     if (!t->host) return ACSE_ERR_NOMEM;
     t->host->wait_ns = TC_WAIT_NS;
@@ -444,6 +636,18 @@ int tc_table_append(TcTable* t, acse_ctx* c) {
 int tc_table_launch(const TcTable* t, cudaStream_t st) {
     const int tiles = t->host->total_tiles;
     if (tiles == 0) return ACSE_OK;
+    if (t->pers) {
+        const int g = tiles < t->nsm ? tiles : t->nsm;
+        if (t->kind == 0) {
+            if (t->bn == 256) k_gemm_tc_pers<0, 256, 4><<<g, TC_THREADS, t->smem, st>>>(t->dev);
+            else k_gemm_tc_pers<0, 128, 6><<<g, TC_THREADS, t->smem, st>>>(t->dev);
+        } else {
+            if (t->bn == 256) k_gemm_tc_pers<1, 256, 4><<<g, TC_THREADS, t->smem, st>>>(t->dev);
+            else k_gemm_tc_pers<1, 128, 6><<<g, TC_THREADS, t->smem, st>>>(t->dev);
+        }
+        ACSE_CUDA_TRY(cudaGetLastError());
+        return ACSE_OK;
+    }
     if (t->kind == 0) {
         if (t->bn == 256) k_gemm_tc<0, 256, 4><<<tiles, TC_THREADS, t->smem, st>>>(t->dev);
         else k_gemm_tc<0, 128, 6><<<tiles, TC_THREADS, t->smem, st>>>(t->dev);
