@@ -118,7 +118,10 @@ int acse_step(acse_ctx* ctx, double* Daa, double* Dab, double* Dbb, double eps,
  * NULL except D_0; missing ones are recomputed from the previous one).  dh and dV are
  * symmetrised (h: p<->q; V: the 8-fold permutational symmetry); dD is projected onto tensors
  * with the symmetries of a 2-RDM (antisymmetric within pairs, pair-Hermitian).  Each output
- * may be NULL. */
+ * may be NULL.  The reverse sweep always runs in FP64; for a context in a split precision it runs
+ * in an FP64 companion context the library creates on first use (same integrals and options), so
+ * the gradient is the FP64 adjoint along the trajectory the checkpoints describe: pass every
+ * checkpoint of the split-precision forward run (checkpoints left NULL are recomputed in FP64). */
 int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_steps, double eps,
                            double wE, double wN, double* dh, double* dV,
                            double* dDaa, double* dDab, double* dDbb);

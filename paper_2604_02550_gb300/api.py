@@ -78,3 +78,48 @@ class ACSE:
             flat.extend(blk if blk is not None else (None, None, None))
         _lib.acse_residual_backward(self.ctx, flat, n_steps, eps, wE, wN, dh, dV, *dD)
         return dh, dV, dD
+
+
+class ACSEObjective(torch.autograd.Function):
+    """f = wE E(D_n) + wN ||A(D_n)||^2 after n fixed Euler steps from D_0, differentiable with respect
+    to h, V and the three blocks of D_0 through the library's adjoint (acse_residual_backward).
+
+    forward(h, V, Daa, Dab, Dbb, n_alpha, n_beta, prec, nsteps, eps, wE, wN): h (r, r) and V
+    (r, r, r, r) float64 device tensors, D_0 blocks (r, r, r, r); returns a 0-d float64 tensor.
+    Every step's D is kept as a checkpoint (n + 1 triples of r^4 doubles), so the reverse sweep
+    recomputes nothing.  Gradients are those of the library: dh and dV on the symmetric integrals
+    (projected onto the p<->q and 8-fold symmetries), dD_0 on 2-RDM-symmetric tensors.  For a split
+    precision the forward steps run in that precision and the reverse sweep in FP64 along them."""
+
+    @staticmethod
+    def forward(fctx, h, V, Daa, Dab, Dbb, n_alpha, n_beta, prec="fp64", nsteps=1, eps=1e-3, wE=1.0, wN=0.0):
+        r = h.shape[0]
+        ctx = ACSE(r, n_alpha, n_beta, h.detach(), V.detach(), prec, device=h.device)
+        D = tuple(x.detach().clone().contiguous() for x in (Daa, Dab, Dbb))
+        ckpt = [tuple(x.clone() for x in D)]
+        for _ in range(nsteps):
+            ctx.step(D, eps)
+            ckpt.append(tuple(x.clone() for x in D))
+        f = torch.zeros((), dtype=torch.float64, device=h.device)
+        if wE != 0.0:
+            f = f + wE * ctx.energy(D)[0]
+        if wN != 0.0:
+            _, n2 = ctx.residual(D)
+            f = f + wN * n2[0]
+        fctx.acse = ctx
+        fctx.ckpt = ckpt
+        fctx.args = (nsteps, eps, wE, wN)
+        return f
+
+    @staticmethod
+    def backward(fctx, gf):
+        nsteps, eps, wE, wN = fctx.args
+        dh, dV, dD = fctx.acse.backward(fctx.ckpt, nsteps, eps, wE, wN)
+        fctx.acse.close()
+        fctx.ckpt = None
+        return (gf * dh, gf * dV, gf * dD[0], gf * dD[1], gf * dD[2]) + (None,) * 7
+
+
+def acse_objective(h, V, D0, n_alpha, n_beta, prec="fp64", nsteps=1, eps=1e-3, wE=1.0, wN=0.0):
+    """Differentiable f = wE E(D_n) + wN ||A(D_n)||^2 (see ACSEObjective); D0 = (Daa, Dab, Dbb)."""
+    return ACSEObjective.apply(h, V, *D0, n_alpha, n_beta, prec, nsteps, eps, wE, wN)

@@ -176,6 +176,7 @@ extern "C" int acse_destroy(acse_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 2 * ACSE_PROF_MAX; ++i)
         if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+    if (c->shadow) acse_destroy(c->shadow);
     adj_free(c);
     tc_plan_destroy(c);
     free_work(c);
@@ -415,7 +416,20 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
 extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps, double wE,
                                       double wN, double* dh, double* dV, double* dDaa, double* dDab, double* dDbb) {
     if (!c) return ACSE_ERR_ARG;
-    return latch(c, acse_residual_backward_impl(c, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
+    if (c->opt.prec == ACSE_FP64)
+        return latch(c, acse_residual_backward_impl(c, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
+    // split precision: the reverse sweep runs in an FP64 companion context (same h, V, options)
+    if (!c->shadow) {
+        acse_opts o = c->opt;
+        o.prec = ACSE_FP64;
+        o.line_search = 0;
+        const int s = acse_create(&c->shadow, &o, c->w.h, c->w.V, (void*)c->stream);
+        if (s != ACSE_OK) {
+            c->shadow = nullptr;
+            return latch(c, s);
+        }
+    }
+    return latch(c, acse_residual_backward_impl(c->shadow, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
 }
 
 // ------------------------------------------------------------------------------ profiling

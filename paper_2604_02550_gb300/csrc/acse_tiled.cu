@@ -166,14 +166,14 @@ __device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, con
 // (the spin-flip sectors drop a sign -1 that their M operand drops too).  The FP64 slices of the
 // next ipb values of p are copied into shared memory (cp.async) while the current ipb slices are
 // multiplied; each thread owns one 4 x 4 output tile of one slice (ipb * (rp/4)^2 threads).
-template <int MODE>
+template <int MODE, int RP = 0>   // RP > 0: compile-time padded size (product loop fully unrolled)
 __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(int r, int ipb, int pchunk, const double* __restrict__ Waa,
                                                          const double* __restrict__ Wab,
                                                          const double* __restrict__ Wbb,
                                                          const double* __restrict__ gam, const __grid_constant__ ZOut o) {
     using T = typename std::conditional<MODE == 0, double, float>::type;
     extern __shared__ __align__(16) unsigned char tl_smem[];
-    const int rp = pad4(r), ldw = rp + 4, R2 = r * r, R2e = (R2 + 1) & ~1;
+    const int rp = RP ? RP : pad4(r), ldw = rp + 4, R2 = r * r, R2e = (R2 + 1) & ~1;
     const int nt = rp / 4, nt2 = nt * nt;
     double* stage = (double*)tl_smem;                    // [ipb][R2e] raw FP64 slices
     T* gT = (T*)(stage + (size_t)ipb * R2e);             // [q][j] = 1D[j][q], row pitch ldw
@@ -242,8 +242,9 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0;
         const T* W = Ws + (size_t)it_me * rp * ldw;
+        // with RP the loop runs over the zero-padded rows too (q < RP), at a constant trip count
 #pragma unroll 4
-        for (int q = 0; q < r; ++q) {
+        for (int q = 0; q < (RP ? RP : r); ++q) {
             T a[4], b[4];
             ld4(gT + q * ldw + j0, a);
             ld4(W + q * ldw + s0, b);
@@ -461,9 +462,12 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
 // and used when H is formed at its end.
 #define BP_MAX_THREADS 512   // r = 64: S = 256, 256 + 256 threads
 
-template <int KIND>
-__device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, const float* B, int ld, int r, int rp,
-                                           int nt, int kb, int lb) {
+// RP > 0: the padded size is a compile-time constant (loops fully unrolled, addresses folded); the
+// padding rows and columns of the shared tiles are zero, so the loops may run to RP.
+template <int KIND, int RP>
+__device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, const float* B, int ld_, int r_, int rp_,
+                                           int nt_, int kb, int lb) {
+    const int rp = RP ? RP : rp_, ld = RP ? RP + 4 : ld_, nt = RP ? RP / 4 : nt_, r = RP ? RP : r_;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -514,10 +518,10 @@ __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, c
 __device__ __forceinline__ int bp_k(int kind, int kb, int nt, int a) { return kind == 0 ? kb + nt * a : 4 * kb + a; }
 __device__ __forceinline__ int bp_l(int kind, int lb, int nt, int b) { return kind == 2 ? lb + nt * b : 4 * lb + b; }
 
-template <int MAXT, int MINB>
+template <int MAXT, int MINB, int RP>
 __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ BTiledArgs<float> a) {
     extern __shared__ __align__(16) unsigned char tl_smem[];
-    const int r = a.r, rp = pad4(r), ld = rp + 4, R2 = r * r, bpitch = r + 1;
+    const int r = a.r, rp = RP ? RP : pad4(r), ld = rp + 4, R2 = r * r, bpitch = r + 1;
     const int nt = rp / 4, nt2 = nt * nt, S = (nt2 + 31) & ~31;
     const size_t tile = (size_t)rp * ld;
     float* gA = (float*)tl_smem;          // 1D_a [p][l]
@@ -628,8 +632,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 }
                 float acc[4][4];
                 const float* wT = (t == 0 || t == 2) ? wAT : wBT;
-                if (kind == 1) bp_product<1>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
-                else bp_product<2>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                if (kind == 1) bp_product<1, RP>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                else bp_product<2, RP>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
                 const float c2 = t == 2 ? 2.f : -2.f;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -642,8 +646,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 }
             } else if (grp == 0 && active) {
                 const float* g1 = (t == 0 || t == 3) ? gA : gB;
-                if (t == 3) bp_product<1>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
-                else bp_product<0>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                if (t == 3) bp_product<1, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                else bp_product<0, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
             }
             __syncthreads();                                // x2 and gathered parts in Bt
             if (grp == 0 && active) {
@@ -782,10 +786,14 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
         o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : (c->opt.prec == ACSE_TF32X3 ? 3 : 2);
         o.ldd = c->nsplit * w.Kp2; o.ldf = c->nsplit * w.Kp1; o.Kp1 = w.Kp1; o.Kp2 = w.Kp2; o.diag = w.zdiag32;
-        const void* kern = o.mode == 1 ? (const void*)k_Z_pipe<1> : o.mode == 3 ? (const void*)k_Z_pipe<3>
-                                                                                : (const void*)k_Z_pipe<2>;
+        const bool r48 = o.mode == 1 && pad4(r) == 48;
+        const void* kern = r48 ? (const void*)k_Z_pipe<1, 48>
+                               : o.mode == 1 ? (const void*)k_Z_pipe<1> : o.mode == 3 ? (const void*)k_Z_pipe<3>
+                                                                                      : (const void*)k_Z_pipe<2>;
         const ZPlan zp = z_plan(r, o.mode, sizeof(float), kern);
-        if (o.mode == 1)
+        if (r48)
+            k_Z_pipe<1, 48><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        else if (o.mode == 1)
             k_Z_pipe<1><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         else if (o.mode == 3)
             k_Z_pipe<3><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
@@ -832,7 +840,9 @@ int launch_B_tiled(acse_ctx* c) {
         const int nt2 = (pad4(r) / 4) * (pad4(r) / 4);
         const int threads = (((nt2 + 31) & ~31) + nt2 + 31) / 32 * 32;
         const bool small = threads <= 320;
-        const void* kern = small ? (const void*)k_B_pipe<320, 2> : (const void*)k_B_pipe<BP_MAX_THREADS, 1>;
+        const bool r48 = pad4(r) == 48;
+        const void* kern = r48 ? (const void*)k_B_pipe<320, 2, 48>
+                               : small ? (const void*)k_B_pipe<320, 2, 0> : (const void*)k_B_pipe<BP_MAX_THREADS, 1, 0>;
         if (cached_r != r) {
             int per_sm = 1, nsm = 152, dev = 0;
             if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -844,8 +854,9 @@ int launch_B_tiled(acse_ctx* c) {
             cached_grid = nsm * per_sm < R2 ? nsm * per_sm : R2;
             cached_r = r;
         }
-        if (small) k_B_pipe<320, 2><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
-        else k_B_pipe<BP_MAX_THREADS, 1><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
+        if (r48) k_B_pipe<320, 2, 48><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
+        else if (small) k_B_pipe<320, 2, 0><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
+        else k_B_pipe<BP_MAX_THREADS, 1, 0><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -856,12 +867,15 @@ int tiled_set_attrs() {
                                        (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bp_smem(48)));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<BP_MAX_THREADS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bp_smem(48)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<BP_MAX_THREADS, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bp_smem(ACSE_MAX_R)));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<1, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     return ACSE_OK;

@@ -347,6 +347,14 @@ __device__ __forceinline__ int tc_find_problem(const TcBatch& b, int t) {
     return lo;
 }
 
+// Tile coordinates of local tile `local` of problem P for the persistent kernel: row-major over the
+// tile grid (measured faster here than walking groups of 16 tile rows column by column).
+template <int BN>
+__device__ __forceinline__ void tc_tile_coords(const TcProb& P, int local, int& m0, int& n0) {
+    m0 = (local / P.tiles_n) * TC_BM;
+    n0 = (local % P.tiles_n) * BN;
+}
+
 template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* __restrict__ bp) {
     const TcBatch& b = *bp;
@@ -395,9 +403,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
             for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
                 const int pi = tc_find_problem(b, t);
                 const TcProb& P = b.p[pi];
-                const int local = t - P.tile_start;
-                const int m0 = (local / P.tiles_n) * TC_BM;
-                const int n0 = (local % P.tiles_n) * BN;
+                int m0, n0;
+                tc_tile_coords<BN>(P, t - P.tile_start, m0, n0);
                 for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (it >= STAGES && !bounded_wait(&empty[s], ((it / STAGES) & 1) ^ 1, b.wait_ns, abort_flag)) {
@@ -465,9 +472,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
             tc_fence_after();
             const int pi = tc_find_problem(b, t);
             const TcProb& P = b.p[pi];
-            const int local = t - P.tile_start;
-            const int m0 = (local / P.tiles_n) * TC_BM;
-            const int n0 = (local % P.tiles_n) * BN;
+            int m0, n0;
+            tc_tile_coords<BN>(P, t - P.tile_start, m0, n0);
             const int row = m0 + q * 32 + lane;
             float* Crow = P.C + (size_t)row * P.ldc;
             const bool vec = (P.ldc & 3) == 0;

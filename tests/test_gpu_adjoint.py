@@ -96,3 +96,55 @@ def test_adjoint_config5_vs_central_differences(api):
         worst = max(worst, rel)
         assert rel < 1e-6, f"direction {k}: adjoint {ad} vs FD {fd}"
     print(f"config 5: worst relative adjoint/FD mismatch over 64 directions {worst:.2e}")
+
+
+def test_autograd_function_matches_oracle(api):
+    """torch.autograd through ACSEObjective: gradients of f with respect to h, V and D_0 tensors equal
+    the oracle's complex-step directional derivatives."""
+    p = I.make_problem(4, 4, 33, "cas", core=[0], active=[1, 2, 3], nelecas=2)
+    eps, nsteps, wE, wN = 1e-3, 3, 1.0, 0.25
+    dev = torch.device("cuda")
+    h = torch.tensor(p.h, device=dev, requires_grad=True)
+    V = torch.tensor(p.V, device=dev, requires_grad=True)
+    D = [torch.tensor(x, device=dev, requires_grad=True) for x in (p.Daa, p.Dab, p.Dbb)]
+    f = api.acse_objective(h, V, D, p.n_alpha, p.n_beta, "fp64", nsteps, eps, wE, wN)
+    f.backward()
+    f_or = O.objective(p.h, p.V, p.N, O.so_from_blocks(p.Daa, p.Dab, p.Dbb), eps, nsteps, wE, wN)
+    assert float(f) == pytest.approx(f_or, rel=1e-12)
+    rng = np.random.default_rng(9)
+    for k in range(4):
+        eh, eV = _sym_dirs(p.r, rng)
+        eD = _sym_D(p.r, 200 + k)
+        want = O.complex_step_dir(p.h, p.V, p.N, O.so_from_blocks(p.Daa, p.Dab, p.Dbb), eps, nsteps, eh, eV,
+                                  O.so_from_blocks(*eD), wE, wN)
+        got = (np.sum(h.grad.cpu().numpy() * eh) + np.sum(V.grad.cpu().numpy() * eV)
+               + sum(np.sum(d.grad.cpu().numpy() * e) for d, e in zip(D, eD)))
+        assert got == pytest.approx(want, rel=1e-9, abs=1e-9 * abs(want)), f"direction {k}"
+
+
+def test_split_precision_adjoint(api):
+    """A BF16x3 context's adjoint is the FP64 reverse sweep along the BF16x3 forward trajectory: with
+    the same checkpoints it equals an FP64 context's adjoint, and it differs from the gradient of the
+    FP64 trajectory only by the split-precision error of the forward steps."""
+    p = I.config_problem(2)
+    eps, nsteps, wE, wN = 1e-3, 3, 1.0, 1e-3
+    D0 = (p.Daa, p.Dab, p.Dbb)
+    cm = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "bf16x3")
+    D = cm.to_blocks(D0)
+    ck = [tuple(x.clone() for x in D)]
+    for _ in range(nsteps):
+        cm.step(D, eps)
+        ck.append(tuple(x.clone() for x in D))
+    gm = cm.backward(ck, nsteps, eps, wE, wN)
+    c64 = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64")
+    g64_same = c64.backward(ck, nsteps, eps, wE, wN)
+    g64_own = c64.backward([c64.to_blocks(D0)], nsteps, eps, wE, wN)
+    flat = lambda g: np.concatenate([g[0].cpu().numpy().ravel(), g[1].cpu().numpy().ravel()]
+                                    + [x.cpu().numpy().ravel() for x in g[2]])
+    a, b, c = flat(gm), flat(g64_same), flat(g64_own)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    rel = np.abs(a - c).max() / np.abs(c).max()
+    print(f"BF16x3-trajectory adjoint vs FP64-trajectory adjoint: max rel diff {rel:.2e}")
+    assert rel < 1e-3
+    cm.close()
+    c64.close()
