@@ -15,6 +15,9 @@ index P = p for alpha and P = r + p for beta), written from the paper's equation
                        it, with the intermediate E^{ij}_{kl}           -> `G_factored`
   * Eq. (update)       Euler step D <- D + eps U                       -> `update`, `step`
   * Methods            stopping rule on E, ||R|| and |dE| < 1e-6       -> `run_acse`
+  * Eq. (NY), App. (NY) Nakatsuji-Yasuda 3-cumulant added to the V terms -> `sigma_hf`,
+                       `cumulant3_NY`, `recon_3rdm_NY`, `_three_body_NY` (every driver
+                       function takes sigma=None for V, the HF occupation signs for NY)
 
 Readings of places where the paper is garbled or silent (each also pinned by tests):
   R1  K = 1/2(<pq|rs> - <pq|sr>) + (h_pr d_qs + h_qs d_pr - h_ps d_qr - h_qr d_ps)/(2(N-1)),
@@ -27,6 +30,8 @@ Readings of places where the paper is garbled or silent (each also pinned by tes
   R7  line search (not in the paper): f(eps) = ||A(D + eps U)||^2 at {0, e0, 2 e0};
       convex parabola -> its minimiser clamped to [e0/4, 2 e0], else the better of e0, 2 e0;
       next e0 = accepted eps.
+  R13 sigma_a of the NY cumulant: +1 for the first n_alpha alpha and the first n_beta beta spatial
+      orbitals (aufbau by orbital index), -1 for the others.
 All functions accept complex arrays too (complex-step derivatives): no abs(), no conj().
 """
 from __future__ import annotations
@@ -139,6 +144,70 @@ def recon_3rdm_V(D, N):
     return D3 / 9.0
 
 
+def sigma_hf(r, n_alpha, n_beta):
+    """sigma_a of the NY functional (Eq. NY): +1 for spin orbitals occupied in the Hartree-Fock
+    reference, -1 otherwise; reading R13: aufbau by orbital index, the first n_alpha alpha and the first
+    n_beta beta spatial orbitals occupied."""
+    sig = -np.ones(2 * r)
+    sig[:n_alpha] = 1.0
+    sig[r:r + n_beta] = 1.0
+    return sig
+
+
+def _perm_sign(p):
+    s = 1
+    for i in range(len(p)):
+        for j in range(i + 1, len(p)):
+            if p[i] > p[j]:
+                s = -s
+    return s
+
+
+def cumulant3_NY(delta, sig):
+    """NY 3-cumulant (Eq. NY, stored as C3[i,j,p,r,q,l] = 3Delta^{ijp}_{rql}): 1/6 sum_a sigma_a A(...)
+    with A the antisymmetriser over the upper (i,j,p) and the lower (r,q,l) indices of
+    2Delta^{ia}_{rq} 2Delta^{jp}_{al} (all 36 signed permutations, a fixed).  O(n^6) memory: tiny n only."""
+    from itertools import permutations
+    X = np.einsum("a,iarq,jpal->ijprql", sig, delta, delta)
+    out = np.zeros_like(X)
+    for pu in permutations(range(3)):
+        for pl in permutations(range(3)):
+            out = out + _perm_sign(pu) * _perm_sign(pl) * X.transpose(list(pu) + [3 + x for x in pl])
+    return out / 6.0
+
+
+def cumulant3_NY_simplified(delta, sig):
+    """The nine-term form of the same cumulant printed in the appendix (pair antisymmetry of 2Delta
+    collapses the 36 terms four by four)."""
+    e = np.einsum
+    t = (4 * e("a,iarq,jpal->ijprql", sig, delta, delta) - 4 * e("a,jarq,ipal->ijprql", sig, delta, delta)
+         - 4 * e("a,parq,jial->ijprql", sig, delta, delta) - 4 * e("a,ialq,jpar->ijprql", sig, delta, delta)
+         + 4 * e("a,jalq,ipar->ijprql", sig, delta, delta) + 4 * e("a,palq,jiar->ijprql", sig, delta, delta)
+         - 4 * e("a,iarl,jpaq->ijprql", sig, delta, delta) + 4 * e("a,jarl,ipaq->ijprql", sig, delta, delta)
+         + 4 * e("a,parl,jiaq->ijprql", sig, delta, delta))
+    return t / 6.0
+
+
+def recon_3rdm_NY(D, N, sig):
+    """NY 3-RDM: the Valdemoro terms plus the NY 3-cumulant (tiny n only)."""
+    g = gamma(D, N)
+    _, delta = cumulant_M(D, g)
+    return recon_3rdm_V(D, N) + cumulant3_NY(delta, sig)
+
+
+def _three_body_NY(W, delta, sig):
+    """sum_{pqr} W^{kp}_{rq} 3Delta^{ijp}_{rql} with the nine-term NY cumulant, each term contracted
+    directly (numpy chooses the pairwise order; 3Delta is never formed)."""
+    e = lambda s_, *a: np.einsum(s_, *a, **_EIN)
+    d = delta
+    t = (4 * e("kprq,a,iarq,jpal->ijkl", W, sig, d, d) - 4 * e("kprq,a,jarq,ipal->ijkl", W, sig, d, d)
+         - 4 * e("kprq,a,parq,jial->ijkl", W, sig, d, d) - 4 * e("kprq,a,ialq,jpar->ijkl", W, sig, d, d)
+         + 4 * e("kprq,a,jalq,ipar->ijkl", W, sig, d, d) + 4 * e("kprq,a,palq,jiar->ijkl", W, sig, d, d)
+         - 4 * e("kprq,a,iarl,jpaq->ijkl", W, sig, d, d) + 4 * e("kprq,a,jarl,ipaq->ijkl", W, sig, d, d)
+         + 4 * e("kprq,a,parl,jiaq->ijkl", W, sig, d, d))
+    return t / 6.0
+
+
 # ----------------------------------------------------------------------------------------
 # residual and update contractions
 # ----------------------------------------------------------------------------------------
@@ -181,21 +250,26 @@ def _three_body_V(W, M, g):
     return (t1 - t2 + E - E.transpose(1, 0, 2, 3)) / 9.0
 
 
-def G_factored(W, D, N):
-    """Same value as G_explicit(W, D, recon_3rdm_V(D, N)) without ever holding 3D.
+def G_factored(W, D, N, sigma=None):
+    """Same value as G_explicit(W, D, recon_3rdm_V(D, N)) without ever holding 3D; with sigma given,
+    the same with the NY 3-RDM (recon_3rdm_NY(D, N, sigma)), whose cumulant is Hermitian too.
 
     The six terms of G_explicit: two 2D terms and four 3D terms; each 3D term is a relabelling
     of sum W^{kp}_{rq} 3D^{ijp}_{rql} (for W^{pq}_{ri} 3D^{jpq}_{rlk} by the Hermiticity of
     3D, which holds for the reconstruction because M and 1D are Hermitian)."""
     e = lambda s, *a: np.einsum(s, *a, **_EIN)
     g = gamma(D, N)
-    M, _ = cumulant_M(D, g)
+    M, delta = cumulant_M(D, g)
     two = 2 * e("pqji,pqlk->ijkl", W, D) - 2 * e("klqp,ijqp->ijkl", W, D)
     T = _three_body_V(W, M, g)                     # T^{ij}_{kl} = sum W^{kp}_{rq} 3D^{ijp}_{rql}
+    if sigma is not None:
+        T = T + _three_body_NY(W, delta, sigma)
     # sum W^{pq}_{ri} 3D^{jpq}_{rlk}: 3D^{jpq}_{rlk} = 3D^{rlk}_{jpq} = 3D^{lkr}_{pqj} (cyclic)
     # so the sum equals  sum_{pqr} Wt^{ir}_{pq} 3D^{lkr}_{pqj} = T'(Wt)^{lk}_{ij}, Wt^{ir}_{pq} = W^{pq}_{ri}
     Wt = W.transpose(3, 2, 0, 1)                   # Wt[i,r,p,q] = W[p,q,r,i]
     Tt = _three_body_V(Wt, M, g)                   # Tt^{ab}_{cd} = sum Wt^{cp}_{rq} 3D^{abp}_{rqd}
+    if sigma is not None:
+        Tt = Tt + _three_body_NY(Wt, delta, sigma)
     # term5:  sum W^{pq}_{ri} 3D^{jpq}_{rlk} = Tt^{lk}_{ij}
     t5 = Tt.transpose(2, 3, 1, 0)                  # [i,j,k,l] <- Tt[l,k,i,j]
     t6 = Tt.transpose(3, 2, 1, 0)                  # [i,j,k,l] <- Tt[l,k,j,i]
@@ -203,18 +277,23 @@ def G_factored(W, D, N):
     return -2.0 * R
 
 
-def residual(K, D, N, explicit=False):
-    """A = <[a+_i a+_j a_l a_k, H]> = G(K/2) (readings R1, R2)."""
+def _recon(D, N, sigma):
+    return recon_3rdm_V(D, N) if sigma is None else recon_3rdm_NY(D, N, sigma)
+
+
+def residual(K, D, N, explicit=False, sigma=None):
+    """A = <[a+_i a+_j a_l a_k, H]> = G(K/2) (readings R1, R2); V reconstruction, or NY when the
+    HF occupation signs sigma are given."""
     if explicit:
-        return G_explicit(0.5 * K, D, recon_3rdm_V(D, N))
-    return G_factored(0.5 * K, D, N)
+        return G_explicit(0.5 * K, D, _recon(D, N, sigma))
+    return G_factored(0.5 * K, D, N, sigma)
 
 
-def update(A, D, N, explicit=False):
+def update(A, D, N, explicit=False, sigma=None):
     """U = 1/2 <[a+_i a+_j a_l a_k, A^]> with the same reconstructed 3D (reading R3, Eq. update)."""
     if explicit:
-        return 0.5 * G_explicit(A, D, recon_3rdm_V(D, N))
-    return 0.5 * G_factored(A, D, N)
+        return 0.5 * G_explicit(A, D, _recon(D, N, sigma))
+    return 0.5 * G_factored(A, D, N, sigma)
 
 
 def norm2(A):
@@ -238,11 +317,11 @@ def active_mask(A, r, act_lo, act_hi):
 # step, line search, driver
 # ----------------------------------------------------------------------------------------
 
-def step(K, D, N, eps, mask=None):
+def step(K, D, N, eps, mask=None, sigma=None):
     """One Euler step of Eq. (update): returns (D_next, A, U) with A evaluated at D."""
-    A = residual(K, D, N)
+    A = residual(K, D, N, sigma=sigma)
     Am = A if mask is None else active_mask(A, *mask)
-    U = update(Am, D, N)
+    U = update(Am, D, N, sigma=sigma)
     return D + eps * U, A, U
 
 
@@ -257,7 +336,7 @@ def line_search_eps(f0, f1, f2, e0):
 
 
 def run_acse(h, V, N, D0, eps, nsteps, line_search=False, mask=None, stop_rule=False,
-             eps0=1e-3, log=None):
+             eps0=1e-3, log=None, sigma=None):
     """The Euler-step driver.  Returns dict(D, E[list], norm2[list], eps[list], steps).
 
     E[n], norm2[n] are at D_n (E[0] at the reference).  With stop_rule the loop ends when E
@@ -268,22 +347,22 @@ def run_acse(h, V, N, D0, eps, nsteps, line_search=False, mask=None, stop_rule=F
     ns = []
     epss = []
     e_ls = eps0
-    A = residual(K, D, N)
+    A = residual(K, D, N, sigma=sigma)
     for n in range(nsteps):
         ns.append(norm2(A))
         Am = A if mask is None else active_mask(A, *mask)
-        U = update(Am, D, N)
+        U = update(Am, D, N, sigma=sigma)
         if line_search:
             f0 = ns[-1]
-            A1 = residual(K, D + e_ls * U, N)
-            A2 = residual(K, D + 2 * e_ls * U, N)
+            A1 = residual(K, D + e_ls * U, N, sigma=sigma)
+            A2 = residual(K, D + 2 * e_ls * U, N, sigma=sigma)
             e_use = line_search_eps(f0, norm2(A1), norm2(A2), e_ls)
             e_ls = e_use
         else:
             e_use = eps
         Dn = D + e_use * U
         En = energy(K, Dn)
-        An = residual(K, Dn, N)
+        An = residual(K, Dn, N, sigma=sigma)
         if stop_rule:
             if En > Es[-1] or norm2(An) > ns[-1]:
                 break
@@ -299,21 +378,21 @@ def run_acse(h, V, N, D0, eps, nsteps, line_search=False, mask=None, stop_rule=F
     return dict(D=D, E=Es, norm2=ns, eps=epss, steps=len(epss))
 
 
-def objective(h, V, N, D0, eps, nsteps, wE=1.0, wN=0.0, mask=None):
+def objective(h, V, N, D0, eps, nsteps, wE=1.0, wN=0.0, mask=None, sigma=None):
     """wE * E(D_n) + wN * ||A(D_n)||^2 after n fixed Euler steps from D0 (the function the
     adjoint differentiates).  Polynomial in (h, V, D0): complex-step exact."""
     K = reduced_hamiltonian(h, V, N)
     D = D0
     for _ in range(nsteps):
-        D, _, _ = step(K, D, N, eps, mask)
-    A = residual(K, D, N)
+        D, _, _ = step(K, D, N, eps, mask, sigma)
+    A = residual(K, D, N, sigma=sigma)
     return wE * energy(K, D) + wN * norm2(A)
 
 
-def complex_step_dir(h, V, N, D0, eps, nsteps, dh, dV, dD0, wE=1.0, wN=0.0, mask=None, t=1e-30):
+def complex_step_dir(h, V, N, D0, eps, nsteps, dh, dV, dD0, wE=1.0, wN=0.0, mask=None, t=1e-30, sigma=None):
     """Directional derivative of `objective` along (dh, dV, dD0), exact to rounding
     (complex step: Im f(x + i t d) / t)."""
-    f = objective(h + 1j * t * dh, V + 1j * t * dV, N, D0 + 1j * t * dD0, eps, nsteps, wE, wN, mask)
+    f = objective(h + 1j * t * dh, V + 1j * t * dV, N, D0 + 1j * t * dD0, eps, nsteps, wE, wN, mask, sigma)
     return float(np.imag(f) / t)
 
 

@@ -376,3 +376,84 @@ def test_residual_entries_match_full_residual(sys4):
     ent = [tuple(int(x) for x in rng.integers(0, 2 * r, 4)) for _ in range(12)]
     e = O.residual_entries(s["h"], s["V"], s["N"], *Db, ent)
     np.testing.assert_allclose(e, [A[t] for t in ent], atol=1e-14)
+
+
+# ----------------------------------------------------------------------- NY reconstruction
+
+def _sig(s):
+    return O.sigma_hf(s["r"], s["na"], s["N"] - s["na"])
+
+
+def test_ny_cumulant_36_terms_equal_printed_nine(sys3, sys4):
+    """Eq. (NY): the 36-term antisymmetrised definition equals the nine-term form printed in the
+    appendix (the two printed forms of the same cumulant, read independently)."""
+    for s in (sys3, sys4):
+        g = O.gamma(s["D"], s["N"])
+        _, delta = O.cumulant_M(s["D"], g)
+        sig = _sig(s)
+        full = O.cumulant3_NY(delta, sig)
+        nine = O.cumulant3_NY_simplified(delta, sig)
+        assert np.abs(full).max() > 1e-4
+        np.testing.assert_allclose(full, nine, atol=1e-14 * np.abs(full).max() * 100)
+
+
+def test_ny_sigma_is_the_hf_occupation():
+    sig = O.sigma_hf(4, 2, 1)
+    np.testing.assert_array_equal(sig, [1, 1, -1, -1, 1, -1, -1, -1])
+
+
+def test_ny_exact_for_determinants():
+    """For a determinant the 2-cumulant vanishes, so the NY cumulant does too and the NY 3-RDM equals
+    the exact one (as the V one does)."""
+    r = 4
+    n = 2 * r
+    a = F.annihilators(n)
+    for occ in ([0, 1, r], [0, 2, r + 1, r + 3]):
+        psi = F.determinant(n, occ)
+        D = F.rdm2(a, psi)
+        na = sum(1 for o in occ if o < r)
+        sig = O.sigma_hf(r, na, len(occ) - na)
+        np.testing.assert_allclose(O.recon_3rdm_NY(D, len(occ), sig), F.rdm3(a, psi), atol=1e-15)
+
+
+def test_ny_cumulant_symmetries(sys4):
+    """Antisymmetric in the upper and in the lower indices, Hermitian (upper <-> lower), and not
+    the exact cumulant of a correlated state (it is an approximation)."""
+    s = sys4
+    g = O.gamma(s["D"], s["N"])
+    _, delta = O.cumulant_M(s["D"], g)
+    C = O.cumulant3_NY(delta, _sig(s))
+    scale = np.abs(C).max()
+    for ax in ((1, 0, 2, 3, 4, 5), (0, 2, 1, 3, 4, 5), (0, 1, 2, 4, 3, 5), (0, 1, 2, 3, 5, 4)):
+        assert np.abs(C + C.transpose(ax)).max() < 1e-15 * 100 * scale
+    assert np.abs(C - C.transpose(3, 4, 5, 0, 1, 2)).max() < 1e-15 * 100 * scale
+    exact = s["D3"] - O.recon_3rdm_V(s["D"], s["N"])
+    assert np.abs(exact - C).max() > 1e-3 * np.abs(exact).max()
+
+
+def test_ny_factored_equals_explicit(sys3, sys4):
+    """The NY contraction without storing 3D equals G with the stored NY 3-RDM, for pair-Hermitian
+    and anti-Hermitian W (residual and update)."""
+    for s in (sys3, sys4):
+        sig = _sig(s)
+        D3 = O.recon_3rdm_NY(s["D"], s["N"], sig)
+        for k, herm in enumerate((1, -1)):
+            W = _antisym_W(s["n"], 300 + k, herm)
+            want = O.G_explicit(W, s["D"], D3)
+            np.testing.assert_allclose(O.G_factored(W, s["D"], s["N"], sig), want, atol=1e-12 * np.abs(want).max())
+
+
+def test_ny_residual_is_commutator_with_ny_3rdm_and_descent_identity(sys4):
+    """With the NY 3-RDM: the printed Eq. (residual) is minus the factored residual, A is
+    anti-Hermitian, and Tr(K U) = -||A||^2 (the descent identity needs only a Hermitian 3-RDM)."""
+    s = sys4
+    sig = _sig(s)
+    K, D, N = s["K"], s["D"], s["N"]
+    A = O.residual(K, D, N, sigma=sig)
+    np.testing.assert_allclose(O.residual_paper_form(K, D, O.recon_3rdm_NY(D, N, sig)), -A,
+                               atol=1e-12 * np.abs(A).max())
+    assert np.abs(A + A.transpose(2, 3, 0, 1)).max() < 1e-12 * np.abs(A).max()
+    U = O.update(A, D, N, sigma=sig)
+    assert np.sum(K * U) == pytest.approx(-O.norm2(A), rel=1e-10)
+    Av = O.residual(K, D, N)
+    assert np.abs(A - Av).max() > 1e-4 * np.abs(Av).max()     # NY changes the residual
