@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--time-to-e", action="store_true",
                     help="time-to-E on the r = 48 workload: BF16x3 vs FP64, Methods stopping rule, step cap")
     ap.add_argument("--cap", type=int, default=100, help="step cap of --time-to-e")
+    ap.add_argument("--line-search", action="store_true", help="--time-to-e with the line search (one context)")
     ap.add_argument("--adjoint", action="store_true",
                     help="adjoint cost relative to the forward steps (FP64, r = 24 CAS(6e,6o), 4 steps)")
     return ap.parse_args()
@@ -370,6 +371,60 @@ def run_time_to_e(args):
     print(json.dumps(out), flush=True)
 
 
+def run_time_to_e_line_search(args):
+    """Time-to-E with the line search (acse_step, one context per precision): steps until the Methods
+    stopping rule fires, evaluated on the host after every step exactly as the oracle's driver does
+    (stop when E rises or ||A|| rises, keeping the previous state, or when |dE| < 1e-6 Eh); the
+    converged E of BF16x3 and TF32x3 against FP64."""
+    import torch
+    from paper_2604_02550_gb300 import api
+    p = workload(args.r)
+    out = {"metric": "time_to_E_line_search", "workload": p.name, "eps0": 1e-3, "cap": args.cap, "runs": {},
+           "hybrid": "bf16x3 while ||A||^2 falls by more than 1e-2 relative per step, then fp64 from the same D "
+                     "and the last accepted eps"}
+    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64", "fp64"):
+        hybrid = prec == "bf16x3+fp64"
+        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "bf16x3" if hybrid else prec, line_search=True,
+                       eps0=1e-3)
+        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+        Es = [float(ctx.energy(D))]
+        n2s = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc, reason, switched = None, "cap", None
+        for k in range(args.cap):
+            if hybrid and switched is None and k >= 2 and (n2s[-2] - n2s[-1]) < 1e-2 * n2s[-2]:
+                ctx.close()
+                ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64", line_search=True, eps0=last_eps)
+                switched = k
+            E, n2, e = ctx.step(D)
+            last_eps = float(e)
+            n2s.append(float(n2))          # ||A(D_k)||^2, before step k
+            Es.append(float(E))            # E(D_{k+1})
+            if k >= 1 and n2s[k] > n2s[k - 1]:
+                acc, reason = k - 1, "norm rose"
+                break
+            if Es[k + 1] > Es[k]:
+                acc, reason = k, "energy rose"
+                break
+            if abs(Es[k + 1] - Es[k]) < 1e-6:
+                acc, reason = k + 1, "converged"
+                break
+        dt = time.perf_counter() - t0
+        ctx.close()
+        if acc is None:
+            acc = len(Es) - 1
+        out["runs"][prec] = {"seconds": dt, "steps": len(n2s), "stop": reason, "accepted_step": acc,
+                             "E_conv": Es[acc], "norm2_last": n2s[-1]}
+        if hybrid:
+            out["runs"][prec]["switched_at_step"] = switched
+    e64 = out["runs"]["fp64"]["E_conv"]
+    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64"):
+        out["runs"][prec]["abs_dE_conv_vs_fp64"] = abs(out["runs"][prec]["E_conv"] - e64)
+        out["runs"][prec]["speedup_vs_fp64"] = out["runs"]["fp64"]["seconds"] / out["runs"][prec]["seconds"]
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint_cost(args):
     """Adjoint cost relative to forward: n FP64 Euler steps through acse_step vs one
     acse_residual_backward over the same n steps with every checkpoint given."""
@@ -430,7 +485,10 @@ def main():
         run_batch(args, rank, world)
         return
     if args.time_to_e:
-        run_time_to_e(args)
+        if args.line_search:
+            run_time_to_e_line_search(args)
+        else:
+            run_time_to_e(args)
         return
     if args.adjoint:
         run_adjoint_cost(args)
