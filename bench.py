@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32", "tf32x3"])
+    ap.add_argument("--recon", default="V", choices=["V", "NY"], help="3-RDM reconstruction")
     ap.add_argument("--r", type=int, default=48, help="orbitals (48: the CAS(8e,8o) workload)")
     ap.add_argument("--eps", type=float, default=None,
                     help="Euler step; default 1e-4 for r >= 32 (1e-3 diverges there), else the paper's 1e-3")
@@ -503,7 +504,7 @@ def main():
     if args.eps is None:
         args.eps = 1e-4 if p.r >= 32 else 1e-3
     stream = torch.cuda.Stream()
-    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream)
+    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream, recon=args.recon)
     with torch.cuda.stream(stream):
         D0 = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
         D = tuple(x.clone() for x in D0)
@@ -563,7 +564,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else f"{prec} (f32 accumulate)",
             "data": "synthetic",
-            "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "eps": args.eps,
+            "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "recon": args.recon, "eps": args.eps,
                        "step": "acse_step: residual + update + axpy + energy",
                        "reset_every": args.reset_every,
                        "l2": "inputs larger than L2 (about 1.5 GB of r^4 tensors touched per step)",

@@ -64,7 +64,14 @@ typedef enum {
  *   ACSE_TF32X3  x = hi + lo (two tf32), products hi.hi + hi.lo + lo.hi, FP32 accumulation (about 2^-21;
  *                limited by the FP32 intermediates). */
 typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2, ACSE_TF32X3 = 3 } acse_prec;
-typedef enum { ACSE_RECON_V = 0 } acse_recon;
+/* 3-RDM reconstruction (Eq. 3rdm_recon / Eq. NY):
+ *   ACSE_RECON_V   Valdemoro: the 3-cumulant is neglected;
+ *   ACSE_RECON_NY  Nakatsuji-Yasuda: the 3-cumulant 1/6 sum_a sigma_a A(2Delta^{ia}_{rq} 2Delta^{jp}_{al})
+ *                  is added, sigma_a = +1 for the first n_alpha alpha and the first n_beta beta spatial
+ *                  orbitals (the Hartree-Fock occupation by orbital index), -1 otherwise.  Its
+ *                  contractions run as dense spin-orbital GEMMs (n = 2r; memory about 12 n^4 elements);
+ *                  not available for acse_residual_backward or the batch (ACSE_ERR_UNSUPPORTED). */
+typedef enum { ACSE_RECON_V = 0, ACSE_RECON_NY = 1 } acse_recon;
 
 typedef struct {
     int r;             /* spatial orbitals, 2 <= r <= 64                                    */

@@ -113,12 +113,15 @@ def current_stream_handle():
     return torch.cuda.current_stream().cuda_stream
 
 
+RECON = {"V": 0, "NY": 1}
+
+
 def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
-                check_inputs=False, stream=None):
+                check_inputs=False, stream=None, recon="V"):
     o = AcseOpts()
     o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
-    o.recon = 0
+    o.recon = RECON[recon] if isinstance(recon, str) else int(recon)
     if mask is not None:
         o.mask_active, o.act_lo, o.act_hi = 1, int(mask[0]), int(mask[1])
     o.line_search = int(bool(line_search))

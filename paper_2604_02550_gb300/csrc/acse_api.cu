@@ -123,7 +123,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         o->n_beta > o->r)
         return ACSE_ERR_SHAPE;
     if (o->prec < ACSE_FP64 || o->prec > ACSE_TF32X3) return ACSE_ERR_ARG;
-    if (o->recon != ACSE_RECON_V) return ACSE_ERR_UNSUPPORTED;
+    if (o->recon != ACSE_RECON_V && o->recon != ACSE_RECON_NY) return ACSE_ERR_UNSUPPORTED;
     if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
     acse_ctx* c = (acse_ctx*)calloc(1, sizeof(acse_ctx));
     if (!c) return ACSE_ERR_NOMEM;
@@ -138,8 +138,10 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         return ACSE_ERR_CUDA;
     }
     int s = tiled_set_attrs();
+    if (s == ACSE_OK) s = ny_set_attrs();
     if (s == ACSE_OK) s = alloc_work(c);
     if (s == ACSE_OK && o->prec != ACSE_FP64) s = tc_plan_create(c);
+    if (s == ACSE_OK && o->recon == ACSE_RECON_NY) s = ny_alloc(c);
     if (s != ACSE_OK) {
         tc_plan_destroy(c);
         free_work(c);
@@ -177,6 +179,7 @@ extern "C" int acse_destroy(acse_ctx* c) {
     for (int i = 0; i < 2 * ACSE_PROF_MAX; ++i)
         if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
     if (c->shadow) acse_destroy(c->shadow);
+    ny_free(c);
     adj_free(c);
     tc_plan_destroy(c);
     free_work(c);
@@ -231,6 +234,7 @@ int acse_contract_gemm(acse_ctx* c) {
 }
 
 int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* const out[3], double* norm2_dst) {
+    if (c->ny) ACSE_TRY(ny_pass(c));   // NY: the 3-cumulant term, added to B by the B kernel
     ACSE_TRY(launch_Q(c));
     ACSE_TRY(launch_build_B(c));
     return launch_assemble_G(c, sW, scale, mask, out, norm2_dst);
@@ -416,6 +420,7 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
 extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps, double wE,
                                       double wN, double* dh, double* dV, double* dDaa, double* dDab, double* dDbb) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->opt.recon != ACSE_RECON_V) return latch(c, ACSE_ERR_UNSUPPORTED);
     if (c->opt.prec == ACSE_FP64)
         return latch(c, acse_residual_backward_impl(c, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
     // split precision: the reverse sweep runs in an FP64 companion context (same h, V, options)

@@ -290,6 +290,8 @@ extern "C" int acse_batch_create(acse_batch** out, int n, const acse_opts* opts,
     *out = nullptr;
     for (int i = 1; i < n; ++i)
         if (opts[i].prec != opts[0].prec) return ACSE_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (opts[i].recon != ACSE_RECON_V) return ACSE_ERR_UNSUPPORTED;   // the batch runs the V reconstruction
     acse_batch* B = (acse_batch*)calloc(1, sizeof(acse_batch));
     if (!B) return ACSE_ERR_NOMEM;
     B->n = n;

@@ -54,6 +54,8 @@ int tc_table_init(TcTable* t, int kind, int bn);
 void tc_table_free(TcTable* t);
 int tc_table_upload(TcTable* t);
 int tc_table_append(TcTable* t, struct acse_ctx* c);
+void tc_table_set_err(TcTable* t, int* err);
+int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha);
 int tc_table_launch(const TcTable* t, cudaStream_t st);
 
 // Scratch layout of one context (all device memory, owned by the context).
@@ -126,6 +128,7 @@ struct acse_ctx {
     void* tc_plan;        // tensor-core GEMM plan (tensor maps etc.)
     void* adj;            // adjoint workspace (allocated by the first acse_residual_backward call)
     struct acse_ctx* shadow;   // FP64 companion of a split-precision context (its adjoint), or null
+    void* ny;             // NY reconstruction workspace (acse_ny.cu), or null for V
     const double* cur_D[3];   // operands of the contraction pass in flight (FP64 GEMM list)
     const double* cur_W[3];
     // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches
@@ -146,6 +149,13 @@ struct acse_ctx {
     } while (0)
 
 int prof_begin(acse_ctx* c);
+
+// NY reconstruction (acse_ny.cu)
+int ny_alloc(acse_ctx* c);
+void ny_free(acse_ctx* c);
+int ny_pass(acse_ctx* c);
+const void* ny_terms(acse_ctx* c, int t);
+int ny_set_attrs();
 int prof_end(acse_ctx* c);
 
 // error helpers ---------------------------------------------------------------------------

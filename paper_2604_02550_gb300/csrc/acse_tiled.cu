@@ -314,6 +314,7 @@ struct BTiledArgs {
     const T* w;
     const T* Q;
     T* H[3];
+    const T* ny[4];     // NY three-body term per spin type (acse_ny.cu), added to B; null for V
 };
 
 // Block (i, j).  Spin types t = 0 (aaaa), 1 (bbbb), 2 (abab), 3 (abba):
@@ -426,7 +427,8 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                             x8 = X8b[((size_t)k * r + i) * ld8 + (size_t)j * r + l];
                         }
                         Bt[k * r + l] = (sgn1 * x1[u][v] - (T)2 * sgn2 * x2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
-                                        (T)(1.0 / 9.0);
+                                            (T)(1.0 / 9.0) +
+                                        (a.ny[t] ? a.ny[t][ij * R2 + (size_t)k * r + l] : (T)0);
                     }
                 }
             }
@@ -641,7 +643,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int l = bp_l(kind, lb, nt, v);
-                        if (k < r && l < r) Bt[k * bpitch + l] = (c2 * acc[u][v] + rest[u][v]) * (1.f / 9.f);
+                        if (k < r && l < r)
+                            Bt[k * bpitch + l] = (c2 * acc[u][v] + rest[u][v]) * (1.f / 9.f) +
+                                                 (a.ny[t] ? a.ny[t][(size_t)ij * R2 + (size_t)k * r + l] : 0.f);
                     }
                 }
             } else if (grp == 0 && active) {
@@ -820,6 +824,7 @@ int launch_B_tiled(acse_ctx* c) {
         a.r = r;
         for (int s = 0; s < 3; ++s) { a.X[s] = w.X[s]; a.Y[s] = w.Y[s]; a.M[s] = w.M[s]; a.H[s] = w.H[s]; }
         a.X5d = w.X5d; a.X5f1 = w.X5f1; a.X5f2 = w.X5f2;
+        for (int t = 0; t < 4; ++t) a.ny[t] = (const double*)ny_terms(c, t);
         a.gam = w.gam; a.w = w.w; a.Q = w.Q;
         if (b_smem(r, sizeof(double), true) <= k_smem_cap)
             k_B_tiled<double, true><<<R2, TL_TPB, b_smem(r, sizeof(double), true), c->stream>>>(a);
@@ -835,6 +840,7 @@ int launch_B_tiled(acse_ctx* c) {
             a.H[s] = w.H32[s];
         }
         a.X5d = w.tc_X5d; a.X5f1 = w.tc_X5f[0]; a.X5f2 = w.tc_X5f[1];
+        for (int t = 0; t < 4; ++t) a.ny[t] = (const float*)ny_terms(c, t);
         a.gam = w.gam32; a.w = w.w32; a.Q = w.Q32;
         static thread_local int cached_r = -1, cached_grid = 0;
         const int nt2 = (pad4(r) / 4) * (pad4(r) / 4);

@@ -603,6 +603,33 @@ int tc_table_upload(TcTable* t) {
     return ACSE_OK;
 }
 
+// Append one problem C[M][N] = alpha * A'[M][L] B'[N][L]^T (K-major split operand rows of L elements,
+// L a multiple of the 128-byte K block) to table t.
+int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) {
+    TcBatch& b = *t->host;
+    const int kel = t->kind == 0 ? 64 : 32;
+    if (b.nprob + 1 > TC_MAXP || L % kel) return ACSE_ERR_SHAPE;
+    const int n = b.nprob;
+    ACSE_TRY(encode_map(t->kind, &b.tmA[n], A, M, L, TC_BM));
+    ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->bn));
+    TcProb& p = b.p[n];
+    p.C = C;
+    p.M = M;
+    p.N = N;
+    p.kblocks = L / kel;
+    p.ldc = ldc;
+    p.alpha = alpha;
+    p.tiles_n = (N + t->bn - 1) / t->bn;
+    p.tile_start = b.total_tiles;
+    p.perm_r = 0;
+    b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
+    b.nprob = n + 1;
+    return ACSE_OK;
+}
+
+// Device flag raised by a launch of table t when a bounded wait runs out.
+void tc_table_set_err(TcTable* t, int* err) { t->host->err = err; }
+
 // Append the nine GEMMs of one contraction pass of context c to table t (tile width t->bn).
 int tc_table_append(TcTable* t, acse_ctx* c) {
     TcBatch& b = *t->host;
@@ -610,31 +637,12 @@ int tc_table_append(TcTable* t, acse_ctx* c) {
     const int r = c->r, R2 = r * r, R22 = 2 * R2;
     const int ns = c->nsplit;
     const int L1 = ns * w.Kp1, L2 = ns * w.Kp2;      // operand row lengths (elements)
-    const int kel = t->kind == 0 ? 64 : 32;
     if (b.nprob + 6 > TC_MAXP) return ACSE_ERR_SHAPE;
-    auto add = [&](const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) -> int {
-        const int n = b.nprob;
-        ACSE_TRY(encode_map(t->kind, &b.tmA[n], A, M, L, TC_BM));
-        ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->bn));
-        TcProb& p = b.p[n];
-        p.C = C;
-        p.M = M;
-        p.N = N;
-        p.kblocks = L / kel;
-        p.ldc = ldc;
-        p.alpha = alpha;
-        p.tiles_n = (N + t->bn - 1) / t->bn;
-        p.tile_start = b.total_tiles;
-        p.perm_r = 0;
-        b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
-        b.nprob = n + 1;
-        return ACSE_OK;
-    };
     // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
-    ACSE_TRY(add(w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f));
+    ACSE_TRY(tc_table_add(t, w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f));
     for (int s = 0; s < 3; ++s)
-        ACSE_TRY(add(w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f));
-    for (int f = 0; f < 2; ++f) ACSE_TRY(add(w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
+        ACSE_TRY(tc_table_add(t, w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, s == 1 ? 2.0f : 1.0f));
+    for (int f = 0; f < 2; ++f) ACSE_TRY(tc_table_add(t, w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
     b.err = w.tc_err;
     return ACSE_OK;
 }
