@@ -179,6 +179,11 @@ extern "C" int acse_destroy(acse_ctx* c) {
     for (int i = 0; i < 2 * ACSE_PROF_MAX; ++i)
         if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
     if (c->shadow) acse_destroy(c->shadow);
+    for (int b = 0; b < 3; ++b) {
+        if (c->aux[b]) cudaStreamDestroy(c->aux[b]);
+        if (c->ev_join[b]) cudaEventDestroy(c->ev_join[b]);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     ny_free(c);
     adj_free(c);
     tc_plan_destroy(c);
@@ -266,21 +271,47 @@ struct Staged {
     int host_in, host_out;
 };
 
+// Copies of up to three r^4 blocks between host and device (null entries skipped), issued on three
+// auxiliary streams forked from and joined back into the context's stream, so that the copy engines
+// move the blocks concurrently.
+static int copy_blocks(acse_ctx* c, void* const dst[3], const void* const src[3], cudaMemcpyKind kind) {
+    if (!c->ev_fork) {
+        ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        for (int b = 0; b < 3; ++b) {
+            ACSE_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking));
+            ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[b], cudaEventDisableTiming));
+        }
+    }
+    const size_t b4 = n4_of(c) * sizeof(double);
+    ACSE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
+    for (int b = 0; b < 3; ++b) {
+        if (!dst[b]) continue;
+        ACSE_CUDA_TRY(cudaStreamWaitEvent(c->aux[b], c->ev_fork, 0));
+        ACSE_CUDA_TRY(cudaMemcpyAsync(dst[b], src[b], b4, kind, c->aux[b]));
+        ACSE_CUDA_TRY(cudaEventRecord(c->ev_join[b], c->aux[b]));
+        ACSE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join[b], 0));
+    }
+    return ACSE_OK;
+}
+
 static int stage_inputs(acse_ctx* c, const double* D0, const double* D1, const double* D2, const double* src[3],
                         int* host) {
     const double* Ds[3] = {D0, D1, D2};
     *host = 0;
-    const size_t b4 = n4_of(c) * sizeof(double);
+    void* dst[3] = {nullptr, nullptr, nullptr};
+    const void* from[3] = {nullptr, nullptr, nullptr};
     for (int s = 0; s < 3; ++s) {
         if (!Ds[s]) return ACSE_ERR_ARG;
         if (is_host_ptr(Ds[s])) {
-            ACSE_CUDA_TRY(cudaMemcpyAsync(c->w.stage_in[s], Ds[s], b4, cudaMemcpyHostToDevice, c->stream));
+            dst[s] = c->w.stage_in[s];
+            from[s] = Ds[s];
             src[s] = c->w.stage_in[s];
             *host = 1;
         } else {
             src[s] = Ds[s];
         }
     }
+    if (*host) ACSE_TRY(copy_blocks(c, dst, from, cudaMemcpyHostToDevice));
     return ACSE_OK;
 }
 
@@ -355,12 +386,16 @@ extern "C" int acse_residual(acse_ctx* c, const double* Daa, const double* Dab, 
         }
     }
     if (s == ACSE_OK) s = residual_dev(c, D, A, c->w.scal + 0);
-    const size_t b4 = n4_of(c) * sizeof(double);
-    for (int b = 0; b < 3 && s == ACSE_OK; ++b)
-        if (host_out[b]) {
-            if (cudaMemcpyAsync(Aout[b], A[b], b4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) s = ACSE_ERR_CUDA;
-            sync = 1;
+    if (s == ACSE_OK && (host_out[0] || host_out[1] || host_out[2])) {
+        void* dst[3];
+        const void* from[3];
+        for (int b = 0; b < 3; ++b) {
+            dst[b] = host_out[b] ? (void*)Aout[b] : nullptr;
+            from[b] = A[b];
         }
+        s = copy_blocks(c, dst, from, cudaMemcpyDeviceToHost);
+        sync = 1;
+    }
     if (s == ACSE_OK) s = put_scalar(c, norm2, c->w.scal + 0, &sync);
     if (s == ACSE_OK && (sync || host_in)) s = sync_and_status(c);
     return latch(c, s);
@@ -402,12 +437,14 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
     }
     if (s == ACSE_OK) s = launch_axpy_energy(c, D, Uc, w.scal + 3, w.scal + 1);
     if (s == ACSE_OK && host_in) {
-        const size_t b4 = n4_of(c) * sizeof(double);
         double* Dh[3] = {Daa, Dab, Dbb};
-        for (int b = 0; b < 3 && s == ACSE_OK; ++b)
-            if (D[b] == w.stage_in[b] &&
-                cudaMemcpyAsync(Dh[b], D[b], b4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-                s = ACSE_ERR_CUDA;
+        void* dst[3];
+        const void* from[3];
+        for (int b = 0; b < 3; ++b) {
+            dst[b] = D[b] == w.stage_in[b] ? (void*)Dh[b] : nullptr;
+            from[b] = D[b];
+        }
+        s = copy_blocks(c, dst, from, cudaMemcpyDeviceToHost);
         sync = 1;
     }
     if (s == ACSE_OK) s = put_scalar(c, E_out, w.scal + 1, &sync);

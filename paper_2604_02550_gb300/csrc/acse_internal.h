@@ -55,6 +55,9 @@ void tc_table_free(TcTable* t);
 int tc_table_upload(TcTable* t);
 int tc_table_append(TcTable* t, struct acse_ctx* c);
 void tc_table_set_err(TcTable* t, int* err);
+int tc_default_bn(int r);
+int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t ldb, float* C, int M, int N, int L,
+                    int ldc, float alpha);
 int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha);
 int tc_table_launch(const TcTable* t, cudaStream_t st);
 
@@ -129,6 +132,8 @@ struct acse_ctx {
     void* adj;            // adjoint workspace (allocated by the first acse_residual_backward call)
     struct acse_ctx* shadow;   // FP64 companion of a split-precision context (its adjoint), or null
     void* ny;             // NY reconstruction workspace (acse_ny.cu), or null for V
+    cudaStream_t aux[3];  // host <-> device copies of the three blocks run concurrently on these
+    cudaEvent_t ev_fork, ev_join[3];
     const double* cur_D[3];   // operands of the contraction pass in flight (FP64 GEMM list)
     const double* cur_W[3];
     // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches

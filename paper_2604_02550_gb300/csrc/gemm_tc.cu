@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const TcBatch* __rest
         const bool store = ok && !*abort_flag && nk > 0;
         const int row = m0 + q * 32 + lane;
         float* Crow = P.C + (size_t)row * P.ldc;
-        const bool vec = (P.ldc & 3) == 0 && P.perm_r == 0;
+        const bool vec = (P.ldc & 3) == 0 && P.perm_r == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0;
         // permuted particle-hole store: row (sK, kk, jj) fixed per thread, columns (sI, i, l)
         const int pr = P.perm_r, pR2 = pr * pr;
         int sK = 0, kk = 0, jj = 0, nsb = 1;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
             tc_tile_coords<BN>(P, t - P.tile_start, m0, n0);
             const int row = m0 + q * 32 + lane;
             float* Crow = P.C + (size_t)row * P.ldc;
-            const bool vec = (P.ldc & 3) == 0;
+            const bool vec = (P.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0;
             const bool store = P.kblocks > 0;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
@@ -552,13 +552,15 @@ static int get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
     return ACSE_OK;
 }
 
-static int encode_map(int kind, CUtensorMap* m, const void* base, int rows, int inner_elems, int box_rows) {
+// 2-D map over `rows` rows of `inner_elems` elements, consecutive rows `row_stride` elements apart.
+static int encode_map(int kind, CUtensorMap* m, const void* base, int rows, int inner_elems, int box_rows,
+                      size_t row_stride) {
     PFN_cuTensorMapEncodeTiled_v12000 enc;
     ACSE_TRY(get_encode(&enc));
     const CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const int es = kind == 0 ? 2 : 4;
     cuuint64_t gdim[2] = {(cuuint64_t)inner_elems, (cuuint64_t)rows};
-    cuuint64_t gstride[1] = {(cuuint64_t)inner_elems * es};
+    cuuint64_t gstride[1] = {(cuuint64_t)row_stride * es};
     cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, dt, 2, const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -603,15 +605,16 @@ int tc_table_upload(TcTable* t) {
     return ACSE_OK;
 }
 
-// Append one problem C[M][N] = alpha * A'[M][L] B'[N][L]^T (K-major split operand rows of L elements,
-// L a multiple of the 128-byte K block) to table t.
-int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) {
+// Append one problem C[M][N] = alpha * A'[M][L] B'[N][L]^T (K-major split operand rows: L elements
+// used, a multiple of the 128-byte K block, consecutive rows lda / ldb elements apart) to table t.
+int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t ldb, float* C, int M, int N, int L,
+                    int ldc, float alpha) {
     TcBatch& b = *t->host;
     const int kel = t->kind == 0 ? 64 : 32;
-    if (b.nprob + 1 > TC_MAXP || L % kel) return ACSE_ERR_SHAPE;
+    if (b.nprob + 1 > TC_MAXP || L % kel || lda < (size_t)L || ldb < (size_t)L) return ACSE_ERR_SHAPE;
     const int n = b.nprob;
-    ACSE_TRY(encode_map(t->kind, &b.tmA[n], A, M, L, TC_BM));
-    ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->bn));
+    ACSE_TRY(encode_map(t->kind, &b.tmA[n], A, M, L, TC_BM, lda));
+    ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->bn, ldb));
     TcProb& p = b.p[n];
     p.C = C;
     p.M = M;
@@ -625,6 +628,10 @@ int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int 
     b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
     b.nprob = n + 1;
     return ACSE_OK;
+}
+
+int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha) {
+    return tc_table_add_ld(t, A, (size_t)L, B, (size_t)L, C, M, N, L, ldc, alpha);
 }
 
 // Device flag raised by a launch of table t when a bounded wait runs out.
