@@ -57,6 +57,31 @@ static int is_host_ptr(const void* p) {
 
 static size_t n4_of(const acse_ctx* c) { return (size_t)c->r * c->r * c->r * c->r; }
 
+// Device-side address of pinned (page-locked) host memory, or null for pageable memory.
+static const void* pinned_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Copy of n doubles by the SMs (16-byte accesses when both ends are 16-byte aligned); used for
+// pinned host memory, which the GPU reads and writes directly over the host link.
+__global__ void __launch_bounds__(256) k_copy_doubles(double* __restrict__ dst, const double* __restrict__ src,
+                                                      size_t n) {
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+        const size_t n2 = n / 2;
+        for (size_t i = t0; i < n2; i += stride)
+            reinterpret_cast<double2*>(dst)[i] = reinterpret_cast<const double2*>(src)[i];
+        if ((n & 1) && t0 == 0) dst[n - 1] = src[n - 1];
+    } else {
+        for (size_t i = t0; i < n; i += stride) dst[i] = src[i];
+    }
+}
+
 // ------------------------------------------------------------------------------- create
 static int alloc_d(void** p, size_t bytes, size_t* total) {
     *total += bytes;
@@ -239,6 +264,7 @@ int acse_contract_gemm(acse_ctx* c) {
 }
 
 int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* const out[3], double* norm2_dst) {
+    if (c->opt.prec != ACSE_FP64) ACSE_TRY(tc_unpack_pairs(c));   // full [X; Y] of the same-spin sectors
     if (c->ny) ACSE_TRY(ny_pass(c));   // NY: the 3-cumulant term, added to B by the B kernel
     ACSE_TRY(launch_Q(c));
     ACSE_TRY(launch_build_B(c));
@@ -282,12 +308,22 @@ static int copy_blocks(acse_ctx* c, void* const dst[3], const void* const src[3]
             ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[b], cudaEventDisableTiming));
         }
     }
-    const size_t b4 = n4_of(c) * sizeof(double);
+    const size_t n4 = n4_of(c), b4 = n4 * sizeof(double);
     ACSE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
     for (int b = 0; b < 3; ++b) {
         if (!dst[b]) continue;
         ACSE_CUDA_TRY(cudaStreamWaitEvent(c->aux[b], c->ev_fork, 0));
-        ACSE_CUDA_TRY(cudaMemcpyAsync(dst[b], src[b], b4, kind, c->aux[b]));
+        // pinned host memory: copied by the SMs over the host link; pageable memory: copy engine
+        const void* hp = kind == cudaMemcpyHostToDevice ? src[b] : dst[b];
+        const void* dp = pinned_device_ptr(hp);
+        if (dp) {
+            double* d = kind == cudaMemcpyHostToDevice ? (double*)dst[b] : (double*)dp;
+            const double* sp = kind == cudaMemcpyHostToDevice ? (const double*)dp : (const double*)src[b];
+            k_copy_doubles<<<152 * 4, 256, 0, c->aux[b]>>>(d, sp, n4);
+            ACSE_LAUNCHED(c);
+        } else {
+            ACSE_CUDA_TRY(cudaMemcpyAsync(dst[b], src[b], b4, kind, c->aux[b]));
+        }
         ACSE_CUDA_TRY(cudaEventRecord(c->ev_join[b], c->aux[b]));
         ACSE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join[b], 0));
     }

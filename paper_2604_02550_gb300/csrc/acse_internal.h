@@ -56,6 +56,7 @@ int tc_table_upload(TcTable* t);
 int tc_table_append(TcTable* t, struct acse_ctx* c);
 void tc_table_set_err(TcTable* t, int* err);
 int tc_default_bn(int r);
+int tc_unpack_pairs(struct acse_ctx* c);
 int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t ldb, float* C, int M, int N, int L,
                     int ldc, float alpha);
 int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha);
@@ -107,6 +108,9 @@ struct Work {
     void* tc_Mf[2];
     void* tc_Zf[2];
     float* tc_pairC[3];   // [X; Y] FP32 (2r^2 x r^2)
+    float* tc_pairCp[3];  // same-spin sectors (aa, bb): the GEMM's packed [X; Y] (2P x P, P = r(r-1)/2
+                          // pairs i < j on rows and columns), expanded into tc_pairC by antisymmetry
+    int KpP;              // padded K (per split term) of the packed same-spin pair operands
     float* tc_X5d;
     float* tc_X5f[2];
     int Kp1, Kp2;         // padded K (per split term) for r^2 and 2 r^2 contractions

@@ -32,8 +32,11 @@ struct MxPtrs {
     void* Zf[2];
     float* M32[3];
     float* gam32;
-    int Kp1, Kp2, ns;
+    int Kp1, Kp2, ns, KpP;
 };
+
+// Packed number of the pair (a, b), a < b, among the r(r-1)/2 same-spin pairs (row-major over a).
+__device__ __forceinline__ int pk_pair(int r, int a, int b) { return a * r - a * (a + 1) / 2 + (b - a - 1); }
 
 static MxPtrs mx_ptrs(acse_ctx* c) {
     MxPtrs p;
@@ -52,6 +55,7 @@ static MxPtrs mx_ptrs(acse_ctx* c) {
     p.gam32 = w.gam32;
     p.Kp1 = w.Kp1;
     p.Kp2 = w.Kp2;
+    p.KpP = w.KpP;
     p.ns = c->nsplit;
     return p;
 }
@@ -85,6 +89,14 @@ __global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restric
     }
     __syncthreads();
     const size_t ld = (size_t)p.ns * p.Kp1;
+    const size_t ldP = (size_t)p.ns * p.KpP;
+    // packed row of a same-spin sector: M rows 0..P-1, D rows P..2P-1 (pairs i < j only)
+    const int P = r * (r - 1) / 2;
+    int prow = -1;
+    {
+        const int rr = mrow ? row : row - R2, ii = rr / r, jj = rr - (rr / r) * r;
+        if (ii < jj) prow = (mrow ? 0 : P) + pk_pair(r, ii, jj);
+    }
     const double* D = (s == 0 ? Daa : (s == 1 ? Dab : Dbb)) + (size_t)(mrow ? row : row - R2) * R2;
     float* Mrow = p.M32[s] + (size_t)row * R2;
     const bool vec = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(s == 0 ? Daa : (s == 1 ? Dab : Dbb)) & 15) == 0);
@@ -112,9 +124,19 @@ __global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restric
             else
                 for (int u = 0; u < nk; ++u) Mrow[k0 + u] = x[u];
         }
-        if (vec && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
-        else
-            for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
+        if (s == 1) {
+            if (vec && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
+            else
+                for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
+        } else if (prow >= 0) {
+            // same-spin sector: rows and K restricted to pairs a < b (antisymmetry; the GEMM's alpha
+            // carries the factor 2 of the (r, s) sum)
+            int kk = k0 / r, l = k0 - kk * r;
+            for (int u = 0; u < nk; ++u) {
+                if (kk < l) put<PREC, 0>(p.pairA[s], (size_t)prow, ldP, p.KpP, pk_pair(r, kk, l), x[u]);
+                if (++l == r) { l = 0; ++kk; }
+            }
+        }
     }
 }
 
@@ -223,9 +245,53 @@ __global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double*
     const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
     float x[4] = {0.f, 0.f, 0.f, 0.f};
     for (int u = 0; u < nk; ++u) x[u] = (float)W[k0 + u];
-    if ((r & 1) == 0 && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
-    else
-        for (int u = 0; u < nk; ++u) put<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0 + u, x[u]);
+    if (s == 1) {
+        if ((r & 1) == 0 && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
+        else
+            for (int u = 0; u < nk; ++u) put<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0 + u, x[u]);
+        return;
+    }
+    // same-spin sector: rows (k, p) and K (r, s) restricted to pairs a < b
+    const int kr = row / r, pr = row - (row / r) * r;
+    if (kr >= pr) return;
+    const size_t ldP = (size_t)p.ns * p.KpP;
+    const int prow = pk_pair(r, kr, pr);
+    int a = k0 / r, b = k0 - a * r;
+    for (int u = 0; u < nk; ++u) {
+        if (a < b) put<PREC, 1>(p.pairB[s], (size_t)prow, ldP, p.KpP, pk_pair(r, a, b), x[u]);
+        if (++b == r) { b = 0; ++a; }
+    }
+}
+
+// [X; Y] of a same-spin sector from the packed GEMM output: X^{ij}_{kp} = s_ij s_kp Xp[pk(ij)][pk(kp)]
+// (s = -1 for a swapped pair, 0 on the diagonal), rows r^2.. for Y likewise.  Blocks over
+// (sector aa/bb, full row); threads over columns.
+__global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, const float* __restrict__ Cp0,
+                                                         const float* __restrict__ Cp2, float* C0, float* C2) {
+    const int R2 = r * r, P = r * (r - 1) / 2;
+    const int sec = blockIdx.x / (2 * R2);
+    const int row = blockIdx.x - sec * 2 * R2;
+    const float* Cp = sec == 0 ? Cp0 : Cp2;
+    float* C = (sec == 0 ? C0 : C2) + (size_t)row * R2;
+    const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - (ij / r) * r;
+    if (i == j) {
+        for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = 0.f;
+        return;
+    }
+    const float si = i < j ? 1.f : -1.f;
+    const float* src = Cp + (size_t)(part * P + (i < j ? pk_pair(r, i, j) : pk_pair(r, j, i))) * P;
+    for (int c = threadIdx.x; c < R2; c += blockDim.x) {
+        const int k = c / r, q = c - (c / r) * r;
+        C[c] = k == q ? 0.f : (k < q ? si * src[pk_pair(r, k, q)] : -si * src[pk_pair(r, q, k)]);
+    }
+}
+
+int tc_unpack_pairs(acse_ctx* c) {
+    const int r = c->r;
+    k_mx_unpack_pairs<<<2 * 2 * r * r, 256, 0, c->stream>>>(r, c->w.tc_pairCp[0], c->w.tc_pairCp[2], c->w.tc_pairC[0],
+                                                         c->w.tc_pairC[2]);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
 }
 
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
@@ -263,9 +329,18 @@ int tc_mixed_alloc(acse_ctx* c) {
     const size_t ns = c->nsplit;
     const size_t L1 = ns * w.Kp1 * es, L2 = ns * w.Kp2 * es;   // row bytes
     // operand buffers are zeroed once: the K padding is never written afterwards
+    const size_t P = r * (r - 1) / 2;
+    w.KpP = (int)((P + kb - 1) / kb * kb);
+    const size_t LP = ns * w.KpP * es;                            // packed same-spin row bytes
     for (int s = 0; s < 3; ++s) {
-        ACSE_TRY(mx_alloc(&w.tc_pairA[s], 2 * R2 * L1, true));
-        ACSE_TRY(mx_alloc(&w.tc_pairB[s], R2 * L1, true));
+        if (s == 1) {
+            ACSE_TRY(mx_alloc(&w.tc_pairA[s], 2 * R2 * L1, true));
+            ACSE_TRY(mx_alloc(&w.tc_pairB[s], R2 * L1, true));
+        } else {
+            ACSE_TRY(mx_alloc(&w.tc_pairA[s], 2 * P * LP, true));
+            ACSE_TRY(mx_alloc(&w.tc_pairB[s], P * LP, true));
+            ACSE_TRY(mx_alloc((void**)&w.tc_pairCp[s], 2 * P * P * sizeof(float), false));
+        }
         ACSE_TRY(mx_alloc((void**)&w.tc_pairC[s], 2 * R2 * R2 * sizeof(float), false));
         ACSE_TRY(mx_alloc((void**)&w.M32[s], n4 * sizeof(float), false));
     }
@@ -288,7 +363,7 @@ int tc_mixed_alloc(acse_ctx* c) {
 
 void tc_mixed_free(acse_ctx* c) {
     Work& w = c->w;
-    void* ptrs[] = {w.tc_pairA[0], w.tc_pairA[1], w.tc_pairA[2], w.tc_pairB[0], w.tc_pairB[1], w.tc_pairB[2],
+    void* ptrs[] = {w.tc_pairCp[0], w.tc_pairCp[2], w.tc_pairA[0], w.tc_pairA[1], w.tc_pairA[2], w.tc_pairB[0], w.tc_pairB[1], w.tc_pairB[2],
                     w.tc_pairC[0], w.tc_pairC[1], w.tc_pairC[2], w.M32[0], w.M32[1], w.M32[2], w.tc_Md, w.tc_Zd,
                     w.tc_Mf[0], w.tc_Mf[1], w.tc_Zf[0], w.tc_Zf[1], w.tc_X5f[0], w.tc_X5f[1], w.tc_X5d,
                     w.H32[0], w.H32[1], w.H32[2], w.zdiag32, w.gam32, w.w32, w.Q32, w.tc_err};
