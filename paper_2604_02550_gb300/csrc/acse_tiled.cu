@@ -547,13 +547,38 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
     // row index of a flat index e < r^2 as (int)((e + 1/2) / r): the fraction stays at least 1/(2r)
     // away from an integer, far above the float rounding of the product for r <= 64
     const float invr = 1.f / (float)r;
-    const int npairs_me = blockIdx.x < R2 ? (R2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int nsteps = 3 * npairs_me;
-    // operands of step s = 3 n + round (pair blockIdx.x + n gridDim.x): X and M rows of sector
-    // round 0 -> aa (0), round 1 -> bb (2), round 2 -> ab (1)
+    // Work items: [0, P) the aa pairs i < j, [P, 2P) the bb pairs i < j, [2P, 2P + r^2) every ab
+    // pair (P = r(r-1)/2).  B and H of a same-spin sector are antisymmetric in (i, j), so the item
+    // (i, j) also writes row (j, i) = -row (i, j); the rows (i, i) are zero.
+    const int P = r * (r - 1) / 2, NI = 2 * P + R2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * (size_t)r * R2;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int sec = e < (size_t)r * R2 ? 0 : 2;
+        const size_t f = e - (sec ? (size_t)r * R2 : 0);
+        const int d = (int)(f / R2);
+        a.H[sec][(size_t)(d * r + d) * R2 + (f - (size_t)d * R2)] = 0.f;
+    }
+    auto item = [&](int L, int& round, int& i, int& j) {
+        if (L < 2 * P) {
+            round = L < P ? 0 : 1;
+            const int q = L - round * P;
+            int ii = 0;
+            while (q >= ii * r - ii * (ii + 1) / 2 + (r - ii - 1)) ++ii;
+            i = ii;
+            j = q - (ii * r - ii * (ii + 1) / 2) + ii + 1;
+        } else {
+            round = 2;
+            i = (L - 2 * P) / r;
+            j = (L - 2 * P) - i * r;
+        }
+    };
+    const int nsteps = (int)blockIdx.x < NI ? (NI - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // operands of step s (item blockIdx.x + s gridDim.x): X and M rows of its sector
+    // (round 0 -> aa (0), round 1 -> bb (2), round 2 -> ab (1))
     auto issue = [&](int step, int slot) {
-        const int n = step / 3, round = step - 3 * n;
-        const size_t ij = (size_t)blockIdx.x + (size_t)n * gridDim.x;
+        int round, ii, jj;
+        item((int)blockIdx.x + step * (int)gridDim.x, round, ii, jj);
+        const size_t ij = (size_t)ii * r + jj;
         const int sec = round == 0 ? 0 : round == 1 ? 2 : 1;
         const float* src[2] = {a.X[sec] + ij * R2, a.M[sec] + ij * R2};
         for (int h = 0; h < 2; ++h) {
@@ -582,9 +607,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
     const int kb = idx / nt, lb = idx - (idx / nt) * nt;
     constexpr int YPT = 2;                         // float4 groups of the Y row held per thread
     for (int step = 0; step < nsteps; ++step) {
-        const int n = step / 3, round = step - 3 * n;
-        const int ij = blockIdx.x + n * gridDim.x;
-        const int i = ij / r, j = ij - (ij / r) * r;
+        int round, i, j;
+        item((int)blockIdx.x + step * (int)gridDim.x, round, i, j);
+        const int ij = i * r + j;
         const int cur = step & 1;
         const int b = round == 0 ? 0 : round == 1 ? 2 : 1;
         cp_async_wait_all();
@@ -682,9 +707,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             }
         }
         __syncthreads();                                    // B types of this round complete
-        const float* P = Bs;
+        const float* Pb = Bs;
         const float* Px = round < 2 ? Bs : Bs + (size_t)r * bpitch;
         float* Hrow = a.H[b] + (size_t)ij * R2;
+        float* Hmir = round < 2 ? a.H[b] + (size_t)(j * r + i) * R2 : nullptr;   // row (j, i) = -row (i, j)
         if (yvec) {
 #pragma unroll
             for (int u = 0; u < YPT; ++u) {
@@ -695,10 +721,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                     int k = (int)(((float)(4 * g) + 0.5f) * invr), l = 4 * g - k * r;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        hh[c] = 4.f * yy[c] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                        hh[c] = 4.f * yy[c] - 12.f * (Pb[k * bpitch + l] - Px[l * bpitch + k]);
                         if (++l == r) { l = 0; ++k; }
                     }
                     reinterpret_cast<float4*>(Hrow)[g] = make_float4(hh[0], hh[1], hh[2], hh[3]);
+                    if (Hmir) reinterpret_cast<float4*>(Hmir)[g] = make_float4(-hh[0], -hh[1], -hh[2], -hh[3]);
                 }
             }
             for (int g = threadIdx.x + YPT * blockDim.x; g < R2 / 4; g += blockDim.x) {   // rows beyond the prefetch
@@ -708,15 +735,18 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 int k = (int)(((float)(4 * g) + 0.5f) * invr), l = 4 * g - k * r;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    hh[c] = 4.f * yy[c] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                    hh[c] = 4.f * yy[c] - 12.f * (Pb[k * bpitch + l] - Px[l * bpitch + k]);
                     if (++l == r) { l = 0; ++k; }
                 }
                 reinterpret_cast<float4*>(Hrow)[g] = make_float4(hh[0], hh[1], hh[2], hh[3]);
+                if (Hmir) reinterpret_cast<float4*>(Hmir)[g] = make_float4(-hh[0], -hh[1], -hh[2], -hh[3]);
             }
         } else {
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
                 const int k = e / r, l = e - k * r;
-                Hrow[e] = 4.f * Yrow[e] - 12.f * (P[k * bpitch + l] - Px[l * bpitch + k]);
+                const float hv = 4.f * Yrow[e] - 12.f * (Pb[k * bpitch + l] - Px[l * bpitch + k]);
+                Hrow[e] = hv;
+                if (Hmir) Hmir[e] = -hv;
             }
         }
     }
@@ -857,7 +887,8 @@ int launch_B_tiled(acse_ctx* c) {
                 cudaGetLastError();
                 per_sm = 1;
             }
-            cached_grid = nsm * per_sm < R2 ? nsm * per_sm : R2;
+            const int items = r * (r - 1) + R2;   // same-spin pairs i < j twice, every mixed pair
+            cached_grid = nsm * per_sm < items ? nsm * per_sm : items;
             cached_r = r;
         }
         if (r48) k_B_pipe<320, 2, 48><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);

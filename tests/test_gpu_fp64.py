@@ -190,3 +190,20 @@ def test_error_codes(acse):
     assert ei.value.status == -3
     assert _lib.lib().acse_last_error(ctx) == -3
     _lib.acse_destroy(ctx)
+
+
+def test_pinned_host_arguments(acse):
+    """Pinned (page-locked) host buffers go through the SM copy path: same results as device ones."""
+    from paper_2604_02550_gb300 import _lib
+    p = _random_problem(6, 3, 2, 8)
+    ctx = acse.ACSE(6, 3, 2, p.h, p.V, "fp64")
+    Dd = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    Dh = [torch.from_numpy(x.copy()).pin_memory() for x in (p.Daa, p.Dab, p.Dbb)]
+    Eh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        E, _, _ = ctx.step(Dd, 1e-3)
+        _lib.acse_step(ctx.ctx, *Dh, 1e-3, Eh, None, None)
+    torch.cuda.synchronize()
+    assert maxrel([x.numpy() for x in Dh], to_np(Dd)) == 0.0
+    assert float(Eh[0]) == float(E)
+    ctx.close()
