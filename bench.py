@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32", "tf32x3"])
     ap.add_argument("--recon", default="V", choices=["V", "NY"], help="3-RDM reconstruction")
+    ap.add_argument("--singlet", action="store_true",
+                    help="spin-flip specialisation of the split path (closed-shell workloads only)")
     ap.add_argument("--r", type=int, default=48, help="orbitals (48: the CAS(8e,8o) workload)")
     ap.add_argument("--eps", type=float, default=None,
                     help="Euler step; default 1e-4 for r >= 32 (1e-3 diverges there), else the paper's 1e-3")
@@ -97,16 +99,20 @@ def gemm_traffic(prec):
     return float(kv["traffic_bytes"])
 
 
-def flops_per_pass(r, packed=False):
+def flops_per_pass(r, packed=False, singlet=False):
     """2 M N K over the O(r^6) GEMMs of one contraction pass G(W):
     pair-pair: 3 spin sectors x ([M; D] (2 r^2 rows) x r^2 x r^2); particle-hole: one
     (2r^2)^3 diagonal-sector GEMM and two (r^2)^3 spin-flip GEMMs  ->  32 r^6.
     packed=True counts the plan the tensor-core path runs: the same-spin pair GEMMs on pairs i < j
-    only (P = r(r-1)/2: [M; D] 2P rows x P columns x P K each)."""
+    only (P = r(r-1)/2: [M; D] 2P rows x P columns x P K each).  singlet=True (spin-flip
+    specialisation) drops the bb pair GEMM, the beta-led rows of the diagonal particle-hole GEMM
+    and the second spin-flip GEMM."""
     R2 = r * r
     if not packed:
         return 2 * (3 * (2 * R2) * R2 * R2 + (2 * R2) ** 3 + 2 * R2 ** 3)
     P = r * (r - 1) // 2
+    if singlet:
+        return 2 * ((2 * P) * P * P + (2 * R2) * R2 * R2 + R2 * (2 * R2) * (2 * R2) + R2 ** 3)
     return 2 * (2 * (2 * P) * P * P + (2 * R2) * R2 * R2 + (2 * R2) ** 3 + 2 * R2 ** 3)
 
 
@@ -509,7 +515,8 @@ def main():
     if args.eps is None:
         args.eps = 1e-4 if p.r >= 32 else 1e-3
     stream = torch.cuda.Stream()
-    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream, recon=args.recon)
+    singlet = bool(args.singlet) and prec != "fp64"
+    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream, recon=args.recon, singlet=singlet)
     with torch.cuda.stream(stream):
         D0 = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
         D = tuple(x.clone() for x in D0)
@@ -542,7 +549,7 @@ def main():
     per_step = ms_max / args.steps
     value = whole_job_rate(args.steps, world, ms_max)
     fl_alg = flops_per_pass(p.r)                       # 32 r^6: the unpacked formulation
-    fl = fl_alg if prec == "fp64" else flops_per_pass(p.r, packed=True)   # what the GEMM launch executes
+    fl = fl_alg if prec == "fp64" else flops_per_pass(p.r, packed=True, singlet=singlet)   # what the GEMM launch executes
     split = 3 if prec in ("bf16x3", "tf32x3") else 1
     # dominant kernel: the grouped O(r^6) GEMM launch (one per contraction pass)
     gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1e3
@@ -574,6 +581,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else f"{prec} (f32 accumulate)",
             "data": "synthetic",
             "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "recon": args.recon, "eps": args.eps,
+                       "singlet": singlet,
                        "step": "acse_step: residual + update + axpy + energy",
                        "reset_every": args.reset_every,
                        "l2": "inputs larger than L2 (about 1.5 GB of r^4 tensors touched per step)",

@@ -84,6 +84,12 @@ typedef struct {
     int line_search;   /* 1: acse_step picks eps from ||A(D + e U)||^2 at {0, e0, 2 e0}     */
     double eps0;       /* initial trial step of the line search (e0); 0 -> 1e-3             */
     int check_inputs;  /* 1: acse_residual / acse_step verify Tr 2D and finiteness (syncs)  */
+    int singlet;       /* 1: the caller asserts spin-flip symmetry (n_alpha = n_beta, D_aa = D_bb,
+                        * D_ab^{ij}_{kl} = D_ab^{ji}_{lk}: singlets and any Ms = 0 state with that
+                        * symmetry); the split precisions then compute only the alpha-led half of
+                        * the spin sectors and copy the beta-beta block of A, U from alpha-alpha
+                        * (Theory: for a singlet the aa and bb residual blocks coincide).  Ignored
+                        * in FP64; rejected (ACSE_ERR_ARG) when n_alpha != n_beta.            */
 } acse_opts;
 
 /* Create a context for one problem.  h (r*r) and V (r^4, chemist's (pq|rs)) are read once to

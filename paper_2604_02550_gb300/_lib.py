@@ -24,7 +24,7 @@ EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_
 class AcseOpts(ctypes.Structure):
     _fields_ = [("r", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("prec", c_int), ("recon", c_int),
                 ("mask_active", c_int), ("act_lo", c_int), ("act_hi", c_int), ("line_search", c_int),
-                ("eps0", c_double), ("check_inputs", c_int)]
+                ("eps0", c_double), ("check_inputs", c_int), ("singlet", c_int)]
 
 
 class AcseError(RuntimeError):
@@ -117,7 +117,7 @@ RECON = {"V": 0, "NY": 1}
 
 
 def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
-                check_inputs=False, stream=None, recon="V"):
+                check_inputs=False, stream=None, recon="V", singlet=False):
     o = AcseOpts()
     o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -127,6 +127,7 @@ def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=Fa
     o.line_search = int(bool(line_search))
     o.eps0 = float(eps0)
     o.check_inputs = int(bool(check_inputs))
+    o.singlet = int(bool(singlet))
     h_ = c_void_p()
     st = current_stream_handle() if stream is None else stream
     _check(lib().acse_create(byref(h_), byref(o), ptr(h), ptr(V), st), "acse_create")

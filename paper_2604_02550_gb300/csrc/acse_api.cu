@@ -149,6 +149,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         return ACSE_ERR_SHAPE;
     if (o->prec < ACSE_FP64 || o->prec > ACSE_TF32X3) return ACSE_ERR_ARG;
     if (o->recon != ACSE_RECON_V && o->recon != ACSE_RECON_NY) return ACSE_ERR_UNSUPPORTED;
+    if (o->singlet && o->n_alpha != o->n_beta) return ACSE_ERR_ARG;
     if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
     acse_ctx* c = (acse_ctx*)calloc(1, sizeof(acse_ctx));
     if (!c) return ACSE_ERR_NOMEM;

@@ -212,8 +212,9 @@ int launch_Q(acse_ctx* c) {
         k_Q_from_X<double><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(r, c->w.X[0], c->w.X[1], c->w.X[2], R2,
                                                                           c->w.Q);
     } else {
-        k_Q_from_X<float><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(r, c->w.tc_pairC[0], c->w.tc_pairC[1],
-                                                                         c->w.tc_pairC[2], R2, c->w.Q32);
+        // spin-flip specialisation: Xbb is the flip of Xaa (same values)
+        k_Q_from_X<float><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(
+            r, c->w.tc_pairC[0], c->w.tc_pairC[1], c->w.tc_pairC[acse_singlet(c) ? 0 : 2], R2, c->w.Q32);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -244,6 +245,7 @@ struct GArgs {
     double* out[3];
     T s, scale;
     int mask, lo, hi;
+    int flip;   // spin-flip specialisation: H[2] is not formed; G_bb = G_aa (written from blk 0)
     double* partial;
 };
 
@@ -278,13 +280,14 @@ struct NormAcc<float> {
 
 template <typename T>
 __device__ __forceinline__ void g_put(const GArgs<T>& a, int blk, int r, int R2, int ij, int kl, T v, NormAcc<T>& nrm) {
-    nrm.add(v, blk == 1 ? (T)4 : (T)1);
+    nrm.add(v, blk == 1 ? (T)4 : (a.flip ? (T)2 : (T)1));
     double o = (double)v;
     if (a.mask) {
         const int i = ij / r, j = ij - i * r, k = kl / r, l = kl - k * r;
         if (i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo && l < a.hi) o = 0.0;
     }
     a.out[blk][(size_t)ij * R2 + kl] = o;
+    if (a.flip && blk == 0) a.out[2][(size_t)ij * R2 + kl] = o;
 }
 
 // G_b = scale (H_b - s H_b^T) (pair transpose), the masked result in FP64 and the unmasked norm
@@ -300,7 +303,8 @@ __global__ void __launch_bounds__(256) k_assemble_G(const __grid_constant__ GArg
     const int nT = (R2 + 31) / 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     NormAcc<T> nrm;
-    for (int w = blockIdx.x; w < 3 * nT * nT; w += gridDim.x) {
+    const int nblk = a.flip ? 2 : 3;
+    for (int w = blockIdx.x; w < nblk * nT * nT; w += gridDim.x) {
         const int blk = w / (nT * nT);
         const int ti = (w / nT) % nT, tj = w % nT;
         if (ti > tj) continue;                              // block-uniform
@@ -345,6 +349,7 @@ static void fill_G(acse_ctx* c, GArgs<T>& a, int sW, double scale, int apply_mas
     a.lo = c->opt.act_lo;
     a.hi = c->opt.act_hi;
     a.partial = c->w.partial;
+    a.flip = acse_singlet(c) ? 1 : 0;
 }
 
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3], double* norm2_dst) {

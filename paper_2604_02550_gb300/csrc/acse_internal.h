@@ -150,6 +150,10 @@ struct acse_ctx {
 };
 #define ACSE_PROF_MAX 256
 
+// Spin-flip specialisation in force (opts.singlet on a split-precision context): only the alpha-led
+// half of the spin sectors is computed and the beta-beta results are taken from alpha-alpha.
+static inline bool acse_singlet(const acse_ctx* c) { return c->opt.singlet && c->opt.prec != ACSE_FP64; }
+
 // count a kernel launch of context c and check the launch error
 #define ACSE_LAUNCHED(c)                                                      \
     do {                                                                      \

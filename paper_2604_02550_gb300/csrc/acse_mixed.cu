@@ -210,18 +210,24 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
     const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
     const int R2 = r * r;
+    // spin-flip specialisation: M_bb = M_aa (the bb sector of [M; D] is not formed) and Mf2 feeds only
+    // the second spin-flip GEMM, which is not run
+    const bool sf = acse_singlet(c);
+    const int nph = sf ? 5 : 6, nsec = sf ? 2 : 3;
+    MxPtrs q = p;
+    if (sf) q.M32[2] = q.M32[0];
     if (c->opt.prec == ACSE_BF16X3) {
-        k_mx_prepD<ACSE_BF16X3><<<6 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_BF16X3><<<nsec * 2 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_BF16X3><<<6 * R2, 256, 0, c->stream>>>(r, p);
+        k_mx_pack_Mph<ACSE_BF16X3><<<nph * R2, 256, 0, c->stream>>>(r, q);
     } else if (c->opt.prec == ACSE_TF32X3) {
-        k_mx_prepD<ACSE_TF32X3><<<6 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_TF32X3><<<nsec * 2 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_TF32X3><<<6 * R2, 256, 0, c->stream>>>(r, p);
+        k_mx_pack_Mph<ACSE_TF32X3><<<nph * R2, 256, 0, c->stream>>>(r, q);
     } else {
-        k_mx_prepD<ACSE_TF32><<<6 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        k_mx_prepD<ACSE_TF32><<<nsec * 2 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_TF32><<<6 * R2, 256, 0, c->stream>>>(r, p);
+        k_mx_pack_Mph<ACSE_TF32><<<nph * R2, 256, 0, c->stream>>>(r, q);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -288,7 +294,8 @@ __global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, const float* __r
 
 int tc_unpack_pairs(acse_ctx* c) {
     const int r = c->r;
-    k_mx_unpack_pairs<<<2 * 2 * r * r, 256, 0, c->stream>>>(r, c->w.tc_pairCp[0], c->w.tc_pairCp[2], c->w.tc_pairC[0],
+    const int nsec = acse_singlet(c) ? 1 : 2;   // the bb sector is not formed under the spin flip
+    k_mx_unpack_pairs<<<nsec * 2 * r * r, 256, 0, c->stream>>>(r, c->w.tc_pairCp[0], c->w.tc_pairCp[2], c->w.tc_pairC[0],
                                                          c->w.tc_pairC[2]);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -298,12 +305,13 @@ int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const int r = c->r;
     const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
+    const dim3 grid((r * r / 4 + 128) / 128, (acse_singlet(c) ? 2 : 3) * r * r);   // no bb pair GEMM under the spin flip
     if (c->opt.prec == ACSE_BF16X3)
-        k_mx_pack_W<ACSE_BF16X3><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_BF16X3><<<grid, 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     else if (c->opt.prec == ACSE_TF32X3)
-        k_mx_pack_W<ACSE_TF32X3><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_TF32X3><<<grid, 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     else
-        k_mx_pack_W<ACSE_TF32><<<dim3((r * r / 4 + 128) / 128, 3 * r * r), 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_TF32><<<grid, 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
     ACSE_LAUNCHED(c);
     return launch_Z_tiled(c, W);   // Z packs and w (the diagonal of Z)
 }

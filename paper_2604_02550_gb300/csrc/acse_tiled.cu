@@ -61,6 +61,8 @@ struct ZOut {
     int ldd, ldf;  // row length in elements
     int Kp1, Kp2;  // K segment length (split modes)
     void* diag;    // [4][r][r][r]: rows j = p of Zd(a,a), Zd(b,b), Zf1, Zf2
+    int ntypes;    // spin types computed (6, or 3 with the spin-flip specialisation) ...
+    int tmap[6];   // ... and which: block type index -> t
 };
 
 template <typename T>
@@ -179,8 +181,9 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
     T* gT = (T*)(stage + (size_t)ipb * R2e);             // [q][j] = 1D[j][q], row pitch ldw
     T* Ws = gT + (size_t)rp * ldw;                       // [ipb][q][s], row pitch ldw
     const int nchunk = (r + pchunk - 1) / pchunk;
-    const int t = blockIdx.x / (r * nchunk);
-    const int rem = blockIdx.x - t * r * nchunk;
+    const int tb = blockIdx.x / (r * nchunk);
+    const int t = o.tmap[tb];
+    const int rem = blockIdx.x - tb * r * nchunk;
     const int k = rem / nchunk;
     const int pb = (rem - k * nchunk) * pchunk;
     const int pe = min(r, pb + pchunk);
@@ -279,13 +282,15 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
 // One block per (spin, k): warp w sums p = w, w + 8, ...; lanes over s; the 8 partials are added
 // in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_w_from_diag(int r, const T* __restrict__ diag, T* __restrict__ wout) {
+__global__ void __launch_bounds__(256) k_w_from_diag(int r, const T* __restrict__ diag, T* __restrict__ wout,
+                                                     int flip) {
     __shared__ T part[8][ACSE_MAX_R];
     const int R2 = r * r;
     const int sp = blockIdx.x / r, k = blockIdx.x % r;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T* d0 = diag + (size_t)(sp == 0 ? 0 : 1) * R2 * r;
-    const T* d1 = diag + (size_t)(sp == 0 ? 2 : 3) * R2 * r;
+    // flip: w_b = w_a (spin-flip specialisation; slots 1 and 3 are not formed)
+    const T* d0 = diag + (size_t)(sp == 0 || flip ? 0 : 1) * R2 * r;
+    const T* d1 = diag + (size_t)(sp == 0 || flip ? 2 : 3) * R2 * r;
     for (int s = lane; s < r; s += 32) {
         T acc = 0;
         for (int p = w; p < r; p += 8) acc += d0[((size_t)k * r + p) * r + s] - d1[((size_t)k * r + p) * r + s];
@@ -315,6 +320,8 @@ struct BTiledArgs {
     const T* Q;
     T* H[3];
     const T* ny[4];     // NY three-body term per spin type (acse_ny.cu), added to B; null for V
+    int flip;           // spin-flip specialisation: no bb items; the b-led particle-hole blocks and the
+                        // second flip sector are read as their alpha-led flips
 };
 
 // Block (i, j).  Spin types t = 0 (aaaa), 1 (bbbb), 2 (abab), 3 (abba):
@@ -550,7 +557,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
     // Work items: [0, P) the aa pairs i < j, [P, 2P) the bb pairs i < j, [2P, 2P + r^2) every ab
     // pair (P = r(r-1)/2).  B and H of a same-spin sector are antisymmetric in (i, j), so the item
     // (i, j) also writes row (j, i) = -row (i, j); the rows (i, i) are zero.
-    const int P = r * (r - 1) / 2, NI = 2 * P + R2;
+    const int P = r * (r - 1) / 2, NB = a.flip ? 0 : P, NI = P + NB + R2;   // NB: bb items
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * (size_t)r * R2;
          e += (size_t)gridDim.x * blockDim.x) {
         const int sec = e < (size_t)r * R2 ? 0 : 2;
@@ -559,7 +566,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
         a.H[sec][(size_t)(d * r + d) * R2 + (f - (size_t)d * R2)] = 0.f;
     }
     auto item = [&](int L, int& round, int& i, int& j) {
-        if (L < 2 * P) {
+        if (L < P + NB) {
             round = L < P ? 0 : 1;
             const int q = L - round * P;
             int ii = 0;
@@ -568,8 +575,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             j = q - (ii * r - ii * (ii + 1) / 2) + ii + 1;
         } else {
             round = 2;
-            i = (L - 2 * P) / r;
-            j = (L - 2 * P) - i * r;
+            i = (L - P - NB) / r;
+            j = (L - P - NB) - i * r;
         }
     };
     const int nsteps = (int)blockIdx.x < NI ? (NI - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -642,7 +649,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 if (t == 0) { X5b = X8b = a.X5d; ld5 = ld8 = R22; }
                 else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
                 else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
-                else { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
+                else if (!a.flip) { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
+                else { X5b = a.X5d + R2; ld5 = R22; X8b = a.X5f1; ld8 = R2; }   // flips of X5d(b,a), X5f2
                 float rest[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -809,13 +817,19 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
     ZOut o;
     Work& w = c->w;
     const int R2 = r * r;
+    const bool sf = acse_singlet(c);
+    // spin-flip specialisation: Zd(b,b), Zd(b,a), Zf2 are the flips of Zd(a,a), Zd(a,b), Zf1 and only
+    // the alpha-led rows of the diagonal particle-hole GEMM are formed
+    o.ntypes = sf ? 3 : 6;
+    const int tm_sf[6] = {0, 1, 4, 0, 0, 0};
+    for (int k = 0; k < 6; ++k) o.tmap[k] = sf ? tm_sf[k] : k;
     if (c->opt.prec == ACSE_FP64) {
         o.Zd = w.Zd; o.Zf[0] = w.Zf1; o.Zf[1] = w.Zf2;
         o.mode = 0; o.ldd = 2 * R2; o.ldf = R2; o.Kp1 = o.Kp2 = 0; o.diag = w.zdiag;
         const ZPlan zp = z_plan(r, 0, sizeof(double), (const void*)k_Z_pipe<0>);
-        k_Z_pipe<0><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        k_Z_pipe<0><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
-        k_w_from_diag<double><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag, w.w);
+        k_w_from_diag<double><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag, w.w, 0);
     } else {
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
         o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : (c->opt.prec == ACSE_TF32X3 ? 3 : 2);
@@ -826,15 +840,15 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
                                                                                       : (const void*)k_Z_pipe<2>;
         const ZPlan zp = z_plan(r, o.mode, sizeof(float), kern);
         if (r48)
-            k_Z_pipe<1, 48><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<1, 48><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         else if (o.mode == 1)
-            k_Z_pipe<1><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<1><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         else if (o.mode == 3)
-            k_Z_pipe<3><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<3><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         else
-            k_Z_pipe<2><<<zp.blocks, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<2><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         ACSE_LAUNCHED(c);
-        k_w_from_diag<float><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag32, w.w32);
+        k_w_from_diag<float><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag32, w.w32, sf ? 1 : 0);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -854,6 +868,7 @@ int launch_B_tiled(acse_ctx* c) {
         a.r = r;
         for (int s = 0; s < 3; ++s) { a.X[s] = w.X[s]; a.Y[s] = w.Y[s]; a.M[s] = w.M[s]; a.H[s] = w.H[s]; }
         a.X5d = w.X5d; a.X5f1 = w.X5f1; a.X5f2 = w.X5f2;
+        a.flip = 0;
         for (int t = 0; t < 4; ++t) a.ny[t] = (const double*)ny_terms(c, t);
         a.gam = w.gam; a.w = w.w; a.Q = w.Q;
         if (b_smem(r, sizeof(double), true) <= k_smem_cap)
@@ -866,20 +881,23 @@ int launch_B_tiled(acse_ctx* c) {
         for (int s = 0; s < 3; ++s) {
             a.X[s] = w.tc_pairC[s];
             a.Y[s] = w.tc_pairC[s] + (size_t)R2 * R2;   // rows r^2.. of [X; Y]
+        }
+        for (int s = 0; s < 3; ++s) {
             a.M[s] = w.M32[s];
             a.H[s] = w.H32[s];
         }
+        a.flip = acse_singlet(c) ? 1 : 0;
         a.X5d = w.tc_X5d; a.X5f1 = w.tc_X5f[0]; a.X5f2 = w.tc_X5f[1];
         for (int t = 0; t < 4; ++t) a.ny[t] = (const float*)ny_terms(c, t);
         a.gam = w.gam32; a.w = w.w32; a.Q = w.Q32;
-        static thread_local int cached_r = -1, cached_grid = 0;
+        static thread_local int cached_r = -1, cached_flip = -1, cached_grid = 0;
         const int nt2 = (pad4(r) / 4) * (pad4(r) / 4);
         const int threads = (((nt2 + 31) & ~31) + nt2 + 31) / 32 * 32;
         const bool small = threads <= 320;
         const bool r48 = pad4(r) == 48;
         const void* kern = r48 ? (const void*)k_B_pipe<320, 2, 48>
                                : small ? (const void*)k_B_pipe<320, 2, 0> : (const void*)k_B_pipe<BP_MAX_THREADS, 1, 0>;
-        if (cached_r != r) {
+        if (cached_r != r || cached_flip != a.flip) {
             int per_sm = 1, nsm = 152, dev = 0;
             if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, bp_smem(r)) != cudaSuccess ||
@@ -887,9 +905,10 @@ int launch_B_tiled(acse_ctx* c) {
                 cudaGetLastError();
                 per_sm = 1;
             }
-            const int items = r * (r - 1) + R2;   // same-spin pairs i < j twice, every mixed pair
+            const int items = (a.flip ? 1 : 2) * (r * (r - 1) / 2) + R2;   // same-spin pairs i < j, mixed pairs
             cached_grid = nsm * per_sm < items ? nsm * per_sm : items;
             cached_r = r;
+            cached_flip = a.flip;
         }
         if (r48) k_B_pipe<320, 2, 48><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);
         else if (small) k_B_pipe<320, 2, 0><<<cached_grid, threads, bp_smem(r), c->stream>>>(a);

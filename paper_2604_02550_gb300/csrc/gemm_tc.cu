@@ -645,16 +645,21 @@ int tc_table_append(TcTable* t, acse_ctx* c) {
     const int ns = c->nsplit;
     const int L1 = ns * w.Kp1, L2 = ns * w.Kp2;      // operand row lengths (elements)
     if (b.nprob + 6 > TC_MAXP) return ACSE_ERR_SHAPE;
-    // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones
-    ACSE_TRY(tc_table_add(t, w.tc_Zd, w.tc_Md, w.tc_X5d, R22, R22, L2, R22, 1.0f));
+    // the diagonal particle-hole GEMM first (largest K), then the pair-pair and spin-flip ones; with the
+    // spin-flip specialisation only the alpha-led rows of the diagonal sector, the aa and ab pair
+    // sectors and the first flip sector
+    const bool sf = acse_singlet(c);
+    ACSE_TRY(tc_table_add(t, w.tc_Zd, w.tc_Md, w.tc_X5d, sf ? R2 : R22, R22, L2, R22, 1.0f));
     // same-spin sectors on packed pairs (i < j rows, k < p columns, r < s K; alpha 2 for the (r, s) sum),
     // the mixed sector on full pairs (alpha 2: both orders of the mixed (r, s) pairs)
     const int P = r * (r - 1) / 2, LP = ns * w.KpP;
     for (int s = 0; s < 3; ++s) {
         if (s == 1) ACSE_TRY(tc_table_add(t, w.tc_pairA[s], w.tc_pairB[s], w.tc_pairC[s], R22, R2, L1, R2, 2.0f));
-        else ACSE_TRY(tc_table_add(t, w.tc_pairA[s], w.tc_pairB[s], w.tc_pairCp[s], 2 * P, P, LP, P, 2.0f));
+        else if (!(sf && s == 2))
+            ACSE_TRY(tc_table_add(t, w.tc_pairA[s], w.tc_pairB[s], w.tc_pairCp[s], 2 * P, P, LP, P, 2.0f));
     }
-    for (int f = 0; f < 2; ++f) ACSE_TRY(tc_table_add(t, w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
+    for (int f = 0; f < (sf ? 1 : 2); ++f)
+        ACSE_TRY(tc_table_add(t, w.tc_Zf[f], w.tc_Mf[f], w.tc_X5f[f], R2, R2, L1, R2, 1.0f));
     b.err = w.tc_err;
     return ACSE_OK;
 }
