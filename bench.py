@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32", "tf32x3"])
+    ap.add_argument("--prec", default=None, choices=["fp64", "bf16x3", "tf32", "tf32x3", "ozaki"])
     ap.add_argument("--recon", default="V", choices=["V", "NY"], help="3-RDM reconstruction")
     ap.add_argument("--singlet", action="store_true",
                     help="spin-flip specialisation of the split path (closed-shell workloads only)")
@@ -97,6 +97,9 @@ def gemm_traffic(prec):
     if hashlib.sha1(open(src, "rb").read()).hexdigest() != kv.get("gemm_tc_sha1"):
         return None
     return float(kv["traffic_bytes"])
+
+
+OZ_SLICES = 8   # default slices of ACSE_OZAKI
 
 
 def flops_per_pass(r, packed=False, singlet=False):
@@ -392,10 +395,10 @@ def run_time_to_e_line_search(args):
     from paper_2604_02550_gb300 import api
     p = workload(args.r)
     out = {"metric": "time_to_E_line_search", "workload": p.name, "eps0": 1e-3, "cap": args.cap, "runs": {},
-           "hybrid": "bf16x3 while ||A||^2 falls by more than 1e-2 relative per step, then fp64 from the same D "
-                     "and the last accepted eps"}
-    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64", "fp64"):
-        hybrid = prec == "bf16x3+fp64"
+           "hybrid": "bf16x3 while ||A||^2 falls by more than 1e-2 relative per step, then fp64 (or ozaki) from "
+                     "the same D and the last accepted eps"}
+    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64", "bf16x3+ozaki", "ozaki", "fp64"):
+        hybrid = prec.startswith("bf16x3+")
         ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "bf16x3" if hybrid else prec, line_search=True,
                        eps0=1e-3)
         D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
@@ -407,7 +410,8 @@ def run_time_to_e_line_search(args):
         for k in range(args.cap):
             if hybrid and switched is None and k >= 2 and (n2s[-2] - n2s[-1]) < 1e-2 * n2s[-2]:
                 ctx.close()
-                ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64", line_search=True, eps0=last_eps)
+                ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec.split("+")[1], line_search=True,
+                               eps0=last_eps)
                 switched = k
             E, n2, e = ctx.step(D)
             last_eps = float(e)
@@ -431,7 +435,7 @@ def run_time_to_e_line_search(args):
         if hybrid:
             out["runs"][prec]["switched_at_step"] = switched
     e64 = out["runs"]["fp64"]["E_conv"]
-    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64"):
+    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64", "bf16x3+ozaki", "ozaki"):
         out["runs"][prec]["abs_dE_conv_vs_fp64"] = abs(out["runs"][prec]["E_conv"] - e64)
         out["runs"][prec]["speedup_vs_fp64"] = out["runs"]["fp64"]["seconds"] / out["runs"][prec]["seconds"]
     print(json.dumps(out), flush=True)
@@ -549,8 +553,10 @@ def main():
     per_step = ms_max / args.steps
     value = whole_job_rate(args.steps, world, ms_max)
     fl_alg = flops_per_pass(p.r)                       # 32 r^6: the unpacked formulation
-    fl = fl_alg if prec == "fp64" else flops_per_pass(p.r, packed=True, singlet=singlet)   # what the GEMM launch executes
+    fl = fl_alg if prec in ("fp64", "ozaki") else flops_per_pass(p.r, packed=True, singlet=singlet)   # what the GEMM launch executes
     split = 3 if prec in ("bf16x3", "tf32x3") else 1
+    if prec == "ozaki":
+        split = OZ_SLICES * (OZ_SLICES + 1) // 2      # bf16 slice products per FP64 GEMM
     # dominant kernel: the grouped O(r^6) GEMM launch (one per contraction pass)
     gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1e3
     peaks = {}
@@ -560,7 +566,7 @@ def main():
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
                 "peak_source": "measured cuBLAS DGEMM 8192^3 on this pool (bench.py --peaks); DFMA pipe"}
         ach = fl / gemm_avg_s / 1e12
-    elif prec == "bf16x3":
+    elif prec in ("bf16x3", "ozaki"):
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks.get("bf16_tflops", 1887.4),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1.9 PF"}
         ach = split * fl / gemm_avg_s / 1e12
@@ -571,14 +577,18 @@ def main():
     roof.update({"achieved": ach, "frac": ach / roof["peak"], "traffic": gemm_traffic(prec) if p.r == 48 else None,
                  "kernel": "grouped O(r^6) GEMM",
                  "flops_per_launch": split * fl,
-                 "flops_note": "2MNK of the GEMMs the launch executes (same-spin pair GEMMs on pairs i<j)"
-                               if prec != "fp64" else "2MNK, 32 r^6 per pass",
+                 "flops_note": {"fp64": "2MNK, 32 r^6 per pass",
+                                "ozaki": f"bf16 slice products of the Ozaki scheme: {split} per FP64 GEMM "
+                                         f"({OZ_SLICES} slices), 2MNK each; 32 r^6 FP64-equivalent per pass"}.get(
+                     prec, "2MNK of the GEMMs the launch executes (same-spin pair GEMMs on pairs i<j)"),
                  "launch_ms": 1e3 * gemm_avg_s,
                  "gemm_share_of_step": 2 * 1e3 * gemm_avg_s / per_step,
                  "timed_launches": gemm_n})
     line = {"metric": "acse_residual_evals_per_s", "value": value, "unit": "residual evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else f"{prec} (f32 accumulate)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "ozaki": "f64 (Ozaki: bf16 slices, exact f32 groups, f64 sums)"}.get(
+                prec, f"{prec} (f32 accumulate)"),
             "data": "synthetic",
             "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "recon": args.recon, "eps": args.eps,
                        "singlet": singlet,

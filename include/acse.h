@@ -62,8 +62,16 @@ typedef enum {
  *                relative per product);
  *   ACSE_TF32    one tf32 product, FP32 accumulation (about 2^-11);
  *   ACSE_TF32X3  x = hi + lo (two tf32), products hi.hi + hi.lo + lo.hi, FP32 accumulation (about 2^-21;
- *                limited by the FP32 intermediates). */
-typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2, ACSE_TF32X3 = 3 } acse_prec;
+ *                limited by the FP32 intermediates);
+ *   ACSE_OZAKI   FP64-accurate: every intermediate is FP64 as in ACSE_FP64, and each O(r^6) GEMM runs by
+ *                the Ozaki scheme (error-free splitting, Ozaki, Ogita, Oishi and Rump, Numer. Algorithms
+ *                59, 2012) on the BF16 tensor cores: each row of an operand is scaled by a power of two and
+ *                cut into `oz_slices` signed 6-bit integer slices (exact in bf16); the slice products
+ *                whose levels s + t <= slices + 1 are summed exactly in FP32 in groups small enough that
+ *                no partial sum reaches 2^24, and the groups are added in FP64.  With the default 8
+ *                slices (48 bits) the GEMM error is of the order of 2^-45 |A||B| K, that of FP64.  The
+ *                adjoint runs in FP64 FMA. */
+typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2, ACSE_TF32X3 = 3, ACSE_OZAKI = 4 } acse_prec;
 /* 3-RDM reconstruction (Eq. 3rdm_recon / Eq. NY):
  *   ACSE_RECON_V   Valdemoro: the 3-cumulant is neglected;
  *   ACSE_RECON_NY  Nakatsuji-Yasuda: the 3-cumulant 1/6 sum_a sigma_a A(2Delta^{ia}_{rq} 2Delta^{jp}_{al})
@@ -90,6 +98,7 @@ typedef struct {
                         * the spin sectors and copy the beta-beta block of A, U from alpha-alpha
                         * (Theory: for a singlet the aa and bb residual blocks coincide).  Ignored
                         * in FP64; rejected (ACSE_ERR_ARG) when n_alpha != n_beta.            */
+    int oz_slices;     /* ACSE_OZAKI: 6-bit slices per operand row, 4..10; 0 -> 8            */
 } acse_opts;
 
 /* Create a context for one problem.  h (r*r) and V (r^4, chemist's (pq|rs)) are read once to

@@ -10,8 +10,8 @@ from ctypes import POINTER, byref, c_double, c_int, c_void_p
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libacse.so")
 
-ACSE_FP64, ACSE_BF16X3, ACSE_TF32, ACSE_TF32X3 = 0, 1, 2, 3
-PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32, "tf32x3": ACSE_TF32X3}
+ACSE_FP64, ACSE_BF16X3, ACSE_TF32, ACSE_TF32X3, ACSE_OZAKI = 0, 1, 2, 3, 4
+PREC = {"fp64": ACSE_FP64, "bf16x3": ACSE_BF16X3, "tf32": ACSE_TF32, "tf32x3": ACSE_TF32X3, "ozaki": ACSE_OZAKI}
 
 # symbols declared in include/acse.h
 EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_step",
@@ -24,7 +24,7 @@ EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_
 class AcseOpts(ctypes.Structure):
     _fields_ = [("r", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("prec", c_int), ("recon", c_int),
                 ("mask_active", c_int), ("act_lo", c_int), ("act_hi", c_int), ("line_search", c_int),
-                ("eps0", c_double), ("check_inputs", c_int), ("singlet", c_int)]
+                ("eps0", c_double), ("check_inputs", c_int), ("singlet", c_int), ("oz_slices", c_int)]
 
 
 class AcseError(RuntimeError):
@@ -117,7 +117,7 @@ RECON = {"V": 0, "NY": 1}
 
 
 def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
-                check_inputs=False, stream=None, recon="V", singlet=False):
+                check_inputs=False, stream=None, recon="V", singlet=False, oz_slices=0):
     o = AcseOpts()
     o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -128,6 +128,7 @@ def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=Fa
     o.eps0 = float(eps0)
     o.check_inputs = int(bool(check_inputs))
     o.singlet = int(bool(singlet))
+    o.oz_slices = int(oz_slices)
     h_ = c_void_p()
     st = current_stream_handle() if stream is None else stream
     _check(lib().acse_create(byref(h_), byref(o), ptr(h), ptr(V), st), "acse_create")

@@ -147,13 +147,20 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     if (o->r < 2 || o->r > ACSE_MAX_R || o->n_alpha < 0 || o->n_beta < 0 || N < 2 || o->n_alpha > o->r ||
         o->n_beta > o->r)
         return ACSE_ERR_SHAPE;
-    if (o->prec < ACSE_FP64 || o->prec > ACSE_TF32X3) return ACSE_ERR_ARG;
+    if (o->prec < ACSE_FP64 || o->prec > ACSE_OZAKI) return ACSE_ERR_ARG;
+    const int oz_slices = o->prec == ACSE_OZAKI ? (o->oz_slices ? o->oz_slices : 8) : 0;
+    if (o->prec == ACSE_OZAKI && (oz_slices < 4 || oz_slices > 10)) return ACSE_ERR_ARG;
     if (o->recon != ACSE_RECON_V && o->recon != ACSE_RECON_NY) return ACSE_ERR_UNSUPPORTED;
     if (o->singlet && o->n_alpha != o->n_beta) return ACSE_ERR_ARG;
     if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
     acse_ctx* c = (acse_ctx*)calloc(1, sizeof(acse_ctx));
     if (!c) return ACSE_ERR_NOMEM;
     c->opt = *o;
+    if (o->prec == ACSE_OZAKI) {   // an FP64 context whose pass GEMMs run by the Ozaki scheme
+        c->opt.prec = ACSE_FP64;
+        c->opt.oz_slices = oz_slices;
+        c->oz = 1;
+    }
     c->r = o->r;
     c->N = N;
     c->stream = (cudaStream_t)stream;
@@ -166,9 +173,11 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     int s = tiled_set_attrs();
     if (s == ACSE_OK) s = ny_set_attrs();
     if (s == ACSE_OK) s = alloc_work(c);
-    if (s == ACSE_OK && o->prec != ACSE_FP64) s = tc_plan_create(c);
+    if (s == ACSE_OK && c->opt.prec != ACSE_FP64) s = tc_plan_create(c);
+    if (s == ACSE_OK && c->oz) s = oz_plan_create(c);
     if (s == ACSE_OK && o->recon == ACSE_RECON_NY) s = ny_alloc(c);
     if (s != ACSE_OK) {
+        oz_plan_destroy(c);
         tc_plan_destroy(c);
         free_work(c);
         free(c);
@@ -190,6 +199,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         s = ACSE_ERR_CUDA;
     if (s != ACSE_OK) {
+        oz_plan_destroy(c);
         tc_plan_destroy(c);
         free_work(c);
         free(c);
@@ -212,6 +222,7 @@ extern "C" int acse_destroy(acse_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     ny_free(c);
     adj_free(c);
+    oz_plan_destroy(c);
     tc_plan_destroy(c);
     free_work(c);
     free(c);
@@ -231,7 +242,8 @@ int acse_contract_pre(acse_ctx* c, const double* const D[3], const double* const
             ACSE_TRY(launch_gamma_M(c, D));
             ACSE_TRY(launch_pack_Mph(c));
         }
-        return launch_W_intermediates(c, W);
+        ACSE_TRY(launch_W_intermediates(c, W));
+        return c->oz ? oz_slice_operands(c, prep_D) : ACSE_OK;
     }
     if (prep_D) ACSE_TRY(launch_gamma(c, D));
     return tc_contract_pre(c, D, W, prep_D);
@@ -255,6 +267,7 @@ int acse_gemm_list_f64(acse_ctx* c, GemmF64* g, int* n) {
 }
 
 int acse_contract_gemm(acse_ctx* c) {
+    if (c->oz) return oz_gemm_launch(c);
     if (c->opt.prec == ACSE_FP64) {
         GemmF64 g[9];
         int n = 0;
@@ -580,6 +593,7 @@ extern "C" int acse_clear_status(acse_ctx* c) {
 
 extern "C" int acse_set_wait_bound_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->oz) return latch(c, oz_set_wait_ns(c, ns, inject_stall));
     if (c->opt.prec == ACSE_FP64) return inject_stall ? latch(c, ACSE_ERR_UNSUPPORTED) : ACSE_OK;
     return latch(c, tc_set_wait_ns(c, ns, inject_stall));
 }

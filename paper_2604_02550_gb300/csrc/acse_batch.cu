@@ -292,6 +292,7 @@ extern "C" int acse_batch_create(acse_batch** out, int n, const acse_opts* opts,
         if (opts[i].prec != opts[0].prec) return ACSE_ERR_ARG;
     for (int i = 0; i < n; ++i)
         if (opts[i].recon != ACSE_RECON_V) return ACSE_ERR_UNSUPPORTED;   // the batch runs the V reconstruction
+    if (opts[0].prec == ACSE_OZAKI) return ACSE_ERR_UNSUPPORTED;           // single contexts only
     acse_batch* B = (acse_batch*)calloc(1, sizeof(acse_batch));
     if (!B) return ACSE_ERR_NOMEM;
     B->n = n;

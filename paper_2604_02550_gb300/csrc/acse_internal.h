@@ -138,6 +138,9 @@ struct acse_ctx {
     void* ny;             // NY reconstruction workspace (acse_ny.cu), or null for V
     cudaStream_t aux[3];  // host <-> device copies of the three blocks run concurrently on these
     cudaEvent_t ev_fork, ev_join[3];
+    int oz;               // ACSE_OZAKI: an FP64 context (opt.prec = ACSE_FP64) whose pass GEMMs run by
+                          // the Ozaki scheme on the BF16 tensor cores (gemm_oz.cu)
+    void* oz_plan;
     const double* cur_D[3];   // operands of the contraction pass in flight (FP64 GEMM list)
     const double* cur_W[3];
     // profiling: kernel launch count and CUDA-event timing of the O(r^6) GEMM launches
@@ -208,6 +211,15 @@ int launch_copy_scalar(acse_ctx* c, double* dst, const double* src);
 
 // GEMM back ends ------------------------------------------------------------------------------
 int gemm_f64_grouped(acse_ctx* c, const GemmF64* probs, int nprob, cudaStream_t s);
+// 2-D bf16 tensor map (128-byte swizzle, box 64 x box_rows) over `rows` rows of `inner_elems`
+// elements, consecutive rows `row_stride` elements apart; `map` points to a CUtensorMap.
+int tc_encode_map_bf16(void* map, const void* base, int rows, int inner_elems, int box_rows, size_t row_stride);
+// Ozaki-scheme FP64 GEMMs of the contraction pass (gemm_oz.cu)
+int oz_plan_create(acse_ctx* c);
+void oz_plan_destroy(acse_ctx* c);
+int oz_slice_operands(acse_ctx* c, int prep_D);   // the pass's FP64 operands -> scaled bf16 slices
+int oz_gemm_launch(acse_ctx* c);                   // every GEMM of the pass, one persistent launch
+int oz_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall);
 
 // contraction pass in three phases (acse_api.cu): operands, the O(r^6) GEMMs, assembly
 int acse_contract_pre(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);

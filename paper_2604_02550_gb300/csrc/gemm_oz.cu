@@ -1,0 +1,605 @@
+// FP64-accurate GEMMs of the contraction pass on the BF16 tensor cores by the Ozaki scheme
+// (error-free splitting: K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, Numer. Algorithms 59 (2012)).
+//
+// C = alpha A B^T with A (M x K) and B (N x K) FP64, both K-major.  Each operand row is scaled by a
+// power of two 2^e chosen so that |a| 2^-e < 1/2 over the row, and cut into S signed digits of base
+// 2^6:  x_1 = a 2^-e,  d_s = rint(2^6 x_s),  x_{s+1} = 2^6 x_s - d_s,  so that
+//     a = 2^e (sum_{s=1..S} d_s 2^-6s + x_{S+1} 2^-6S),   |d_s| <= 32,  |x_{S+1}| <= 1/2,
+// every step exact in FP64 and every digit exact in bf16.  Then
+//     A B^T = 2^(ea + eb) sum_{s,t} 2^-6(s+t) D_s E_t^T,
+// of which the levels L = s + t <= S + 1 are kept (the rest is below 2^-6(S+1) relative).  A product
+// of digit matrices is an integer matrix with entries of at most K 32^2; g products of one level
+// summed in one FP32 accumulator stay exact while g K 2^10 < 2^24, so each level is run as
+// ceil((L-1)/g) such groups, and the groups are added in FP64.
+//
+// Operand layout: slice s of an A row at K segment s-1, slice t of a B row at K segment S-t
+// (reversed), each segment Kp = K rounded up to 64 elements (zero padded).  The products (s, L-s),
+// s0 <= s <= s1, of level L are then one contiguous K range of A, [(s0-1) Kp, s1 Kp), against one
+// of B, [(S-L+s0) Kp, (S-L+s1+1) Kp): a single UMMA accumulation of (s1-s0+1) Kp.
+//
+// Kernels: the persistent tcgen05 GEMM of gemm_tc.cu with the accumulation unit changed from a tile
+// to a (tile, group): the MMA thread runs the groups of a tile one after another into the two TMEM
+// buffers, and the epilogue warps store each group's exact integer sum (int32) to a staging array.
+// A second, HBM-bound kernel adds the groups of every element exactly in int64 and writes the FP64
+// result with one rounding.  (Adding the groups into the FP64 output from the epilogue instead, a
+// read-modify-write of the tile per group, measured eight times slower.)  Every wait is bounded as
+// in gemm_tc.cu.
+#include <cuda.h>
+#include <string.h>
+
+#include "acse_internal.h"
+#include "tc_ptx.cuh"
+
+#define OZ_BETA 6            // bits per digit (base 2^6, |digit| <= 32)
+#define OZ_MAXS 10
+#define OZ_MAXP 12           // GEMMs of one launch
+#define OZ_MAXJ 16           // operands of one slicing launch
+#define OZ_THREADS 192
+#define OZ_BN 256
+#define OZ_STAGES 4
+#define OZ_DRAIN_NS 2000000000ull
+#define OZ_WAIT_NS 4000000000ull
+#define OZ_SLICE_EPT 32      // elements per thread of a sliced row: K <= 256 * 32 = 2 * 64^2
+
+struct OzProb {
+    double* C;
+    int* stage;         // [ngroups][M][N]: the exact integer sum of each group
+    const double* sa;   // 2^ea per row of A
+    const double* sb;   // 2^eb per row of B
+    double alpha;
+    int M, N, ldc;
+    int kbs;            // 64-element K blocks per slice segment
+    int g;              // slice products per exactly accumulated group
+    int ngroups;
+    int tiles_n, tile_start;
+};
+
+struct __align__(64) OzBatch {
+    CUtensorMap tmA[OZ_MAXP];
+    CUtensorMap tmB[OZ_MAXP];
+    OzProb p[OZ_MAXP];
+    int nprob;
+    int total_tiles;
+    int S;
+    int* err;
+    unsigned long long wait_ns;
+    int inject_stall;
+};
+
+__host__ __device__ inline int oz_ngroups(int S, int g) {
+    int n = 0;
+    for (int L = 2; L <= S + 1; ++L) n += (L - 2) / g + 1;   // ceil((L - 1) / g)
+    return n;
+}
+
+// group index -> level L and the A slices [s0, s1] of its products (s, L - s)
+__device__ __forceinline__ void oz_group(int S, int g, int idx, int& L, int& s0, int& s1) {
+    for (L = 2; L <= S + 1; ++L) {
+        const int n = (L - 2) / g + 1;
+        if (idx < n) {
+            s0 = 1 + idx * g;
+            s1 = min(L - 1, s0 + g - 1);
+            return;
+        }
+        idx -= n;
+    }
+    L = S + 1;
+    s0 = s1 = 1;
+}
+
+// 2^n for -1022 <= n <= 1023, built from its bit pattern (exact)
+__host__ __device__ __forceinline__ double oz_pow2(int n) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)(n + 1023) << 52);
+#else
+    const long long bits = (long long)(n + 1023) << 52;
+    double d;
+    memcpy(&d, &bits, sizeof(d));
+    return d;
+#endif
+}
+
+__device__ __forceinline__ int oz_find_problem(const OzBatch& b, int t) {
+    int lo = 0, hi = b.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.p[mid].tile_start <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------------ slicing
+struct OzSliceJob {
+    const double* src;
+    size_t lds;             // source row stride (elements)
+    __nv_bfloat16* dst;
+    size_t ldd;             // S * Kp
+    double* scale;          // 2^e per row (NaN for a row with a non-finite entry)
+    int rows, K, Kp, reverse, row0;
+};
+
+struct OzSliceBatch {
+    OzSliceJob j[OZ_MAXJ];
+    int njobs;
+    int S;
+};
+
+// One block per operand row: the row is held in registers, its largest magnitude fixes e, and the
+// S digits of every element are written to the S K segments of the row.
+__global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSliceBatch b) {
+    __shared__ double red_m[8];
+    __shared__ int red_b[8];
+    int ji = 0;
+    while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= (int)blockIdx.x) ++ji;
+    const OzSliceJob& J = b.j[ji];
+    const int row = (int)blockIdx.x - J.row0;
+    const double* src = J.src + (size_t)row * J.lds;
+    const int K = J.K;
+    double v[OZ_SLICE_EPT];
+    double m = 0.0;
+    int bad = 0;
+#pragma unroll
+    for (int u = 0; u < OZ_SLICE_EPT; ++u) {
+        const int k = threadIdx.x + u * 256;
+        v[u] = k < K ? src[k] : 0.0;
+        bad |= !isfinite(v[u]);
+        m = fmax(m, fabs(v[u]));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+        red_m[w] = m;
+        red_b[w] = bad;
+    }
+    __syncthreads();
+    m = red_m[0];
+    bad = red_b[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+        m = fmax(m, red_m[i]);
+        bad |= red_b[i];
+    }
+    // m < 2^(ilogb(m) + 1), so e = ilogb(m) + 2 gives |a| 2^-e < 1/2 (clamped to the normal range)
+    int e = 0;
+    if (m > 0.0 && !bad) e = min(1000, max(-1000, ilogb(m) + 2));
+    const double inv = oz_pow2(-e);
+    if (threadIdx.x == 0) J.scale[row] = bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_pow2(e);
+    __nv_bfloat16* drow = J.dst + (size_t)row * J.ldd;
+    const int S = b.S;
+#pragma unroll
+    for (int u = 0; u < OZ_SLICE_EPT; ++u) {
+        const int k = threadIdx.x + u * 256;
+        if (k < K) {
+            double x = v[u] * inv;
+            for (int s = 0; s < S; ++s) {
+                const double y = x * 64.0;
+                const double d = rint(y);
+                x = y - d;
+                const int seg = J.reverse ? S - 1 - s : s;
+                drow[(size_t)seg * J.Kp + k] = __float2bfloat16_rn((float)d);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------- GEMM
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __restrict__ bp) {
+    const OzBatch& b = *bp;
+    constexpr int A_BYTES = TC_BM * 128;
+    constexpr int B_BYTES = BN * 128;
+    constexpr int KELEM = 64;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;   // [2]
+    uint64_t* acce = accf + 2;         // [2]
+    uint64_t* never = acce + 2;
+    uint64_t* drainb = never + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drainb + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = b.total_tiles, S = b.S;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], 4);
+        }
+        mbar_init(never, 1);
+        mbar_init(drainb, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                const int pi = oz_find_problem(b, t);
+                const OzProb& P = b.p[pi];
+                const int local = t - P.tile_start;
+                const int m0 = (local / P.tiles_n) * TC_BM, n0 = (local % P.tiles_n) * BN;
+                for (int gi = 0; gi < P.ngroups && !stop; ++gi) {
+                    int L, s0, s1;
+                    oz_group(S, P.g, gi, L, s0, s1);
+                    const int ka = (s0 - 1) * P.kbs, kb0 = (S - L + s0) * P.kbs, n = (s1 - s0 + 1) * P.kbs;
+                    for (int kb = 0; kb < n; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        if (it >= STAGES && !bounded_wait(&empty[s], ((it / STAGES) & 1) ^ 1, b.wait_ns, abort_flag)) {
+                            raise_abort(b.err, abort_flag);
+                            stop = true;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                        tma_load_2d(sA + s * A_BYTES, &b.tmA[pi], (ka + kb) * KELEM, m0, &full[s]);
+                        tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], (kb0 + kb) * KELEM, n0, &full[s]);
+                    }
+                }
+            }
+            // every issued copy must have landed before the CTA may exit
+            for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k)
+                if (!bounded_wait(&full[k % STAGES], (k / STAGES) & 1, OZ_DRAIN_NS, nullptr))
+                    raise_abort(b.err, abort_flag);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc<0, BN>();
+            if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
+            int it = 0, lt = 0;
+            for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
+                const OzProb& P = b.p[oz_find_problem(b, t)];
+                for (int gi = 0; gi < P.ngroups && !*abort_flag; ++gi, ++lt) {
+                    int L, s0, s1;
+                    oz_group(S, P.g, gi, L, s0, s1);
+                    const int n = (s1 - s0 + 1) * P.kbs;
+                    const int ab = lt & 1, use = lt >> 1;
+                    if (use >= 1 && !bounded_wait(&acce[ab], (use - 1) & 1, b.wait_ns + OZ_DRAIN_NS, abort_flag)) {
+                        raise_abort(b.err, abort_flag);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t acc = tmem + (uint32_t)(ab * BN);
+                    for (int kb = 0; kb < n; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        if (!bounded_wait(&full[s], (it / STAGES) & 1, b.wait_ns, abort_flag)) {
+                            raise_abort(b.err, abort_flag);
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t da = smem_desc(sA + s * A_BYTES);
+                        const uint64_t db = smem_desc(sB + s * B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) umma<0>(acc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                        umma_commit(&empty[s]);
+                    }
+                    umma_commit(&accf[ab]);   // the epilogue of this group may start when its MMAs are done
+                }
+            }
+            umma_commit(drainb);
+            if (!bounded_wait(drainb, 0, OZ_DRAIN_NS, nullptr)) raise_abort(b.err, abort_flag);
+        }
+    } else {
+        const int q = warp & 3;   // TMEM lane quadrant this warp may access
+        int lt = 0;
+        bool run = true;
+        for (int t = blockIdx.x; t < T && run; t += gridDim.x) {
+            const OzProb& P = b.p[oz_find_problem(b, t)];
+            const int local = t - P.tile_start;
+            const int m0 = (local / P.tiles_n) * TC_BM, n0 = (local % P.tiles_n) * BN;
+            const int row = m0 + q * 32 + lane;
+            const bool rok = row < P.M;
+            const bool vec = (P.N & 3) == 0 && (reinterpret_cast<uintptr_t>(P.stage) & 15) == 0;
+            for (int gi = 0; gi < P.ngroups; ++gi, ++lt) {
+                const int ab = lt & 1, use = lt >> 1;
+                int go = 0;
+                if (lane == 0) {
+                    const bool ok = bounded_wait(&accf[ab], use & 1, b.wait_ns + OZ_DRAIN_NS, abort_flag);
+                    if (!ok) raise_abort(b.err, abort_flag);
+                    go = ok && !*abort_flag;
+                }
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) {
+                    run = false;
+                    break;
+                }
+                tc_fence_after();
+                // the group's sum is an integer below 2^24 in magnitude: exact in FP32 and in int32
+                int* srow = P.stage + (size_t)gi * P.M * P.N + (size_t)(rok ? row : 0) * P.N;
+#pragma unroll 1
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t v[32];
+                    __syncwarp();
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);   // warp-collective
+                    const int col0 = n0 + c * 32;
+                    if (!rok || col0 >= P.N) continue;
+                    if (vec && col0 + 32 <= P.N) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<int4*>(srow + col0 + j) =
+                                make_int4(__float2int_rn(__uint_as_float(v[j])), __float2int_rn(__uint_as_float(v[j + 1])),
+                                          __float2int_rn(__uint_as_float(v[j + 2])), __float2int_rn(__uint_as_float(v[j + 3])));
+                    } else {
+                        const int nc = min(32, P.N - col0);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < nc) srow[col0 + j] = __float2int_rn(__uint_as_float(v[j]));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[ab]);   // this warp's quarter of the buffer is free
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
+// C = alpha 2^(ea_i + eb_j) sum_g 2^-6L_g v_g for every element, from the staged group sums v_g.
+// With w_L = 36 - 6 (L - 2) the terms v_g 2^w_L (an arithmetic right shift where w_L < 0, which drops
+// only bits below 2^-48 of the level-2 unit) are added in int64 (|sum| < 2^61), and the conversion of
+// the sum to FP64 is the single rounding; the scale alpha 2^(ea + eb - 48) is a power of two times
+// alpha (1 or 2).  HBM-bound: the groups of an element are read once, coalesced, and C written once.
+__global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ bp) {
+    const OzBatch& b = *bp;
+    const OzProb& P = b.p[blockIdx.y];
+    const int N = P.N, g = P.g, S = b.S;
+    const size_t MN = (size_t)P.M * N;
+    const int* __restrict__ st = P.stage;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.x * blockDim.x) {
+        long long acc = 0;
+        size_t off = e;
+        for (int L = 2; L <= S + 1; ++L) {
+            const int w = 36 - OZ_BETA * (L - 2);
+            const int nl = (L - 2) / g + 1;
+#pragma unroll 2
+            for (int q = 0; q < nl; ++q, off += MN) {
+                const long long v = st[off];
+                acc += w >= 0 ? v * (1ll << w) : (v >> -w);   // arithmetic shift: floor
+            }
+        }
+        const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
+        const double sc = P.alpha * P.sa[i] * P.sb[j] * oz_pow2(-12 - 36);
+        P.C[(size_t)i * P.ldc + j] = __ll2double_rn(acc) * sc;
+    }
+}
+
+// --------------------------------------------------------------------------- host plan
+// Operands of the nine GEMMs of a pass (the list of acse_gemm_list_f64):
+//   A: M_aa, M_ab, M_bb, D_aa, D_ab, D_bb (r^2 x r^2), Zd (2r^2 x 2r^2), Zf1, Zf2 (r^2 x r^2);
+//   B: W_aa, W_ab, W_bb (r^2 x r^2), Md (2r^2 x 2r^2), Mf1, Mf2 (r^2 x r^2).
+struct OzOp {
+    __nv_bfloat16* sl;
+    double* scale;
+    int rows, K, Kp;
+};
+
+struct OzPlan {
+    OzBatch* host;
+    OzBatch* dev;
+    int S, bn;
+    size_t smem;
+    int nsm;
+    int tiles;
+    OzOp A[9], B[6];
+    int* err;
+};
+
+static size_t oz_smem(int bn) { return (size_t)OZ_STAGES * (TC_BM + bn) * 128 + 1024 + 256; }
+
+static int oz_op_alloc(OzOp& o, int rows, int K, int S) {
+    o.rows = rows;
+    o.K = K;
+    o.Kp = (K + 63) / 64 * 64;
+    const size_t bytes = (size_t)rows * S * o.Kp * sizeof(__nv_bfloat16);
+    if (cudaMalloc((void**)&o.sl, bytes) != cudaSuccess || cudaMalloc((void**)&o.scale, rows * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACSE_ERR_NOMEM;
+    }
+    ACSE_CUDA_TRY(cudaMemset(o.sl, 0, bytes));   // the K padding of every segment stays zero
+    return ACSE_OK;
+}
+
+static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, double alpha) {
+    OzBatch& B = *pl->host;
+    if (B.nprob >= OZ_MAXP || a.K != b.K || a.Kp != b.Kp) return ACSE_ERR_SHAPE;
+    const int n = B.nprob;
+    const size_t ld = (size_t)pl->S * a.Kp;
+    ACSE_TRY(tc_encode_map_bf16(&B.tmA[n], a.sl, a.rows, (int)ld, TC_BM, ld));
+    ACSE_TRY(tc_encode_map_bf16(&B.tmB[n], b.sl, b.rows, (int)ld, pl->bn, ld));
+    OzProb& p = B.p[n];
+    p.C = C;
+    p.sa = a.scale;
+    p.sb = b.scale;
+    p.alpha = alpha;
+    p.M = a.rows;
+    p.N = b.rows;
+    p.ldc = ldc;
+    p.kbs = a.Kp / 64;
+    // g K 2^(2 (OZ_BETA - 1)) < 2^24: the FP32 accumulation of a group is exact
+    const long long cap = ((1ll << 24) - 1) / ((long long)a.K << (2 * (OZ_BETA - 1)));
+    p.g = cap < 1 ? 1 : (int)(cap < pl->S ? cap : pl->S);
+    p.ngroups = oz_ngroups(pl->S, p.g);
+    if (cudaMalloc((void**)&p.stage, (size_t)p.ngroups * p.M * p.N * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        p.stage = nullptr;
+        return ACSE_ERR_NOMEM;
+    }
+    p.tiles_n = (p.N + pl->bn - 1) / pl->bn;
+    p.tile_start = B.total_tiles;
+    B.total_tiles += ((p.M + TC_BM - 1) / TC_BM) * p.tiles_n;
+    B.nprob = n + 1;
+    return cap < 1 ? ACSE_ERR_SHAPE : ACSE_OK;
+}
+
+int oz_plan_create(acse_ctx* c) {
+    OzPlan* pl = (OzPlan*)calloc(1, sizeof(OzPlan));
+    if (!pl) return ACSE_ERR_NOMEM;
+    c->oz_plan = pl;
+    const int r = c->r, R2 = r * r, R22 = 2 * R2;
+    pl->S = c->opt.oz_slices;
+    pl->bn = R2 >= 256 ? OZ_BN : 128;
+    pl->smem = oz_smem(pl->bn);
+    if (pl->bn == 256)
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<256, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+    else
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<128, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+    pl->nsm = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        pl->nsm = 152;
+    }
+    for (int i = 0; i < 6; ++i) ACSE_TRY(oz_op_alloc(pl->A[i], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[6], R22, R22, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[7], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[8], R2, R2, pl->S));
+    for (int i = 0; i < 3; ++i) ACSE_TRY(oz_op_alloc(pl->B[i], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->B[3], R22, R22, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->B[4], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->B[5], R2, R2, pl->S));
+    if (cudaMalloc((void**)&pl->err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACSE_ERR_NOMEM;
+    }
+    ACSE_CUDA_TRY(cudaMemset(pl->err, 0, sizeof(int)));
+    if (!c->w.tc_err) c->w.tc_err = pl->err;   // read by acse_sync_status
+    pl->host = (OzBatch*)calloc(1, sizeof(OzBatch));
+    if (!pl->host) return ACSE_ERR_NOMEM;
+    OzBatch& B = *pl->host;
+    B.S = pl->S;
+    B.err = pl->err;
+    B.wait_ns = OZ_WAIT_NS;
+    Work& w = c->w;
+    // the largest-K GEMM first, then the pair GEMMs (X_s = f M_s W_s^T, Y_s = f D_s W_s^T; f = 2 for the
+    // mixed-spin sector) and the spin-flip ones: the FP64 GEMM list of the pass
+    ACSE_TRY(oz_add(pl, pl->A[6], pl->B[3], w.X5d, R22, 1.0));
+    for (int s = 0; s < 3; ++s) {
+        const double f = s == 1 ? 2.0 : 1.0;
+        ACSE_TRY(oz_add(pl, pl->A[s], pl->B[s], w.X[s], R2, f));
+        ACSE_TRY(oz_add(pl, pl->A[3 + s], pl->B[s], w.Y[s], R2, f));
+    }
+    ACSE_TRY(oz_add(pl, pl->A[7], pl->B[4], w.X5f1, R2, 1.0));
+    ACSE_TRY(oz_add(pl, pl->A[8], pl->B[5], w.X5f2, R2, 1.0));
+    pl->tiles = B.total_tiles;
+    if (cudaMalloc((void**)&pl->dev, sizeof(OzBatch)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACSE_ERR_NOMEM;
+    }
+    ACSE_CUDA_TRY(cudaMemcpy(pl->dev, pl->host, sizeof(OzBatch), cudaMemcpyHostToDevice));
+    return ACSE_OK;
+}
+
+void oz_plan_destroy(acse_ctx* c) {
+    OzPlan* pl = (OzPlan*)c->oz_plan;
+    if (!pl) return;
+    for (int i = 0; i < 9; ++i) {
+        if (pl->A[i].sl) cudaFree(pl->A[i].sl);
+        if (pl->A[i].scale) cudaFree(pl->A[i].scale);
+    }
+    for (int i = 0; i < 6; ++i) {
+        if (pl->B[i].sl) cudaFree(pl->B[i].sl);
+        if (pl->B[i].scale) cudaFree(pl->B[i].scale);
+    }
+    if (pl->err) {
+        if (c->w.tc_err == pl->err) c->w.tc_err = nullptr;
+        cudaFree(pl->err);
+    }
+    if (pl->host)
+        for (int i = 0; i < pl->host->nprob; ++i)
+            if (pl->host->p[i].stage) cudaFree(pl->host->p[i].stage);
+    if (pl->dev) cudaFree(pl->dev);
+    free(pl->host);
+    free(pl);
+    c->oz_plan = nullptr;
+}
+
+static void oz_job(OzSliceBatch& b, int& rows, const OzOp& o, const double* src, size_t lds, int reverse) {
+    OzSliceJob& j = b.j[b.njobs++];
+    j.src = src;
+    j.lds = lds;
+    j.dst = o.sl;
+    j.ldd = (size_t)b.S * o.Kp;
+    j.scale = o.scale;
+    j.rows = o.rows;
+    j.K = o.K;
+    j.Kp = o.Kp;
+    j.reverse = reverse;
+    j.row0 = rows;
+    rows += o.rows;
+}
+
+int oz_slice_operands(acse_ctx* c, int prep_D) {
+    OzPlan* pl = (OzPlan*)c->oz_plan;
+    if (!pl) return ACSE_ERR_UNSUPPORTED;
+    const int r = c->r;
+    const size_t R2 = (size_t)r * r;
+    Work& w = c->w;
+    OzSliceBatch b;
+    memset(&b, 0, sizeof(b));
+    b.S = pl->S;
+    int rows = 0;
+    // A slices in order (segment s - 1), B slices reversed (segment S - t)
+    if (prep_D) {
+        for (int s = 0; s < 3; ++s) oz_job(b, rows, pl->A[s], w.M[s], R2, 0);
+        for (int s = 0; s < 3; ++s) oz_job(b, rows, pl->A[3 + s], c->cur_D[s], R2, 0);
+        oz_job(b, rows, pl->B[3], w.Md, 2 * R2, 1);
+        oz_job(b, rows, pl->B[4], w.Mf1, R2, 1);
+        oz_job(b, rows, pl->B[5], w.Mf2, R2, 1);
+    }
+    for (int s = 0; s < 3; ++s) oz_job(b, rows, pl->B[s], c->cur_W[s], R2, 1);
+    oz_job(b, rows, pl->A[6], w.Zd, 2 * R2, 0);
+    oz_job(b, rows, pl->A[7], w.Zf1, R2, 0);
+    oz_job(b, rows, pl->A[8], w.Zf2, R2, 0);
+    k_oz_slice<<<rows, 256, 0, c->stream>>>(b);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
+}
+
+int oz_gemm_launch(acse_ctx* c) {
+    OzPlan* pl = (OzPlan*)c->oz_plan;
+    if (!pl) return ACSE_ERR_UNSUPPORTED;
+    if (pl->tiles == 0) return ACSE_OK;
+    const int g = pl->tiles < pl->nsm ? pl->tiles : pl->nsm;
+    ACSE_TRY(prof_begin(c));
+    if (pl->bn == 256) k_gemm_oz<256, OZ_STAGES><<<g, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
+    else k_gemm_oz<128, OZ_STAGES><<<g, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
+    ACSE_LAUNCHED(c);
+    k_oz_reduce<<<dim3(2 * pl->nsm, pl->host->nprob), 256, 0, c->stream>>>(pl->dev);
+    ACSE_LAUNCHED(c);
+    return prof_end(c);
+}
+
+int oz_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
+    OzPlan* pl = (OzPlan*)c->oz_plan;
+    if (!pl) return ACSE_ERR_UNSUPPORTED;
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    pl->host->wait_ns = ns ? ns : OZ_WAIT_NS;
+    pl->host->inject_stall = inject_stall;
+    ACSE_CUDA_TRY(cudaMemcpy(pl->dev, pl->host, sizeof(OzBatch), cudaMemcpyHostToDevice));
+    return ACSE_OK;
+}

@@ -29,7 +29,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 R = 48
 # normwise relative tolerances on sampled entries: FP64 sums of ~r^3 terms per entry; BF16x3 as in
 # the small-size tests (about 2^-16 per product, some cancellation between GEMM outputs)
-TOL_ENT = {"fp64": 1e-11, "bf16x3": 5e-4}
+TOL_ENT = {"fp64": 1e-11, "ozaki": 1e-11, "bf16x3": 5e-4}
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +82,7 @@ def oracle_samples():
     return out
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64", "ozaki"])
 def test_fullsize_sampled_entries(acse, oracle_samples, prec):
     for p, ent, want in oracle_samples:
         ctx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec)
@@ -97,7 +97,7 @@ def test_fullsize_sampled_entries(acse, oracle_samples, prec):
         ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64", "ozaki"])
 def test_fullsize_invariants(acse, prec):
     """The benchmark's call (one context, default plan, step with eps = 1e-4) at r = 48."""
     p = I.config_problem(3)
@@ -112,7 +112,8 @@ def test_fullsize_invariants(acse, prec):
     Aa = to_np(A)
     n2 = float(n2)
     assert n2 == pytest.approx(np.sum(Aa[0] ** 2) + np.sum(Aa[2] ** 2) + 4 * np.sum(Aa[1] ** 2), rel=1e-12)
-    sym = 1e-12 if prec == "fp64" else 1e-6
+    f64 = prec in ("fp64", "ozaki")
+    sym = 1e-12 if f64 else 1e-6
     for blk in Aa:
         assert np.abs(blk + blk.transpose(2, 3, 0, 1)).max() <= sym * np.abs(blk).max()
     for blk in (Aa[0], Aa[2]):
@@ -123,7 +124,7 @@ def test_fullsize_invariants(acse, prec):
     assert float(n2s) == pytest.approx(n2, rel=1e-12)
     U = tuple((a - b) / eps for a, b in zip(to_np(D), (p.Daa, p.Dab, p.Dbb)))
     trKU = np.sum(Kb[0] * U[0]) + np.sum(Kb[2] * U[2]) + 4 * np.sum(Kb[1] * U[1])
-    tol = 1e-9 if prec == "fp64" else 2e-4
+    tol = 1e-9 if f64 else 2e-4
     print(f"r=48 {prec}: ||A||^2 {n2:.6e}, Tr(KU) {trKU:.6e}, dE/eps {(E1 - E0) / eps:.6e}")
     assert trKU == pytest.approx(-n2, rel=tol)
     assert (E1 - E0) / eps == pytest.approx(trKU, rel=1e-6)
@@ -132,7 +133,7 @@ def test_fullsize_invariants(acse, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "ozaki"])
 def test_golden_line_search_trajectory(acse, prec):
     """50 line-searched Euler steps of the r = 24 CAS(6e,6o) system against the stored oracle
     trajectory: accepted eps, ||A||^2 before each step and E after it.
@@ -169,8 +170,11 @@ def test_golden_line_search_trajectory(acse, prec):
     drop = abs(Ew[-1] - g["E"][0])
     print(f"{prec}: max rel eps (conditioned steps) {de:.2e}, max rel ||A||^2 {dn:.2e}, "
           f"max |dE| conditioned {dE:.2e}, all steps {dE_all.max():.2e} (E drop {drop:.1f})")
-    if prec == "fp64":
-        assert de < 1e-7 and dn < 1e-9 and dE_all.max() < 1e-7
+    if prec in ("fp64", "ozaki"):
+        # FP64-accurate paths: exact agreement while the merit falls; in the flat regime a flipped
+        # curvature branch changes one step's eps, so E may move by a step's eps ||A||^2 (about 1e-7 Eh
+        # here), below the 1e-6 Eh stopping threshold
+        assert de < 1e-7 and dn < 1e-9 and dE < 1e-9 and dE_all.max() < 1e-6
     else:
         # BF16x3 noise in f (about 3e-5 relative) moves the accepted eps by about 1e-4 relative, and
         # each step changes E by eps ||A||^2 (up to 4 Eh here): E may drift by about 1e-4 of the total
