@@ -25,6 +25,7 @@
 // read-modify-write of the tile per group, measured eight times slower.)  Every wait is bounded as
 // in gemm_tc.cu.
 #include <cuda.h>
+#include <math.h>
 #include <string.h>
 
 #include "acse_internal.h"
@@ -39,7 +40,7 @@
 #define OZ_STAGES 4
 #define OZ_DRAIN_NS 2000000000ull
 #define OZ_WAIT_NS 4000000000ull
-#define OZ_SLICE_EPT 32      // elements per thread of a sliced row: K <= 256 * 32 = 2 * 64^2
+#define OZ_SLICE_PPT 16      // element pairs per thread of a sliced row: K <= 2 * 256 * 16 = 2 * 64^2
 
 struct OzProb {
     double* C;
@@ -47,6 +48,7 @@ struct OzProb {
     const double* sa;   // 2^ea per row of A
     const double* sb;   // 2^eb per row of B
     double alpha;
+    int ealpha;         // alpha = 2^ealpha
     int M, N, ldc;
     int kbs;            // 64-element K blocks per slice segment
     int g;              // slice products per exactly accumulated group
@@ -54,7 +56,7 @@ struct OzProb {
     int tiles_n, tile_start;
 };
 
-struct __align__(64) OzBatch {
+struct __align__(128) OzBatch {
     CUtensorMap tmA[OZ_MAXP];
     CUtensorMap tmB[OZ_MAXP];
     OzProb p[OZ_MAXP];
@@ -125,64 +127,83 @@ struct OzSliceBatch {
     int S;
 };
 
-// One block per operand row: the row is held in registers, its largest magnitude fixes e, and the
-// S digits of every element are written to the S K segments of the row.
+// Fixed-point value of one element: X = round(a 2^(6S - e)) from the bit pattern of a, |X| < 2^(6S-1)
+// (integer arithmetic only: FP64 is slow on this GPU).  The rounding drops bits below 2^-6S of the
+// row scale, as the remainder x_{S+1} of the digit recursion does.
+__device__ __forceinline__ long long oz_fixed(unsigned long long bits, int S, int e) {
+    const int E = (int)((bits >> 52) & 0x7FF);
+    const long long m = (long long)(bits & 0xFFFFFFFFFFFFFull) | (E ? (1ll << 52) : 0ll);
+    const int sh = (E ? E : 1) - 1075 + 6 * S - e;   // a = m 2^((E ? E : 1) - 1075)
+    long long X;
+    if (sh >= 0) X = m << sh;                         // < 2^(6S-1) by the choice of e
+    else if (sh > -63) X = (m + (1ll << (-sh - 1))) >> -sh;
+    else X = 0;
+    return (bits >> 63) ? -X : X;
+}
+
+// One block per operand row.  The row's bit patterns are held in registers, its largest magnitude
+// fixes e (|a| 2^-e < 1/2), and every element's fixed-point value X is cut into S balanced base-64
+// digits from the least significant one up (d = ((X + 32) mod 64) - 32, X <- (X - d) / 64, exact;
+// the last quotient is the leading digit, of magnitude at most 32).  Digits go out as bf16 pairs,
+// each slice to its K segment of the row.
 __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSliceBatch b) {
-    __shared__ double red_m[8];
-    __shared__ int red_b[8];
+    __shared__ unsigned long long red[8];
+    __shared__ unsigned short tab[65];   // bf16 bits of the digits -32..32
+    if (threadIdx.x < 65) tab[threadIdx.x] = __bfloat16_as_ushort(__float2bfloat16_rn((float)((int)threadIdx.x - 32)));
     int ji = 0;
     while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= (int)blockIdx.x) ++ji;
     const OzSliceJob& J = b.j[ji];
     const int row = (int)blockIdx.x - J.row0;
-    const double* src = J.src + (size_t)row * J.lds;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(J.src + (size_t)row * J.lds);
     const int K = J.K;
-    double v[OZ_SLICE_EPT];
-    double m = 0.0;
-    int bad = 0;
+    unsigned long long v[2 * OZ_SLICE_PPT];
+    unsigned long long mx = 0;
 #pragma unroll
-    for (int u = 0; u < OZ_SLICE_EPT; ++u) {
-        const int k = threadIdx.x + u * 256;
-        v[u] = k < K ? src[k] : 0.0;
-        bad |= !isfinite(v[u]);
-        m = fmax(m, fabs(v[u]));
+    for (int u = 0; u < OZ_SLICE_PPT; ++u) {
+        const int k = 2 * ((int)threadIdx.x + u * 256);
+        v[2 * u] = k < K ? src[k] : 0ull;
+        v[2 * u + 1] = k + 1 < K ? src[k + 1] : 0ull;
+        mx = max(mx, max(v[2 * u] & 0x7FFFFFFFFFFFFFFFull, v[2 * u + 1] & 0x7FFFFFFFFFFFFFFFull));
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    }
-    if (lane == 0) {
-        red_m[w] = m;
-        red_b[w] = bad;
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[w] = mx;
     __syncthreads();
-    m = red_m[0];
-    bad = red_b[0];
+    mx = red[0];
 #pragma unroll
-    for (int i = 1; i < 8; ++i) {
-        m = fmax(m, red_m[i]);
-        bad |= red_b[i];
-    }
-    // m < 2^(ilogb(m) + 1), so e = ilogb(m) + 2 gives |a| 2^-e < 1/2 (clamped to the normal range)
+    for (int i = 1; i < 8; ++i) mx = max(mx, red[i]);
+    // non-negative doubles order like their bit patterns; an all-ones exponent is Inf or NaN
+    const bool bad = mx >= 0x7FF0000000000000ull;
     int e = 0;
-    if (m > 0.0 && !bad) e = min(1000, max(-1000, ilogb(m) + 2));
-    const double inv = oz_pow2(-e);
+    if (!bad && mx != 0) e = min(1000, max(-1000, (int)(mx >> 52) - 1023 + 2));
     if (threadIdx.x == 0) J.scale[row] = bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_pow2(e);
     __nv_bfloat16* drow = J.dst + (size_t)row * J.ldd;
     const int S = b.S;
 #pragma unroll
-    for (int u = 0; u < OZ_SLICE_EPT; ++u) {
-        const int k = threadIdx.x + u * 256;
-        if (k < K) {
-            double x = v[u] * inv;
-            for (int s = 0; s < S; ++s) {
-                const double y = x * 64.0;
-                const double d = rint(y);
-                x = y - d;
-                const int seg = J.reverse ? S - 1 - s : s;
-                drow[(size_t)seg * J.Kp + k] = __float2bfloat16_rn((float)d);
+    for (int u = 0; u < OZ_SLICE_PPT; ++u) {
+        const int k = 2 * ((int)threadIdx.x + u * 256);
+        if (k >= K) continue;
+        long long X0 = bad ? 0 : oz_fixed(v[2 * u], S, e);
+        long long X1 = bad ? 0 : oz_fixed(v[2 * u + 1], S, e);
+        for (int t = 0; t < S; ++t) {   // slice s = S - t
+            int d0, d1;
+            if (t < S - 1) {
+                d0 = (int)(((X0 + 32) & 63) - 32);
+                d1 = (int)(((X1 + 32) & 63) - 32);
+                X0 = (X0 - d0) >> 6;
+                X1 = (X1 - d1) >> 6;
+            } else {
+                d0 = (int)X0;
+                d1 = (int)X1;
             }
+            const int sl = S - t;
+            const int seg = J.reverse ? S - sl : sl - 1;
+            __nv_bfloat16* dst = drow + (size_t)seg * J.Kp + k;
+            if (k + 1 < K)
+                *reinterpret_cast<unsigned int*>(dst) = (unsigned int)tab[d0 + 32] | ((unsigned int)tab[d1 + 32] << 16);
+            else
+                *reinterpret_cast<unsigned short*>(dst) = tab[d0 + 32];
         }
     }
 }
@@ -358,11 +379,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
     }
 }
 
+// acc 2^ex rounded to the nearest double (ties to even), with integer operations only (FP64 is slow on
+// this GPU): the leading bit of |acc| fixes the exponent, the 53 bits below it the significand, the
+// rest decides the rounding.  Results outside the normal range take the FP64 route.
+__device__ __forceinline__ double oz_ll_scaled(long long acc, int ex) {
+    if (acc == 0) return 0.0;
+    const unsigned long long sign = acc < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long u = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+    int msb = 63 - __clzll((long long)u);
+    unsigned long long mant;
+    if (msb <= 52) {
+        mant = u << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        mant = u >> sh;
+        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) {
+            if (++mant == (1ull << 53)) {
+                mant >>= 1;
+                ++msb;
+            }
+        }
+    }
+    const int E = msb + ex + 1023;
+    if (E < 1 || E > 2046) return __ll2double_rn(acc) * oz_pow2(min(1023, max(-1022, ex)));
+    return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // C = alpha 2^(ea_i + eb_j) sum_g 2^-6L_g v_g for every element, from the staged group sums v_g.
 // With w_L = 36 - 6 (L - 2) the terms v_g 2^w_L (an arithmetic right shift where w_L < 0, which drops
 // only bits below 2^-48 of the level-2 unit) are added in int64 (|sum| < 2^61), and the conversion of
-// the sum to FP64 is the single rounding; the scale alpha 2^(ea + eb - 48) is a power of two times
-// alpha (1 or 2).  HBM-bound: the groups of an element are read once, coalesced, and C written once.
+// the sum, scaled by the power of two alpha 2^(ea + eb - 48), to FP64 is the single rounding.
+// HBM-bound: the groups of an element are read once, coalesced, and C is written once.
 __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ bp) {
     const OzBatch& b = *bp;
     const OzProb& P = b.p[blockIdx.y];
@@ -382,8 +430,11 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ b
             }
         }
         const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
-        const double sc = P.alpha * P.sa[i] * P.sb[j] * oz_pow2(-12 - 36);
-        P.C[(size_t)i * P.ldc + j] = __ll2double_rn(acc) * sc;
+        const int ea = (int)((__double_as_longlong(P.sa[i]) >> 52) & 0x7FF);   // row scales are powers of two
+        const int eb = (int)((__double_as_longlong(P.sb[j]) >> 52) & 0x7FF);
+        P.C[(size_t)i * P.ldc + j] = (ea == 0x7FF || eb == 0x7FF)
+                                         ? __longlong_as_double(0x7ff8000000000000ll)
+                                         : oz_ll_scaled(acc, ea + eb - 2046 + P.ealpha - 48);
     }
 }
 
@@ -435,6 +486,9 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
     p.sa = a.scale;
     p.sb = b.scale;
     p.alpha = alpha;
+    int ex = 0;
+    if (frexp(alpha, &ex) != 0.5) return ACSE_ERR_ARG;   // alpha must be a power of two
+    p.ealpha = ex - 1;
     p.M = a.rows;
     p.N = b.rows;
     p.ldc = ldc;

@@ -35,7 +35,7 @@ struct TcProb {
                   // Cp[sK * nsb + sI][(i,j)][(k,l)] (nsb = N / r^2), the row order the B kernel reads
 };
 
-struct __align__(64) TcBatch {
+struct __align__(128) TcBatch {
     CUtensorMap tmA[TC_MAXP];
     CUtensorMap tmB[TC_MAXP];
     TcProb p[TC_MAXP];
