@@ -38,6 +38,40 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
 }
 
+// Double-float: an FP64 value carried as the unevaluated sum h + l of two floats (about 48 significant
+// bits).  The Ozaki path runs its O(r^5) products in it: FP32 arithmetic is many times faster than
+// FP64 on this GPU.  The all-zero bit pattern is 0.
+struct __align__(8) dfl {
+    float h, l;
+    __device__ __forceinline__ operator double() const { return (double)h + (double)l; }
+};
+__device__ __forceinline__ dfl to_dfl(double x) {
+    const float h = (float)x;
+    return dfl{h, (float)(x - (double)h)};   // x - h is exact in FP64
+}
+// acc += a b: the rounding error of the product by FMA (the l.l term is dropped), that of the sum by
+// Knuth's TwoSum; both go to acc.l.
+__device__ __forceinline__ void df_mac(dfl& acc, const dfl& a, const dfl& b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    const float s = acc.h + p;
+    const float bb = s - acc.h;
+    const float t = (acc.h - (s - bb)) + (p - bb);
+    acc.h = s;
+    acc.l += t + e;
+}
+__device__ __forceinline__ void ld4(const dfl* p, dfl (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    const float4 y = *reinterpret_cast<const float4*>(p + 2);
+    v[0] = dfl{x.x, x.y}; v[1] = dfl{x.z, x.w}; v[2] = dfl{y.x, y.y}; v[3] = dfl{y.z, y.w};
+}
+// conversions and multiply-add for the element types of the tiled kernels
+template <typename T> __device__ __forceinline__ T tconv(double x) { return (T)x; }
+template <> __device__ __forceinline__ dfl tconv<dfl>(double x) { return to_dfl(x); }
+template <typename T> __device__ __forceinline__ void tmac(T& acc, const T& a, const T& b) { acc += a * b; }
+template <> __device__ __forceinline__ void tmac<dfl>(dfl& acc, const dfl& a, const dfl& b) { df_mac(acc, a, b); }
+
 // acc[a][b] += sum_q A[q][i0 + a] * B[q][j0 + b]  (A, B: [rp][rp] shared arrays, rp % 4 == 0)
 template <typename T>
 __device__ __forceinline__ void mma4x4(T (&acc)[4][4], const T* A, const T* B, int rp, int n, int i0, int j0) {
@@ -49,7 +83,7 @@ __device__ __forceinline__ void mma4x4(T (&acc)[4][4], const T* A, const T* B, i
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+            for (int v = 0; v < 4; ++v) tmac(acc[u][v], a[u], b[v]);
     }
 }
 
@@ -99,7 +133,7 @@ __device__ __forceinline__ void z_store4(const ZOut& o, int which, size_t row, i
     void* base = which < 0 ? o.Zd : o.Zf[which];
     const size_t ld = which < 0 ? (size_t)o.ldd : (size_t)o.ldf;
     const int Kp = which < 0 ? o.Kp2 : o.Kp1;
-    if (MODE == 0) {
+    if (MODE == 0 || MODE == 4) {
         double* q = (double*)base + row * ld + col;
         *reinterpret_cast<double2*>(q) = make_double2((double)v[0], (double)v[1]);
         *reinterpret_cast<double2*>(q + 2) = make_double2((double)v[2], (double)v[3]);
@@ -168,12 +202,14 @@ __device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, con
 // (the spin-flip sectors drop a sign -1 that their M operand drops too).  The FP64 slices of the
 // next ipb values of p are copied into shared memory (cp.async) while the current ipb slices are
 // multiplied; each thread owns one 4 x 4 output tile of one slice (ipb * (rp/4)^2 threads).
+// MODE 4 (the Ozaki path): FP64 output as MODE 0, products in double-float.
 template <int MODE, int RP = 0>   // RP > 0: compile-time padded size (product loop fully unrolled)
-__global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(int r, int ipb, int pchunk, const double* __restrict__ Waa,
+__global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 : 3) k_Z_pipe(int r, int ipb, int pchunk, const double* __restrict__ Waa,
                                                          const double* __restrict__ Wab,
                                                          const double* __restrict__ Wbb,
                                                          const double* __restrict__ gam, const __grid_constant__ ZOut o) {
-    using T = typename std::conditional<MODE == 0, double, float>::type;
+    using T = typename std::conditional<MODE == 0, double,
+                                        typename std::conditional<MODE == 4, dfl, float>::type>::type;
     extern __shared__ __align__(16) unsigned char tl_smem[];
     const int rp = RP ? RP : pad4(r), ldw = rp + 4, R2 = r * r, R2e = (R2 + 1) & ~1;
     const int nt = rp / 4, nt2 = nt * nt;
@@ -192,11 +228,11 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
     const float invr = 1.f / (float)r;
     const bool vec_ld = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(Waa) | reinterpret_cast<uintptr_t>(Wab) |
                                           reinterpret_cast<uintptr_t>(Wbb)) & 15) == 0;
-    for (int e = threadIdx.x; e < (1 + ipb) * rp * ldw; e += blockDim.x) gT[e] = (T)0;
+    for (int e = threadIdx.x; e < (1 + ipb) * rp * ldw; e += blockDim.x) gT[e] = tconv<T>(0.0);
     __syncthreads();
     for (int e = threadIdx.x; e < R2; e += blockDim.x) {
         const int u = e / r, v = e - u * r;
-        gT[v * ldw + u] = (T)g[e];                       // g[j][q] -> gT[q][j]
+        gT[v * ldw + u] = tconv<T>(g[e]);                // g[j][q] -> gT[q][j]
     }
     auto issue = [&](int p0) {
         const int n = min(ipb, pe - p0);
@@ -230,7 +266,7 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
             T* W = Ws + (size_t)it * rp * ldw;
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
                 const int u = (int)(((float)e + 0.5f) * invr), v = e - u * r;   // e / r, see invr
-                const T x = (T)st[e];
+                const T x = tconv<T>(st[e]);
                 if (tr) W[v * ldw + u] = x;                // src[s][q] -> W[q][s]
                 else W[u * ldw + v] = x;
             }
@@ -243,7 +279,7 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+            for (int v = 0; v < 4; ++v) acc[u][v] = tconv<T>(0.0);
         const T* W = Ws + (size_t)it_me * rp * ldw;
         // with RP the loop runs over the zero-padded rows too (q < RP), at a constant trip count
 #pragma unroll 4
@@ -254,7 +290,7 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+                for (int v = 0; v < 4; ++v) tmac(acc[u][v], a[u], b[v]);
         }
         const int col0 = sP * R2 + p * r + s0;
         const bool vec_st = s0 + 3 < r && ((size_t)col0 & 3) == 0 && (ld & 3) == 0;
@@ -271,7 +307,11 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, MODE == 0 ? 2 : 3) k_Z_pipe(in
             if (dslot >= 0 && j == p)
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    if (s0 + v < r) ((T*)o.diag)[((size_t)dslot * R2 + (size_t)k * r + p) * r + s0 + v] = acc[u][v];
+                    if (s0 + v < r) {
+                        const size_t di = ((size_t)dslot * R2 + (size_t)k * r + p) * r + s0 + v;
+                        if (MODE == 4) ((double*)o.diag)[di] = (double)acc[u][v];
+                        else ((T*)o.diag)[di] = acc[u][v];
+                    }
         }
     }
     cp_async_wait_all();
@@ -332,17 +372,21 @@ struct BTiledArgs {
 //   H_ab = 4 Y_ab - 12 (B2 - B3_{k<->l}).
 // STAGE: the particle-hole rows (x5, x8) and the Q / 1D vectors of (x4, x7) are staged in shared
 // memory with coalesced loads before the products (off when shared memory would not fit).
-template <typename T, bool STAGE>
+// DF (T = double, the Ozaki path): the two products in double-float (C = dfl, the same 8 bytes as
+// double in shared memory), everything else in FP64.
+template <typename T, bool STAGE, bool DF = false>
 __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTiledArgs<T> a) {
+    using C = typename std::conditional<DF, dfl, T>::type;
+    static_assert(sizeof(C) == sizeof(T), "product operands share the layout of T");
     extern __shared__ __align__(16) unsigned char tl_smem[];
     const int r = a.r;
     const int rp = pad4(r);
     const int R2 = r * r;
-    T* XT = (T*)tl_smem;      // [p][k]
-    T* G1 = XT + rp * rp;     // [p][l]
-    T* WT = G1 + rp * rp;     // [p][k]
-    T* MT = WT + rp * rp;     // [p][l]
-    T* Bs = MT + rp * rp;     // [2][r][r]: current pair of B types
+    C* XT = (C*)tl_smem;      // [p][k]
+    C* G1 = XT + rp * rp;     // [p][l]
+    C* WT = G1 + rp * rp;     // [p][k]
+    C* MT = WT + rp * rp;     // [p][l]
+    T* Bs = (T*)(MT + rp * rp);   // [2][r][r]: current pair of B types
     T* X5s = Bs + 2 * R2;     // [k][l] (STAGE)
     T* X8s = X5s + R2;
     T* vq = X8s + R2;         // 4 vectors of r: Q column, 1D row, Q column, 1D row (x4, x7)
@@ -354,7 +398,7 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
     const T* Qb = a.Q + R2;
     const int nt = rp / 4;
     const size_t R22 = 2 * (size_t)R2;
-    for (int e = threadIdx.x; e < 4 * rp * rp; e += blockDim.x) XT[e] = (T)0;   // zero padding once
+    for (int e = threadIdx.x; e < 4 * rp * rp; e += blockDim.x) XT[e] = tconv<C>(0.0);   // zero padding once
     for (int round = 0; round < 3; ++round) {
         const int ntypes = round < 2 ? 1 : 2;
         for (int tt = 0; tt < ntypes; ++tt) {
@@ -386,10 +430,10 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             __syncthreads();
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
                 const int u = e / r, v = e - u * r;
-                XT[xT ? u * rp + v : v * rp + u] = Xrow[e];   // T3 uses Xab[ij][p][k]
-                G1[u * rp + v] = g1[e];
-                WT[v * rp + u] = wv[e];                      // w[k][p] -> WT[p][k]
-                MT[mT ? v * rp + u : u * rp + v] = Mrow[e];  // M[(l,p)] -> MT[p][l]  or  M[(p,l)]
+                XT[xT ? u * rp + v : v * rp + u] = tconv<C>(Xrow[e]);   // T3 uses Xab[ij][p][k]
+                G1[u * rp + v] = tconv<C>(g1[e]);
+                WT[v * rp + u] = tconv<C>(wv[e]);                      // w[k][p] -> WT[p][k]
+                MT[mT ? v * rp + u : u * rp + v] = tconv<C>(Mrow[e]);  // M[(l,p)] -> MT[p][l]  or  M[(p,l)]
                 if (STAGE) {
                     X5s[e] = X5b[((size_t)u * r + j) * ld5 + (size_t)i * r + v];   // (k, l) = (u, v)
                     X8s[e] = X8b[((size_t)u * r + i) * ld8 + (size_t)j * r + v];
@@ -406,13 +450,13 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             T* Bt = Bs + (size_t)tt * R2;
             for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
                 const int k0 = (tile / nt) * 4, l0 = (tile % nt) * 4;
-                T x1[4][4], x2[4][4];
+                C x1[4][4], x2[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) x1[u][v] = x2[u][v] = 0;
-                mma4x4<T>(x1, XT, G1, rp, r, k0, l0);
-                mma4x4<T>(x2, WT, MT, rp, r, k0, l0);
+                    for (int v = 0; v < 4; ++v) x1[u][v] = x2[u][v] = tconv<C>(0.0);
+                mma4x4<C>(x1, XT, G1, rp, r, k0, l0);
+                mma4x4<C>(x2, WT, MT, rp, r, k0, l0);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = k0 + u;
@@ -433,7 +477,7 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                             x5 = X5b[((size_t)k * r + j) * ld5 + (size_t)i * r + l];
                             x8 = X8b[((size_t)k * r + i) * ld8 + (size_t)j * r + l];
                         }
-                        Bt[k * r + l] = (sgn1 * x1[u][v] - (T)2 * sgn2 * x2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
+                        Bt[k * r + l] = (sgn1 * (T)x1[u][v] - (T)2 * sgn2 * (T)x2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
                                             (T)(1.0 / 9.0) +
                                         (a.ny[t] ? a.ny[t][ij * R2 + (size_t)k * r + l] : (T)0);
                     }
@@ -803,8 +847,8 @@ static ZPlan z_plan_compute(int r, size_t es, const void* kern) {
 
 // cached per host thread, output mode and r (the occupancy query is not free)
 static ZPlan z_plan(int r, int mode, size_t es, const void* kern) {
-    static thread_local int cached_r[4] = {-1, -1, -1, -1};
-    static thread_local ZPlan cached[4];
+    static thread_local int cached_r[5] = {-1, -1, -1, -1, -1};
+    static thread_local ZPlan cached[5];
     if (cached_r[mode] != r) {
         cached[mode] = z_plan_compute(r, es, kern);
         cached_r[mode] = r;
@@ -826,8 +870,13 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
     if (c->opt.prec == ACSE_FP64) {
         o.Zd = w.Zd; o.Zf[0] = w.Zf1; o.Zf[1] = w.Zf2;
         o.mode = 0; o.ldd = 2 * R2; o.ldf = R2; o.Kp1 = o.Kp2 = 0; o.diag = w.zdiag;
-        const ZPlan zp = z_plan(r, 0, sizeof(double), (const void*)k_Z_pipe<0>);
-        k_Z_pipe<0><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        if (c->oz) {   // Ozaki path: double-float products, FP64 output
+            const ZPlan zp = z_plan(r, 4, sizeof(double), (const void*)k_Z_pipe<4>);
+            k_Z_pipe<4><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        } else {
+            const ZPlan zp = z_plan(r, 0, sizeof(double), (const void*)k_Z_pipe<0>);
+            k_Z_pipe<0><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+        }
         ACSE_LAUNCHED(c);
         k_w_from_diag<double><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag, w.w, 0);
     } else {
@@ -871,10 +920,15 @@ int launch_B_tiled(acse_ctx* c) {
         a.flip = 0;
         for (int t = 0; t < 4; ++t) a.ny[t] = (const double*)ny_terms(c, t);
         a.gam = w.gam; a.w = w.w; a.Q = w.Q;
-        if (b_smem(r, sizeof(double), true) <= k_smem_cap)
-            k_B_tiled<double, true><<<R2, TL_TPB, b_smem(r, sizeof(double), true), c->stream>>>(a);
-        else
-            k_B_tiled<double, false><<<R2, TL_TPB, b_smem(r, sizeof(double), false), c->stream>>>(a);
+        const bool st = b_smem(r, sizeof(double), true) <= k_smem_cap;
+        const size_t sm = b_smem(r, sizeof(double), st);
+        if (c->oz) {   // Ozaki path: double-float products
+            if (st) k_B_tiled<double, true, true><<<R2, TL_TPB, sm, c->stream>>>(a);
+            else k_B_tiled<double, false, true><<<R2, TL_TPB, sm, c->stream>>>(a);
+        } else {
+            if (st) k_B_tiled<double, true><<<R2, TL_TPB, sm, c->stream>>>(a);
+            else k_B_tiled<double, false><<<R2, TL_TPB, sm, c->stream>>>(a);
+        }
     } else {
         BTiledArgs<float> a;
         a.r = r;
@@ -923,6 +977,11 @@ int tiled_set_attrs() {
                                        (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k_smem_cap));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bp_smem(48)));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,

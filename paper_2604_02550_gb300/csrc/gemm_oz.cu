@@ -411,30 +411,51 @@ __device__ __forceinline__ double oz_ll_scaled(long long acc, int ex) {
 // only bits below 2^-48 of the level-2 unit) are added in int64 (|sum| < 2^61), and the conversion of
 // the sum, scaled by the power of two alpha 2^(ea + eb - 48), to FP64 is the single rounding.
 // HBM-bound: the groups of an element are read once, coalesced, and C is written once.
+__device__ __forceinline__ long long oz_term(int v, int w) {
+    return w >= 0 ? (long long)v * (1ll << w) : ((long long)v >> -w);   // arithmetic shift: floor
+}
+
 __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ bp) {
     const OzBatch& b = *bp;
     const OzProb& P = b.p[blockIdx.y];
     const int N = P.N, g = P.g, S = b.S;
     const size_t MN = (size_t)P.M * N;
     const int* __restrict__ st = P.stage;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.x * blockDim.x) {
-        long long acc = 0;
+    // four consecutive elements of one row per thread (int4 loads) when N % 4 == 0, else one
+    const int vw = (N & 3) == 0 ? 4 : 1;
+    const size_t nunit = MN / vw;
+    for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < nunit; u += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = u * vw;
+        long long acc[4] = {0, 0, 0, 0};
         size_t off = e;
         for (int L = 2; L <= S + 1; ++L) {
             const int w = 36 - OZ_BETA * (L - 2);
             const int nl = (L - 2) / g + 1;
-#pragma unroll 2
-            for (int q = 0; q < nl; ++q, off += MN) {
-                const long long v = st[off];
-                acc += w >= 0 ? v * (1ll << w) : (v >> -w);   // arithmetic shift: floor
+            if (vw == 4) {
+#pragma unroll 4
+                for (int q = 0; q < nl; ++q, off += MN) {
+                    const int4 v = *reinterpret_cast<const int4*>(st + off);
+                    acc[0] += oz_term(v.x, w);
+                    acc[1] += oz_term(v.y, w);
+                    acc[2] += oz_term(v.z, w);
+                    acc[3] += oz_term(v.w, w);
+                }
+            } else {
+#pragma unroll 4
+                for (int q = 0; q < nl; ++q, off += MN) acc[0] += oz_term(st[off], w);
             }
         }
-        const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
+        const int i = (int)(e / N), j0 = (int)(e - (size_t)i * N);
         const int ea = (int)((__double_as_longlong(P.sa[i]) >> 52) & 0x7FF);   // row scales are powers of two
-        const int eb = (int)((__double_as_longlong(P.sb[j]) >> 52) & 0x7FF);
-        P.C[(size_t)i * P.ldc + j] = (ea == 0x7FF || eb == 0x7FF)
-                                         ? __longlong_as_double(0x7ff8000000000000ll)
-                                         : oz_ll_scaled(acc, ea + eb - 2046 + P.ealpha - 48);
+        double* crow = P.C + (size_t)i * P.ldc;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < vw) {
+                const int eb = (int)((__double_as_longlong(P.sb[j0 + k]) >> 52) & 0x7FF);
+                crow[j0 + k] = (ea == 0x7FF || eb == 0x7FF) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                             : oz_ll_scaled(acc[k], ea + eb - 2046 + P.ealpha - 48);
+            }
+        }
     }
 }
 
