@@ -553,7 +553,8 @@ def main():
     per_step = ms_max / args.steps
     value = whole_job_rate(args.steps, world, ms_max)
     fl_alg = flops_per_pass(p.r)                       # 32 r^6: the unpacked formulation
-    fl = fl_alg if prec in ("fp64", "ozaki") else flops_per_pass(p.r, packed=True, singlet=singlet)   # what the GEMM launch executes
+    # what the GEMM launch executes (the same-spin pair GEMMs on packed pairs on every path but FP64 FMA)
+    fl = fl_alg if prec == "fp64" else flops_per_pass(p.r, packed=True, singlet=singlet)
     split = 3 if prec in ("bf16x3", "tf32x3") else 1
     if prec == "ozaki":
         split = OZ_SLICES * (OZ_SLICES + 1) // 2      # bf16 slice products per FP64 GEMM
@@ -579,7 +580,7 @@ def main():
                  "flops_per_launch": split * fl,
                  "flops_note": {"fp64": "2MNK, 32 r^6 per pass",
                                 "ozaki": f"bf16 slice products of the Ozaki scheme: {split} per FP64 GEMM "
-                                         f"({OZ_SLICES} slices), 2MNK each; 32 r^6 FP64-equivalent per pass"}.get(
+                                         f"({OZ_SLICES} slices), 2MNK each, same-spin pair GEMMs on pairs i<j"}.get(
                      prec, "2MNK of the GEMMs the launch executes (same-spin pair GEMMs on pairs i<j)"),
                  "launch_ms": 1e3 * gemm_avg_s,
                  "gemm_share_of_step": 2 * 1e3 * gemm_avg_s / per_step,

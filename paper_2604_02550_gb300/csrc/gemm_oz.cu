@@ -115,9 +115,11 @@ __device__ __forceinline__ int oz_find_problem(const OzBatch& b, int t) {
 struct OzSliceJob {
     const double* src;
     size_t lds;             // source row stride (elements)
-    __nv_bfloat16* dst;
+    const int* rowmap;      // source row of each output row (null: the same row)
+    const int* colmap;      // source column of each K index (null: the same column)
+    __nv_bfloat16* dst;     // first output row of the job
     size_t ldd;             // S * Kp
-    double* scale;          // 2^e per row (NaN for a row with a non-finite entry)
+    double* scale;          // 2^e per output row (NaN for a row with a non-finite entry)
     int rows, K, Kp, reverse, row0;
 };
 
@@ -154,15 +156,17 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSlic
     while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= (int)blockIdx.x) ++ji;
     const OzSliceJob& J = b.j[ji];
     const int row = (int)blockIdx.x - J.row0;
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(J.src + (size_t)row * J.lds);
+    const int srow = J.rowmap ? J.rowmap[row] : row;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(J.src + (size_t)srow * J.lds);
     const int K = J.K;
+    const int* cm = J.colmap;
     unsigned long long v[2 * OZ_SLICE_PPT];
     unsigned long long mx = 0;
 #pragma unroll
     for (int u = 0; u < OZ_SLICE_PPT; ++u) {
         const int k = 2 * ((int)threadIdx.x + u * 256);
-        v[2 * u] = k < K ? src[k] : 0ull;
-        v[2 * u + 1] = k + 1 < K ? src[k + 1] : 0ull;
+        v[2 * u] = k < K ? src[cm ? cm[k] : k] : 0ull;
+        v[2 * u + 1] = k + 1 < K ? src[cm ? cm[k + 1] : k + 1] : 0ull;
         mx = max(mx, max(v[2 * u] & 0x7FFFFFFFFFFFFFFFull, v[2 * u + 1] & 0x7FFFFFFFFFFFFFFFull));
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -459,10 +463,37 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ b
     }
 }
 
+// Same-spin pair GEMMs on packed pairs (as on the split path): in the aa and bb sectors the rows (ij),
+// the columns (kp) and the contraction (rs) of [M; D] W^T are antisymmetric pairs, so those GEMMs run
+// on pairs i < j only (P = r(r-1)/2; alpha 2 for the halved (rs) sum) and k_oz_unpack rebuilds the
+// full X and Y rows by antisymmetry.  pk(a, b), a < b, numbers the pairs row by row.
+__host__ __device__ __forceinline__ int oz_pk(int r, int a, int b) { return a * r - a * (a + 1) / 2 + (b - a - 1); }
+
+// X_s, Y_s (s = aa, bb; r^2 x r^2 FP64) from the packed [X; Y] (2P x P): one block per output row.
+__global__ void __launch_bounds__(256) k_oz_unpack(int r, const double* __restrict__ Cp0, const double* __restrict__ Cp2,
+                                                   double* X0, double* Y0, double* X2, double* Y2) {
+    const int R2 = r * r, P = r * (r - 1) / 2;
+    const int sec = blockIdx.x / (2 * R2);
+    const int row = blockIdx.x - sec * 2 * R2;
+    const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - i * r;
+    double* dst = (sec == 0 ? (part ? Y0 : X0) : (part ? Y2 : X2)) + (size_t)ij * R2;
+    if (i == j) {
+        for (int c = threadIdx.x; c < R2; c += blockDim.x) dst[c] = 0.0;
+        return;
+    }
+    const double si = i < j ? 1.0 : -1.0;
+    const double* src = (sec == 0 ? Cp0 : Cp2) + (size_t)(part * P + (i < j ? oz_pk(r, i, j) : oz_pk(r, j, i))) * P;
+    for (int c = threadIdx.x; c < R2; c += blockDim.x) {
+        const int k = c / r, q = c - (c / r) * r;
+        dst[c] = k == q ? 0.0 : (k < q ? si * src[oz_pk(r, k, q)] : -si * src[oz_pk(r, q, k)]);
+    }
+}
+
 // --------------------------------------------------------------------------- host plan
-// Operands of the nine GEMMs of a pass (the list of acse_gemm_list_f64):
-//   A: M_aa, M_ab, M_bb, D_aa, D_ab, D_bb (r^2 x r^2), Zd (2r^2 x 2r^2), Zf1, Zf2 (r^2 x r^2);
-//   B: W_aa, W_ab, W_bb (r^2 x r^2), Md (2r^2 x 2r^2), Mf1, Mf2 (r^2 x r^2).
+// Operands of the GEMMs of a pass (the products of acse_gemm_list_f64, the same-spin ones packed):
+//   A: [M_aa; D_aa] packed (2P x P), M_ab, D_ab (r^2 x r^2), [M_bb; D_bb] packed, Zd (2r^2 x 2r^2),
+//      Zf1, Zf2 (r^2 x r^2);
+//   B: W_aa packed (P x P), W_ab (r^2 x r^2), W_bb packed, Md (2r^2 x 2r^2), Mf1, Mf2 (r^2 x r^2).
 struct OzOp {
     __nv_bfloat16* sl;
     double* scale;
@@ -476,7 +507,9 @@ struct OzPlan {
     size_t smem;
     int nsm;
     int tiles;
-    OzOp A[9], B[6];
+    OzOp A[7], B[6];
+    int* pmap;          // pair index -> i r + j (i < j), P entries
+    double* Cp[2];      // packed [X; Y] of the aa and bb sectors (2P x P)
     int* err;
 };
 
@@ -534,7 +567,7 @@ int oz_plan_create(acse_ctx* c) {
     OzPlan* pl = (OzPlan*)calloc(1, sizeof(OzPlan));
     if (!pl) return ACSE_ERR_NOMEM;
     c->oz_plan = pl;
-    const int r = c->r, R2 = r * r, R22 = 2 * R2;
+    const int r = c->r, R2 = r * r, R22 = 2 * R2, P = r * (r - 1) / 2;
     pl->S = c->opt.oz_slices;
     pl->bn = R2 >= 256 ? OZ_BN : 128;
     pl->smem = oz_smem(pl->bn);
@@ -549,14 +582,37 @@ int oz_plan_create(acse_ctx* c) {
         cudaGetLastError();
         pl->nsm = 152;
     }
-    for (int i = 0; i < 6; ++i) ACSE_TRY(oz_op_alloc(pl->A[i], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[6], R22, R22, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[7], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[8], R2, R2, pl->S));
-    for (int i = 0; i < 3; ++i) ACSE_TRY(oz_op_alloc(pl->B[i], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[0], 2 * P, P, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[1], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[2], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[3], 2 * P, P, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[4], R22, R22, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[5], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->A[6], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->B[0], P, P, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->B[1], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl->B[2], P, P, pl->S));
     ACSE_TRY(oz_op_alloc(pl->B[3], R22, R22, pl->S));
     ACSE_TRY(oz_op_alloc(pl->B[4], R2, R2, pl->S));
     ACSE_TRY(oz_op_alloc(pl->B[5], R2, R2, pl->S));
+    {
+        int* hm = (int*)malloc((size_t)P * sizeof(int));
+        if (!hm) return ACSE_ERR_NOMEM;
+        for (int a = 0; a < r; ++a)
+            for (int b = a + 1; b < r; ++b) hm[oz_pk(r, a, b)] = a * r + b;
+        const bool ok = cudaMalloc((void**)&pl->pmap, (size_t)P * sizeof(int)) == cudaSuccess &&
+                        cudaMemcpy(pl->pmap, hm, (size_t)P * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        free(hm);
+        if (!ok) {
+            cudaGetLastError();
+            return ACSE_ERR_NOMEM;
+        }
+    }
+    for (int s = 0; s < 2; ++s)
+        if (cudaMalloc((void**)&pl->Cp[s], (size_t)2 * P * P * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return ACSE_ERR_NOMEM;
+        }
     if (cudaMalloc((void**)&pl->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return ACSE_ERR_NOMEM;
@@ -570,16 +626,15 @@ int oz_plan_create(acse_ctx* c) {
     B.err = pl->err;
     B.wait_ns = OZ_WAIT_NS;
     Work& w = c->w;
-    // the largest-K GEMM first, then the pair GEMMs (X_s = f M_s W_s^T, Y_s = f D_s W_s^T; f = 2 for the
-    // mixed-spin sector) and the spin-flip ones: the FP64 GEMM list of the pass
-    ACSE_TRY(oz_add(pl, pl->A[6], pl->B[3], w.X5d, R22, 1.0));
-    for (int s = 0; s < 3; ++s) {
-        const double f = s == 1 ? 2.0 : 1.0;
-        ACSE_TRY(oz_add(pl, pl->A[s], pl->B[s], w.X[s], R2, f));
-        ACSE_TRY(oz_add(pl, pl->A[3 + s], pl->B[s], w.Y[s], R2, f));
-    }
-    ACSE_TRY(oz_add(pl, pl->A[7], pl->B[4], w.X5f1, R2, 1.0));
-    ACSE_TRY(oz_add(pl, pl->A[8], pl->B[5], w.X5f2, R2, 1.0));
+    // the largest-K GEMM first, then the mixed-spin pair GEMMs (X_ab = 2 M_ab W_ab^T, Y_ab = 2 D_ab W_ab^T),
+    // the spin-flip ones and the packed same-spin ones (alpha 2 for the halved (rs) sum)
+    ACSE_TRY(oz_add(pl, pl->A[4], pl->B[3], w.X5d, R22, 1.0));
+    ACSE_TRY(oz_add(pl, pl->A[1], pl->B[1], w.X[1], R2, 2.0));
+    ACSE_TRY(oz_add(pl, pl->A[2], pl->B[1], w.Y[1], R2, 2.0));
+    ACSE_TRY(oz_add(pl, pl->A[5], pl->B[4], w.X5f1, R2, 1.0));
+    ACSE_TRY(oz_add(pl, pl->A[6], pl->B[5], w.X5f2, R2, 1.0));
+    ACSE_TRY(oz_add(pl, pl->A[0], pl->B[0], pl->Cp[0], P, 2.0));
+    ACSE_TRY(oz_add(pl, pl->A[3], pl->B[2], pl->Cp[1], P, 2.0));
     pl->tiles = B.total_tiles;
     if (cudaMalloc((void**)&pl->dev, sizeof(OzBatch)) != cudaSuccess) {
         cudaGetLastError();
@@ -592,7 +647,7 @@ int oz_plan_create(acse_ctx* c) {
 void oz_plan_destroy(acse_ctx* c) {
     OzPlan* pl = (OzPlan*)c->oz_plan;
     if (!pl) return;
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < 7; ++i) {
         if (pl->A[i].sl) cudaFree(pl->A[i].sl);
         if (pl->A[i].scale) cudaFree(pl->A[i].scale);
     }
@@ -600,6 +655,9 @@ void oz_plan_destroy(acse_ctx* c) {
         if (pl->B[i].sl) cudaFree(pl->B[i].sl);
         if (pl->B[i].scale) cudaFree(pl->B[i].scale);
     }
+    if (pl->pmap) cudaFree(pl->pmap);
+    for (int s = 0; s < 2; ++s)
+        if (pl->Cp[s]) cudaFree(pl->Cp[s]);
     if (pl->err) {
         if (c->w.tc_err == pl->err) c->w.tc_err = nullptr;
         cudaFree(pl->err);
@@ -613,43 +671,56 @@ void oz_plan_destroy(acse_ctx* c) {
     c->oz_plan = nullptr;
 }
 
-static void oz_job(OzSliceBatch& b, int& rows, const OzOp& o, const double* src, size_t lds, int reverse) {
+// One slicing job: `rows` rows of operand o starting at output row `orow`, read from src (row stride
+// lds) through the optional row / column maps.
+static void oz_job(OzSliceBatch& b, int& rows, const OzOp& o, int orow, int nrows, const double* src, size_t lds,
+                   const int* rowmap, const int* colmap, int reverse) {
     OzSliceJob& j = b.j[b.njobs++];
     j.src = src;
     j.lds = lds;
-    j.dst = o.sl;
+    j.rowmap = rowmap;
+    j.colmap = colmap;
     j.ldd = (size_t)b.S * o.Kp;
-    j.scale = o.scale;
-    j.rows = o.rows;
+    j.dst = o.sl + (size_t)orow * j.ldd;
+    j.scale = o.scale + orow;
+    j.rows = nrows;
     j.K = o.K;
     j.Kp = o.Kp;
     j.reverse = reverse;
     j.row0 = rows;
-    rows += o.rows;
+    rows += nrows;
 }
 
 int oz_slice_operands(acse_ctx* c, int prep_D) {
     OzPlan* pl = (OzPlan*)c->oz_plan;
     if (!pl) return ACSE_ERR_UNSUPPORTED;
-    const int r = c->r;
+    const int r = c->r, P = r * (r - 1) / 2;
     const size_t R2 = (size_t)r * r;
+    const int iR2 = (int)R2;
     Work& w = c->w;
     OzSliceBatch b;
     memset(&b, 0, sizeof(b));
     b.S = pl->S;
     int rows = 0;
+    const int* pm = pl->pmap;
     // A slices in order (segment s - 1), B slices reversed (segment S - t)
     if (prep_D) {
-        for (int s = 0; s < 3; ++s) oz_job(b, rows, pl->A[s], w.M[s], R2, 0);
-        for (int s = 0; s < 3; ++s) oz_job(b, rows, pl->A[3 + s], c->cur_D[s], R2, 0);
-        oz_job(b, rows, pl->B[3], w.Md, 2 * R2, 1);
-        oz_job(b, rows, pl->B[4], w.Mf1, R2, 1);
-        oz_job(b, rows, pl->B[5], w.Mf2, R2, 1);
+        oz_job(b, rows, pl->A[0], 0, P, w.M[0], R2, pm, pm, 0);
+        oz_job(b, rows, pl->A[0], P, P, c->cur_D[0], R2, pm, pm, 0);
+        oz_job(b, rows, pl->A[1], 0, iR2, w.M[1], R2, nullptr, nullptr, 0);
+        oz_job(b, rows, pl->A[2], 0, iR2, c->cur_D[1], R2, nullptr, nullptr, 0);
+        oz_job(b, rows, pl->A[3], 0, P, w.M[2], R2, pm, pm, 0);
+        oz_job(b, rows, pl->A[3], P, P, c->cur_D[2], R2, pm, pm, 0);
+        oz_job(b, rows, pl->B[3], 0, 2 * iR2, w.Md, 2 * R2, nullptr, nullptr, 1);
+        oz_job(b, rows, pl->B[4], 0, iR2, w.Mf1, R2, nullptr, nullptr, 1);
+        oz_job(b, rows, pl->B[5], 0, iR2, w.Mf2, R2, nullptr, nullptr, 1);
     }
-    for (int s = 0; s < 3; ++s) oz_job(b, rows, pl->B[s], c->cur_W[s], R2, 1);
-    oz_job(b, rows, pl->A[6], w.Zd, 2 * R2, 0);
-    oz_job(b, rows, pl->A[7], w.Zf1, R2, 0);
-    oz_job(b, rows, pl->A[8], w.Zf2, R2, 0);
+    oz_job(b, rows, pl->B[0], 0, P, c->cur_W[0], R2, pm, pm, 1);
+    oz_job(b, rows, pl->B[1], 0, iR2, c->cur_W[1], R2, nullptr, nullptr, 1);
+    oz_job(b, rows, pl->B[2], 0, P, c->cur_W[2], R2, pm, pm, 1);
+    oz_job(b, rows, pl->A[4], 0, 2 * iR2, w.Zd, 2 * R2, nullptr, nullptr, 0);
+    oz_job(b, rows, pl->A[5], 0, iR2, w.Zf1, R2, nullptr, nullptr, 0);
+    oz_job(b, rows, pl->A[6], 0, iR2, w.Zf2, R2, nullptr, nullptr, 0);
     k_oz_slice<<<rows, 256, 0, c->stream>>>(b);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -666,7 +737,11 @@ int oz_gemm_launch(acse_ctx* c) {
     ACSE_LAUNCHED(c);
     k_oz_reduce<<<dim3(2 * pl->nsm, pl->host->nprob), 256, 0, c->stream>>>(pl->dev);
     ACSE_LAUNCHED(c);
-    return prof_end(c);
+    ACSE_TRY(prof_end(c));
+    Work& w = c->w;
+    k_oz_unpack<<<2 * 2 * c->r * c->r, 256, 0, c->stream>>>(c->r, pl->Cp[0], pl->Cp[1], w.X[0], w.Y[0], w.X[2], w.Y[2]);
+    ACSE_LAUNCHED(c);
+    return ACSE_OK;
 }
 
 int oz_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
