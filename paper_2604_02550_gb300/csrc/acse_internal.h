@@ -49,7 +49,12 @@ struct TcTable {
     size_t smem;
     int pers;        // 1: persistent kernel (one CTA per SM, double-buffered TMEM accumulators)
     int nsm;         // multiprocessors of the device (grid of the persistent kernel)
+    int* sched;      // device: tile order of the persistent kernel, then the CTAs' start offsets
+    int sched_cap;   // ints allocated at sched
 };
+// Longest-processing-time assignment of T tiles of the given costs to G CTAs: order[] lists the tile
+// indices CTA by CTA (costliest first within a CTA), CTA c owning order[start[c] .. start[c+1]).
+void tc_lpt_schedule(const long long* cost, int T, int G, int* order, int* start);
 int tc_table_init(TcTable* t, int kind, int bn);
 void tc_table_free(TcTable* t);
 int tc_table_upload(TcTable* t);

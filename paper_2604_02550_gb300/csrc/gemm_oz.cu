@@ -66,6 +66,8 @@ struct __align__(128) OzBatch {
     int* err;
     unsigned long long wait_ns;
     int inject_stall;
+    const int* order;     // tiles of CTA c: order[cta_start[c] .. cta_start[c+1]) (longest first)
+    const int* cta_start;
 };
 
 __host__ __device__ inline int oz_ngroups(int S, int g) {
@@ -233,7 +235,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = b.total_tiles, S = b.S;
+    const int S = b.S;
+    const int q0 = b.cta_start[blockIdx.x], q1 = b.cta_start[blockIdx.x + 1];   // this CTA's tiles
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -258,7 +261,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
         if (lane == 0) {
             int it = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+            for (int qi = q0; qi < q1 && !stop; ++qi) {
+                const int t = b.order[qi];
                 const int pi = oz_find_problem(b, t);
                 const OzProb& P = b.p[pi];
                 const int local = t - P.tile_start;
@@ -290,8 +294,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
             const uint32_t idesc = make_idesc<0, BN>();
             if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
             int it = 0, lt = 0;
-            for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
-                const OzProb& P = b.p[oz_find_problem(b, t)];
+            for (int qi = q0; qi < q1 && !*abort_flag; ++qi) {
+                const OzProb& P = b.p[oz_find_problem(b, b.order[qi])];
                 for (int gi = 0; gi < P.ngroups && !*abort_flag; ++gi, ++lt) {
                     int L, s0, s1;
                     oz_group(S, P.g, gi, L, s0, s1);
@@ -326,7 +330,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
         const int q = warp & 3;   // TMEM lane quadrant this warp may access
         int lt = 0;
         bool run = true;
-        for (int t = blockIdx.x; t < T && run; t += gridDim.x) {
+        for (int qi = q0; qi < q1 && run; ++qi) {
+            const int t = b.order[qi];
             const OzProb& P = b.p[oz_find_problem(b, t)];
             const int local = t - P.tile_start;
             const int m0 = (local / P.tiles_n) * TC_BM, n0 = (local % P.tiles_n) * BN;
@@ -510,6 +515,7 @@ struct OzPlan {
     OzOp A[7], B[6];
     int* pmap;          // pair index -> i r + j (i < j), P entries
     double* Cp[2];      // packed [X; Y] of the aa and bb sectors (2P x P)
+    int* sched;         // tile lists of the persistent kernel (OzBatch::order, cta_start)
     int* err;
 };
 
@@ -636,6 +642,32 @@ int oz_plan_create(acse_ctx* c) {
     ACSE_TRY(oz_add(pl, pl->A[0], pl->B[0], pl->Cp[0], P, 2.0));
     ACSE_TRY(oz_add(pl, pl->A[3], pl->B[2], pl->Cp[1], P, 2.0));
     pl->tiles = B.total_tiles;
+    if (pl->tiles > 0) {   // longest-processing-time tile lists (tile cost: its K blocks over all groups)
+        const int T = pl->tiles, G = T < pl->nsm ? T : pl->nsm;
+        const int nprod = pl->S * (pl->S + 1) / 2;
+        int* hs = (int*)malloc((size_t)(T + G + 1) * sizeof(int));
+        long long* cost = (long long*)malloc((size_t)T * sizeof(long long));
+        if (!hs || !cost) {
+            free(hs);
+            free(cost);
+            return ACSE_ERR_NOMEM;
+        }
+        for (int p = 0; p < B.nprob; ++p) {
+            const int n = ((B.p[p].M + TC_BM - 1) / TC_BM) * B.p[p].tiles_n;
+            for (int k = 0; k < n; ++k) cost[B.p[p].tile_start + k] = (long long)nprod * B.p[p].kbs + 4 * B.p[p].ngroups;
+        }
+        tc_lpt_schedule(cost, T, G, hs, hs + T);
+        const bool ok = cudaMalloc((void**)&pl->sched, (size_t)(T + G + 1) * sizeof(int)) == cudaSuccess &&
+                        cudaMemcpy(pl->sched, hs, (size_t)(T + G + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        free(hs);
+        free(cost);
+        if (!ok) {
+            cudaGetLastError();
+            return ACSE_ERR_NOMEM;
+        }
+        B.order = pl->sched;
+        B.cta_start = pl->sched + T;
+    }
     if (cudaMalloc((void**)&pl->dev, sizeof(OzBatch)) != cudaSuccess) {
         cudaGetLastError();
         return ACSE_ERR_NOMEM;
@@ -656,6 +688,7 @@ void oz_plan_destroy(acse_ctx* c) {
         if (pl->B[i].scale) cudaFree(pl->B[i].scale);
     }
     if (pl->pmap) cudaFree(pl->pmap);
+    if (pl->sched) cudaFree(pl->sched);
     for (int s = 0; s < 2; ++s)
         if (pl->Cp[s]) cudaFree(pl->Cp[s]);
     if (pl->err) {

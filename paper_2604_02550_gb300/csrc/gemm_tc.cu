@@ -17,6 +17,11 @@
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include <algorithm>
+#include <queue>
+#include <utility>
+#include <vector>
+
 #include "acse_internal.h"
 
 #define TC_MAXP 160          // problems of one grouped launch (16 instances x 9 GEMMs fit)
@@ -44,6 +49,8 @@ struct __align__(128) TcBatch {
     int* err;
     unsigned long long wait_ns;
     int inject_stall;     // test knob: the MMA thread first waits on a barrier nothing signals
+    const int* order;     // persistent kernel: tiles of CTA c are order[cta_start[c] .. cta_start[c+1])
+    const int* cta_start;
 };
 
 #include "tc_ptx.cuh"
@@ -197,8 +204,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const TcBatch* __rest
 }
 
 // ------------------------------------------------------------------ persistent variant
-// One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (the table lists the
-// largest-K problem first).  The shared-memory ring runs on across tiles (a global K-block counter
+// One CTA per SM walks its list of tiles, assigned on the host by longest processing time (tile cost =
+// its K blocks plus a per-tile epilogue allowance), costliest first: static round-robin over tiles of
+// unequal K left the busiest SM about 8 % above the mean at r = 48.  The shared-memory ring runs on across tiles (a global K-block counter
 // gives stage and phase), and the accumulator is double-buffered in TMEM (2 x BN columns): the MMA
 // thread fills buffer (tile & 1) while warps 2-5 drain the other one, so a tile's epilogue and the
 // next tile's first loads and MMAs overlap.  Barriers: full/empty per stage, accf[2] (MMA -> epilogue,
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = b.total_tiles;
+    const int q0 = b.cta_start[blockIdx.x], q1 = b.cta_start[blockIdx.x + 1];   // this CTA's tiles
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -269,7 +277,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
         if (lane == 0) {
             int it = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+            for (int qi = q0; qi < q1 && !stop; ++qi) {
+                const int t = b.order[qi];
                 const int pi = tc_find_problem(b, t);
                 const TcProb& P = b.p[pi];
                 int m0, n0;
@@ -296,7 +305,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
             const uint32_t idesc = make_idesc<KIND, BN>();
             if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
             int it = 0, lt = 0;
-            for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x, ++lt) {
+            for (int qi = q0; qi < q1 && !*abort_flag; ++qi, ++lt) {
+                const int t = b.order[qi];
                 const int pi = tc_find_problem(b, t);
                 const int nk = b.p[pi].kblocks;
                 const int ab = lt & 1, use = lt >> 1;
@@ -327,7 +337,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
     } else {
         const int q = warp & 3;   // TMEM lane quadrant this warp may access
         int lt = 0;
-        for (int t = blockIdx.x; t < T; t += gridDim.x, ++lt) {
+        for (int qi = q0; qi < q1; ++qi, ++lt) {
+            const int t = b.order[qi];
             const int ab = lt & 1, use = lt >> 1;
             // lane 0 waits and the warp follows its verdict (tcgen05.ld below is warp-collective)
             int go = 0;
@@ -469,11 +480,62 @@ int tc_table_init(TcTable* t, int kind, int bn) {
 
 void tc_table_free(TcTable* t) {
     if (t->dev) cudaFree(t->dev);
+    if (t->sched) cudaFree(t->sched);
     free(t->host);
     memset(t, 0, sizeof(*t));
 }
 
+void tc_lpt_schedule(const long long* cost, int T, int G, int* order, int* start) {
+    std::vector<int> idx(T);
+    for (int i = 0; i < T; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // min-heap of (load, cta)
+    std::priority_queue<std::pair<long long, int>, std::vector<std::pair<long long, int>>,
+                        std::greater<std::pair<long long, int>>> heap;
+    for (int c = 0; c < G; ++c) heap.push({0, c});
+    std::vector<std::vector<int>> lists(G);
+    for (int i : idx) {
+        auto top = heap.top();
+        heap.pop();
+        lists[top.second].push_back(i);
+        heap.push({top.first + cost[i], top.second});
+    }
+    int q = 0;
+    for (int c = 0; c < G; ++c) {
+        start[c] = q;
+        for (int i : lists[c]) order[q++] = i;
+    }
+    start[G] = q;
+}
+
+// Uploads the table and the persistent kernel's tile schedule (for the grid tc_table_launch uses).
 int tc_table_upload(TcTable* t) {
+    TcBatch& b = *t->host;
+    const int T = b.total_tiles;
+    const int G = T < t->nsm ? T : t->nsm;
+    if (T > 0) {
+        std::vector<long long> cost(T);
+        for (int p = 0; p < b.nprob; ++p) {
+            const int n = ((b.p[p].M + TC_BM - 1) / TC_BM) * b.p[p].tiles_n;
+            for (int k = 0; k < n; ++k) cost[b.p[p].tile_start + k] = b.p[p].kblocks + 4;
+        }
+        const int need = T + G + 1;
+        if (t->sched_cap < need) {
+            if (t->sched) cudaFree(t->sched);
+            t->sched = nullptr;
+            t->sched_cap = 0;
+            if (cudaMalloc((void**)&t->sched, (size_t)need * sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                return ACSE_ERR_NOMEM;
+            }
+            t->sched_cap = need;
+        }
+        std::vector<int> h(need);
+        tc_lpt_schedule(cost.data(), T, G, h.data(), h.data() + T);
+        ACSE_CUDA_TRY(cudaMemcpy(t->sched, h.data(), (size_t)need * sizeof(int), cudaMemcpyHostToDevice));
+        b.order = t->sched;
+        b.cta_start = t->sched + T;
+    }
     ACSE_CUDA_TRY(cudaMemcpy(t->dev, t->host, sizeof(TcBatch), cudaMemcpyHostToDevice));
     return ACSE_OK;
 }
