@@ -285,11 +285,42 @@ int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* cons
     return launch_assemble_G(c, sW, scale, mask, out, norm2_dst);
 }
 
+static int ensure_aux(acse_ctx* c) {
+    if (c->ev_fork) return ACSE_OK;
+    ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    for (int b = 0; b < 3; ++b) {
+        ACSE_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking));
+        ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[b], cudaEventDisableTiming));
+    }
+    return ACSE_OK;
+}
+
 // G(W) for the current D: operands, every O(r^6) GEMM of the pass in one grouped launch, assembly.
-// prep_D = 1 recomputes 1D, M and the particle-hole layout of M.
+// prep_D = 1 recomputes 1D, M and the particle-hole layout of M.  On the split path the operands of
+// D (M, [M; D], the particle-hole M) and those of W (the W rows, Z, w) are independent once 1D is
+// known, so the W side runs on an auxiliary stream forked from and joined back into the context's.
 int acse_contract(acse_ctx* c, const double* const D[3], const double* const W[3], int sW, double scale, int mask,
                   double* const out[3], double* norm2_dst, int prep_D) {
-    ACSE_TRY(acse_contract_pre(c, D, W, prep_D));
+    if (prep_D && c->opt.prec != ACSE_FP64 && !c->ny) {
+        for (int s = 0; s < 3; ++s) {
+            c->cur_D[s] = D[s];
+            c->cur_W[s] = W[s];
+        }
+        ACSE_TRY(ensure_aux(c));
+        ACSE_TRY(launch_gamma(c, D));
+        ACSE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
+        ACSE_CUDA_TRY(cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0));
+        cudaStream_t main = c->stream;
+        c->stream = c->aux[0];
+        const int sw = tc_mixed_prep_W(c, W);
+        c->stream = main;
+        ACSE_TRY(sw);
+        ACSE_CUDA_TRY(cudaEventRecord(c->ev_join[0], c->aux[0]));
+        ACSE_TRY(tc_mixed_prep_D(c, D));
+        ACSE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join[0], 0));
+    } else {
+        ACSE_TRY(acse_contract_pre(c, D, W, prep_D));
+    }
     ACSE_TRY(acse_contract_gemm(c));
     return acse_contract_post(c, sW, scale, mask, out, norm2_dst);
 }
@@ -315,13 +346,7 @@ struct Staged {
 // auxiliary streams forked from and joined back into the context's stream, so that the copy engines
 // move the blocks concurrently.
 static int copy_blocks(acse_ctx* c, void* const dst[3], const void* const src[3], cudaMemcpyKind kind) {
-    if (!c->ev_fork) {
-        ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-        for (int b = 0; b < 3; ++b) {
-            ACSE_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking));
-            ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[b], cudaEventDisableTiming));
-        }
-    }
+    ACSE_TRY(ensure_aux(c));
     const size_t n4 = n4_of(c), b4 = n4 * sizeof(double);
     ACSE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
     for (int b = 0; b < 3; ++b) {

@@ -62,6 +62,8 @@ int tc_table_append(TcTable* t, struct acse_ctx* c);
 void tc_table_set_err(TcTable* t, int* err);
 int tc_default_bn(int r);
 int tc_unpack_pairs(struct acse_ctx* c);
+int tc_mixed_prep_D(struct acse_ctx* c, const double* const D[3]);   // split operands of D (needs 1D)
+int tc_mixed_prep_W(struct acse_ctx* c, const double* const W[3]);   // split operands of W, Z and w
 int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t ldb, float* C, int M, int N, int L,
                     int ldc, float alpha);
 int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha);

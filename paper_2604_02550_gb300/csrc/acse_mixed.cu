@@ -15,14 +15,6 @@
 #include "acse_internal.h"
 #include "acse_split.cuh"
 
-#define MX_TPB 256
-
-static inline int mx_grid(size_t n) {
-    size_t g = (n + MX_TPB - 1) / MX_TPB;
-    if (g > 152 * 16) g = 152 * 16;
-    return (int)(g < 1 ? 1 : g);
-}
-
 struct MxPtrs {
     void* pairA[3];
     void* pairB[3];
@@ -207,7 +199,6 @@ __global__ void __launch_bounds__(256) k_mx_pack_Mph(int r, const __grid_constan
 
 int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
     const int r = c->r;
-    const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
     const int R2 = r * r;
     // spin-flip specialisation: M_bb = M_aa (the bb sector of [M; D] is not formed) and Mf2 feeds only
@@ -270,25 +261,40 @@ __global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double*
 }
 
 // [X; Y] of a same-spin sector from the packed GEMM output: X^{ij}_{kp} = s_ij s_kp Xp[pk(ij)][pk(kp)]
-// (s = -1 for a swapped pair, 0 on the diagonal), rows r^2.. for Y likewise.  Blocks over
-// (sector aa/bb, full row); threads over columns.
+// (s = -1 for a swapped pair, 0 on the diagonal), rows r^2.. for Y likewise.  One block per (sector
+// aa/bb, full row): the packed source row is staged in shared memory (coalesced), then the full row is
+// written four columns at a time.
 __global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, const float* __restrict__ Cp0,
                                                          const float* __restrict__ Cp2, float* C0, float* C2) {
+    __shared__ float srow[ACSE_MAX_R * (ACSE_MAX_R - 1) / 2];
     const int R2 = r * r, P = r * (r - 1) / 2;
     const int sec = blockIdx.x / (2 * R2);
     const int row = blockIdx.x - sec * 2 * R2;
     const float* Cp = sec == 0 ? Cp0 : Cp2;
     float* C = (sec == 0 ? C0 : C2) + (size_t)row * R2;
     const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - (ij / r) * r;
-    if (i == j) {
+    if (i == j) {   // block-uniform
         for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = 0.f;
         return;
     }
     const float si = i < j ? 1.f : -1.f;
     const float* src = Cp + (size_t)(part * P + (i < j ? pk_pair(r, i, j) : pk_pair(r, j, i))) * P;
-    for (int c = threadIdx.x; c < R2; c += blockDim.x) {
-        const int k = c / r, q = c - (c / r) * r;
-        C[c] = k == q ? 0.f : (k < q ? si * src[pk_pair(r, k, q)] : -si * src[pk_pair(r, q, k)]);
+    for (int e = threadIdx.x; e < P; e += blockDim.x) srow[e] = si * src[e];
+    __syncthreads();
+    auto val = [&](int k, int q) { return k == q ? 0.f : (k < q ? srow[pk_pair(r, k, q)] : -srow[pk_pair(r, q, k)]); };
+    if ((R2 & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) {
+        for (int g = threadIdx.x; g < R2 / 4; g += blockDim.x) {
+            int k = (4 * g) / r, q = 4 * g - k * r;
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = val(k, q);
+                if (++q == r) { q = 0; ++k; }
+            }
+            reinterpret_cast<float4*>(C)[g] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    } else {
+        for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = val(c / r, c - (c / r) * r);
     }
 }
 
@@ -303,7 +309,6 @@ int tc_unpack_pairs(acse_ctx* c) {
 
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const int r = c->r;
-    const size_t n4 = (size_t)r * r * r * r;
     MxPtrs p = mx_ptrs(c);
     const dim3 grid((r * r / 4 + 128) / 128, (acse_singlet(c) ? 2 : 3) * r * r);   // no bb pair GEMM under the spin flip
     if (c->opt.prec == ACSE_BF16X3)

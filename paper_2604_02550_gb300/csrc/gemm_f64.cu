@@ -81,7 +81,6 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ GemmF6
     for (int i = 0; i < 4; ++i) {
         const int m = m0 + ty + 16 * i;
         if (m >= M) continue;
-        double* Crow = P.C + (size_t)m * P.ldc;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx + 16 * j;
@@ -98,7 +97,6 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ GemmF6
             double v = alpha * acc[i][j];
             if (beta != 0.0) v += beta * P.C[dst];
             P.C[dst] = v;
-            (void)Crow;
         }
     }
 }

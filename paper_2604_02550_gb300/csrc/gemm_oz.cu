@@ -474,23 +474,34 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ b
 // full X and Y rows by antisymmetry.  pk(a, b), a < b, numbers the pairs row by row.
 __host__ __device__ __forceinline__ int oz_pk(int r, int a, int b) { return a * r - a * (a + 1) / 2 + (b - a - 1); }
 
-// X_s, Y_s (s = aa, bb; r^2 x r^2 FP64) from the packed [X; Y] (2P x P): one block per output row.
+// X_s, Y_s (s = aa, bb; r^2 x r^2 FP64) from the packed [X; Y] (2P x P): one block per output row, the
+// packed source row staged in shared memory, the full row written two columns at a time.
 __global__ void __launch_bounds__(256) k_oz_unpack(int r, const double* __restrict__ Cp0, const double* __restrict__ Cp2,
                                                    double* X0, double* Y0, double* X2, double* Y2) {
+    __shared__ double srow[ACSE_MAX_R * (ACSE_MAX_R - 1) / 2];
     const int R2 = r * r, P = r * (r - 1) / 2;
     const int sec = blockIdx.x / (2 * R2);
     const int row = blockIdx.x - sec * 2 * R2;
     const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - i * r;
     double* dst = (sec == 0 ? (part ? Y0 : X0) : (part ? Y2 : X2)) + (size_t)ij * R2;
-    if (i == j) {
+    if (i == j) {   // block-uniform
         for (int c = threadIdx.x; c < R2; c += blockDim.x) dst[c] = 0.0;
         return;
     }
     const double si = i < j ? 1.0 : -1.0;
     const double* src = (sec == 0 ? Cp0 : Cp2) + (size_t)(part * P + (i < j ? oz_pk(r, i, j) : oz_pk(r, j, i))) * P;
-    for (int c = threadIdx.x; c < R2; c += blockDim.x) {
-        const int k = c / r, q = c - (c / r) * r;
-        dst[c] = k == q ? 0.0 : (k < q ? si * src[oz_pk(r, k, q)] : -si * src[oz_pk(r, q, k)]);
+    for (int e = threadIdx.x; e < P; e += blockDim.x) srow[e] = si * src[e];
+    __syncthreads();
+    auto val = [&](int k, int q) { return k == q ? 0.0 : (k < q ? srow[oz_pk(r, k, q)] : -srow[oz_pk(r, q, k)]); };
+    if ((R2 & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        for (int g = threadIdx.x; g < R2 / 2; g += blockDim.x) {
+            int k = (2 * g) / r, q = 2 * g - k * r;
+            const double v0 = val(k, q);
+            if (++q == r) { q = 0; ++k; }
+            reinterpret_cast<double2*>(dst)[g] = make_double2(v0, val(k, q));
+        }
+    } else {
+        for (int c = threadIdx.x; c < R2; c += blockDim.x) dst[c] = val(c / r, c - (c / r) * r);
     }
 }
 

@@ -629,8 +629,6 @@ int tc_default_bn(int r) { return r * r >= 256 ? 256 : 128; }
 
 int tc_mixed_alloc(acse_ctx* c);
 void tc_mixed_free(acse_ctx* c);
-int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]);
-int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]);
 
 int tc_plan_create(acse_ctx* c) {
     TcPlan* pl = (TcPlan*)calloc(1, sizeof(TcPlan));
