@@ -282,15 +282,39 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 :
             for (int v = 0; v < 4; ++v) acc[u][v] = tconv<T>(0.0);
         const T* W = Ws + (size_t)it_me * rp * ldw;
         // with RP the loop runs over the zero-padded rows too (q < RP), at a constant trip count
+        if constexpr (std::is_same<T, float>::value) {
+            // packed FP32x2 FMA, pairs along s (the same FMA sequence per element as scalar code)
+            float2 c2[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c2[u][0] = c2[u][1] = make_float2(0.f, 0.f);
 #pragma unroll 4
-        for (int q = 0; q < (RP ? RP : r); ++q) {
-            T a[4], b[4];
-            ld4(gT + q * ldw + j0, a);
-            ld4(W + q * ldw + s0, b);
+            for (int q = 0; q < (RP ? RP : r); ++q) {
+                float a[4], b[4];
+                ld4(gT + q * ldw + j0, a);
+                ld4(W + q * ldw + s0, b);
+                const float2 b0 = make_float2(b[0], b[1]), b1 = make_float2(b[2], b[3]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 4; ++u) {
+                    const float2 x = make_float2(a[u], a[u]);
+                    c2[u][0] = __ffma2_rn(x, b0, c2[u][0]);
+                    c2[u][1] = __ffma2_rn(x, b1, c2[u][1]);
+                }
+            }
 #pragma unroll
-                for (int v = 0; v < 4; ++v) tmac(acc[u][v], a[u], b[v]);
+            for (int u = 0; u < 4; ++u) {
+                acc[u][0] = c2[u][0].x; acc[u][1] = c2[u][0].y; acc[u][2] = c2[u][1].x; acc[u][3] = c2[u][1].y;
+            }
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < (RP ? RP : r); ++q) {
+                T a[4], b[4];
+                ld4(gT + q * ldw + j0, a);
+                ld4(W + q * ldw + s0, b);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) tmac(acc[u][v], a[u], b[v]);
+            }
         }
         const int col0 = sP * R2 + p * r + s0;
         const bool vec_st = s0 + 3 < r && ((size_t)col0 & 3) == 0 && (ld & 3) == 0;
@@ -521,10 +545,12 @@ template <int KIND, int RP>
 __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, const float* B, int ld_, int r_, int rp_,
                                            int nt_, int kb, int lb) {
     const int rp = RP ? RP : rp_, ld = RP ? RP + 4 : ld_, nt = RP ? RP / 4 : nt_, r = RP ? RP : r_;
+    // paired accumulators for the packed FP32x2 FMA (two independent round-to-nearest FMAs, the same
+    // sequence per element as scalar FMAs): c[a][h] = (acc[a][2h], acc[a][2h+1]) for RR and CR,
+    // c[a][h] = (acc[2h][a], acc[2h+1][a]) for CC
+    float2 c[4][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int a = 0; a < 4; ++a) c[a][0] = c[a][1] = make_float2(0.f, 0.f);
     if (KIND == 0) {   // RR
         for (int q = 0; q < rp; q += 4) {
             float av[4][4], bv[4][4];
@@ -535,9 +561,11 @@ __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, c
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += av[a][u] * bv[u][b];
+                for (int u = 0; u < 4; ++u) {
+                    const float2 x = make_float2(av[a][u], av[a][u]);
+                    c[a][0] = __ffma2_rn(x, make_float2(bv[u][0], bv[u][1]), c[a][0]);
+                    c[a][1] = __ffma2_rn(x, make_float2(bv[u][2], bv[u][3]), c[a][1]);
+                }
         }
     } else if (KIND == 1) {   // CR
 #pragma unroll 4
@@ -545,10 +573,13 @@ __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, c
             float av[4], bv[4];
             ld4(A + q * ld + 4 * kb, av);
             ld4(B + q * ld + 4 * lb, bv);
+            const float2 b0 = make_float2(bv[0], bv[1]), b1 = make_float2(bv[2], bv[3]);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+            for (int a = 0; a < 4; ++a) {
+                const float2 x = make_float2(av[a], av[a]);
+                c[a][0] = __ffma2_rn(x, b0, c[a][0]);
+                c[a][1] = __ffma2_rn(x, b1, c[a][1]);
+            }
         }
     } else {   // CC
         for (int q = 0; q < rp; q += 4) {
@@ -558,11 +589,26 @@ __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, c
 #pragma unroll
             for (int b = 0; b < 4; ++b) ld4(B + (lb + nt * b) * ld + q, bv[b]);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int u = 0; u < 4; ++u) {
+                const float2 a0 = make_float2(av[u][0], av[u][1]), a1 = make_float2(av[u][2], av[u][3]);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int b = 0; b < 4; ++b) {
+                    const float2 y = make_float2(bv[b][u], bv[b][u]);
+                    c[b][0] = __ffma2_rn(a0, y, c[b][0]);
+                    c[b][1] = __ffma2_rn(a1, y, c[b][1]);
+                }
+            }
+        }
+    }
+    if (KIND == 2) {
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += av[u][a] * bv[b][u];
+        for (int b = 0; b < 4; ++b) {
+            acc[0][b] = c[b][0].x; acc[1][b] = c[b][0].y; acc[2][b] = c[b][1].x; acc[3][b] = c[b][1].y;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            acc[a][0] = c[a][0].x; acc[a][1] = c[a][0].y; acc[a][2] = c[a][1].x; acc[a][3] = c[a][1].y;
         }
     }
 }
