@@ -968,9 +968,8 @@ int launch_B_tiled(acse_ctx* c) {
         a.gam = w.gam; a.w = w.w; a.Q = w.Q;
         const bool st = b_smem(r, sizeof(double), true) <= k_smem_cap;
         const size_t sm = b_smem(r, sizeof(double), st);
-        if (c->oz) {   // Ozaki path: double-float products
-            if (st) k_B_tiled<double, true, true><<<R2, TL_TPB, sm, c->stream>>>(a);
-            else k_B_tiled<double, false, true><<<R2, TL_TPB, sm, c->stream>>>(a);
+        if (c->oz) {   // Ozaki path: double-float products; without staging two blocks fit an SM
+            k_B_tiled<double, false, true><<<R2, TL_TPB, b_smem(r, sizeof(double), false), c->stream>>>(a);
         } else {
             if (st) k_B_tiled<double, true><<<R2, TL_TPB, sm, c->stream>>>(a);
             else k_B_tiled<double, false><<<R2, TL_TPB, sm, c->stream>>>(a);
