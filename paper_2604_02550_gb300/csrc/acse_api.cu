@@ -285,13 +285,15 @@ int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* cons
     return launch_assemble_G(c, sW, scale, mask, out, norm2_dst);
 }
 
+// The auxiliary streams and their events, created on first use; ev_fork is created last, so a
+// non-null ev_fork means that every stream and event exists.
 static int ensure_aux(acse_ctx* c) {
     if (c->ev_fork) return ACSE_OK;
-    ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     for (int b = 0; b < 3; ++b) {
-        ACSE_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking));
-        ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[b], cudaEventDisableTiming));
+        if (!c->aux[b]) ACSE_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking));
+        if (!c->ev_join[b]) ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[b], cudaEventDisableTiming));
     }
+    ACSE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     return ACSE_OK;
 }
 
