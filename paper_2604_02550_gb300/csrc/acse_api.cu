@@ -190,6 +190,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         cudaMemcpyAsync(c->w.V, V, R2 * R2 * sizeof(double), kv, c->stream) != cudaSuccess)
         s = ACSE_ERR_CUDA;
     if (s == ACSE_OK) s = launch_build_K(c);
+    if (s == ACSE_OK && c->opt.prec != ACSE_FP64) s = tc_make_Kh32(c);   // the FP32 K/2 of the split path
     if (s == ACSE_OK) {
         k_set1<<<1, 1, 0, c->stream>>>(c->w.scal + 2, o->eps0 > 0.0 ? o->eps0 : 1e-3);
         if (cudaGetLastError() != cudaSuccess) s = ACSE_ERR_CUDA;

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_Q_from_X(int r, const T* __restrict__ X
     if (lane == 0) Qv[t] = acc;
 }
 
-int launch_W_intermediates(acse_ctx* c, const double* const W[3]) { return launch_Z_tiled(c, W); }
+int launch_W_intermediates(acse_ctx* c, const double* const W[3]) { return launch_Z_tiled(c, W, nullptr); }
 
 int launch_Q(acse_ctx* c) {
     const int r = c->r;
@@ -246,6 +246,7 @@ struct GArgs {
     T s, scale;
     int mask, lo, hi;
     int flip;   // spin-flip specialisation: H[2] is not formed; G_bb = G_aa (written from blk 0)
+    float* out32[3];   // split path, output into the context's A: the same (FP32-valued) result in FP32
     double* partial;
 };
 
@@ -288,6 +289,10 @@ __device__ __forceinline__ void g_put(const GArgs<T>& a, int blk, int r, int R2,
     }
     a.out[blk][(size_t)ij * R2 + kl] = o;
     if (a.flip && blk == 0) a.out[2][(size_t)ij * R2 + kl] = o;
+    if (a.out32[0]) {
+        a.out32[blk][(size_t)ij * R2 + kl] = (float)o;   // exact: o is an FP32 value (or 0)
+        if (a.flip && blk == 0) a.out32[2][(size_t)ij * R2 + kl] = (float)o;
+    }
 }
 
 // G_b = scale (H_b - s H_b^T) (pair transpose), the masked result in FP64 and the unmasked norm
@@ -350,6 +355,7 @@ static void fill_G(acse_ctx* c, GArgs<T>& a, int sW, double scale, int apply_mas
     a.hi = c->opt.act_hi;
     a.partial = c->w.partial;
     a.flip = acse_singlet(c) ? 1 : 0;
+    for (int s = 0; s < 3; ++s) a.out32[s] = nullptr;
 }
 
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3], double* norm2_dst) {
@@ -362,6 +368,11 @@ int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double*
         GArgs<float> a;
         fill_G(c, a, sW, scale, apply_mask, out);
         for (int s = 0; s < 3; ++s) a.H[s] = c->w.H32[s];
+        // into the context's A: also its FP32 copy, the W of the update pass that follows
+        const bool intoA = out[0] == c->w.A[0] && out[1] == c->w.A[1] && out[2] == c->w.A[2];
+        if (intoA)
+            for (int s = 0; s < 3; ++s) a.out32[s] = c->w.A32[s];
+        c->a32_valid = intoA ? 1 : c->a32_valid;
         k_assemble_G<float><<<G_GRID, 256, 0, c->stream>>>(a);
     }
     ACSE_LAUNCHED(c);

@@ -64,6 +64,7 @@ int tc_default_bn(int r);
 int tc_unpack_pairs(struct acse_ctx* c);
 int tc_mixed_prep_D(struct acse_ctx* c, const double* const D[3]);   // split operands of D (needs 1D)
 int tc_mixed_prep_W(struct acse_ctx* c, const double* const W[3]);   // split operands of W, Z and w
+int tc_make_Kh32(struct acse_ctx* c);                                  // FP32 copy of K/2 (once)
 int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t ldb, float* C, int M, int N, int L,
                     int ldc, float alpha);
 int tc_table_add(TcTable* t, const void* A, const void* B, float* C, int M, int N, int L, int ldc, float alpha);
@@ -129,6 +130,11 @@ struct Work {
     float* H32[3];
     float* zdiag32;
     int* tc_err;          // device flag: a bounded wait inside the tensor-core GEMM ran out
+    // FP32 copies of the W operand of a pass (split path; Z and the W packs read these): K/2 (made
+    // once), the residual A (written by the G assembly beside w.A) and a scratch copy for any other W
+    float* Kh32[3];
+    float* A32[3];
+    float* W32s[3];
 };
 
 struct acse_ctx {
@@ -145,6 +151,7 @@ struct acse_ctx {
     void* ny;             // NY reconstruction workspace (acse_ny.cu), or null for V
     cudaStream_t aux[3];  // host <-> device copies of the three blocks run concurrently on these
     cudaEvent_t ev_fork, ev_join[3];
+    int a32_valid;        // split path: w.A32 holds the FP32 values of the last A written to w.A
     int oz;               // ACSE_OZAKI: an FP64 context (opt.prec = ACSE_FP64) whose pass GEMMs run by
                           // the Ozaki scheme on the BF16 tensor cores (gemm_oz.cu)
     void* oz_plan;
@@ -201,7 +208,7 @@ int launch_gamma_M(acse_ctx* c, const double* const D[3]);
 int launch_pack_Mph(acse_ctx* c);
 int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
 int launch_build_B(acse_ctx* c);
-int launch_Z_tiled(acse_ctx* c, const double* const W[3]);
+int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32[3]);
 int launch_B_tiled(acse_ctx* c);
 int tiled_set_attrs();
 int launch_Q(acse_ctx* c);

@@ -227,8 +227,8 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
 // --------------------------------------------------------------------------- per W
 // Pair operand B: W blocks as (kp) x (rs) rows.
 template <int PREC>
-__global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double* __restrict__ Wab,
-                            const double* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
+__global__ void k_mx_pack_W(int r, const float* __restrict__ Waa, const float* __restrict__ Wab,
+                            const float* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
     // grid: x over groups of four columns, y over (sector, row)
     const int R2 = r * r;
     const int c4 = (R2 + 3) >> 2;
@@ -237,11 +237,11 @@ __global__ void k_mx_pack_W(int r, const double* __restrict__ Waa, const double*
     const int s = blockIdx.y / R2;
     const int row = blockIdx.y - s * R2;
     const size_t ld = (size_t)p.ns * p.Kp1;
-    const double* W = (s == 0 ? Waa : (s == 1 ? Wab : Wbb)) + (size_t)row * R2;
+    const float* W = (s == 0 ? Waa : (s == 1 ? Wab : Wbb)) + (size_t)row * R2;   // FP32 copy of W
     const int k0 = q4 * 4;
     const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
     float x[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int u = 0; u < nk; ++u) x[u] = (float)W[k0 + u];
+    for (int u = 0; u < nk; ++u) x[u] = W[k0 + u];
     if (s == 1) {
         if ((r & 1) == 0 && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
         else
@@ -307,18 +307,59 @@ int tc_unpack_pairs(acse_ctx* c) {
     return ACSE_OK;
 }
 
+// FP32 copy of n doubles (the W operands: their FP32 values are all the split path reads).
+__global__ void __launch_bounds__(256) k_mx_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+        for (size_t i = t0; i < n / 2; i += stride) {
+            const double2 v = reinterpret_cast<const double2*>(src)[i];
+            reinterpret_cast<float2*>(dst)[i] = make_float2((float)v.x, (float)v.y);
+        }
+        if ((n & 1) && t0 == 0) dst[n - 1] = (float)src[n - 1];
+    } else {
+        for (size_t i = t0; i < n; i += stride) dst[i] = (float)src[i];
+    }
+}
+
+static int to_f32(acse_ctx* c, const double* const W[3], float* const out[3]) {
+    const size_t r = c->r, n4 = r * r * r * r;
+    for (int s = 0; s < 3; ++s) {
+        k_mx_to_f32<<<152 * 8, 256, 0, c->stream>>>(W[s], out[s], n4);
+        ACSE_LAUNCHED(c);
+    }
+    return ACSE_OK;
+}
+
+int tc_make_Kh32(acse_ctx* c) {
+    const double* W[3] = {c->w.Kh[0], c->w.Kh[1], c->w.Kh[2]};
+    return to_f32(c, W, c->w.Kh32);
+}
+
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const int r = c->r;
+    Work& w = c->w;
     MxPtrs p = mx_ptrs(c);
+    // the FP32 copy of W: K/2 (made at creation), the residual just assembled into w.A (its FP32 values
+    // written beside it), else converted here
+    const float* W32[3];
+    if (W[0] == w.Kh[0] && W[1] == w.Kh[1] && W[2] == w.Kh[2]) {
+        for (int s = 0; s < 3; ++s) W32[s] = w.Kh32[s];
+    } else if (c->a32_valid && W[0] == w.A[0] && W[1] == w.A[1] && W[2] == w.A[2]) {
+        for (int s = 0; s < 3; ++s) W32[s] = w.A32[s];
+    } else {
+        ACSE_TRY(to_f32(c, W, w.W32s));
+        for (int s = 0; s < 3; ++s) W32[s] = w.W32s[s];
+    }
     const dim3 grid((r * r / 4 + 128) / 128, (acse_singlet(c) ? 2 : 3) * r * r);   // no bb pair GEMM under the spin flip
     if (c->opt.prec == ACSE_BF16X3)
-        k_mx_pack_W<ACSE_BF16X3><<<grid, 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_BF16X3><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p);
     else if (c->opt.prec == ACSE_TF32X3)
-        k_mx_pack_W<ACSE_TF32X3><<<grid, 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_TF32X3><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p);
     else
-        k_mx_pack_W<ACSE_TF32><<<grid, 128, 0, c->stream>>>(r, W[0], W[1], W[2], p);
+        k_mx_pack_W<ACSE_TF32><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p);
     ACSE_LAUNCHED(c);
-    return launch_Z_tiled(c, W);   // Z packs and w (the diagonal of Z)
+    return launch_Z_tiled(c, W, W32);   // Z packs and w (the diagonal of Z)
 }
 
 // ------------------------------------------------------------------------ workspace
@@ -356,6 +397,9 @@ int tc_mixed_alloc(acse_ctx* c) {
         }
         ACSE_TRY(mx_alloc((void**)&w.tc_pairC[s], 2 * R2 * R2 * sizeof(float), false));
         ACSE_TRY(mx_alloc((void**)&w.M32[s], n4 * sizeof(float), false));
+        ACSE_TRY(mx_alloc((void**)&w.Kh32[s], n4 * sizeof(float), false));
+        ACSE_TRY(mx_alloc((void**)&w.A32[s], n4 * sizeof(float), false));
+        ACSE_TRY(mx_alloc((void**)&w.W32s[s], n4 * sizeof(float), false));
     }
     ACSE_TRY(mx_alloc(&w.tc_Md, 2 * R2 * L2, true));
     ACSE_TRY(mx_alloc(&w.tc_Zd, 2 * R2 * L2, true));
@@ -379,7 +423,8 @@ void tc_mixed_free(acse_ctx* c) {
     void* ptrs[] = {w.tc_pairCp[0], w.tc_pairCp[2], w.tc_pairA[0], w.tc_pairA[1], w.tc_pairA[2], w.tc_pairB[0], w.tc_pairB[1], w.tc_pairB[2],
                     w.tc_pairC[0], w.tc_pairC[1], w.tc_pairC[2], w.M32[0], w.M32[1], w.M32[2], w.tc_Md, w.tc_Zd,
                     w.tc_Mf[0], w.tc_Mf[1], w.tc_Zf[0], w.tc_Zf[1], w.tc_X5f[0], w.tc_X5f[1], w.tc_X5d,
-                    w.H32[0], w.H32[1], w.H32[2], w.zdiag32, w.gam32, w.w32, w.Q32, w.tc_err};
+                    w.H32[0], w.H32[1], w.H32[2], w.zdiag32, w.gam32, w.w32, w.Q32, w.tc_err,
+                    w.Kh32[0], w.Kh32[1], w.Kh32[2], w.A32[0], w.A32[1], w.A32[2], w.W32s[0], w.W32s[1], w.W32s[2]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }

@@ -174,6 +174,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
@@ -182,8 +186,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // The r x r slice W_kp[q][s] of spin type t (t = 0..5, see k_Z_pipe) and whether it is stored [s][q].
-__device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, const double* Waa, const double* Wab,
-                                                 const double* Wbb, bool& transposed) {
+template <typename WT>
+__device__ __forceinline__ const WT* z_slice(int t, int k, int p, int r, const WT* Waa, const WT* Wab, const WT* Wbb,
+                                             bool& transposed) {
     const size_t r3 = (size_t)r * r * r, R2 = (size_t)r * r;
     switch (t) {
         case 0: transposed = false; return Waa + k * r3 + p * R2;
@@ -199,21 +204,27 @@ __device__ __forceinline__ const double* z_slice(int t, int k, int p, int r, con
 //   t=0 Zd(a,a): W_kp[q][s] = Waa[k][p][q][s], ga      t=1 Zd(a,b): Wab[k][p][q][s], ga
 //   t=2 Zd(b,a): W_kp[q][s] = Wab[p][k][s][q], gb      t=3 Zd(b,b): Wbb[k][p][q][s], gb
 //   t=4 Zf1:     W_kp[q][s] = Wab[k][p][s][q], gb      t=5 Zf2:     Wab[p][k][q][s], ga
-// (the spin-flip sectors drop a sign -1 that their M operand drops too).  The FP64 slices of the
-// next ipb values of p are copied into shared memory (cp.async) while the current ipb slices are
-// multiplied; each thread owns one 4 x 4 output tile of one slice (ipb * (rp/4)^2 threads).
-// MODE 4 (the Ozaki path): FP64 output as MODE 0, products in double-float.
+// (the spin-flip sectors drop a sign -1 that their M operand drops too).  The W slices of the next ipb
+// values of p are copied into shared memory (cp.async) while the current ipb slices are multiplied;
+// each thread owns one 4 x 4 output tile of one slice (ipb * (rp/4)^2 threads).  W is FP64 on the FP64
+// paths (MODE 0, and MODE 4, the Ozaki path: FP64 output as MODE 0, products in double-float) and the
+// FP32 copy of W on the split path (MODE 1-3), so that no FP64 conversion runs here.
+template <int MODE>
+using ZWT = typename std::conditional<MODE == 0 || MODE == 4, double, float>::type;
+
 template <int MODE, int RP = 0>   // RP > 0: compile-time padded size (product loop fully unrolled)
-__global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 : 3) k_Z_pipe(int r, int ipb, int pchunk, const double* __restrict__ Waa,
-                                                         const double* __restrict__ Wab,
-                                                         const double* __restrict__ Wbb,
+__global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 : 3) k_Z_pipe(int r, int ipb, int pchunk, const ZWT<MODE>* __restrict__ Waa,
+                                                         const ZWT<MODE>* __restrict__ Wab,
+                                                         const ZWT<MODE>* __restrict__ Wbb,
                                                          const double* __restrict__ gam, const __grid_constant__ ZOut o) {
     using T = typename std::conditional<MODE == 0, double,
                                         typename std::conditional<MODE == 4, dfl, float>::type>::type;
+    using WT = ZWT<MODE>;
+    constexpr int WV = 16 / sizeof(WT);                  // elements of a 16-byte copy
     extern __shared__ __align__(16) unsigned char tl_smem[];
-    const int rp = RP ? RP : pad4(r), ldw = rp + 4, R2 = r * r, R2e = (R2 + 1) & ~1;
+    const int rp = RP ? RP : pad4(r), ldw = rp + 4, R2 = r * r, R2e = (R2 + WV - 1) / WV * WV;
     const int nt = rp / 4, nt2 = nt * nt;
-    double* stage = (double*)tl_smem;                    // [ipb][R2e] raw FP64 slices
+    WT* stage = (WT*)tl_smem;                            // [ipb][R2e] raw W slices
     T* gT = (T*)(stage + (size_t)ipb * R2e);             // [q][j] = 1D[j][q], row pitch ldw
     T* Ws = gT + (size_t)rp * ldw;                       // [ipb][q][s], row pitch ldw
     const int nchunk = (r + pchunk - 1) / pchunk;
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 :
     const double* g = gam + ((t == 2 || t == 3 || t == 4) ? R2 : 0);
     // (int)((e + 1/2) / r) = e / r for e < r^2: the fraction stays at least 1/(2r) from an integer
     const float invr = 1.f / (float)r;
-    const bool vec_ld = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(Waa) | reinterpret_cast<uintptr_t>(Wab) |
+    const bool vec_ld = R2 % WV == 0 && ((reinterpret_cast<uintptr_t>(Waa) | reinterpret_cast<uintptr_t>(Wab) |
                                           reinterpret_cast<uintptr_t>(Wbb)) & 15) == 0;
     for (int e = threadIdx.x; e < (1 + ipb) * rp * ldw; e += blockDim.x) gT[e] = tconv<T>(0.0);
     __syncthreads();
@@ -238,12 +249,14 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 :
         const int n = min(ipb, pe - p0);
         for (int it = 0; it < n; ++it) {
             bool tr;
-            const double* src = z_slice(t, k, p0 + it, r, Waa, Wab, Wbb, tr);
-            double* dst = stage + (size_t)it * R2e;
+            const WT* src = z_slice<WT>(t, k, p0 + it, r, Waa, Wab, Wbb, tr);
+            WT* dst = stage + (size_t)it * R2e;
             if (vec_ld)
-                for (int e = threadIdx.x; e < R2 / 2; e += blockDim.x) cp_async16(dst + 2 * e, src + 2 * e);
-            else
+                for (int e = threadIdx.x; e < R2 / WV; e += blockDim.x) cp_async16(dst + WV * e, src + WV * e);
+            else if (sizeof(WT) == 8)
                 for (int e = threadIdx.x; e < R2; e += blockDim.x) cp_async8(dst + e, src + e);
+            else
+                for (int e = threadIdx.x; e < R2; e += blockDim.x) cp_async4(dst + e, src + e);
         }
         cp_async_commit();
     };
@@ -261,12 +274,14 @@ __global__ void __launch_bounds__(ZP_MAX_THREADS, (MODE == 0 || MODE == 4) ? 2 :
         __syncthreads();                                 // slices landed; previous products done with Ws
         for (int it = 0; it < n; ++it) {
             bool tr;
-            z_slice(t, k, p0 + it, r, Waa, Wab, Wbb, tr);
-            const double* st = stage + (size_t)it * R2e;
+            z_slice<WT>(t, k, p0 + it, r, Waa, Wab, Wbb, tr);
+            const WT* st = stage + (size_t)it * R2e;
             T* W = Ws + (size_t)it * rp * ldw;
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
                 const int u = (int)(((float)e + 0.5f) * invr), v = e - u * r;   // e / r, see invr
-                const T x = tconv<T>(st[e]);
+                T x;
+                if constexpr (std::is_same<T, WT>::value) x = st[e];   // FP32 W on the split path
+                else x = tconv<T>((double)st[e]);
                 if (tr) W[v * ldw + u] = x;                // src[s][q] -> W[q][s]
                 else W[u * ldw + v] = x;
             }
@@ -864,15 +879,16 @@ struct ZPlan {
     int ipb, threads, pchunk, blocks;
     size_t smem;
 };
-static ZPlan z_plan_compute(int r, size_t es, const void* kern) {
+static ZPlan z_plan_compute(int r, size_t es, size_t ws, const void* kern) {   // es: tile, ws: W element bytes
     ZPlan z;
     const int rp = pad4(r), nt = rp / 4, nt2 = nt * nt;
     z.ipb = ZP_MAX_THREADS / nt2;
     if (z.ipb > 4) z.ipb = 4;
     if (z.ipb < 1) z.ipb = 1;
     z.threads = (z.ipb * nt2 + 31) / 32 * 32;
-    const int R2e = (r * r + 1) & ~1;
-    z.smem = (size_t)z.ipb * R2e * sizeof(double) + (size_t)(1 + z.ipb) * rp * (rp + 4) * es;
+    const int wv = (int)(16 / ws);
+    const int R2e = (r * r + wv - 1) / wv * wv;
+    z.smem = (size_t)z.ipb * R2e * ws + (size_t)(1 + z.ipb) * rp * (rp + 4) * es;
     int per_sm = 1, nsm = 152, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, z.threads, z.smem) != cudaSuccess || per_sm < 1) {
@@ -896,13 +912,14 @@ static ZPlan z_plan(int r, int mode, size_t es, const void* kern) {
     static thread_local int cached_r[5] = {-1, -1, -1, -1, -1};
     static thread_local ZPlan cached[5];
     if (cached_r[mode] != r) {
-        cached[mode] = z_plan_compute(r, es, kern);
+        cached[mode] = z_plan_compute(r, es, (mode == 0 || mode == 4) ? sizeof(double) : sizeof(float), kern);
         cached_r[mode] = r;
     }
     return cached[mode];
 }
 
-int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
+// W: the FP64 operand (FP64 and Ozaki paths); W32: its FP32 copy (split path).
+int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32[3]) {
     const int r = c->r;
     ZOut o;
     Work& w = c->w;
@@ -935,13 +952,13 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3]) {
                                                                                       : (const void*)k_Z_pipe<2>;
         const ZPlan zp = z_plan(r, o.mode, sizeof(float), kern);
         if (r48)
-            k_Z_pipe<1, 48><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<1, 48><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W32[0], W32[1], W32[2], w.gam, o);
         else if (o.mode == 1)
-            k_Z_pipe<1><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<1><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W32[0], W32[1], W32[2], w.gam, o);
         else if (o.mode == 3)
-            k_Z_pipe<3><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<3><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W32[0], W32[1], W32[2], w.gam, o);
         else
-            k_Z_pipe<2><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
+            k_Z_pipe<2><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W32[0], W32[1], W32[2], w.gam, o);
         ACSE_LAUNCHED(c);
         k_w_from_diag<float><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag32, w.w32, sf ? 1 : 0);
     }

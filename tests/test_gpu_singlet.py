@@ -138,3 +138,24 @@ def test_singlet_ignored_in_fp64(acse):
         assert np.array_equal(x, y)
     c1.close()
     c0.close()
+
+
+def test_singlet_with_ny_reconstruction(acse):
+    """The spin-flip specialisation with the NY 3-cumulant added (its sigma is flip-symmetric for
+    n_alpha = n_beta): against the oracle's NY residual."""
+    from oracle import acse_oracle as O
+    p = _problem(6, 3, 41, "state")
+    Db = (p.Daa, p.Dab, p.Dbb)
+    ctx = acse.ACSE(6, 3, 3, p.h, p.V, "bf16x3", recon="NY", singlet=True)
+    A, n2 = ctx.residual(ctx.to_blocks(Db))
+    K = O.reduced_hamiltonian(p.h, p.V, p.N)
+    sig = O.sigma_hf(p.r, 3, 3)
+    Aw = O.residual(K, O.so_from_blocks(*Db), p.N, sigma=sig)
+    want = O.blocks_from_so(Aw)
+    got = to_np(A)
+    err = maxrel(got, want)
+    print(f"singlet NY bf16x3: max rel err {err:.3e}")
+    assert err < TOL["bf16x3"]
+    assert float(n2) == pytest.approx(O.norm2(Aw), rel=4 * TOL["bf16x3"])
+    assert np.array_equal(got[0], got[2])
+    ctx.close()
