@@ -744,30 +744,30 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             const int t = round < 2 ? round : 2 + tt;
             float* Bt = Bs + (size_t)tt * r * bpitch;
             float x1[4][4];
+            // the particle-hole sources: x5 at row (k, j), column (i, l); x8 at row (k, i), column (j, l)
+            const float* X5b;
+            const float* X8b;
+            size_t ld5, ld8;
+            if (t == 0) { X5b = X8b = a.X5d; ld5 = ld8 = R22; }
+            else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
+            else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
+            else if (!a.flip) { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
+            else { X5b = a.X5d + R2; ld5 = R22; X8b = a.X5f1; ld8 = R2; }   // flips of X5d(b,a), X5f2
+            float part1[4][4];   // x1 group: (s1 x1 + x7 - x4 - 2 x8) / 9, added after the barrier
             if (grp == 1) {
-                // x2 = sum_p w[k][p] M(l, p) (types 0, 1, 3: M row holds M[l][p]; type 2: M[p][l]),
-                // plus the gathered terms of B
+                // x2 = sum_p w[k][p] M(l, p) (types 0, 1, 3: M row holds M[l][p]; type 2: M[p][l]) and the
+                // gathered x5 (loaded before the product)
                 const int kind = t == 2 ? 1 : 2;
-                const float* X5b;
-                const float* X8b;
-                size_t ld5, ld8;
-                if (t == 0) { X5b = X8b = a.X5d; ld5 = ld8 = R22; }
-                else if (t == 1) { X5b = X8b = a.X5d + R2 * R22 + R2; ld5 = ld8 = R22; }
-                else if (t == 2) { X5b = a.X5f1; ld5 = R2; X8b = a.X5d + R2; ld8 = R22; }
-                else if (!a.flip) { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
-                else { X5b = a.X5d + R2; ld5 = R22; X8b = a.X5f1; ld8 = R2; }   // flips of X5d(b,a), X5f2
-                float rest[4][4];
+                float g5[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = bp_k(kind, kb, nt, u);
                     const int kc = k < r ? k : r - 1;
                     const float* x5r = X5b + ((size_t)kc * r + j) * ld5 + (size_t)i * r;
-                    const float* x8r = X8b + ((size_t)kc * r + i) * ld8 + (size_t)j * r;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int l = bp_l(kind, lb, nt, v);
-                        const int lc = l < r ? l : r - 1;
-                        rest[u][v] = 2.f * (x5r[lc] - x8r[lc]);
+                        g5[u][v] = x5r[l < r ? l : r - 1];
                     }
                 }
                 float acc[4][4];
@@ -782,20 +782,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                     for (int v = 0; v < 4; ++v) {
                         const int l = bp_l(kind, lb, nt, v);
                         if (k < r && l < r)
-                            Bt[k * bpitch + l] = (c2 * acc[u][v] + rest[u][v]) * (1.f / 9.f) +
+                            Bt[k * bpitch + l] = (c2 * acc[u][v] + 2.f * g5[u][v]) * (1.f / 9.f) +
                                                  (a.ny[t] ? a.ny[t][(size_t)ij * R2 + (size_t)k * r + l] : 0.f);
                     }
                 }
             } else if (grp == 0 && active) {
-                const float* g1 = (t == 0 || t == 3) ? gA : gB;
-                if (t == 3) bp_product<1, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
-                else bp_product<0, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
-            }
-            __syncthreads();                                // x2 and gathered parts in Bt
-            if (grp == 0 && active) {
                 const int kind1 = t == 3 ? 1 : 0;
-                const float s1 = t == 3 ? -1.f : 1.f;
-                // x7 - x4 = Q7[k][j] g7[i][l] - Q4[k][i] g4[j][l] (zero where a type has no such term)
+                // x7 - x4 - 2 x8, x7 - x4 = Q7[k][j] g7[i][l] - Q4[k][i] g4[j][l] (zero where a type has no
+                // such term), loaded before the product
                 const float* ga = a.gam;
                 const float* gb = a.gam + R2;
                 const float* Q4 = t == 0 ? a.Q : t == 1 ? a.Q + R2 : t == 2 ? a.Q : nullptr;
@@ -805,16 +799,38 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = bp_k(kind1, kb, nt, u);
-                    if (k >= r) continue;
-                    const float q4 = Q4 ? Q4[k * r + i] : 0.f;
-                    const float q7 = Q7 ? Q7[k * r + j] : 0.f;
+                    const int kc = k < r ? k : r - 1;
+                    const float q4 = Q4 ? Q4[kc * r + i] : 0.f;
+                    const float q7 = Q7 ? Q7[kc * r + j] : 0.f;
+                    const float* x8r = X8b + ((size_t)kc * r + i) * ld8 + (size_t)j * r;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int l = 4 * lb + v;
-                        if (l < r) {
-                            const float x47 = (Q7 ? q7 * g7[i * r + l] : 0.f) - (Q4 ? q4 * g4[j * r + l] : 0.f);
-                            Bt[k * bpitch + l] += (s1 * x1[u][v] + x47) * (1.f / 9.f);
-                        }
+                        const int lc = l < r ? l : r - 1;
+                        const float x47 = (Q7 ? q7 * g7[i * r + lc] : 0.f) - (Q4 ? q4 * g4[j * r + lc] : 0.f);
+                        part1[u][v] = x47 - 2.f * x8r[lc];
+                    }
+                }
+                const float* g1 = (t == 0 || t == 3) ? gA : gB;
+                if (t == 3) bp_product<1, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                else bp_product<0, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                const float s1 = t == 3 ? -1.f : 1.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) part1[u][v] = (s1 * x1[u][v] + part1[u][v]) * (1.f / 9.f);
+            }
+            __syncthreads();                                // x2, x5 and ny in Bt
+            if (grp == 0 && active) {
+                const int kind1 = t == 3 ? 1 : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = bp_k(kind1, kb, nt, u);
+                    if (k >= r) continue;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int l = 4 * lb + v;
+                        if (l < r) Bt[k * bpitch + l] += part1[u][v];
                     }
                 }
             }
