@@ -261,48 +261,56 @@ __global__ void k_mx_pack_W(int r, const float* __restrict__ Waa, const float* _
 }
 
 // [X; Y] of a same-spin sector from the packed GEMM output: X^{ij}_{kp} = s_ij s_kp Xp[pk(ij)][pk(kp)]
-// (s = -1 for a swapped pair, 0 on the diagonal), rows r^2.. for Y likewise.  One block per (sector
-// aa/bb, full row): the packed source row is staged in shared memory (coalesced), then the full row is
-// written four columns at a time.
+// (s = -1 for a swapped pair, 0 on the diagonal), rows r^2.. for Y likewise.  Each block writes
+// UP_ROWS consecutive full rows of one sector: a column map (packed index and sign of every column) is
+// built once in shared memory, then per row the packed source row is staged (coalesced) and the full
+// row written four columns at a time.
+#define UP_ROWS 8
 __global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, const float* __restrict__ Cp0,
                                                          const float* __restrict__ Cp2, float* C0, float* C2) {
     __shared__ float srow[ACSE_MAX_R * (ACSE_MAX_R - 1) / 2];
+    __shared__ __align__(16) int cmap[ACSE_MAX_R * ACSE_MAX_R];   // -1: diagonal; bit 30: negated
     const int R2 = r * r, P = r * (r - 1) / 2;
-    const int sec = blockIdx.x / (2 * R2);
-    const int row = blockIdx.x - sec * 2 * R2;
+    const int nblk_sec = (2 * R2 + UP_ROWS - 1) / UP_ROWS;
+    const int sec = blockIdx.x / nblk_sec;
+    const int row0 = (blockIdx.x - sec * nblk_sec) * UP_ROWS;
     const float* Cp = sec == 0 ? Cp0 : Cp2;
-    float* C = (sec == 0 ? C0 : C2) + (size_t)row * R2;
-    const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - (ij / r) * r;
-    if (i == j) {   // block-uniform
-        for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = 0.f;
-        return;
+    float* Cs = sec == 0 ? C0 : C2;
+    for (int c = threadIdx.x; c < R2; c += blockDim.x) {
+        const int k = c / r, q = c - (c / r) * r;
+        cmap[c] = k == q ? -1 : (k < q ? pk_pair(r, k, q) : (pk_pair(r, q, k) | 0x40000000));
     }
-    const float si = i < j ? 1.f : -1.f;
-    const float* src = Cp + (size_t)(part * P + (i < j ? pk_pair(r, i, j) : pk_pair(r, j, i))) * P;
-    for (int e = threadIdx.x; e < P; e += blockDim.x) srow[e] = si * src[e];
-    __syncthreads();
-    auto val = [&](int k, int q) { return k == q ? 0.f : (k < q ? srow[pk_pair(r, k, q)] : -srow[pk_pair(r, q, k)]); };
-    if ((R2 & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) {
-        for (int g = threadIdx.x; g < R2 / 4; g += blockDim.x) {
-            int k = (4 * g) / r, q = 4 * g - k * r;
-            float v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                v[u] = val(k, q);
-                if (++q == r) { q = 0; ++k; }
-            }
-            reinterpret_cast<float4*>(C)[g] = make_float4(v[0], v[1], v[2], v[3]);
+    const bool vec = (R2 & 3) == 0 && (reinterpret_cast<uintptr_t>(Cs) & 15) == 0;
+    for (int row = row0; row < row0 + UP_ROWS && row < 2 * R2; ++row) {
+        float* C = Cs + (size_t)row * R2;
+        const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - (ij / r) * r;
+        __syncthreads();   // the previous row's reads of srow are done (and cmap is built)
+        if (i == j) {      // block-uniform
+            for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = 0.f;
+            continue;
         }
-    } else {
-        for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = val(c / r, c - (c / r) * r);
+        const float si = i < j ? 1.f : -1.f;
+        const float* src = Cp + (size_t)(part * P + (i < j ? pk_pair(r, i, j) : pk_pair(r, j, i))) * P;
+        for (int e = threadIdx.x; e < P; e += blockDim.x) srow[e] = si * src[e];
+        __syncthreads();
+        auto val = [&](int m) { return m < 0 ? 0.f : ((m & 0x40000000) ? -srow[m & 0x3FFFFFFF] : srow[m]); };
+        if (vec) {
+            for (int g = threadIdx.x; g < R2 / 4; g += blockDim.x) {
+                const int4 m = reinterpret_cast<const int4*>(cmap)[g];
+                reinterpret_cast<float4*>(C)[g] = make_float4(val(m.x), val(m.y), val(m.z), val(m.w));
+            }
+        } else {
+            for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = val(cmap[c]);
+        }
     }
 }
 
 int tc_unpack_pairs(acse_ctx* c) {
     const int r = c->r;
     const int nsec = acse_singlet(c) ? 1 : 2;   // the bb sector is not formed under the spin flip
-    k_mx_unpack_pairs<<<nsec * 2 * r * r, 256, 0, c->stream>>>(r, c->w.tc_pairCp[0], c->w.tc_pairCp[2], c->w.tc_pairC[0],
-                                                         c->w.tc_pairC[2]);
+    const int nblk_sec = (2 * r * r + UP_ROWS - 1) / UP_ROWS;
+    k_mx_unpack_pairs<<<nsec * nblk_sec, 256, 0, c->stream>>>(r, c->w.tc_pairCp[0], c->w.tc_pairCp[2], c->w.tc_pairC[0],
+                                                              c->w.tc_pairC[2]);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
