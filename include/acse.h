@@ -97,7 +97,9 @@ typedef struct {
                         * symmetry); the split precisions then compute only the alpha-led half of
                         * the spin sectors and copy the beta-beta block of A, U from alpha-alpha
                         * (Theory: for a singlet the aa and bb residual blocks coincide).  Ignored
-                        * in FP64; rejected (ACSE_ERR_ARG) when n_alpha != n_beta.            */
+                        * by ACSE_FP64 and ACSE_OZAKI; rejected (ACSE_ERR_ARG) when n_alpha !=
+                        * n_beta.  The library does not symmetrise D: on an asymmetric D the
+                        * beta-beta results are those of the alpha-alpha block.             */
     int oz_slices;     /* ACSE_OZAKI: 6-bit slices per operand row, 4..10; 0 -> 8            */
 } acse_opts;
 
