@@ -1055,8 +1055,6 @@ int tiled_set_attrs() {
                                        (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
-    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));

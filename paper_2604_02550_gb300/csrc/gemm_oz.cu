@@ -32,7 +32,6 @@
 #include "tc_ptx.cuh"
 
 #define OZ_BETA 6            // bits per digit (base 2^6, |digit| <= 32)
-#define OZ_MAXS 10
 #define OZ_MAXP 12           // GEMMs of one launch
 #define OZ_MAXJ 16           // operands of one slicing launch
 #define OZ_THREADS 192
