@@ -177,6 +177,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     if (s == ACSE_OK && c->oz) s = oz_plan_create(c);
     if (s == ACSE_OK && o->recon == ACSE_RECON_NY) s = ny_alloc(c);
     if (s != ACSE_OK) {
+        ny_free(c);
         oz_plan_destroy(c);
         tc_plan_destroy(c);
         free_work(c);
@@ -200,6 +201,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         s = ACSE_ERR_CUDA;
     if (s != ACSE_OK) {
+        ny_free(c);
         oz_plan_destroy(c);
         tc_plan_destroy(c);
         free_work(c);
