@@ -281,7 +281,7 @@ int acse_contract_gemm(acse_ctx* c) {
 }
 
 int acse_contract_post(acse_ctx* c, int sW, double scale, int mask, double* const out[3], double* norm2_dst) {
-    if (c->opt.prec != ACSE_FP64) ACSE_TRY(tc_unpack_pairs(c));   // full [X; Y] of the same-spin sectors
+    if (c->opt.prec != ACSE_FP64) ACSE_TRY(tc_unpack_pairs(c));   // rows i < j of the same-spin [X; Y]
     if (c->ny) ACSE_TRY(ny_pass(c));   // NY: the 3-cumulant term, added to B by the B kernel
     ACSE_TRY(launch_Q(c));
     ACSE_TRY(launch_build_B(c));

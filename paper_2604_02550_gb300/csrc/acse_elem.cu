@@ -183,20 +183,31 @@ int launch_pack_Mph(acse_ctx* c) {
 // X^{ij}_{kp} = sum_rs M^{ij}_{rs} W^{kp}_{rs}:  Q^k_i = sum_P X^{iP}_{kP}, i.e.
 //   Q_a[k][i] = sum_p Xaa[(i,p)][(k,p)] + sum_p Xab[(i,p)][(k,p)]
 //   Q_b[k][i] = sum_p Xbb[(i,p)][(k,p)] + sum_p Xab[(p,i)][(p,k)]
-// (O(r^3) instead of O(r^5); Xab already carries the factor 2 of the mixed-spin (rs) sum).
+// (O(r^3) instead of O(r^5); Xab already carries the factor 2 of the mixed-spin (rs) sum).  With Xpaa /
+// Xpbb set (split path), the same-spin X is read from the packed GEMM output (rows and columns over
+// the pairs a < b, row pitch P):  X[(i,p)][(k,p)] = s_ip s_kp Xp[pk(i,p)][pk(k,p)], zero for i = p or
+// k = p (s_ab = -1 for a > b), the values the unpacked rows hold.
+template <typename T>
+__device__ __forceinline__ T q_packed(const T* __restrict__ Xp, int r, int P, int i, int k, int p) {
+    if (i == p || k == p) return (T)0;
+    const T v = Xp[(size_t)(i < p ? pk_pair(r, i, p) : pk_pair(r, p, i)) * P + (k < p ? pk_pair(r, k, p) : pk_pair(r, p, k))];
+    return (i < p) == (k < p) ? v : -v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_Q_from_X(int r, const T* __restrict__ Xaa, const T* __restrict__ Xab,
-                                                  const T* __restrict__ Xbb, size_t ldx, T* __restrict__ Qv) {
+                                                  const T* __restrict__ Xbb, size_t ldx, const T* __restrict__ Xpaa,
+                                                  const T* __restrict__ Xpbb, T* __restrict__ Qv) {
     // one warp per output element, lanes over p, fixed-order warp reduction
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (t >= 2 * r * r) return;
-    const int sp = t / (r * r), k = (t / r) % r, i = t % r;
+    const int sp = t / (r * r), k = (t / r) % r, i = t % r, P = r * (r - 1) / 2;
     T acc = 0;
     for (int p = lane; p < r; p += 32) {
-        if (sp == 0)
-            acc += Xaa[(size_t)(i * r + p) * ldx + k * r + p] + Xab[(size_t)(i * r + p) * ldx + k * r + p];
-        else
-            acc += Xbb[(size_t)(i * r + p) * ldx + k * r + p] + Xab[(size_t)(p * r + i) * ldx + p * r + k];
+        const T xs = Xpaa ? q_packed(sp == 0 ? Xpaa : Xpbb, r, P, i, k, p)
+                          : (sp == 0 ? Xaa : Xbb)[(size_t)(i * r + p) * ldx + k * r + p];
+        const T xab = sp == 0 ? Xab[(size_t)(i * r + p) * ldx + k * r + p] : Xab[(size_t)(p * r + i) * ldx + p * r + k];
+        acc += xs + xab;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -210,11 +221,13 @@ int launch_Q(acse_ctx* c) {
     const size_t R2 = (size_t)r * r;
     if (c->opt.prec == ACSE_FP64) {
         k_Q_from_X<double><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(r, c->w.X[0], c->w.X[1], c->w.X[2], R2,
-                                                                          c->w.Q);
+                                                                          nullptr, nullptr, c->w.Q);
     } else {
-        // spin-flip specialisation: Xbb is the flip of Xaa (same values)
+        // same-spin X from the packed GEMM output; spin-flip specialisation: Xbb is the flip of Xaa (same
+        // values)
         k_Q_from_X<float><<<(2 * r * r + 7) / 8, 256, 0, c->stream>>>(
-            r, c->w.tc_pairC[0], c->w.tc_pairC[1], c->w.tc_pairC[acse_singlet(c) ? 0 : 2], R2, c->w.Q32);
+            r, nullptr, c->w.tc_pairC[1], nullptr, R2, c->w.tc_pairCp[0], c->w.tc_pairCp[acse_singlet(c) ? 0 : 2],
+            c->w.Q32);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;

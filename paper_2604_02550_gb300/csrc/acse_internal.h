@@ -10,6 +10,10 @@
 
 #define ACSE_MAX_R 64
 
+// Packed number of the pair (a, b), a < b, among the r(r-1)/2 same-spin pairs (row-major over a):
+// the row and column order of the packed same-spin GEMM operands and outputs of the split path.
+__host__ __device__ __forceinline__ int pk_pair(int r, int a, int b) { return a * r - a * (a + 1) / 2 + (b - a - 1); }
+
 // ------------------------------------------------------------------------------------------
 // Dense GEMM problem: C[m*ldc + n] = alpha * sum_k A(m,k) B(n,k) (+ beta*C), with
 //   A(m,k) = A[m*lda + k] (transA = 0, K-major) or A[k*lda + m] (transA = 1),
@@ -115,7 +119,7 @@ struct Work {
     void* tc_Zd;
     void* tc_Mf[2];
     void* tc_Zf[2];
-    float* tc_pairC[3];   // [X; Y] FP32 (2r^2 x r^2)
+    float* tc_pairC[3];   // [X; Y] FP32 (2r^2 x r^2); same-spin sectors: only the rows i < j are formed
     float* tc_pairCp[3];  // same-spin sectors (aa, bb): the GEMM's packed [X; Y] (2P x P, P = r(r-1)/2
                           // pairs i < j on rows and columns), expanded into tc_pairC by antisymmetry
     int KpP;              // padded K (per split term) of the packed same-spin pair operands

@@ -27,9 +27,6 @@ struct MxPtrs {
     int Kp1, Kp2, ns, KpP;
 };
 
-// Packed number of the pair (a, b), a < b, among the r(r-1)/2 same-spin pairs (row-major over a).
-__device__ __forceinline__ int pk_pair(int r, int a, int b) { return a * r - a * (a + 1) / 2 + (b - a - 1); }
-
 static MxPtrs mx_ptrs(acse_ctx* c) {
     MxPtrs p;
     Work& w = c->w;
@@ -260,40 +257,69 @@ __global__ void k_mx_pack_W(int r, const float* __restrict__ Waa, const float* _
     }
 }
 
-// [X; Y] of a same-spin sector from the packed GEMM output: X^{ij}_{kp} = s_ij s_kp Xp[pk(ij)][pk(kp)]
-// (s = -1 for a swapped pair, 0 on the diagonal), rows r^2.. for Y likewise.  Each block writes
-// UP_ROWS consecutive full rows of one sector: a column map (packed index and sign of every column) is
-// built once in shared memory, then per row the packed source row is staged (coalesced) and the full
-// row written four columns at a time.
+// Rows (i, j), i < j, of [X; Y] of a same-spin sector from the packed GEMM output:
+// X^{ij}_{kp} = s_kp Xp[pk(ij)][pk(kp)] (s_kp = -1 for k > p, 0 for k = p), rows r^2 + (i, j) for Y
+// likewise.  These are the only rows read: the B kernel's same-spin items are the pairs i < j, and Q
+// reads the packed output itself; rows i >= j are not formed.  Each block writes nrow consecutive
+// packed rows (a contiguous range of the packed output): the range is copied into shared memory
+// (cp.async, every copy in flight at once) while a column map (packed index and sign of every column)
+// is built there, then the full rows are written four columns at a time.
 #define UP_ROWS 8
-__global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, const float* __restrict__ Cp0,
-                                                         const float* __restrict__ Cp2, float* C0, float* C2) {
-    __shared__ float srow[ACSE_MAX_R * (ACSE_MAX_R - 1) / 2];
-    __shared__ __align__(16) int cmap[ACSE_MAX_R * ACSE_MAX_R];   // -1: diagonal; bit 30: negated
+__device__ __forceinline__ void up_cp_async16(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void up_cp_async4(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
+// rows per block of k_mx_unpack_pairs: its staged rows and column map within 48 KB of shared memory
+static int up_rows(int r) {
     const int R2 = r * r, P = r * (r - 1) / 2;
-    const int nblk_sec = (2 * R2 + UP_ROWS - 1) / UP_ROWS;
+    int n = (48 * 1024 - 4 * R2) / (4 * P);
+    return n > UP_ROWS ? UP_ROWS : (n < 1 ? 1 : n);
+}
+
+__global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, int nrow, const float* __restrict__ Cp0,
+                                                         const float* __restrict__ Cp2, float* C0, float* C2) {
+    extern __shared__ __align__(16) int up_smem[];
+    const int R2 = r * r, P = r * (r - 1) / 2;
+    int* cmap = up_smem;                                    // [R2]: -1 diagonal; bit 30: negated
+    float* srow = reinterpret_cast<float*>(up_smem + R2);   // [nrow][P]: the packed rows of the block
+    const int nblk_sec = (2 * P + nrow - 1) / nrow;
     const int sec = blockIdx.x / nblk_sec;
-    const int row0 = (blockIdx.x - sec * nblk_sec) * UP_ROWS;
-    const float* Cp = sec == 0 ? Cp0 : Cp2;
+    const int q0 = (blockIdx.x - sec * nblk_sec) * nrow;   // packed row: part * P + pk(i, j)
+    const int nr = min(nrow, 2 * P - q0);
+    const float* src = (sec == 0 ? Cp0 : Cp2) + (size_t)q0 * P;
     float* Cs = sec == 0 ? C0 : C2;
+    // 16-byte copies when the range and every staged row start on a 16-byte boundary
+    if ((P & 3) == 0 && (R2 & 3) == 0)
+        for (int e = threadIdx.x; e < nr * P / 4; e += blockDim.x) up_cp_async16(srow + 4 * e, src + 4 * e);
+    else
+        for (int e = threadIdx.x; e < nr * P; e += blockDim.x) up_cp_async4(srow + e, src + e);
     for (int c = threadIdx.x; c < R2; c += blockDim.x) {
         const int k = c / r, q = c - (c / r) * r;
         cmap[c] = k == q ? -1 : (k < q ? pk_pair(r, k, q) : (pk_pair(r, q, k) | 0x40000000));
     }
-    const bool vec = (R2 & 3) == 0 && (reinterpret_cast<uintptr_t>(Cs) & 15) == 0;
-    for (int row = row0; row < row0 + UP_ROWS && row < 2 * R2; ++row) {
-        float* C = Cs + (size_t)row * R2;
-        const int part = row / R2, ij = row - part * R2, i = ij / r, j = ij - (ij / r) * r;
-        __syncthreads();   // the previous row's reads of srow are done (and cmap is built)
-        if (i == j) {      // block-uniform
-            for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = 0.f;
-            continue;
+    // (part, i, j) of the first packed row; the following rows advance over the pairs i < j
+    int part = q0 / P, i = 0, j;
+    {
+        int base = 0;
+        const int pr = q0 - part * P;
+        while (pr >= base + (r - 1 - i)) {
+            base += r - 1 - i;
+            ++i;
         }
-        const float si = i < j ? 1.f : -1.f;
-        const float* src = Cp + (size_t)(part * P + (i < j ? pk_pair(r, i, j) : pk_pair(r, j, i))) * P;
-        for (int e = threadIdx.x; e < P; e += blockDim.x) srow[e] = si * src[e];
-        __syncthreads();
-        auto val = [&](int m) { return m < 0 ? 0.f : ((m & 0x40000000) ? -srow[m & 0x3FFFFFFF] : srow[m]); };
+        j = i + 1 + (pr - base);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    const bool vec = (R2 & 3) == 0 && (reinterpret_cast<uintptr_t>(Cs) & 15) == 0;
+    for (int u = 0; u < nr; ++u) {
+        float* C = Cs + ((size_t)part * R2 + (size_t)i * r + j) * R2;
+        const float* sr = srow + (size_t)u * P;
+        auto val = [&](int m) { return m < 0 ? 0.f : ((m & 0x40000000) ? -sr[m & 0x3FFFFFFF] : sr[m]); };
         if (vec) {
             for (int g = threadIdx.x; g < R2 / 4; g += blockDim.x) {
                 const int4 m = reinterpret_cast<const int4*>(cmap)[g];
@@ -302,15 +328,26 @@ __global__ void __launch_bounds__(256) k_mx_unpack_pairs(int r, const float* __r
         } else {
             for (int c = threadIdx.x; c < R2; c += blockDim.x) C[c] = val(cmap[c]);
         }
+        if (++j == r) {   // next pair; after (r-2, r-1) the first pair of the next part
+            ++i;
+            j = i + 1;
+            if (i == r - 1) {
+                ++part;
+                i = 0;
+                j = 1;
+            }
+        }
     }
 }
 
 int tc_unpack_pairs(acse_ctx* c) {
-    const int r = c->r;
+    const int r = c->r, R2 = r * r, P = r * (r - 1) / 2;
     const int nsec = acse_singlet(c) ? 1 : 2;   // the bb sector is not formed under the spin flip
-    const int nblk_sec = (2 * r * r + UP_ROWS - 1) / UP_ROWS;
-    k_mx_unpack_pairs<<<nsec * nblk_sec, 256, 0, c->stream>>>(r, c->w.tc_pairCp[0], c->w.tc_pairCp[2], c->w.tc_pairC[0],
-                                                              c->w.tc_pairC[2]);
+    const int nrow = up_rows(r);
+    const int nblk_sec = (2 * P + nrow - 1) / nrow;
+    const size_t smem = (size_t)4 * R2 + (size_t)4 * nrow * P;
+    k_mx_unpack_pairs<<<nsec * nblk_sec, 256, smem, c->stream>>>(r, nrow, c->w.tc_pairCp[0], c->w.tc_pairCp[2],
+                                                                 c->w.tc_pairC[0], c->w.tc_pairC[2]);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
