@@ -568,8 +568,9 @@ def main():
                 "peak_source": "measured cuBLAS DGEMM 8192^3 on this pool (bench.py --peaks); DFMA pipe"}
         ach = fl / gemm_avg_s / 1e12
     elif prec in ("bf16x3", "ozaki"):
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks.get("bf16_tflops", 1887.4),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1.9 PF"}
+        measured = "bf16_tflops" in peaks
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops"] if measured else 1900.0,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if measured else "fallback 1.9 PFLOP/s"}
         ach = split * fl / gemm_avg_s / 1e12
     else:
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": TF32_PEAK_TFLOPS,
