@@ -107,7 +107,8 @@ typedef struct {
  * build the spin-blocked reduced Hamiltonian K of Eq. (2); they may be freed afterwards.
  * `cuda_stream` is a cudaStream_t (NULL = legacy default stream) on which every call of this
  * context is ordered.  All device workspace is allocated here (about 40 r^4 doubles plus the
- * split-precision operand copies), so later calls allocate nothing. */
+ * split-precision operand copies), so later calls allocate nothing.  On any failure *ctx is set
+ * to NULL (when ctx itself is not NULL) and nothing stays allocated. */
 int acse_create(acse_ctx** ctx, const acse_opts* opts, const double* h, const double* V,
                 void* cuda_stream);
 

@@ -141,8 +141,8 @@ static int alloc_work(acse_ctx* c) {
 __global__ void k_set1(double* dst, double v) { *dst = v; }
 
 extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, const double* V, void* stream) {
+    if (out) *out = nullptr;   // every failure leaves *out = NULL
     if (!out || !o || !h || !V) return ACSE_ERR_ARG;
-    *out = nullptr;
     const int N = o->n_alpha + o->n_beta;
     if (o->r < 2 || o->r > ACSE_MAX_R || o->n_alpha < 0 || o->n_beta < 0 || N < 2 || o->n_alpha > o->r ||
         o->n_beta > o->r)
