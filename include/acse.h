@@ -165,7 +165,8 @@ int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_ste
  *   acse_batch_run: nsteps graph replays; per instance (host arrays of n, each may be NULL): E and
  *     ||A||^2 at the current D, accepted steps, stop reason (0 running, 1 E or ||A|| rose, 2 converged).
  *   acse_batch_info: the tile choice (0 all 256 wide, 1 all 128 wide, 2 split at r^2 = split_r2) and
- *     the kernels launched so far.  n <= 64. */
+ *     the kernels launched so far.  1 <= n <= 64 (ACSE_ERR_ARG otherwise, and for mixed precisions);
+ *     ACSE_ERR_UNSUPPORTED for the NY reconstruction or ACSE_OZAKI; a failed create leaves *batch NULL. */
 typedef struct acse_batch acse_batch;
 int acse_batch_create(acse_batch** batch, int n, const acse_opts* opts, const double* const* h,
                       const double* const* V, void* cuda_stream);

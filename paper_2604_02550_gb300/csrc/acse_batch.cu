@@ -286,8 +286,8 @@ extern "C" int acse_batch_destroy(acse_batch* B) {
 
 extern "C" int acse_batch_create(acse_batch** out, int n, const acse_opts* opts, const double* const* h,
                                  const double* const* V, void* stream) {
+    if (out) *out = nullptr;   // every failure leaves *out = NULL
     if (!out || !opts || !h || !V || n < 1 || n > 64) return ACSE_ERR_ARG;
-    *out = nullptr;
     for (int i = 1; i < n; ++i)
         if (opts[i].prec != opts[0].prec) return ACSE_ERR_ARG;
     for (int i = 0; i < n; ++i)

@@ -3,8 +3,10 @@
 `acse_create` validates the options (include/acse.h: 2 <= r <= 64, N >= 2, electrons per spin <= r,
 a known precision, 4..10 Ozaki slices, a known reconstruction, n_alpha = n_beta for the spin-flip
 option, a non-empty active range inside [0, r)) before it allocates anything or touches the device;
-`acse_energy_noalloc` rejects null pointers, empty shapes and r above its static scratch first; the
-entry points taking a context reject a null one.  Each case must return its documented status.
+`acse_energy_noalloc` rejects null pointers, empty shapes and r above its static scratch first;
+`acse_batch_create` rejects 0 or more than 64 instances, mixed precisions, the NY reconstruction and
+the Ozaki precision; the entry points taking a context or a batch reject a null one.  Each case must
+return its documented status, and a failed create must leave its output handle NULL.
 """
 import ctypes
 import os
@@ -90,3 +92,36 @@ def test_every_status_has_its_own_text(L):
     assert texts[0] == "ok"
     assert len(set(texts.values())) == len(texts)
     assert _lib.strerror(-42) == "unknown status"
+
+
+def _batch_create(L, n, opts_list, with_out=True):
+    h = np.zeros((6, 6))
+    V = np.zeros((6,) * 4)
+    k = max(n, 1)
+    arr = (_lib.AcseOpts * k)(*(opts_list + [_opts()] * (k - len(opts_list))))
+    hp = (ctypes.c_void_p * k)(*([h.ctypes.data] * k))
+    Vp = (ctypes.c_void_p * k)(*([V.ctypes.data] * k))
+    out = ctypes.c_void_p(123)
+    st = L.acse_batch_create(ctypes.byref(out) if with_out else None, n, arr, hp, Vp, None)
+    if with_out:
+        assert out.value is None, "a failed batch create leaves *batch = NULL"
+    return st
+
+
+def test_batch_create_rejects_invalid_arguments(L):
+    assert _batch_create(L, 0, []) == ARG
+    assert _batch_create(L, 65, []) == ARG
+    assert _batch_create(L, 2, [], with_out=False) == ARG
+    # one precision for the whole batch
+    assert _batch_create(L, 2, [_opts(prec=_lib.ACSE_BF16X3), _opts(prec=_lib.ACSE_TF32)]) == ARG
+    # the batch runs the V reconstruction, and not the Ozaki precision
+    assert _batch_create(L, 2, [_opts(), _opts(recon=1)]) == UNSUPPORTED
+    assert _batch_create(L, 1, [_opts(prec=_lib.ACSE_OZAKI)]) == UNSUPPORTED
+
+
+def test_batch_entry_points_reject_a_null_batch(L):
+    assert L.acse_batch_destroy(None) == ARG
+    assert L.acse_batch_set_D(None, 0, None, None, None, 0.0) == ARG
+    assert L.acse_batch_get_D(None, 0, None, None, None) == ARG
+    assert L.acse_batch_run(None, 1, 0, None, None, None, None) == ARG
+    assert L.acse_batch_info(None, None, None, None) == ARG
