@@ -208,13 +208,16 @@ int acse_set_wait_bound_ns(acse_ctx* ctx, unsigned long long ns, int inject_stal
  * allocates nothing: its only scratch is a file-scope static device array of 64 x 64 doubles
  * (32 KiB, held by every GPU that loads the library until the process exits), one FP64 partial
  * sum per (i, j).
- *   r, n_alpha, n_beta: as in acse_opts (N = n_alpha + n_beta >= 2); r <= 64, larger r returns
- *     ACSE_ERR_TOO_LARGE.
- *   h (r*r), V (r^4, chemist's (pq|rs)), Daa, Dab, Dbb (r^4 each), E (one double): DEVICE
- *     pointers only (a host pointer returns ACSE_ERR_ARG); the caller owns all of them.
+ *   r, n_alpha, n_beta: as in acse_opts and checked as acse_create checks them (2 <= r,
+ *     n_alpha <= r, n_beta <= r, N = n_alpha + n_beta >= 2; ACSE_ERR_SHAPE otherwise); r <= 64,
+ *     larger r returns ACSE_ERR_TOO_LARGE.
+ *   h (r*r), V (r^4, chemist's (pq|rs)), Daa, Dab, Dbb (r^4 each), E (one double): device memory
+ *     of the CURRENT device, or managed memory (a host pointer or another GPU's memory returns
+ *     ACSE_ERR_ARG); the caller owns all of them.
  *   cuda_stream: the cudaStream_t the two kernels are launched on; the call is asynchronous.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current and caches it; make that first call before any stream capture.  Every
+ * that device current and caches it with the identity of the device's CUDA context (after a device
+ * reset the next call looks it up again); make that first call before any stream capture.  Every
  * call shares the one array and it keeps the last call's contents; nothing in it needs to start
  * at zero (each call writes every slot it reads before reading it), but calls whose kernels
  * overlap on the GPU (other streams, other threads) race on it and must be ordered by the

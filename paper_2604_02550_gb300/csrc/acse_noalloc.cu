@@ -9,6 +9,8 @@
 // forms the reduced Hamiltonian element by element inside the kernel (no K buffer), and keeps
 // its only scratch -- one FP64 partial sum per (i, j) row of the pair index -- in a file-scope
 // static device array.  It calls no allocating routine.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "acse_internal.h"
@@ -21,8 +23,17 @@
 // 32 KiB of device memory, held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) double g_energy_scratch[ACSE_NOALLOC_SLOTS];
 
-static void* g_scratch_addr[ACSE_NOALLOC_MAX_DEVICES];   // device address of the array, per device
+// Device address of the array per device, and the identity of the CUDA context it belongs to: a
+// device reset (or any other end of the primary context) unloads the module, and the array of the
+// next context lives at another address, so a cached address is reused only within its context.
+static void* g_scratch_addr[ACSE_NOALLOC_MAX_DEVICES];
+static unsigned long long g_scratch_ctx[ACSE_NOALLOC_MAX_DEVICES];
 static std::mutex g_scratch_mu;
+
+typedef CUresult (*pfn_ctx_current)(CUcontext*);
+typedef CUresult (*pfn_ctx_id)(CUcontext, unsigned long long*);
+static pfn_ctx_current g_ctx_current;
+static pfn_ctx_id g_ctx_id;
 
 __device__ __forceinline__ double na_warp_sum(double v) {
 #pragma unroll
@@ -76,28 +87,55 @@ __global__ void k_energy_noalloc_final(int n, const double* __restrict__ scratch
     if (threadIdx.x == 0) *E = v;
 }
 
-static int is_device_ptr(const void* p) {
+// 1 if p is memory the current device `dev` reads as its own: device memory of that device, or
+// managed memory; 0 for host memory and for another GPU's device memory (which the kernels would
+// reach only through peer access, if at all).
+static int is_device_ptr(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return 1;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-static int scratch_address(double** out) {
-    int dev = 0;
-    ACSE_CUDA_TRY(cudaGetDevice(&dev));
+// Unique id of the current CUDA context (0 when it cannot be had: the address is then looked up on
+// every call, which is correct, only slower).
+static unsigned long long current_ctx_id() {
+    if (!g_ctx_current || !g_ctx_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return 0;
+        }
+        g_ctx_current = (pfn_ctx_current)f1;
+        g_ctx_id = (pfn_ctx_id)f2;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device `dev`, looked up once per device and
+// context (the caller has made a runtime call on `dev` before, so its primary context is current).
+static int scratch_address(int dev, double** out) {
     if (dev < 0 || dev >= ACSE_NOALLOC_MAX_DEVICES) return ACSE_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_scratch_addr[dev] || id == 0 || id != g_scratch_ctx[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_energy_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
+            g_scratch_addr[dev] = nullptr;
             return ACSE_ERR_CUDA;
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = id;
     }
     *out = (double*)g_scratch_addr[dev];
     return ACSE_OK;
@@ -108,13 +146,16 @@ extern "C" int acse_energy_noalloc(int r, int n_alpha, int n_beta, const double*
                                    void* cuda_stream) {
     if (!h || !V || !Daa || !Dab || !Dbb || !E) return ACSE_ERR_ARG;
     const int N = n_alpha + n_beta;
-    if (r < 1 || n_alpha < 0 || n_beta < 0 || N < 2) return ACSE_ERR_SHAPE;
+    // the shape rules of acse_create, then the static scratch's own limit
+    if (r < 2 || n_alpha < 0 || n_beta < 0 || N < 2 || n_alpha > r || n_beta > r) return ACSE_ERR_SHAPE;
     if (r > ACSE_NOALLOC_MAX_R) return ACSE_ERR_TOO_LARGE;
+    int dev = 0;
+    ACSE_CUDA_TRY(cudaGetDevice(&dev));
     const void* ptrs[] = {h, V, Daa, Dab, Dbb, E};
     for (const void* p : ptrs)
-        if (!is_device_ptr(p)) return ACSE_ERR_ARG;
+        if (!is_device_ptr(p, dev)) return ACSE_ERR_ARG;
     double* scratch = nullptr;
-    ACSE_TRY(scratch_address(&scratch));
+    ACSE_TRY(scratch_address(dev, &scratch));
     cudaStream_t st = (cudaStream_t)cuda_stream;
     k_energy_noalloc_rows<<<r * r, 256, 0, st>>>(r, 1.0 / (2.0 * (N - 1)), h, V, Daa, Dab, Dbb, scratch);
     ACSE_CUDA_TRY(cudaGetLastError());

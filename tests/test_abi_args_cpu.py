@@ -84,6 +84,9 @@ def test_energy_noalloc_host_checks(L):
     assert L.acse_energy_noalloc(6, 2, 2, None, *p[1:], None) == ARG
     assert L.acse_energy_noalloc(0, 2, 2, *p, None) == SHAPE
     assert L.acse_energy_noalloc(6, 1, 0, *p, None) == SHAPE
+    assert L.acse_energy_noalloc(1, 1, 1, *p, None) == SHAPE       # r = 1: acse_create rejects it too
+    assert L.acse_energy_noalloc(3, 4, 0, *p, None) == SHAPE       # more alpha electrons than orbitals
+    assert L.acse_energy_noalloc(3, 1, 4, *p, None) == SHAPE
     assert L.acse_energy_noalloc(65, 2, 2, *p, None) == TOO_LARGE
 
 

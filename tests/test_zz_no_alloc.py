@@ -29,6 +29,8 @@ def test_energy_noalloc_matches_context_energy_twice():
     ctx.close()
     # a second, different 2-RDM for the second call (the scratch keeps the first call's contents)
     q = I.make_problem(10, 8, 21, "cas", core=[0, 1], active=[2, 3, 4, 5], nelecas=4, root=1)
+    # both calls pass p's integrals: q must share them (same seed), so that E2_ref is their energy
+    assert np.array_equal(p.h, q.h) and np.array_equal(p.V, q.V)
     D2 = [torch.from_numpy(x).to(dev) for x in (q.Daa, q.Dab, q.Dbb)]
     ctx2 = ACSE(q.r, q.n_alpha, q.n_beta, q.h, q.V, "fp64")
     E2_ref = float(ctx2.energy(D2))
