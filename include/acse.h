@@ -101,6 +101,17 @@ typedef struct {
                         * n_beta.  The library does not symmetrise D: on an asymmetric D the
                         * beta-beta results are those of the alpha-alpha block.             */
     int oz_slices;     /* ACSE_OZAKI: 6-bit slices per operand row, 4..10; 0 -> 8            */
+    int refine;        /* precision schedule of acse_step: 0 off; 1 the steps run in `prec` (any precision,
+                        * ACSE_OZAKI with oz_slices included) until the switch rule fires, every later step
+                        * in ACSE_OZAKI with refine_slices slices (FP64-accurate), from the same D and
+                        * line-search state.  Rule, checked after every step: switch once ||A||^2 has
+                        * fallen by less than refine_tol (relative) over the step, or risen.  The
+                        * FP64-accurate context is created here with this one (its workspace besides);
+                        * while the schedule has not switched, acse_step reads ||A||^2 back to the host
+                        * after every step (one stream synchronisation per step).  acse_residual and
+                        * acse_energy run in the precision in force.  Not with opts.singlet.            */
+    int refine_slices; /* slices of the refined precision, 4..10; 0 -> 8                                */
+    double refine_tol; /* relative fall of ||A||^2 per step below which the schedule switches; 0 -> 1e-2 */
 } acse_opts;
 
 /* Create a context for one problem.  h (r*r) and V (r^4, chemist's (pq|rs)) are read once to
@@ -177,6 +188,29 @@ int acse_batch_get_D(acse_batch* batch, int i, double* Daa, double* Dab, double*
 int acse_batch_run(acse_batch* batch, int nsteps, int stop_rule, double* E_out, double* norm2_out,
                    int* steps_out, int* reason_out);
 int acse_batch_info(const acse_batch* batch, int* tune_choice, int* split_r2, long long* launches);
+
+/* Fit of the asymptotic regime of an energy trajectory.  The Results section describes the energy along
+ * lambda = eps n (eps the Euler step, n the iteration; with varying steps lambda_n is the sum of the steps
+ * before n) as an exponentially damped region followed by an asymptotic regime in which E changes about
+ * linearly in lambda, and the Conclusions propose extrapolation and fitting to estimate the solution once a
+ * trajectory stably enters that regime; the paper gives no fit.  The library fits
+ *     E(lambda) ~ a + b lambda + c exp(-k lambda),  k > 0,
+ * by least squares over the points n >= n_skip: in t = (lambda - lambda_first)/span, kappa = k span is
+ * scanned on 256 points evenly spaced in log kappa over [0.25, 4 (m - 1)] (m fitted points), the best
+ * point refined to dF/dkappa = 0 by bisection between its neighbours; a is the extrapolated energy (the
+ * asymptote's value at lambda = 0), b its slope.
+ *   acse_extrapolate: lam, E (n doubles each) and out (6 doubles: a, b, c, k, rss, flag) are device memory
+ *     of the current device (or managed); 4 <= n - n_skip <= 4096 (ACSE_ERR_SHAPE otherwise); asynchronous
+ *     on cuda_stream.  flag: 0 refined minimum, 1 minimum on the edge of the kappa grid or not bracketed
+ *     (no refinement), 3 lambda not increasing (then a..rss are NaN).
+ *   acse_batch_history: the batch records, per instance, lambda and E of D_0 and of every accepted step
+ *     (an undone step's point is dropped; at most 4096 points).  Copies up to cap points of instance i
+ *     into lam and E (host or device) and sets *count to the number recorded.
+ *   acse_batch_extrapolate: the fit of every instance's record in one launch (one block per instance);
+ *     out: host array of 6 n doubles (flag 2 and NaNs for an instance with fewer than n_skip + 4 points). */
+int acse_extrapolate(int n, const double* lam, const double* E, int n_skip, double* out, void* cuda_stream);
+int acse_batch_history(acse_batch* batch, int i, double* lam, double* E, int cap, int* count);
+int acse_batch_extrapolate(acse_batch* batch, int n_skip, double* out);
 
 /* Profiling (not part of the method).  acse_profile(ctx, 1) resets the counters and starts
  * recording a CUDA-event pair around every O(r^6) GEMM launch of this context (up to 256

@@ -18,13 +18,15 @@ EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_
            "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_sync_status",
            "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_batch_create",
            "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D", "acse_batch_run", "acse_batch_info",
+           "acse_extrapolate", "acse_batch_history", "acse_batch_extrapolate",
            "acse_strerror", "acse_last_error", "acse_version")
 
 
 class AcseOpts(ctypes.Structure):
     _fields_ = [("r", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("prec", c_int), ("recon", c_int),
                 ("mask_active", c_int), ("act_lo", c_int), ("act_hi", c_int), ("line_search", c_int),
-                ("eps0", c_double), ("check_inputs", c_int), ("singlet", c_int), ("oz_slices", c_int)]
+                ("eps0", c_double), ("check_inputs", c_int), ("singlet", c_int), ("oz_slices", c_int),
+                ("refine", c_int), ("refine_slices", c_int), ("refine_tol", c_double)]
 
 
 class AcseError(RuntimeError):
@@ -66,8 +68,12 @@ def lib():
         L.acse_batch_get_D.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
         L.acse_batch_run.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
         L.acse_batch_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_longlong)]
+        L.acse_extrapolate.argtypes = [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
+        L.acse_batch_history.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, POINTER(c_int)]
+        L.acse_batch_extrapolate.argtypes = [c_void_p, c_int, c_void_p]
         for name in ("acse_batch_create", "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D",
-                     "acse_batch_run", "acse_batch_info"):
+                     "acse_batch_run", "acse_batch_info", "acse_extrapolate", "acse_batch_history",
+                     "acse_batch_extrapolate"):
             getattr(L, name).restype = c_int
         L.acse_sync_status.argtypes = [c_void_p]
         L.acse_clear_status.argtypes = [c_void_p]
@@ -117,7 +123,8 @@ RECON = {"V": 0, "NY": 1}
 
 
 def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
-                check_inputs=False, stream=None, recon="V", singlet=False, oz_slices=0):
+                check_inputs=False, stream=None, recon="V", singlet=False, oz_slices=0, refine=False,
+                refine_slices=0, refine_tol=0.0):
     o = AcseOpts()
     o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -129,6 +136,9 @@ def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=Fa
     o.check_inputs = int(bool(check_inputs))
     o.singlet = int(bool(singlet))
     o.oz_slices = int(oz_slices)
+    o.refine = int(bool(refine))
+    o.refine_slices = int(refine_slices)
+    o.refine_tol = float(refine_tol)
     h_ = c_void_p()
     st = current_stream_handle() if stream is None else stream
     _check(lib().acse_create(byref(h_), byref(o), ptr(h), ptr(V), st), "acse_create")
@@ -245,3 +255,33 @@ def acse_batch_info(b):
     nl = ctypes.c_longlong()
     _check(lib().acse_batch_info(b, byref(t), byref(sp), byref(nl)), "acse_batch_info")
     return t.value, sp.value, nl.value
+
+
+FIT_KEYS = ("a", "b", "c", "k", "rss", "flag")
+
+
+def acse_extrapolate(lam, E, out, n_skip=0, stream=None):
+    """E(lambda) fit of one trajectory: lam, E (n float64 device tensors), out (6 float64, device)."""
+    st = current_stream_handle() if stream is None else stream
+    _check(lib().acse_extrapolate(int(lam.numel()), ptr(lam), ptr(E), int(n_skip), ptr(out), st),
+           "acse_extrapolate")
+
+
+def acse_batch_history(b, i, cap=4096):
+    """(lambda, E) recorded for instance i, as numpy arrays."""
+    import numpy as np
+    lam = np.zeros(cap)
+    E = np.zeros(cap)
+    n = c_int()
+    _check(lib().acse_batch_history(b, int(i), lam.ctypes.data, E.ctypes.data, int(cap), byref(n)),
+           "acse_batch_history")
+    k = min(n.value, cap)
+    return lam[:k].copy(), E[:k].copy()
+
+
+def acse_batch_extrapolate(b, n, n_skip=0):
+    """The fit of every instance's record: a list of n dicts (a, b, c, k, rss, flag)."""
+    import numpy as np
+    out = np.zeros(6 * n)
+    _check(lib().acse_batch_extrapolate(b, int(n_skip), out.ctypes.data), "acse_batch_extrapolate")
+    return [dict(zip(FIT_KEYS, out[6 * i:6 * i + 6])) for i in range(n)]

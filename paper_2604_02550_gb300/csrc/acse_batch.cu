@@ -48,7 +48,16 @@ struct acse_batch {
     int stop_rule;
     cudaGraphExec_t graph;
     int graph_ready;
+    // trajectory record per instance (device): lambda and E of every accepted step, D_0 first;
+    // instance i at hist + 2 i ACSE_HIST_CAP (lambda) and + ACSE_HIST_CAP (E), hcount[i] points
+    double* hist;
+    int* hcount;
+    double* fitout;    // 6 doubles per instance: the last acse_batch_extrapolate results (device)
 };
+#define ACSE_HIST_CAP 4096
+
+int fit_launch(const double* lam, const double* E, const int* count, int n_fixed, size_t stride, int ntraj,
+               int n_skip, double* out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------- kernels
 // Stopping rule for one instance at the start of a step (E = energy of the current D, N2 = ||A||^2 at
@@ -94,6 +103,26 @@ __global__ void k_cond_copy3(size_t n4, const double* __restrict__ s, int slot, 
         else if (b == 1) b1[g] = a1[g];
         else b2[g] = a2[g];
     }
+}
+
+// Trajectory record, at the end of a step: an undone step (restore) drops its point; a step taken
+// (eps used > 0) appends lambda + eps and the new E, until the record is full.
+__global__ void k_batch_hist(const double* __restrict__ s, double* __restrict__ hist, int* __restrict__ count) {
+    int n = *count;
+    if (s[S_RESTORE] == 1.0 && n > 1) --n;
+    if (s[S_EPS_USED] != 0.0 && n < ACSE_HIST_CAP) {
+        hist[n] = hist[n - 1] + s[S_EPS_USED];
+        hist[ACSE_HIST_CAP + n] = s[S_E];
+        ++n;
+    }
+    *count = n;
+}
+
+// A fresh record: lambda = 0 at the E of D_0.
+__global__ void k_batch_hist_reset(const double* __restrict__ s, double* __restrict__ hist, int* __restrict__ count) {
+    hist[0] = 0.0;
+    hist[ACSE_HIST_CAP] = s[S_E];
+    *count = 1;
 }
 
 static int cgrid(size_t n) {
@@ -179,6 +208,8 @@ static int batch_step(acse_batch* B) {
         double* Dm[3] = {B->D[3 * i], B->D[3 * i + 1], B->D[3 * i + 2]};
         const double* Uc[3] = {w.U[0], w.U[1], w.U[2]};
         ACSE_TRY(launch_axpy_energy(c, Dm, Uc, w.scal + S_EPS_USED, w.scal + S_E));
+        k_batch_hist<<<1, 1, 0, c->stream>>>(w.scal, B->hist + 2 * (size_t)ACSE_HIST_CAP * i, B->hcount + i);
+        ACSE_LAUNCHED(c);
     }
     return join_all(B);
 }
@@ -275,6 +306,9 @@ extern "C" int acse_batch_destroy(acse_batch* B) {
             if (B->Dprev[3 * i + b]) cudaFree(B->Dprev[3 * i + b]);
         }
     }
+    if (B->hist) cudaFree(B->hist);
+    if (B->hcount) cudaFree(B->hcount);
+    if (B->fitout) cudaFree(B->fitout);
     if (B->fork) cudaEventDestroy(B->fork);
     if (B->stream) cudaStreamDestroy(B->stream);
     free(B->ctx);
@@ -306,6 +340,11 @@ extern "C" int acse_batch_create(acse_batch** out, int n, const acse_opts* opts,
     if (s == ACSE_OK && (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess))
         s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK && (cudaMalloc((void**)&B->hist, 2 * (size_t)ACSE_HIST_CAP * n * sizeof(double)) != cudaSuccess ||
+                         cudaMalloc((void**)&B->hcount, n * sizeof(int)) != cudaSuccess ||
+                         cudaMalloc((void**)&B->fitout, 6 * (size_t)n * sizeof(double)) != cudaSuccess ||
+                         cudaMemset(B->hcount, 0, n * sizeof(int)) != cudaSuccess))
+        s = ACSE_ERR_NOMEM;
     for (int i = 0; i < n && s == ACSE_OK; ++i) {
         if (cudaStreamCreateWithFlags(&B->sub[i], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) != cudaSuccess) {
@@ -315,6 +354,7 @@ extern "C" int acse_batch_create(acse_batch** out, int n, const acse_opts* opts,
         acse_opts o = opts[i];
         o.line_search = 0;
         o.check_inputs = 0;
+        o.refine = 0;      // the batch steps in one precision
         s = acse_create(&B->ctx[i], &o, h[i], V[i], B->sub[i]);
         const size_t b4 = (size_t)o.r * o.r * o.r * o.r * sizeof(double);
         for (int b = 0; b < 3 && s == ACSE_OK; ++b)
@@ -349,6 +389,8 @@ extern "C" int acse_batch_set_D(acse_batch* B, int i, const double* Daa, const d
     ACSE_CUDA_TRY(cudaMemcpy(c->w.scal, sc, sizeof(sc), cudaMemcpyHostToDevice));
     const double* Dc[3] = {B->D[3 * i], B->D[3 * i + 1], B->D[3 * i + 2]};
     ACSE_TRY(launch_energy(c, Dc, c->w.scal + S_E));
+    k_batch_hist_reset<<<1, 1, 0, c->stream>>>(c->w.scal, B->hist + 2 * (size_t)ACSE_HIST_CAP * i, B->hcount + i);
+    ACSE_LAUNCHED(c);
     ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return ACSE_OK;
 }
@@ -401,6 +443,30 @@ extern "C" int acse_batch_run(acse_batch* B, int nsteps, int stop_rule, double* 
         if (steps_out) steps_out[i] = (int)sc[S_STEPS];
         if (reason_out) reason_out[i] = (int)sc[S_FROZEN];
     }
+    return ACSE_OK;
+}
+
+extern "C" int acse_batch_history(acse_batch* B, int i, double* lam, double* E, int cap, int* count) {
+    if (!B || i < 0 || i >= B->n || cap < 0 || (cap > 0 && (!lam || !E))) return ACSE_ERR_ARG;
+    ACSE_CUDA_TRY(cudaStreamSynchronize(B->stream));
+    int n = 0;
+    ACSE_CUDA_TRY(cudaMemcpy(&n, B->hcount + i, sizeof(int), cudaMemcpyDeviceToHost));
+    const double* h = B->hist + 2 * (size_t)ACSE_HIST_CAP * i;
+    const int k = n < cap ? n : cap;
+    if (k > 0) {
+        ACSE_CUDA_TRY(cudaMemcpy(lam, h, k * sizeof(double), cudaMemcpyDefault));
+        ACSE_CUDA_TRY(cudaMemcpy(E, h + ACSE_HIST_CAP, k * sizeof(double), cudaMemcpyDefault));
+    }
+    if (count) *count = n;
+    return ACSE_OK;
+}
+
+extern "C" int acse_batch_extrapolate(acse_batch* B, int n_skip, double* out) {
+    if (!B || !out || n_skip < 0) return ACSE_ERR_ARG;
+    ACSE_TRY(fit_launch(B->hist, B->hist + ACSE_HIST_CAP, B->hcount, 0, 2 * (size_t)ACSE_HIST_CAP, B->n, n_skip,
+                        B->fitout, B->stream));
+    ACSE_CUDA_TRY(cudaMemcpyAsync(out, B->fitout, 6 * (size_t)B->n * sizeof(double), cudaMemcpyDefault, B->stream));
+    ACSE_CUDA_TRY(cudaStreamSynchronize(B->stream));
     return ACSE_OK;
 }
 
