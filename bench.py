@@ -5,10 +5,13 @@ A step is one Euler step of Eq. (update) through the C ABI (`acse_step`): the re
 (1-RDM, M, pair-pair and particle-hole GEMMs, B and G assembly, FP64 norm), the update
 U = 1/2 G(A) with the same reconstruction, D <- D + eps U and the FP64 energy.  The workload is
 the r = 48, N = 20, CAS(8e,8o) system (synthetic integrals, seed 0).  The metric is ACSE
-residual evaluations per second (one per step) over all ranks; TFLOP/s counts the O(r^6)
-GEMM work, 2 M N K summed over the GEMMs (32 r^6 per contraction pass, two passes per step).
+residual evaluations per second over all ranks, one evaluation being one contraction pass G(W)
+with the reconstructed 3-RDM (the residual G(K/2), or the update's G(A), the same contraction with
+another W): a step is two evaluations (its axpy and energy are not counted).  TFLOP/s counts the
+O(r^6) GEMM work, 2 M N K summed over the GEMMs (32 r^6 per contraction pass).
 
---impl reference times the FP64 numpy oracle on the host cores instead (rank 0 only).
+--impl reference times the FP64 numpy oracle on the host cores instead (rank 0 only): one full
+oracle residual evaluation of the same workload per step.
 Multi-GPU: independent replicas (one problem per rank, no collective on the data path).
 """
 from __future__ import annotations
@@ -120,7 +123,7 @@ def flops_per_pass(r, packed=False, singlet=False):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -134,7 +137,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -193,6 +196,10 @@ def dist_init(args):
     return rank, world, local
 
 
+EVALS_PER_STEP = 2     # contraction passes of one acse_step: the residual and the update
+SUSTAIN_S = 1.5        # untimed run of the same steps before the timed region (clock record)
+
+
 def cpu_oracle_timing(p, n_evals=1):
     """The FP64 oracle (spin-orbital numpy, all host cores) on `n_evals` residual evaluations."""
     import numpy as np
@@ -207,73 +214,32 @@ def cpu_oracle_timing(p, n_evals=1):
     return n_evals / dt, dt, os.cpu_count()
 
 
-REF_BUDGET_S = 150.0   # host time the reference arm may spend on its warm-up + timed steps
-
-
-def truncated_problem(p, rs):
-    """The workload restricted to its first rs orbitals (h, V and the D blocks sliced; N unchanged).
-    Every occupied and active orbital of the CAS workloads lies below rs >= act_hi, so the 2-RDM keeps
-    all of its nonzero entries."""
-    import numpy as np
-    s = slice(0, rs)
-    cut = lambda x: np.ascontiguousarray(x[(s,) * x.ndim])
-    return type(p)(f"{p.name}[:{rs}]", rs, p.n_alpha, p.n_beta, cut(p.h), cut(p.V), cut(p.Daa), cut(p.Dab),
-                   cut(p.Dbb), p.act_lo, p.act_hi, None)
-
-
-def reference_sample_size(p, nsteps):
-    """Largest orbital count rs (a multiple of 4, >= the occupied + active orbitals, <= r) for which
-    nsteps oracle residual evaluations of the truncated problem fit REF_BUDGET_S; the cost is predicted
-    from one timed evaluation at 16 orbitals scaled by rs^6 (an over-estimate: the oracle's BLAS
-    contractions run more efficiently at larger sizes)."""
-    from oracle import acse_oracle as O
-    r0 = max(16, p.act_hi)
-    q = truncated_problem(p, r0)
-    K = O.reduced_hamiltonian(q.h, q.V, q.N)
-    D = O.so_from_blocks(q.Daa, q.Dab, q.Dbb)
-    t0 = time.perf_counter()
-    O.residual(K, D, q.N)
-    t16 = time.perf_counter() - t0
-    best = r0
-    for rs in range(r0, p.r + 1, 4):
-        if nsteps * t16 * (rs / r0) ** 6 <= REF_BUDGET_S:
-            best = rs
-    return best
-
-
 def run_reference(args, rank, world):
-    """The FP64 oracle on the host cores, each step one oracle residual evaluation of a bounded sample
-    of the workload: the problem truncated to its first rs orbitals, rs chosen so that the warm-up and
-    timed steps fit a few minutes; the rate is scaled to evaluations of the full workload by the
-    O(r^6) contraction count, (rs / r)^6."""
+    """The FP64 oracle on the host cores: each step one full oracle residual evaluation of the workload
+    (about 23 s at r = 48 on a 16-core Grace host), warm-up steps the same."""
     if rank != 0:
         return
     from oracle import acse_oracle as O
     p = workload(args.r)
-    rs = reference_sample_size(p, args.steps + args.warmup)
-    q = truncated_problem(p, rs) if rs < p.r else p
-    K = O.reduced_hamiltonian(q.h, q.V, q.N)
-    D = O.so_from_blocks(q.Daa, q.Dab, q.Dbb)
+    K = O.reduced_hamiltonian(p.h, p.V, p.N)
+    D = O.so_from_blocks(p.Daa, p.Dab, p.Dbb)
     for _ in range(args.warmup):
-        O.residual(K, D, q.N)
+        O.residual(K, D, p.N)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        A = O.residual(K, D, q.N)
+        A = O.residual(K, D, p.N)
         times.append(time.perf_counter() - t0)
         del A
     total = sum(times)
-    scale = (rs / p.r) ** 6
-    val = scale * args.steps / total
-    sample = (f"per step one FP64 oracle residual evaluation of {p.name} truncated to its first {rs} of {p.r} "
-              f"orbitals ({total / args.steps:.3f} s), rate scaled by (rs/r)^6 = {scale:.3g} to evaluations of "
-              f"the full workload" if rs < p.r else f"per step one FP64 oracle residual evaluation of {p.name}")
+    val = args.steps / total
+    sample = f"per step one full FP64 oracle residual evaluation of {p.name} ({total / args.steps:.2f} s each)"
     line = {"metric": "acse_residual_evals_per_s", "value": val, "unit": "residual evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": "fp64 (numpy oracle, spin-orbital basis)",
-                       "sample_r": rs},
+                       "step": "one residual evaluation G(K/2)"},
             "cpu_baseline": {"kind": "oracle", "value": val, "unit": "residual evals/s", "cores": os.cpu_count(),
                              "sample": sample},
             "e2e": {"value": val, "unit": "residual evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -527,12 +493,29 @@ def main():
         for _ in range(args.warmup):
             ctx.step(D, args.eps)
     stream.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # clocks: sampled over a window of the same steps (about SUSTAIN_S long, untimed) run directly
+    # before the timed region and over the timed region itself, so that a short timed region still
+    # has a clock record taken under this load
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
+    t_s = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while time.perf_counter() - t_s < SUSTAIN_S:
+            for dst, src in zip(D, D0):      # back to D_0 every 100 steps, as the timed region does
+                dst.copy_(src)
+            for k in range(100):
+                ctx.step(D, args.eps)
+                if k % 10 == 9:
+                    stream.synchronize()
+                    if time.perf_counter() - t_s >= SUSTAIN_S:
+                        break
+        for dst, src in zip(D, D0):
+            dst.copy_(src)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     _lib.acse_profile(ctx.ctx, 1)
     with torch.cuda.stream(stream):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -551,7 +534,7 @@ def main():
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, dist)
     per_step = ms_max / args.steps
-    value = whole_job_rate(args.steps, world, ms_max)
+    value = whole_job_rate(EVALS_PER_STEP * args.steps, world, ms_max)
     fl_alg = flops_per_pass(p.r)                       # 32 r^6: the unpacked formulation
     # what the GEMM launch executes (the same-spin pair GEMMs on packed pairs on every path but FP64 FMA)
     fl = fl_alg if prec == "fp64" else flops_per_pass(p.r, packed=True, singlet=singlet)
@@ -586,15 +569,18 @@ def main():
                  "launch_ms": 1e3 * gemm_avg_s,
                  "gemm_share_of_step": 2 * 1e3 * gemm_avg_s / per_step,
                  "timed_launches": gemm_n})
+    clocks["window"] = (f"sampled every 100 ms over {SUSTAIN_S:.1f} s of the same untimed steps directly before "
+                        f"the timed region and over the timed region")
     line = {"metric": "acse_residual_evals_per_s", "value": value, "unit": "residual evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
+            "evals_per_step": EVALS_PER_STEP, "acse_steps_per_s": value / EVALS_PER_STEP,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "ozaki": "f64 (Ozaki: bf16 slices, exact f32 groups, f64 sums)"}.get(
                 prec, f"{prec} (f32 accumulate)"),
             "data": "synthetic",
             "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "recon": args.recon, "eps": args.eps,
                        "singlet": singlet,
-                       "step": "acse_step: residual + update + axpy + energy",
+                       "step": "acse_step: residual + update + axpy + energy (two residual evaluations)",
                        "reset_every": args.reset_every,
                        "l2": "inputs larger than L2 (about 1.5 GB of r^4 tensors touched per step)",
                        "parallelism": f"replicas x{world}"},
@@ -616,7 +602,8 @@ def main():
             _lib.acse_step(ctx.ctx, *Dh, args.eps, Eh, Nh, Sh)
         dt = time.perf_counter() - t0
         n4 = p.r ** 4
-        line["e2e"] = {"value": args.steps / dt, "unit": "residual evals/s", "h2d_bytes_per_step": 3 * n4 * 8,
+        line["e2e"] = {"value": EVALS_PER_STEP * args.steps / dt, "unit": "residual evals/s",
+                       "h2d_bytes_per_step": 3 * n4 * 8,
                        "d2h_bytes_per_step": 3 * n4 * 8 + 3 * 8,
                        "how": "acse_step on pinned host D blocks: staged H2D, step, D2H of D, E, ||A||^2, eps"}
     if not args.no_cpu_baseline and rank == 0 and world == 1:

@@ -20,7 +20,8 @@ class ACSE:
     """One ACSE problem (integrals and options) bound to a CUDA stream."""
 
     def __init__(self, r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
-                 check_inputs=False, device="cuda", stream=None, recon="V", singlet=False, oz_slices=0):
+                 check_inputs=False, device="cuda", stream=None, recon="V", singlet=False, oz_slices=0,
+                 refine=False, refine_slices=0, refine_tol=0.0):
         self.r, self.n_alpha, self.n_beta = r, n_alpha, n_beta
         self.device = torch.device(device)
         self.prec = prec
@@ -30,7 +31,8 @@ class ACSE:
             V_t = _dev(V, self.device)
             self.ctx = _lib.acse_create(r, n_alpha, n_beta, h_t, V_t, prec, mask, line_search, eps0, check_inputs,
                                         stream=self.stream.cuda_stream, recon=recon, singlet=singlet,
-                                        oz_slices=oz_slices)
+                                        oz_slices=oz_slices, refine=refine, refine_slices=refine_slices,
+                                        refine_tol=refine_tol)
         self._scal = torch.zeros(3, dtype=torch.float64, device=self.device)
 
     def close(self):

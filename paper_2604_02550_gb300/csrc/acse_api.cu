@@ -153,6 +153,10 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     if (o->recon != ACSE_RECON_V && o->recon != ACSE_RECON_NY) return ACSE_ERR_UNSUPPORTED;
     if (o->singlet && o->n_alpha != o->n_beta) return ACSE_ERR_ARG;
     if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
+    if (o->refine != 0 && o->refine != 1) return ACSE_ERR_ARG;
+    if (o->refine && (o->singlet || o->refine_tol < 0.0 || !(o->refine_tol == o->refine_tol) ||
+                      (o->refine_slices != 0 && (o->refine_slices < 4 || o->refine_slices > 10))))
+        return ACSE_ERR_ARG;
     acse_ctx* c = (acse_ctx*)calloc(1, sizeof(acse_ctx));
     if (!c) return ACSE_ERR_NOMEM;
     c->opt = *o;
@@ -200,6 +204,14 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     if (s == ACSE_OK && (kh == cudaMemcpyHostToDevice || kv == cudaMemcpyHostToDevice) &&
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         s = ACSE_ERR_CUDA;
+    if (s == ACSE_OK && o->refine) {   // the FP64-accurate context the schedule switches to
+        acse_opts f = *o;
+        f.prec = ACSE_OZAKI;
+        f.oz_slices = o->refine_slices ? o->refine_slices : 8;
+        f.refine = 0;
+        s = acse_create(&c->fine, &f, c->w.h, c->w.V, stream);
+        c->sched_n2 = -1.0;
+    }
     if (s != ACSE_OK) {
         ny_free(c);
         oz_plan_destroy(c);
@@ -218,6 +230,7 @@ extern "C" int acse_destroy(acse_ctx* c) {
     for (int i = 0; i < 2 * ACSE_PROF_MAX; ++i)
         if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
     if (c->shadow) acse_destroy(c->shadow);
+    if (c->fine) acse_destroy(c->fine);
     for (int b = 0; b < 3; ++b) {
         if (c->aux[b]) cudaStreamDestroy(c->aux[b]);
         if (c->ev_join[b]) cudaEventDestroy(c->ev_join[b]);
@@ -434,6 +447,7 @@ static int put_scalar(acse_ctx* c, double* dst, const double* src_dev, int* need
 // ------------------------------------------------------------------------------ energy
 extern "C" int acse_energy(acse_ctx* c, const double* Daa, const double* Dab, const double* Dbb, double* E) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->refined) return latch(c, acse_energy(c->fine, Daa, Dab, Dbb, E));
     if (!E) return latch(c, ACSE_ERR_ARG);
     const double* D[3];
     int host_in = 0, sync = 0;
@@ -448,6 +462,7 @@ extern "C" int acse_energy(acse_ctx* c, const double* Daa, const double* Dab, co
 extern "C" int acse_residual(acse_ctx* c, const double* Daa, const double* Dab, const double* Dbb, double* Aaa,
                              double* Aab, double* Abb, double* norm2) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->refined) return latch(c, acse_residual(c->fine, Daa, Dab, Dbb, Aaa, Aab, Abb, norm2));
     const double* D[3];
     int host_in = 0, sync = 0;
     int s = stage_inputs(c, Daa, Dab, Dbb, D, &host_in);
@@ -482,9 +497,38 @@ extern "C" int acse_residual(acse_ctx* c, const double* Daa, const double* Dab, 
 }
 
 // -------------------------------------------------------------------------------- step
+static int step_impl(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double eps, double* E_out,
+                     double* norm2_out, double* eps_used);
+
+// Precision schedule: after a step in the starting precision, read ||A||^2 at the D before the step and
+// switch once it has fallen by less than refine_tol (relative) since the previous step, or risen; the
+// line-search state (the next trial step) moves to the FP64-accurate context with the switch.
+static int sched_after_step(acse_ctx* c) {
+    double n2 = 0.0;
+    ACSE_CUDA_TRY(cudaMemcpyAsync(&n2, c->w.scal + 0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double tol = c->opt.refine_tol > 0.0 ? c->opt.refine_tol : 1e-2;
+    c->sched_steps++;
+    if (c->sched_n2 > 0.0 && !(c->sched_n2 - n2 >= tol * c->sched_n2)) {
+        ACSE_CUDA_TRY(cudaMemcpyAsync(c->fine->w.scal + 2, c->w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice,
+                                      c->stream));
+        c->refined = 1;
+    }
+    c->sched_n2 = n2;
+    return ACSE_OK;
+}
+
 extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double eps, double* E_out,
                          double* norm2_out, double* eps_used) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->refined) return latch(c, acse_step(c->fine, Daa, Dab, Dbb, eps, E_out, norm2_out, eps_used));
+    int s = step_impl(c, Daa, Dab, Dbb, eps, E_out, norm2_out, eps_used);
+    if (s == ACSE_OK && c->fine) s = sched_after_step(c);
+    return latch(c, s);
+}
+
+static int step_impl(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double eps, double* E_out,
+                     double* norm2_out, double* eps_used) {
     Work& w = c->w;
     const double* Din[3];
     int host_in = 0, sync = 0;
@@ -531,7 +575,7 @@ extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, dou
     if (s == ACSE_OK) s = put_scalar(c, norm2_out, w.scal + 0, &sync);
     if (s == ACSE_OK) s = put_scalar(c, eps_used, w.scal + 3, &sync);
     if (s == ACSE_OK && sync) s = sync_and_status(c);
-    return latch(c, s);
+    return s;
 }
 
 extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps, double wE,
@@ -545,6 +589,7 @@ extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, 
         acse_opts o = c->opt;
         o.prec = ACSE_FP64;
         o.line_search = 0;
+        o.refine = 0;
         const int s = acse_create(&c->shadow, &o, c->w.h, c->w.V, (void*)c->stream);
         if (s != ACSE_OK) {
             c->shadow = nullptr;
@@ -591,6 +636,7 @@ static int prof_drain(acse_ctx* c) {
 
 extern "C" int acse_profile(acse_ctx* c, int enable) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->fine) ACSE_TRY(acse_profile(c->fine, enable));
     int s = prof_drain(c);
     c->prof_on = enable;
     c->prof_ms = 0.0;
@@ -602,15 +648,22 @@ extern "C" int acse_profile(acse_ctx* c, int enable) {
 extern "C" int acse_profile_read(acse_ctx* c, double* gemm_ms, long long* gemm_launches, long long* launches) {
     if (!c) return ACSE_ERR_ARG;
     int s = prof_drain(c);
-    if (gemm_ms) *gemm_ms = c->prof_ms;
-    if (gemm_launches) *gemm_launches = c->prof_count;
-    if (launches) *launches = c->launches;
+    double fm = 0.0;
+    long long fg = 0, fl = 0;
+    if (s == ACSE_OK && c->fine) s = acse_profile_read(c->fine, &fm, &fg, &fl);
+    if (gemm_ms) *gemm_ms = c->prof_ms + fm;
+    if (gemm_launches) *gemm_launches = c->prof_count + fg;
+    if (launches) *launches = c->launches + fl;
     return latch(c, s);
 }
 
 // ------------------------------------------------------------------------------ status
 extern "C" int acse_sync_status(acse_ctx* c) {
     if (!c) return ACSE_ERR_ARG;
+    if (c->fine) {
+        const int sf = acse_sync_status(c->fine);
+        if (sf != ACSE_OK) return latch(c, sf);
+    }
     return latch(c, sync_and_status(c));
 }
 

@@ -168,6 +168,12 @@ struct acse_ctx {
     cudaEvent_t prof_ev[2 * 256];
     double prof_ms;       // summed GEMM time of pairs already read back
     long long prof_count;
+    // precision schedule (opts.refine): the FP64-accurate context the steps continue in, whether the
+    // switch has happened, and ||A||^2 of the last step taken before it (host copy; < 0: none yet)
+    struct acse_ctx* fine;
+    int refined;
+    double sched_n2;
+    int sched_steps;      // steps taken in the starting precision
 };
 #define ACSE_PROF_MAX 256
 

@@ -2,7 +2,8 @@
 
 `acse_create` validates the options (include/acse.h: 2 <= r <= 64, N >= 2, electrons per spin <= r,
 a known precision, 4..10 Ozaki slices, a known reconstruction, n_alpha = n_beta for the spin-flip
-option, a non-empty active range inside [0, r)) before it allocates anything or touches the device;
+option, a non-empty active range inside [0, r), a precision schedule that is off or on, without the
+spin-flip option, with 4..10 slices and a finite threshold >= 0) before it allocates anything or touches the device;
 `acse_energy_noalloc` rejects null pointers, empty shapes and r above its static scratch first;
 `acse_batch_create` rejects 0 or more than 64 instances, mixed precisions, the NY reconstruction and
 the Ozaki precision; the entry points taking a context or a batch reject a null one.  Each case must
@@ -54,6 +55,9 @@ def _create(L, opts, with_h=True, with_V=True, with_out=True):
     (dict(singlet=1, n_alpha=3, n_beta=2), ARG),
     (dict(mask_active=1, act_lo=2, act_hi=2), SHAPE), (dict(mask_active=1, act_lo=-1, act_hi=3), SHAPE),
     (dict(mask_active=1, act_lo=0, act_hi=7), SHAPE),
+    (dict(refine=2), ARG), (dict(refine=1, singlet=1), ARG), (dict(refine=1, refine_slices=3), ARG),
+    (dict(refine=1, refine_slices=11), ARG), (dict(refine=1, refine_tol=-1e-3), ARG),
+    (dict(refine=1, refine_tol=float("nan")), ARG),
 ])
 def test_create_rejects_invalid_options(L, kw, want):
     assert _create(L, _opts(**kw)) == want

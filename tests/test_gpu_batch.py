@@ -107,6 +107,24 @@ def test_batch_config4_sixteen_instances(libs):
             Es, _, _ = ctx.step(D, eps)
         assert E[i] == pytest.approx(float(Es), rel=1e-11), p.name
         ctx.close()
+    # the two r = 12 instances (ground state and second root) against the FP64 oracle's own trajectory:
+    # the split-precision error of a step is about 1e-5 of what the step changes (E and D)
+    for i in (0, 1):
+        p = probs[i]
+        K = O.reduced_hamiltonian(p.h, p.V, p.N)
+        D0 = O.so_from_blocks(p.Daa, p.Dab, p.Dbb)
+        want = O.run_acse(p.h, p.V, p.N, D0, eps, int(S[i]))
+        got = tuple(np.zeros_like(p.Daa) for _ in range(3))
+        _lib.acse_batch_get_D(b, i, *got)
+        Dw = O.blocks_from_so(want["D"])
+        dD = max(np.abs(g - w).max() for g, w in zip(got, Dw))
+        moved = max(np.abs(w - d).max() for w, d in zip(Dw, (p.Daa, p.Dab, p.Dbb)))
+        drop = abs(want["E"][-1] - want["E"][0])
+        print(f"{p.name}: |E - E_oracle| {abs(E[i] - want['E'][-1]):.2e} of a drop {drop:.3f}; "
+              f"max |D - D_oracle| {dD:.2e} of a change {moved:.3e}")
+        assert abs(E[i] - want["E"][-1]) < 1e-5 * drop
+        assert dD < 1e-5 * moved
+        assert O.energy(K, O.so_from_blocks(*got)) == pytest.approx(E[i], abs=1e-9)
     tune, split, launches = _lib.acse_batch_info(b)
     print(f"config 4 batch: tile choice {tune} (split r^2 {split}), steps {list(S)}, reasons {list(R)}")
     _lib.acse_batch_destroy(b)

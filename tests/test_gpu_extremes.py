@@ -13,7 +13,8 @@ from tests.gpu_helpers import maxrel, oracle_residual_blocks, to_np
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "ozaki": 1e-12, "bf16x3": 5e-4, "tf32x3": 5e-5, "tf32": 2e-2}
+# split precisions: about five times the largest error measured on a GB300 at r = 2 (1.2e-5, 3.4e-7, 7.1e-4)
+TOL = {"fp64": 1e-12, "ozaki": 1e-12, "bf16x3": 6e-5, "tf32x3": 2e-6, "tf32": 3.5e-3}
 
 
 @pytest.fixture(scope="module")

@@ -29,7 +29,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 R = 48
 # normwise relative tolerances on sampled entries: FP64 sums of ~r^3 terms per entry; BF16x3 as in
 # the small-size tests (about 2^-16 per product, some cancellation between GEMM outputs)
-TOL_ENT = {"fp64": 1e-11, "ozaki": 1e-11, "bf16x3": 5e-4}
+# BF16x3: about five times the largest error measured on a GB300 (1.1e-5 on the random pair tensor)
+TOL_ENT = {"fp64": 1e-11, "ozaki": 1e-11, "bf16x3": 5e-5}
 
 
 @pytest.fixture(scope="module")
@@ -124,7 +125,7 @@ def test_fullsize_invariants(acse, prec):
     assert float(n2s) == pytest.approx(n2, rel=1e-12)
     U = tuple((a - b) / eps for a, b in zip(to_np(D), (p.Daa, p.Dab, p.Dbb)))
     trKU = np.sum(Kb[0] * U[0]) + np.sum(Kb[2] * U[2]) + 4 * np.sum(Kb[1] * U[1])
-    tol = 1e-9 if f64 else 2e-4
+    tol = 1e-9 if f64 else 1e-6        # BF16x3: Tr(KU) + ||A||^2 measured 1.7e-7 relative
     print(f"r=48 {prec}: ||A||^2 {n2:.6e}, Tr(KU) {trKU:.6e}, dE/eps {(E1 - E0) / eps:.6e}")
     assert trKU == pytest.approx(-n2, rel=tol)
     assert (E1 - E0) / eps == pytest.approx(trKU, rel=1e-6)
@@ -174,11 +175,47 @@ def test_golden_line_search_trajectory(acse, prec):
         # FP64-accurate paths: exact agreement while the merit falls; in the flat regime a flipped
         # curvature branch changes one step's eps, so E may move by a step's eps ||A||^2 (about 1e-7 Eh
         # here), below the 1e-6 Eh stopping threshold
-        assert de < 1e-7 and dn < 1e-9 and dE < 1e-9 and dE_all.max() < 1e-6
+        # (measured: eps 9.6e-13, ||A||^2 3.0e-10, E 1.3e-12 Eh on the conditioned steps)
+        assert de < 1e-11 and dn < 2e-9 and dE < 1e-10 and dE_all.max() < 1e-6
     else:
         # BF16x3 noise in f (about 3e-5 relative) moves the accepted eps by about 1e-4 relative, and
         # each step changes E by eps ||A||^2 (up to 4 Eh here): E may drift by about 1e-4 of the total
         # drop over the conditioned steps; in the flat regime the mixed run may keep stepping
-        assert de < 1e-2 and dn < 1e-3
-        assert dE < 1e-4 * drop and dE_all.max() < 1e-3 * drop
+        # (measured: eps 8.9e-5, ||A||^2 2.2e-5, E 9.3e-5 Eh conditioned, 5.5e-3 Eh over all steps)
+        assert de < 5e-4 and dn < 1e-4
+        assert dE < 5e-4 and dE_all.max() < 1e-3 * drop
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki", "bf16x3"])
+def test_golden_config3_fixed_step_trajectory(acse, prec):
+    """The headline r = 48 CAS(8e,8o) workload: five Euler steps at eps = 1e-4 against the stored oracle
+    trajectory (tests/golden/cfg3_fixed_eps_5.json, written by make_golden.py from the oracle alone):
+    E and ||A||^2 at every step and 64 seeded entries of each block of D_5.  FP64-accurate paths: 1e-10 Eh
+    on E and 1e-12 relative on ||A||^2 and D; BF16x3: its error grows with what the steps change, a bound
+    of 1e-5 of the energy drop so far (measured 8e-6 Eh after the first step, whose drop is 6 Eh)."""
+    g = json.load(open(os.path.join(HERE, "golden", "cfg3_fixed_eps_5.json")))
+    p = I.config_problem(3)
+    assert p.name == g["system"] and p.r == R
+    ctx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec)
+    D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    E0 = float(ctx.energy(D))
+    assert E0 == pytest.approx(g["E"][0], abs=1e-10)
+    dEs, dNs = [], []
+    for k in range(g["nsteps"]):
+        E, n2, _ = ctx.step(D, g["eps"])
+        dEs.append(abs(float(E) - g["E"][k + 1]))
+        dNs.append(abs(float(n2) / g["norm2"][k] - 1.0))
+    idx = np.array(g["D_final_index"])
+    got = to_np(D)
+    dD = max(np.abs(got[s][tuple(idx[s].T)] - np.array(g["D_final_aa_ab_bb"][s])).max() for s in range(3))
+    scale = max(np.abs(np.array(v)).max() for v in g["D_final_aa_ab_bb"])
+    print(f"{prec} config 3: per-step |dE| " + " ".join(f"{x:.2e}" for x in dEs) +
+          f"; max rel ||A||^2 {max(dNs):.2e}; sampled D_5 {dD / scale:.2e}")
+    if prec in ("fp64", "ozaki"):
+        assert max(dEs) < 1e-10 and max(dNs) < 1e-12 and dD < 1e-12 * scale
+    else:
+        for k, d in enumerate(dEs):
+            assert d < 1e-5 * abs(g["E"][k + 1] - g["E"][0]), f"step {k}"
+        assert max(dNs) < 1e-4 and dD < 1e-4 * scale
     ctx.close()

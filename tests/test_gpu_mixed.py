@@ -1,11 +1,12 @@
 """Split-precision (BF16x3, TF32) tensor-core path vs the FP64 oracle and the FP64 GPU path.
 
-Tolerances (normwise relative, max|dA| / max|A|): BF16x3 represents each operand as hi + lo with
-about 16 significant bits and drops the lo.lo product, so each product carries a relative error
-of about 2^-16 = 1.5e-5 before FP32 accumulation; the residual combines GEMM outputs of similar
-size with some cancellation, hence 5e-4.  TF32 (one product, 11 significant bits, 2^-11 = 4.9e-4
-per product) gets 2e-2.  TF32x3 (hi + lo in tf32, about 2^-21 per product, then limited by the FP32
-intermediates M, Z, w, B and the FP32 accumulation) gets 5e-5.
+Tolerances (normwise relative, max|dA| / max|A|), about five times the largest error measured on a
+GB300 over these cases: BF16x3 represents each operand as hi + lo with about 16 significant bits and
+drops the lo.lo product (about 2^-16 = 1.5e-5 relative per product before FP32 accumulation; measured
+3.9e-6 ... 5.5e-6 on the residual): 3e-5.  TF32 (one product, 11 significant bits, 2^-11 = 4.9e-4 per
+product; measured 1.6e-4 ... 3.0e-4): 1.5e-3.  TF32x3 (hi + lo in tf32, about 2^-21 per product, then
+limited by the FP32 intermediates M, Z, w, B and the FP32 accumulation; measured 2.3e-7 ... 3.6e-6):
+2e-5.  ||A||^2 (relative; measured up to 2.9e-6, 4.8e-5 and 5.9e-6): NTOL.
 """
 import numpy as np
 import pytest
@@ -17,7 +18,8 @@ from tests.gpu_helpers import maxrel, oracle_residual_blocks, oracle_step_blocks
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x3": 5e-4, "tf32": 2e-2, "tf32x3": 5e-5}
+TOL = {"bf16x3": 3e-5, "tf32": 1.5e-3, "tf32x3": 2e-5}
+NTOL = {"bf16x3": 1.5e-5, "tf32": 2.5e-4, "tf32x3": 3e-5}
 
 
 @pytest.fixture(scope="module")
@@ -50,7 +52,7 @@ def test_residual_parity_mixed(acse, prec, r, na, nb, kind):
     err = maxrel(to_np(A), want)
     print(f"{prec} r={r}: max rel err {err:.3e}, norm2 rel err {abs(float(n2) - n2w) / n2w:.3e}")
     assert err < TOL[prec]
-    assert float(n2) == pytest.approx(n2w, rel=4 * TOL[prec])
+    assert float(n2) == pytest.approx(n2w, rel=NTOL[prec])
     ctx.close()
 
 
@@ -67,7 +69,8 @@ def test_step_parity_mixed(acse, prec):
     err = maxrel(Ug, Uw)
     print(f"{prec} step: U rel err {err:.3e}, E err {abs(float(E) - Ew):.3e}")
     assert err < 2 * TOL[prec]
-    assert abs(float(E) - Ew) < {"bf16x3": 1e-6, "tf32x3": 1e-7, "tf32": 1e-4}[prec]
+    # measured 7.5e-9, 3.8e-9, 5.5e-8 Eh
+    assert abs(float(E) - Ew) < {"bf16x3": 4e-8, "tf32x3": 2e-8, "tf32": 3e-7}[prec]
     ctx.close()
 
 
@@ -90,7 +93,10 @@ def test_mixed_vs_fp64_gpu_config2(acse):
         Emx, _, _ = cmx.step(Dmx, 1e-3)
         dE.append(abs(float(Emx) - float(E64)))
     print("per-step |E_bf16x3 - E_fp64|:", " ".join(f"{x:.2e}" for x in dE))
-    assert max(dE) < 1e-3
+    # the split-precision error of E grows about linearly with the steps (measured 8.2e-7 after the first
+    # step, 8.4e-5 after the tenth): a bound of about five times that per step
+    for n, d in enumerate(dE):
+        assert d < 5e-6 + 5e-5 * n, f"step {n}: {d:.2e}"
     c64.close()
     cmx.close()
 

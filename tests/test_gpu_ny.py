@@ -15,7 +15,8 @@ from tests.gpu_helpers import maxrel, to_np
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "bf16x3": 5e-4, "tf32x3": 5e-5}
+# split precisions: about five times the largest normwise error measured on a GB300 (9.7e-6, 1.4e-6)
+TOL = {"fp64": 1e-12, "bf16x3": 5e-5, "tf32x3": 7e-6}
 
 
 @pytest.fixture(scope="module")

@@ -16,7 +16,8 @@ from tests.gpu_helpers import maxrel, oracle_residual_blocks, oracle_step_blocks
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x3": 5e-4, "tf32": 2e-2, "tf32x3": 5e-5}
+# about five times the largest normwise error measured on a GB300 (1.2e-5, 4.9e-4, 3.4e-6)
+TOL = {"bf16x3": 6e-5, "tf32": 2.5e-3, "tf32x3": 1.5e-5}
 
 
 @pytest.fixture(scope="module")
@@ -112,7 +113,7 @@ def test_singlet_trajectory_config2(acse):
         Es, _, _ = cs.step(Ds, 1e-3)
         Eg, _, _ = cg.step(Dg, 1e-3)
         E64, _, _ = c64.step(D64, 1e-3)
-        assert abs(float(Es) - float(E64)) < 1e-3, f"step {k}"
+        assert abs(float(Es) - float(E64)) < 5e-4, f"step {k}"   # BF16x3 vs FP64: 8.4e-5 after 10 steps
         assert abs(float(Es) - float(Eg)) < 1e-4, f"step {k}"
     got = to_np(Ds)
     assert np.array_equal(got[0], got[2])
