@@ -117,9 +117,13 @@ typedef struct {
 /* Create a context for one problem.  h (r*r) and V (r^4, chemist's (pq|rs)) are read once to
  * build the spin-blocked reduced Hamiltonian K of Eq. (2); they may be freed afterwards.
  * `cuda_stream` is a cudaStream_t (NULL = legacy default stream) on which every call of this
- * context is ordered.  All device workspace is allocated here (about 40 r^4 doubles plus the
- * split-precision operand copies), so later calls allocate nothing.  On any failure *ctx is set
- * to NULL (when ctx itself is not NULL) and nothing stays allocated. */
+ * context is ordered.  All device workspace of the forward calls is allocated here (about 40 r^4
+ * doubles plus the split-precision operand copies, and the FP64-accurate context of a precision
+ * schedule), so acse_energy, acse_residual and acse_step allocate nothing.  The one exception is
+ * acse_residual_backward: its first call on a context allocates the adjoint workspace (about 65 r^4
+ * doubles, 2.8 GB at r = 48) and, for a split precision, the FP64 companion context; both stay until
+ * acse_destroy.  On any failure *ctx is set to NULL (when ctx itself is not NULL) and nothing stays
+ * allocated. */
 int acse_create(acse_ctx** ctx, const acse_opts* opts, const double* h, const double* V,
                 void* cuda_stream);
 
@@ -161,6 +165,11 @@ int acse_step(acse_ctx* ctx, double* Daa, double* Dab, double* Dbb, double eps,
 int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_steps, double eps,
                            double wE, double wN, double* dh, double* dV,
                            double* dDaa, double* dDab, double* dDbb);
+
+/* State of the precision schedule (opts.refine): *refined = 1 once acse_step has switched to the
+ * FP64-accurate precision, *steps = the steps taken in the starting precision (host pointers, each may be
+ * NULL; both 0 without a schedule). */
+int acse_schedule_state(const acse_ctx* ctx, int* refined, int* steps);
 
 /* Batched propagation: n independent instances (electronic states, or molecules with different r)
  * advanced together.  Each Euler step runs one grouped GEMM launch per contraction pass over all

@@ -18,7 +18,7 @@ EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_
            "acse_residual_backward", "acse_profile", "acse_profile_read", "acse_sync_status",
            "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_batch_create",
            "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D", "acse_batch_run", "acse_batch_info",
-           "acse_extrapolate", "acse_batch_history", "acse_batch_extrapolate",
+           "acse_extrapolate", "acse_batch_history", "acse_batch_extrapolate", "acse_schedule_state",
            "acse_strerror", "acse_last_error", "acse_version")
 
 
@@ -71,6 +71,8 @@ def lib():
         L.acse_extrapolate.argtypes = [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
         L.acse_batch_history.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, POINTER(c_int)]
         L.acse_batch_extrapolate.argtypes = [c_void_p, c_int, c_void_p]
+        L.acse_schedule_state.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int)]
+        L.acse_schedule_state.restype = c_int
         for name in ("acse_batch_create", "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D",
                      "acse_batch_run", "acse_batch_info", "acse_extrapolate", "acse_batch_history",
                      "acse_batch_extrapolate"):
@@ -285,3 +287,11 @@ def acse_batch_extrapolate(b, n, n_skip=0):
     out = np.zeros(6 * n)
     _check(lib().acse_batch_extrapolate(b, int(n_skip), out.ctypes.data), "acse_batch_extrapolate")
     return [dict(zip(FIT_KEYS, out[6 * i:6 * i + 6])) for i in range(n)]
+
+
+def acse_schedule_state(ctx):
+    """(switched to the FP64-accurate precision, steps taken in the starting precision)."""
+    r = c_int()
+    n = c_int()
+    _check(lib().acse_schedule_state(ctx, byref(r), byref(n)), "acse_schedule_state")
+    return bool(r.value), n.value

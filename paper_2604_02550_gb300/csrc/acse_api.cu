@@ -578,6 +578,13 @@ static int step_impl(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double 
     return s;
 }
 
+extern "C" int acse_schedule_state(const acse_ctx* c, int* refined, int* steps) {
+    if (!c) return ACSE_ERR_ARG;
+    if (refined) *refined = c->refined;
+    if (steps) *steps = c->sched_steps;
+    return ACSE_OK;
+}
+
 extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, int n_steps, double eps, double wE,
                                       double wN, double* dh, double* dV, double* dDaa, double* dDab, double* dDbb) {
     if (!c) return ACSE_ERR_ARG;

@@ -82,13 +82,14 @@ def test_fit_of_stored_line_search_trajectory(lib):
 
 
 def test_batch_record_and_fit_fp64(lib):
-    """FP64 batch of the config-2 system and a second seed at eps = 1e-3 for 30 steps (no stopping rule):
+    """FP64 batch of the config-2 system and a second seed at eps = 3e-4 for 30 steps (no stopping rule; the
+    second seed diverges at 1e-3):
     the record is the trajectory of the batch's own energies, and the device fit of every record matches
     the oracle's fit of the same points."""
     probs = [I.config_problem(2, 0), I.config_problem(2, 1)]
     b = lib.acse_batch_create(probs, "fp64")
     for i, p in enumerate(probs):
-        lib.acse_batch_set_D(b, i, p.Daa, p.Dab, p.Dbb, 1e-3)
+        lib.acse_batch_set_D(b, i, p.Daa, p.Dab, p.Dbb, 3e-4)
     E_last = None
     for _ in range(30):
         E_last, _, _, _ = lib.acse_batch_run(b, len(probs), 1, stop_rule=False)
@@ -96,7 +97,7 @@ def test_batch_record_and_fit_fp64(lib):
     for i in range(len(probs)):
         lam, E = lib.acse_batch_history(b, i)
         assert lam.size == 31
-        assert np.allclose(lam, 1e-3 * np.arange(31), rtol=0, atol=1e-15)
+        assert np.allclose(lam, 3e-4 * np.arange(31), rtol=0, atol=1e-15)
         assert E[-1] == E_last[i]
         _compare(fits[i], X.fit(lam, E, 2))
     lib.acse_batch_destroy(b)
