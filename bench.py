@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--cap", type=int, default=100, help="step cap of --time-to-e")
     ap.add_argument("--line-search", action="store_true", help="--time-to-e with the line search (one context)")
     ap.add_argument("--adjoint", action="store_true",
-                    help="adjoint cost relative to the forward steps (FP64, r = 24 CAS(6e,6o), 4 steps)")
+                    help="adjoint cost relative to the forward steps (FP64 and Ozaki, r = 32 CAS(6e,6o), 4 steps)")
     return ap.parse_args()
 
 
@@ -408,20 +408,15 @@ def run_time_to_e_line_search(args):
 
 
 def run_adjoint_cost(args):
-    """Adjoint cost relative to forward: n FP64 Euler steps through acse_step vs one
-    acse_residual_backward over the same n steps with every checkpoint given."""
+    """Adjoint cost relative to forward on the r = 32 CAS(6e,6o) workload: n Euler steps through acse_step vs
+    one acse_residual_backward over the same n steps (every checkpoint given, and only D_0), for the FP64
+    FMA path and the Ozaki path (every GEMM of the reverse sweep on the BF16 tensor cores)."""
     import torch
     from paper_2604_02550_gb300 import api
-    p = workload(24)
-    n, eps = 4, 1e-3
-    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "fp64")
-    D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
-    ck = [tuple(x.clone() for x in D)]
-    for _ in range(n):
-        ctx.step(D, eps)
-        ck.append(tuple(x.clone() for x in D))
-    ctx.backward(ck, n, eps, 1.0, 0.5)                    # warm-up (allocates the adjoint workspace)
-    torch.cuda.synchronize()
+    p = workload(32)
+    n, eps = 4, 1e-4
+    out = {"metric": "adjoint_cost_ratio", "workload": p.name, "steps": n, "eps": eps,
+           "objective": "E(D_n) + 0.5 ||A(D_n)||^2", "runs": {}}
 
     def timed(fn, reps=3):
         best = 1e30
@@ -435,20 +430,31 @@ def run_adjoint_cost(args):
             best = min(best, e0.elapsed_time(e1))
         return best
 
-    def fwd():
-        Dw = tuple(x.clone() for x in ck[0])
+    for prec in ("fp64", "ozaki"):
+        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec)
+        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+        ck = [tuple(x.clone() for x in D)]
         for _ in range(n):
-            ctx.step(Dw, eps)
+            ctx.step(D, eps)
+            ck.append(tuple(x.clone() for x in D))
+        ctx.backward(ck, n, eps, 1.0, 0.5)                    # warm-up (allocates the adjoint workspace)
+        torch.cuda.synchronize()
 
-    t_f = timed(fwd)
-    t_b = timed(lambda: ctx.backward(ck, n, eps, 1.0, 0.5))
-    ck_sparse = [ck[0]] + [None] * n                       # only D_0: every D_k recomputed
-    t_b0 = timed(lambda: ctx.backward(ck_sparse, n, eps, 1.0, 0.5))
-    ctx.close()
-    print(json.dumps({"metric": "adjoint_cost_ratio", "workload": p.name, "prec": "fp64", "steps": n, "eps": eps,
-                      "forward_ms": t_f, "backward_ms_all_checkpoints": t_b, "ratio_all_checkpoints": t_b / t_f,
-                      "backward_ms_only_D0": t_b0, "ratio_only_D0": t_b0 / t_f,
-                      "objective": "E(D_n) + 0.5 ||A(D_n)||^2"}), flush=True)
+        def fwd():
+            Dw = tuple(x.clone() for x in ck[0])
+            for _ in range(n):
+                ctx.step(Dw, eps)
+
+        t_f = timed(fwd)
+        t_b = timed(lambda: ctx.backward(ck, n, eps, 1.0, 0.5))
+        ck_sparse = [ck[0]] + [None] * n                       # only D_0: every D_k recomputed
+        t_b0 = timed(lambda: ctx.backward(ck_sparse, n, eps, 1.0, 0.5))
+        ctx.close()
+        out["runs"][prec] = {"forward_ms": t_f, "backward_ms_all_checkpoints": t_b, "ratio_all_checkpoints": t_b / t_f,
+                             "backward_ms_only_D0": t_b0, "ratio_only_D0": t_b0 / t_f}
+    out["backward_speedup_ozaki_vs_fp64"] = (out["runs"]["fp64"]["backward_ms_all_checkpoints"] /
+                                             out["runs"]["ozaki"]["backward_ms_all_checkpoints"])
+    print(json.dumps(out), flush=True)
 
 
 def main():

@@ -640,7 +640,7 @@ static int vjp_D(acse_ctx* c, const double* const W[3], int sW, double scale, co
     g[n++] = GemmF64{a->X5bd, w.Zd, a->Mbd, R22, R22, R22, R22, R22, R22, 1.0, 0.0, 0, 1, 1};
     g[n++] = GemmF64{a->X5bf[0], w.Zf1, a->Mbf[0], R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 1, 1};
     g[n++] = GemmF64{a->X5bf[1], w.Zf2, a->Mbf[1], R2, R2, R2, R2, R2, R2, 1.0, 0.0, 0, 1, 1};
-    ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
+    ACSE_TRY(c->oz ? oz_gemm_list(c, g, n, 0) : gemm_f64_grouped(c, g, n, c->stream));
     // w routes into the diagonals of Z; then Zb -> gbar
     k_adj_w_to_Z<<<ad_grid(2 * (size_t)R2 * r), AD_TPB, 0, c->stream>>>(r, a->wb, a->Zbd, a->Zbf[0], a->Zbf[1]);
     AL(c);
@@ -661,7 +661,7 @@ static int vjp_D(acse_ctx* c, const double* const W[3], int sW, double scale, co
         g[n++] = GemmF64{a->Xb[s], W[s], a->Mb[s], R2, R2, R2, R2, R2, R2, f, 1.0, 0, 0, 1};
         g[n++] = GemmF64{a->Yb[s], W[s], Dacc[s], R2, R2, R2, R2, R2, R2, f, 1.0, 0, 0, 1};
     }
-    ACSE_TRY(gemm_f64_grouped(c, g, n, c->stream));
+    ACSE_TRY(c->oz ? oz_gemm_list(c, g, n, 1) : gemm_f64_grouped(c, g, n, c->stream));
     k_adj_M_gamma<<<2 * R2, AD_TPB, 0, c->stream>>>(r, a->Mb[0], a->Mb[1], a->Mb[2], w.gam, a->gb);
     AL(c);
     k_adj_to_D<<<ad_grid(3 * n4), AD_TPB, 0, c->stream>>>(r, 2.0 / (c->N - 1), a->Mb[0], a->Mb[1], a->Mb[2], a->gb,

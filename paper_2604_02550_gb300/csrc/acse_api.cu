@@ -591,10 +591,13 @@ extern "C" int acse_residual_backward(acse_ctx* c, const double* const* D_ckpt, 
     if (c->opt.recon != ACSE_RECON_V) return latch(c, ACSE_ERR_UNSUPPORTED);
     if (c->opt.prec == ACSE_FP64)
         return latch(c, acse_residual_backward_impl(c, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
-    // split precision: the reverse sweep runs in an FP64 companion context (same h, V, options)
+    // split precision: the reverse sweep runs in an FP64-accurate companion context (same h, V, options;
+    // the Ozaki precision, so that its GEMMs run on the tensor cores too)
     if (!c->shadow) {
         acse_opts o = c->opt;
-        o.prec = ACSE_FP64;
+        o.prec = ACSE_OZAKI;
+        o.oz_slices = 8;
+        o.singlet = 0;
         o.line_search = 0;
         o.refine = 0;
         const int s = acse_create(&c->shadow, &o, c->w.h, c->w.V, (void*)c->stream);

@@ -220,6 +220,7 @@ int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
 int launch_build_B(acse_ctx* c);
 int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32[3]);
 int launch_B_tiled(acse_ctx* c);
+int launch_Z_tc(acse_ctx* c, const float* const W32[3], int ntypes, const int* tmap);   // acse_ztc.cu
 int tiled_set_attrs();
 int launch_Q(acse_ctx* c);
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3],
@@ -244,6 +245,9 @@ void oz_plan_destroy(acse_ctx* c);
 int oz_slice_operands(acse_ctx* c, int prep_D);   // the pass's FP64 operands -> scaled bf16 slices
 int oz_gemm_launch(acse_ctx* c);                   // every GEMM of the pass, one persistent launch
 int oz_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall);
+// Any list of up to 12 FP64 GEMMs (alpha a power of two, beta 0 or 1, operands possibly transposed) by
+// the Ozaki scheme; `slot` (0 or 1) names the list's plan, built on its first use (the adjoint's lists)
+int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot);
 
 // contraction pass in three phases (acse_api.cu): operands, the O(r^6) GEMMs, assembly
 int acse_contract_pre(acse_ctx* c, const double* const D[3], const double* const W[3], int prep_D);

@@ -962,6 +962,14 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
         o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : (c->opt.prec == ACSE_TF32X3 ? 3 : 2);
         o.ldd = c->nsplit * w.Kp2; o.ldf = c->nsplit * w.Kp1; o.Kp1 = w.Kp1; o.Kp2 = w.Kp2; o.diag = w.zdiag32;
+        // BF16x3 with r a multiple of 16: the products on the tensor cores (acse_ztc.cu)
+        const int zs = launch_Z_tc(c, W32, o.ntypes, o.tmap);
+        if (zs == ACSE_OK) {
+            k_w_from_diag<float><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag32, w.w32, sf ? 1 : 0);
+            ACSE_LAUNCHED(c);
+            return ACSE_OK;
+        }
+        if (zs != ACSE_ERR_UNSUPPORTED) return zs;
         const bool r48 = o.mode == 1 && pad4(r) == 48;
         const void* kern = r48 ? (const void*)k_Z_pipe<1, 48>
                                : o.mode == 1 ? (const void*)k_Z_pipe<1> : o.mode == 3 ? (const void*)k_Z_pipe<3>

@@ -1,0 +1,239 @@
+// Z = 1D . W_kp on the tensor cores (BF16x3 path): the O(r^5) particle-hole operand of a contraction
+// pass, Z^{kp}_{js} = sum_q W^{kp}_{qs} 1D^j_q for the six spin types of k_Z_pipe (acse_tiled.cu), as
+// one tcgen05 GEMM per tile instead of FP32 FMAs on the CUDA cores.
+//
+// Tile: 128 consecutive (p, s) of one (type, k), i.e. rows m = p r + s of W_k^T; per tile
+//     D[m][j] = sum_q W_kp[q][s] 1D[j][q]          (UMMA M = 128, N = r, K = q padded to 64)
+// in BF16x3: A = W^T rows as K segments [hi | lo | hi], B = 1D rows as [hi | hi | lo], so one
+// accumulation over the three 64-element K blocks gives hi.hi + lo.hi + hi.lo in FP32 (TMEM).
+// The 128 threads first convert the tile's W values (FP32, read coalesced, the transposed spin types
+// with 32-byte vector loads) into the 128-byte-swizzled K-major layout the UMMA descriptors expect,
+// one thread per row; one thread issues the MMAs; each warp then reads its TMEM lane quarter (one row
+// m per thread, r columns j) and writes the split Z rows of the particle-hole GEMM operand
+// ([hi | hi | lo] at row (sK, k, j), column (sP, p, s)) and, for j = p, the diagonal rows of w.
+// The wait for the MMAs is bounded; on expiry the kernel raises the device flag and returns.
+// Used for r a multiple of 16 (r <= 64); other r take the FP32 kernel.
+#include <cuda_bf16.h>
+
+#include "acse_internal.h"
+#include "tc_ptx.cuh"
+
+#define ZTC_THREADS 128
+#define ZTC_A_SEG (TC_BM * 128)     // one K block of the A tile: 128 rows x 128 bytes
+#define ZTC_WAIT_NS 4000000000ull
+
+struct ZtcArgs {
+    const float* W[3];      // FP32 W blocks aa, ab, bb (r^4 each)
+    const double* gam;      // 1D per spin [2][r][r]
+    __nv_bfloat16* Zd;      // (2 r^2) rows of ldd elements, K segments of Kp2
+    __nv_bfloat16* Zf[2];   // r^2 rows of ldf elements, K segments of Kp1
+    float* diag;            // [4][r][r][r]: rows j = p of Zd(a,a), Zd(b,b), Zf1, Zf2
+    int ldd, ldf, Kp1, Kp2;
+    int tmap[6];            // block type index -> spin type t
+    int* err;
+};
+
+static __device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Byte offset of the 16-byte chunk c of row n in a 128-byte-swizzled K-major tile (8-row atoms).
+static __device__ __forceinline__ uint32_t sw128(int n, int c) { return (uint32_t)n * 128u + (uint32_t)((c ^ (n & 7)) << 4); }
+
+static __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&x)[8]) {
+    uint4 u;
+    memcpy(&u, x, 16);
+    return u;
+}
+
+template <int R>
+__global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ ZtcArgs a) {
+    static_assert(R % 16 == 0 && R <= 64, "N = r must be a multiple of 16 and K = r fit one 64-element block");
+    constexpr int R2 = R * R, NT = (R2 + TC_BM - 1) / TC_BM;
+    extern __shared__ uint8_t zs_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)zs_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;                                  // 3 K blocks of 128 x 128 B
+    uint8_t* sB = smem + 3 * ZTC_A_SEG;                  // 3 K blocks of R x 128 B
+    uint64_t* bar = (uint64_t*)(sB + 3 * R * 128);
+    uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tb = blockIdx.x / (R * NT);
+    const int t = a.tmap[tb];
+    const int rem = blockIdx.x - tb * R * NT;
+    const int k = rem / NT;
+    const int m0 = (rem - k * NT) * TC_BM;
+    const size_t r3 = (size_t)R * R2;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, 64);
+
+    // A: row m = p r + s of W_k^T, K = q; the slice W_kp[q][s] of type t (see k_Z_pipe)
+    {
+        const int ml = threadIdx.x, m = m0 + ml;
+        const bool valid = m < R2;
+        const int p = valid ? m / R : 0, s = valid ? m - p * R : 0;
+        const float* base;
+        bool tr;
+        switch (t) {
+            case 0: tr = false; base = a.W[0] + k * r3 + (size_t)p * R2; break;
+            case 1: tr = false; base = a.W[1] + k * r3 + (size_t)p * R2; break;
+            case 2: tr = true; base = a.W[1] + (size_t)p * r3 + (size_t)k * R2; break;
+            case 3: tr = false; base = a.W[2] + k * r3 + (size_t)p * R2; break;
+            case 4: tr = true; base = a.W[1] + k * r3 + (size_t)p * R2; break;
+            default: tr = false; base = a.W[1] + (size_t)p * r3 + (size_t)k * R2; break;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            __nv_bfloat16 hi[8], lo[8];
+            if (valid && 8 * c < R) {
+                float x[8];
+                if (tr) {   // W_kp[q][s] = base[s R + q]: 32 contiguous bytes per thread
+                    const float4 v0 = *reinterpret_cast<const float4*>(base + (size_t)s * R + 8 * c);
+                    const float4 v1 = *reinterpret_cast<const float4*>(base + (size_t)s * R + 8 * c + 4);
+                    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+                    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+                } else {    // W_kp[q][s] = base[q R + s]: coalesced across the warp's consecutive s
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) x[u] = base[(size_t)(8 * c + u) * R + s];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    hi[u] = __float2bfloat16_rn(x[u]);
+                    lo[u] = __float2bfloat16_rn(x[u] - __bfloat162float(hi[u]));
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) hi[u] = lo[u] = __float2bfloat16_rn(0.f);
+            }
+            const uint32_t off = sw128(ml, c);
+            const uint4 H = pack8(hi), L = pack8(lo);
+            *reinterpret_cast<uint4*>(sA + off) = H;
+            *reinterpret_cast<uint4*>(sA + ZTC_A_SEG + off) = L;
+            *reinterpret_cast<uint4*>(sA + 2 * ZTC_A_SEG + off) = H;
+        }
+    }
+    // B: row j of 1D (spin of type t), K = q
+    {
+        const double* g = a.gam + ((t == 2 || t == 3 || t == 4) ? R2 : 0);
+        for (int e = threadIdx.x; e < R * 8; e += ZTC_THREADS) {
+            const int j = e >> 3, c = e & 7;
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float x = 8 * c + u < R ? (float)g[j * R + 8 * c + u] : 0.f;
+                hi[u] = __float2bfloat16_rn(x);
+                lo[u] = __float2bfloat16_rn(x - __bfloat162float(hi[u]));
+            }
+            const uint32_t off = sw128(j, c);
+            const uint4 H = pack8(hi), L = pack8(lo);
+            *reinterpret_cast<uint4*>(sB + off) = H;
+            *reinterpret_cast<uint4*>(sB + R * 128 + off) = H;
+            *reinterpret_cast<uint4*>(sB + 2 * R * 128 + off) = L;
+        }
+    }
+    fence_proxy_async_smem();   // the generic-proxy writes above, visible to the tensor cores
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = make_idesc<0, R>();
+#pragma unroll
+        for (int seg = 0; seg < 3; ++seg) {
+            const uint64_t da = smem_desc(sA + seg * ZTC_A_SEG);
+            const uint64_t db = smem_desc(sB + seg * R * 128);
+#pragma unroll
+            for (int kk = 0; kk < R / 16; ++kk) umma<0>(tmem, da + 2 * kk, db + 2 * kk, idesc, (seg | kk) != 0);
+        }
+        umma_commit(bar);
+    }
+    const bool ok = bounded_wait(bar, 0, ZTC_WAIT_NS, nullptr);
+    if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+    tc_fence_after();
+    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows m), columns j
+    {
+        const int ml = warp * 32 + lane, m = m0 + ml;
+        const bool valid = ok && m < R2;
+        const int p = m / R, s = m - p * R;
+        int which, sK, sP;
+        if (t < 4) { which = -1; sK = t >> 1; sP = t & 1; }
+        else { which = t - 4; sK = 0; sP = 0; }
+        const int dslot = t == 0 ? 0 : t == 3 ? 1 : t == 4 ? 2 : t == 5 ? 3 : -1;
+        __nv_bfloat16* base = which < 0 ? a.Zd : a.Zf[which];
+        const size_t ld = which < 0 ? (size_t)a.ldd : (size_t)a.ldf;
+        const int Kp = which < 0 ? a.Kp2 : a.Kp1;
+        const size_t col = (size_t)sP * R2 + m;
+        uint32_t v[2][32];
+        __syncwarp();
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v[0]);
+        if (R > 32) tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, v[1]);
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const float x = __uint_as_float(v[j >> 5][j & 31]);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+                __nv_bfloat16* row = base + ((size_t)sK * R2 + (size_t)k * R + j) * ld + col;
+                row[0] = hi;
+                row[Kp] = hi;
+                row[2 * Kp] = lo;
+                if (dslot >= 0 && j == p) a.diag[(((size_t)dslot * R2 + (size_t)k * R + p) * R) + s] = x;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 64);
+    }
+}
+
+template <int R>
+static int ztc_launch(const ZtcArgs& a, int ntypes, cudaStream_t st) {
+    constexpr int R2 = R * R, NT = (R2 + TC_BM - 1) / TC_BM;
+    const size_t smem = 1024 + 3 * (size_t)ZTC_A_SEG + 3 * (size_t)R * 128 + 64;
+    static bool attr = false;
+    if (!attr) {
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_Z_tc<R><<<ntypes * R * NT, ZTC_THREADS, smem, st>>>(a);
+    ACSE_CUDA_TRY(cudaGetLastError());
+    return ACSE_OK;
+}
+
+// Z, its split rows and the diagonal rows of w on the tensor cores (BF16x3 contexts with r a multiple
+// of 16); ACSE_ERR_UNSUPPORTED when the context is outside that range (the caller then uses the FP32
+// kernel).
+int launch_Z_tc(acse_ctx* c, const float* const W32[3], int ntypes, const int* tmap) {
+    const int r = c->r;
+    if (c->opt.prec != ACSE_BF16X3 || r % 16 != 0 || r > 64) return ACSE_ERR_UNSUPPORTED;
+    Work& w = c->w;
+    ZtcArgs a;
+    for (int s = 0; s < 3; ++s) a.W[s] = W32[s];
+    a.gam = w.gam;
+    a.Zd = (__nv_bfloat16*)w.tc_Zd;
+    a.Zf[0] = (__nv_bfloat16*)w.tc_Zf[0];
+    a.Zf[1] = (__nv_bfloat16*)w.tc_Zf[1];
+    a.diag = w.zdiag32;
+    a.Kp1 = w.Kp1;
+    a.Kp2 = w.Kp2;
+    a.ldd = c->nsplit * w.Kp2;
+    a.ldf = c->nsplit * w.Kp1;
+    for (int i = 0; i < 6; ++i) a.tmap[i] = tmap[i];
+    a.err = w.tc_err;
+    int s;
+    switch (r) {
+        case 16: s = ztc_launch<16>(a, ntypes, c->stream); break;
+        case 32: s = ztc_launch<32>(a, ntypes, c->stream); break;
+        case 48: s = ztc_launch<48>(a, ntypes, c->stream); break;
+        default: s = ztc_launch<64>(a, ntypes, c->stream); break;
+    }
+    if (s == ACSE_OK) c->launches++;
+    return s;
+}

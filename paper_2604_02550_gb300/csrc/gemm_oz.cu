@@ -53,6 +53,7 @@ struct OzProb {
     int g;              // slice products per exactly accumulated group
     int ngroups;
     int tiles_n, tile_start;
+    int accum;          // 1: C += result (one FP64 addition), 0: C = result
 };
 
 struct __align__(128) OzBatch {
@@ -460,8 +461,9 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ b
         for (int k = 0; k < 4; ++k) {
             if (k < vw) {
                 const int eb = (int)((__double_as_longlong(P.sb[j0 + k]) >> 52) & 0x7FF);
-                crow[j0 + k] = (ea == 0x7FF || eb == 0x7FF) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                             : oz_ll_scaled(acc[k], ea + eb - 2046 + P.ealpha - 48);
+                const double v = (ea == 0x7FF || eb == 0x7FF) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                               : oz_ll_scaled(acc[k], ea + eb - 2046 + P.ealpha - 48);
+                crow[j0 + k] = P.accum ? crow[j0 + k] + v : v;
             }
         }
     }
@@ -522,11 +524,16 @@ struct OzPlan {
     size_t smem;
     int nsm;
     int tiles;
-    OzOp A[7], B[6];
+    OzOp A[OZ_MAXP], B[OZ_MAXP];
     int* pmap;          // pair index -> i r + j (i < j), P entries
     double* Cp[2];      // packed [X; Y] of the aa and bb sectors (2P x P)
     int* sched;         // tile lists of the persistent kernel (OzBatch::order, cta_start)
     int* err;
+    // GEMM lists of the adjoint (oz_gemm_list): a plan per list slot, and the column maps of the
+    // transposed operands (K index k -> source offset k ld)
+    struct OzPlan* lists[2];
+    int cm_K[4], cm_ld[4];
+    int* cm[4];
 };
 
 static size_t oz_smem(int bn) { return (size_t)OZ_STAGES * (TC_BM + bn) * 128 + 1024 + 256; }
@@ -579,13 +586,12 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
     return cap < 1 ? ACSE_ERR_SHAPE : ACSE_OK;
 }
 
-int oz_plan_create(acse_ctx* c) {
-    OzPlan* pl = (OzPlan*)calloc(1, sizeof(OzPlan));
-    if (!pl) return ACSE_ERR_NOMEM;
-    c->oz_plan = pl;
-    const int r = c->r, R2 = r * r, R22 = 2 * R2, P = r * (r - 1) / 2;
-    pl->S = c->opt.oz_slices;
-    pl->bn = R2 >= 256 ? OZ_BN : 128;
+static int oz_plan_finish(OzPlan* pl);
+
+// Kernel attributes, SM count and the zeroed problem table of a plan.
+static int oz_plan_init(OzPlan* pl, int S, int bn) {
+    pl->S = S;
+    pl->bn = bn;
     pl->smem = oz_smem(pl->bn);
     if (pl->bn == 256)
         ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<256, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
@@ -598,6 +604,19 @@ int oz_plan_create(acse_ctx* c) {
         cudaGetLastError();
         pl->nsm = 152;
     }
+    pl->host = (OzBatch*)calloc(1, sizeof(OzBatch));
+    if (!pl->host) return ACSE_ERR_NOMEM;
+    pl->host->S = S;
+    pl->host->wait_ns = OZ_WAIT_NS;
+    return ACSE_OK;
+}
+
+int oz_plan_create(acse_ctx* c) {
+    OzPlan* pl = (OzPlan*)calloc(1, sizeof(OzPlan));
+    if (!pl) return ACSE_ERR_NOMEM;
+    c->oz_plan = pl;
+    const int r = c->r, R2 = r * r, R22 = 2 * R2, P = r * (r - 1) / 2;
+    ACSE_TRY(oz_plan_init(pl, c->opt.oz_slices, R2 >= 256 ? OZ_BN : 128));
     ACSE_TRY(oz_op_alloc(pl->A[0], 2 * P, P, pl->S));
     ACSE_TRY(oz_op_alloc(pl->A[1], R2, R2, pl->S));
     ACSE_TRY(oz_op_alloc(pl->A[2], R2, R2, pl->S));
@@ -635,12 +654,7 @@ int oz_plan_create(acse_ctx* c) {
     }
     ACSE_CUDA_TRY(cudaMemset(pl->err, 0, sizeof(int)));
     if (!c->w.tc_err) c->w.tc_err = pl->err;   // read by acse_sync_status
-    pl->host = (OzBatch*)calloc(1, sizeof(OzBatch));
-    if (!pl->host) return ACSE_ERR_NOMEM;
-    OzBatch& B = *pl->host;
-    B.S = pl->S;
-    B.err = pl->err;
-    B.wait_ns = OZ_WAIT_NS;
+    pl->host->err = pl->err;
     Work& w = c->w;
     // the largest-K GEMM first, then the mixed-spin pair GEMMs (X_ab = 2 M_ab W_ab^T, Y_ab = 2 D_ab W_ab^T),
     // the spin-flip ones and the packed same-spin ones (alpha 2 for the halved (rs) sum)
@@ -651,8 +665,15 @@ int oz_plan_create(acse_ctx* c) {
     ACSE_TRY(oz_add(pl, pl->A[6], pl->B[5], w.X5f2, R2, 1.0));
     ACSE_TRY(oz_add(pl, pl->A[0], pl->B[0], pl->Cp[0], P, 2.0));
     ACSE_TRY(oz_add(pl, pl->A[3], pl->B[2], pl->Cp[1], P, 2.0));
+    return oz_plan_finish(pl);
+}
+
+// Longest-processing-time tile lists of the persistent kernel (tile cost: its K blocks over all groups)
+// and the device copy of the problem table.
+static int oz_plan_finish(OzPlan* pl) {
+    OzBatch& B = *pl->host;
     pl->tiles = B.total_tiles;
-    if (pl->tiles > 0) {   // longest-processing-time tile lists (tile cost: its K blocks over all groups)
+    if (pl->tiles > 0) {
         const int T = pl->tiles, G = T < pl->nsm ? T : pl->nsm;
         const int nprod = pl->S * (pl->S + 1) / 2;
         int* hs = (int*)malloc((size_t)(T + G + 1) * sizeof(int));
@@ -686,31 +707,36 @@ int oz_plan_create(acse_ctx* c) {
     return ACSE_OK;
 }
 
-void oz_plan_destroy(acse_ctx* c) {
-    OzPlan* pl = (OzPlan*)c->oz_plan;
+static void oz_plan_free(OzPlan* pl) {
     if (!pl) return;
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < OZ_MAXP; ++i) {
         if (pl->A[i].sl) cudaFree(pl->A[i].sl);
         if (pl->A[i].scale) cudaFree(pl->A[i].scale);
-    }
-    for (int i = 0; i < 6; ++i) {
         if (pl->B[i].sl) cudaFree(pl->B[i].sl);
         if (pl->B[i].scale) cudaFree(pl->B[i].scale);
     }
     if (pl->pmap) cudaFree(pl->pmap);
     if (pl->sched) cudaFree(pl->sched);
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < 2; ++s) {
         if (pl->Cp[s]) cudaFree(pl->Cp[s]);
-    if (pl->err) {
-        if (c->w.tc_err == pl->err) c->w.tc_err = nullptr;
-        cudaFree(pl->err);
+        oz_plan_free(pl->lists[s]);
     }
+    for (int i = 0; i < 4; ++i)
+        if (pl->cm[i]) cudaFree(pl->cm[i]);
+    if (pl->err) cudaFree(pl->err);
     if (pl->host)
         for (int i = 0; i < pl->host->nprob; ++i)
             if (pl->host->p[i].stage) cudaFree(pl->host->p[i].stage);
     if (pl->dev) cudaFree(pl->dev);
     free(pl->host);
     free(pl);
+}
+
+void oz_plan_destroy(acse_ctx* c) {
+    OzPlan* pl = (OzPlan*)c->oz_plan;
+    if (!pl) return;
+    if (pl->err && c->w.tc_err == pl->err) c->w.tc_err = nullptr;
+    oz_plan_free(pl);
     c->oz_plan = nullptr;
 }
 
@@ -794,5 +820,128 @@ int oz_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
     pl->host->wait_ns = ns ? ns : OZ_WAIT_NS;
     pl->host->inject_stall = inject_stall;
     ACSE_CUDA_TRY(cudaMemcpy(pl->dev, pl->host, sizeof(OzBatch), cudaMemcpyHostToDevice));
+    return ACSE_OK;
+}
+
+// ------------------------------------------------------------------ GEMM lists of the adjoint
+// The reverse sweep's FP64 GEMMs (acse_adjoint.cu) of an Ozaki context run through the same kernels:
+// any list of up to OZ_MAXP GEMMs C (+)= alpha A B^T, alpha a power of two, beta 0 or 1, either operand
+// stored transposed (GemmF64::transA / transB).  A transposed operand is sliced through a column map
+// (K index k at source offset k ld, row n at offset n): its reads are strided, one 8-byte element per
+// 32-byte sector, cheap next to the GEMM.  One plan per list slot, built on the first call (its slices
+// and group-sum staging stay until the context is destroyed); a later call whose shapes differ from
+// the slot's plan is refused (ACSE_ERR_SHAPE).
+
+// Column map k -> k ld for K indices, cached per (K, ld).
+static int oz_colmap(OzPlan* root, int K, int ld, const int** out) {
+    for (int i = 0; i < 4; ++i)
+        if (root->cm[i] && root->cm_K[i] == K && root->cm_ld[i] == ld) {
+            *out = root->cm[i];
+            return ACSE_OK;
+        }
+    for (int i = 0; i < 4; ++i) {
+        if (root->cm[i]) continue;
+        int* h = (int*)malloc((size_t)K * sizeof(int));
+        if (!h) return ACSE_ERR_NOMEM;
+        for (int k = 0; k < K; ++k) h[k] = k * ld;
+        const bool ok = cudaMalloc((void**)&root->cm[i], (size_t)K * sizeof(int)) == cudaSuccess &&
+                        cudaMemcpy(root->cm[i], h, (size_t)K * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        free(h);
+        if (!ok) {
+            cudaGetLastError();
+            return ACSE_ERR_NOMEM;
+        }
+        root->cm_K[i] = K;
+        root->cm_ld[i] = ld;
+        *out = root->cm[i];
+        return ACSE_OK;
+    }
+    return ACSE_ERR_UNSUPPORTED;
+}
+
+static int oz_list_create(OzPlan* root, const GemmF64* g, int n, OzPlan** out) {
+    OzPlan* pl = (OzPlan*)calloc(1, sizeof(OzPlan));
+    if (!pl) return ACSE_ERR_NOMEM;
+    *out = pl;
+    int maxN = 0;
+    for (int i = 0; i < n; ++i) maxN = g[i].N > maxN ? g[i].N : maxN;
+    ACSE_TRY(oz_plan_init(pl, root->S, maxN >= 256 ? OZ_BN : 128));
+    pl->host->err = root->err;
+    for (int i = 0; i < n; ++i) {
+        ACSE_TRY(oz_op_alloc(pl->A[i], g[i].M, g[i].K, pl->S));
+        ACSE_TRY(oz_op_alloc(pl->B[i], g[i].N, g[i].K, pl->S));
+        ACSE_TRY(oz_add(pl, pl->A[i], pl->B[i], g[i].C, g[i].ldc, g[i].alpha));
+    }
+    return oz_plan_finish(pl);
+}
+
+int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
+    OzPlan* root = (OzPlan*)c->oz_plan;
+    if (!root || slot < 0 || slot > 1 || n < 1 || n > OZ_MAXP) return ACSE_ERR_UNSUPPORTED;
+    for (int i = 0; i < n; ++i) {
+        int ex = 0;
+        if (frexp(g[i].alpha, &ex) != 0.5 || (g[i].beta != 0.0 && g[i].beta != 1.0) || g[i].perm_r) return ACSE_ERR_ARG;
+    }
+    if (!root->lists[slot]) {
+        const int s = oz_list_create(root, g, n, &root->lists[slot]);
+        if (s != ACSE_OK) {
+            oz_plan_free(root->lists[slot]);
+            root->lists[slot] = nullptr;
+            return s;
+        }
+    }
+    OzPlan* pl = root->lists[slot];
+    OzBatch& B = *pl->host;
+    if (B.nprob != n) return ACSE_ERR_SHAPE;
+    for (int i = 0; i < n; ++i)
+        if (B.p[i].M != g[i].M || B.p[i].N != g[i].N || pl->A[i].K != g[i].K) return ACSE_ERR_SHAPE;
+    // slices of every operand (A in order, B reversed), at most OZ_MAXJ jobs a launch
+    OzSliceBatch sb;
+    memset(&sb, 0, sizeof(sb));
+    sb.S = pl->S;
+    int rows = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int side = 0; side < 2; ++side) {
+            const double* src = side ? g[i].B : g[i].A;
+            const int tr = side ? g[i].transB : g[i].transA;
+            const int ld = side ? g[i].ldb : g[i].lda;
+            const OzOp& o = side ? pl->B[i] : pl->A[i];
+            const int* cm = nullptr;
+            if (tr) ACSE_TRY(oz_colmap(root, o.K, ld, &cm));
+            oz_job(sb, rows, o, 0, o.rows, src, tr ? 1 : (size_t)ld, nullptr, cm, side);
+            if (sb.njobs == OZ_MAXJ) {
+                k_oz_slice<<<rows, 256, 0, c->stream>>>(sb);
+                ACSE_LAUNCHED(c);
+                memset(&sb, 0, sizeof(sb));
+                sb.S = pl->S;
+                rows = 0;
+            }
+        }
+    }
+    if (sb.njobs) {
+        k_oz_slice<<<rows, 256, 0, c->stream>>>(sb);
+        ACSE_LAUNCHED(c);
+    }
+    // this call's outputs, scales and accumulation
+    for (int i = 0; i < n; ++i) {
+        OzProb& p = B.p[i];
+        int ex = 0;
+        frexp(g[i].alpha, &ex);
+        p.C = g[i].C;
+        p.ldc = g[i].ldc;
+        p.alpha = g[i].alpha;
+        p.ealpha = ex - 1;
+        p.accum = g[i].beta != 0.0;
+    }
+    B.wait_ns = root->host->wait_ns;
+    B.inject_stall = root->host->inject_stall;
+    ACSE_CUDA_TRY(cudaMemcpyAsync(pl->dev, pl->host, sizeof(OzBatch), cudaMemcpyHostToDevice, c->stream));
+    if (pl->tiles == 0) return ACSE_OK;
+    const int grid = pl->tiles < pl->nsm ? pl->tiles : pl->nsm;
+    if (pl->bn == 256) k_gemm_oz<256, OZ_STAGES><<<grid, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
+    else k_gemm_oz<128, OZ_STAGES><<<grid, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
+    ACSE_LAUNCHED(c);
+    k_oz_reduce<<<dim3(2 * pl->nsm, B.nprob), 256, 0, c->stream>>>(pl->dev);
+    ACSE_LAUNCHED(c);
     return ACSE_OK;
 }

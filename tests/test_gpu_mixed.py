@@ -41,7 +41,8 @@ def _problem(r, na, nb, seed, kind):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32", "tf32x3"])
 @pytest.mark.parametrize("r,na,nb,kind", [(4, 2, 2, "state"), (6, 3, 2, "state"), (9, 3, 3, "pair"),
-                                          (12, 4, 3, "pair"), (17, 5, 4, "pair")])
+                                          (12, 4, 3, "pair"), (16, 5, 4, "pair"), (17, 5, 4, "pair"),
+                                          (32, 7, 6, "pair")])
 def test_residual_parity_mixed(acse, prec, r, na, nb, kind):
     p = _problem(r, na, nb, 100 + r, kind)
     ctx = acse.ACSE(r, na, nb, p.h, p.V, prec)
