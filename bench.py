@@ -50,15 +50,17 @@ def parse():
                     help="Euler step; default 1e-4 for r >= 32 (1e-3 diverges there), else the paper's 1e-3")
     ap.add_argument("--reset-every", type=int, default=200,
                     help="copy D_0 back into D every this many steps (keeps long runs on the stable stretch)")
+    ap.add_argument("--sustain-s", type=float, default=1.5,
+                    help="seconds of untimed steps before the timed region, sampled for the clock record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="measure FP64/TF32/BF16 matmul peaks and exit")
     ap.add_argument("--batch", action="store_true",
                     help="time the 16-instance batch (r = 12..40, CAS(4e,4o) ground + excited) instead")
     ap.add_argument("--time-to-e", action="store_true",
-                    help="time-to-E on the r = 48 workload: BF16x3 vs FP64, Methods stopping rule, step cap")
+                    help="time to a converged energy (Methods stopping rule, line search) per precision and "
+                         "schedule, then per-iteration errors of fixed steps, against FP64")
     ap.add_argument("--cap", type=int, default=100, help="step cap of --time-to-e")
-    ap.add_argument("--line-search", action="store_true", help="--time-to-e with the line search (one context)")
     ap.add_argument("--adjoint", action="store_true",
                     help="adjoint cost relative to the forward steps (FP64 and Ozaki, r = 32 CAS(6e,6o), 4 steps)")
     return ap.parse_args()
@@ -197,7 +199,6 @@ def dist_init(args):
 
 
 EVALS_PER_STEP = 2     # contraction passes of one acse_step: the residual and the update
-SUSTAIN_S = 1.5        # untimed run of the same steps before the timed region (clock record)
 
 
 def cpu_oracle_timing(p, n_evals=1):
@@ -314,96 +315,74 @@ def run_batch(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+TTE_VARIANTS = (   # (label, precision, options) of the time-to-E runs
+    ("fp64", "fp64", {}),
+    ("ozaki", "ozaki", {}),
+    ("ozaki6->ozaki", "ozaki", dict(oz_slices=6, refine=True, refine_tol=0.1)),
+    ("bf16x3->ozaki", "bf16x3", dict(refine=True, refine_tol=0.1)),
+    ("bf16x3", "bf16x3", {}),
+    ("tf32x3", "tf32x3", {}),
+)
+
+
 def run_time_to_e(args):
-    """Wall time from the initial D until the stopping rule of the Methods section fires (E or ||A|| rises,
-    or |dE| < 1e-6 Eh), capped at args.cap steps, for BF16x3 and FP64 on the same workload: one batch of
-    one instance, one graph-replayed step per call so that E is logged at every iteration."""
+    """Time to a converged energy (Methods: stop when E or ||A|| rises, or |dE| < 1e-6 Eh) on one workload,
+    for FP64 FMA, the FP64-accurate Ozaki precision, two precision schedules (Ozaki with 6 slices, or
+    BF16x3, until ||A||^2 falls by less than 10 % a step, then Ozaki with 8) and the split precisions:
+    one context each, the line search from eps0 (1e-4 for r >= 32, where 1e-3 makes ||A|| rise at the first
+    step; else the paper's 1e-3), at most --cap steps; wall time of the host loop (E and ||A||^2 read after
+    every step), the stopping energy against FP64's and |E_k - E_k(FP64)| at every iteration.  Then the
+    fixed-step leg: --cap steps at eps (1e-4 for r >= 32) in every precision, |E_k - E_k(FP64)| per step."""
     import numpy as np
-    from paper_2604_02550_gb300 import _lib
-    p = workload(args.r)
-    eps = args.eps if args.eps is not None else (1e-4 if p.r >= 32 else 1e-3)
-    out = {"metric": "time_to_E", "workload": p.name, "eps": eps, "cap": args.cap, "runs": {}}
-    logs = {}
-    for prec in ("bf16x3", "fp64"):
-        b = _lib.acse_batch_create([p], prec)
-        _lib.acse_batch_set_D(b, 0, p.Daa, p.Dab, p.Dbb, eps)
-        _lib.acse_batch_run(b, 1, 0, stop_rule=True)       # capture + autotune, no step
-        Es, n2s = [], []
-        t0 = time.perf_counter()
-        steps, reason = 0, 0
-        for _ in range(args.cap):
-            E, N2, S, R = _lib.acse_batch_run(b, 1, 1, stop_rule=True)
-            Es.append(float(E[0]))
-            n2s.append(float(N2[0]))
-            steps, reason = int(S[0]), int(R[0])
-            if reason:
-                break
-        dt = time.perf_counter() - t0
-        _lib.acse_batch_destroy(b)
-        logs[prec] = Es
-        out["runs"][prec] = {"seconds": dt, "steps": steps, "stop_reason": reason, "E_final": Es[-1],
-                             "norm2_final": n2s[-1], "E_first": Es[0]}
-    m = min(len(logs["bf16x3"]), len(logs["fp64"]))
-    dE = np.abs(np.array(logs["bf16x3"][:m]) - np.array(logs["fp64"][:m]))
-    out["max_abs_dE_per_iteration"] = float(dE.max())
-    out["abs_dE_final"] = float(abs(logs["bf16x3"][-1] - logs["fp64"][-1]))
-    out["dE_every_10"] = [float(x) for x in dE[::10]]
-    out["speedup_bf16x3_vs_fp64"] = out["runs"]["fp64"]["seconds"] / out["runs"]["bf16x3"]["seconds"]
-    print(json.dumps(out), flush=True)
-
-
-def run_time_to_e_line_search(args):
-    """Time-to-E with the line search (acse_step, one context per precision): steps until the Methods
-    stopping rule fires, evaluated on the host after every step exactly as the oracle's driver does
-    (stop when E rises or ||A|| rises, keeping the previous state, or when |dE| < 1e-6 Eh); the
-    converged E of BF16x3 and TF32x3 against FP64."""
     import torch
-    from paper_2604_02550_gb300 import api
+    from paper_2604_02550_gb300 import _lib, api
     p = workload(args.r)
-    out = {"metric": "time_to_E_line_search", "workload": p.name, "eps0": 1e-3, "cap": args.cap, "runs": {},
-           "hybrid": "bf16x3 while ||A||^2 falls by more than 1e-2 relative per step, then fp64 (or ozaki) from "
-                     "the same D and the last accepted eps"}
-    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64", "bf16x3+ozaki", "ozaki", "fp64"):
-        hybrid = prec.startswith("bf16x3+")
-        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "bf16x3" if hybrid else prec, line_search=True,
-                       eps0=1e-3)
+    eps0 = 1e-4 if p.r >= 32 else 1e-3
+    eps_fixed = args.eps if args.eps is not None else eps0
+    out = {"metric": "time_to_E", "workload": p.name, "r": p.r, "cap": args.cap, "eps0": eps0,
+           "stop_rule": "E or ||A|| rises (beyond 1e-12 |E|, 1e-10 ||A||^2), or |dE| < 1e-6 Eh",
+           "line_search": {}, "fixed_step": {"eps": eps_fixed}}
+    ls = out["line_search"]
+    for label, prec, kw in TTE_VARIANTS:
+        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, line_search=True, eps0=eps0, **kw)
         D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
-        Es = [float(ctx.energy(D))]
-        n2s = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        acc, reason, switched = None, "cap", None
-        for k in range(args.cap):
-            if hybrid and switched is None and k >= 2 and (n2s[-2] - n2s[-1]) < 1e-2 * n2s[-2]:
-                ctx.close()
-                ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec.split("+")[1], line_search=True,
-                               eps0=last_eps)
-                switched = k
-            E, n2, e = ctx.step(D)
-            last_eps = float(e)
-            n2s.append(float(n2))          # ||A(D_k)||^2, before step k
-            Es.append(float(E))            # E(D_{k+1})
-            if k >= 1 and n2s[k] > n2s[k - 1]:
-                acc, reason = k - 1, "norm rose"
-                break
-            if Es[k + 1] > Es[k]:
-                acc, reason = k, "energy rose"
-                break
-            if abs(Es[k + 1] - Es[k]) < 1e-6:
-                acc, reason = k + 1, "converged"
-                break
+        res = ctx.run_until_stop(D, args.cap)
+        dt = time.perf_counter() - t0
+        sw, nsw = _lib.acse_schedule_state(ctx.ctx)
+        ctx.close()
+        ls[label] = {"seconds": dt, "steps": len(res["eps"]), "stop": res["reason"], "accepted": res["accepted"],
+                     "E_stop": res["E_stop"], "E": res["E"]}
+        if kw.get("refine"):
+            ls[label]["switched_after_step"] = nsw if sw else None
+    ref = ls["fp64"]
+    for label, r_ in ls.items():
+        m = min(len(r_["E"]), len(ref["E"]))
+        dE = np.abs(np.array(r_["E"][:m]) - np.array(ref["E"][:m]))
+        r_["abs_dE_stop_vs_fp64"] = abs(r_["E_stop"] - ref["E_stop"])
+        r_["speedup_vs_fp64"] = ref["seconds"] / r_["seconds"]
+        r_["abs_dE_per_iteration"] = [float(x) for x in dE]
+        del r_["E"]
+    fx = out["fixed_step"]
+    E64 = None
+    for label, prec, kw in (("fp64", "fp64", {}), ("ozaki", "ozaki", {}), ("ozaki6", "ozaki", dict(oz_slices=6)),
+                            ("bf16x3", "bf16x3", {}), ("tf32x3", "tf32x3", {})):
+        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, **kw)
+        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+        Es = [float(ctx.energy(D))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.cap):
+            E, _, _ = ctx.step(D, eps_fixed)
+            Es.append(float(E))
         dt = time.perf_counter() - t0
         ctx.close()
-        if acc is None:
-            acc = len(Es) - 1
-        out["runs"][prec] = {"seconds": dt, "steps": len(n2s), "stop": reason, "accepted_step": acc,
-                             "E_conv": Es[acc], "norm2_last": n2s[-1]}
-        if hybrid:
-            out["runs"][prec]["switched_at_step"] = switched
-    e64 = out["runs"]["fp64"]["E_conv"]
-    for prec in ("bf16x3", "tf32x3", "bf16x3+fp64", "bf16x3+ozaki", "ozaki"):
-        out["runs"][prec]["abs_dE_conv_vs_fp64"] = abs(out["runs"][prec]["E_conv"] - e64)
-        out["runs"][prec]["speedup_vs_fp64"] = out["runs"]["fp64"]["seconds"] / out["runs"][prec]["seconds"]
+        if E64 is None:
+            E64 = np.array(Es)
+        dE = np.abs(np.array(Es) - E64)
+        fx[label] = {"seconds": dt, "E_final": Es[-1], "max_abs_dE": float(dE.max()),
+                     "abs_dE_per_iteration": [float(x) for x in dE]}
     print(json.dumps(out), flush=True)
 
 
@@ -473,10 +452,7 @@ def main():
         run_batch(args, rank, world)
         return
     if args.time_to_e:
-        if args.line_search:
-            run_time_to_e_line_search(args)
-        else:
-            run_time_to_e(args)
+        run_time_to_e(args)
         return
     if args.adjoint:
         run_adjoint_cost(args)
@@ -499,7 +475,7 @@ def main():
         for _ in range(args.warmup):
             ctx.step(D, args.eps)
     stream.synchronize()
-    # clocks: sampled over a window of the same steps (about SUSTAIN_S long, untimed) run directly
+    # clocks: sampled over a window of the same steps (about --sustain-s long, untimed) run directly
     # before the timed region and over the timed region itself, so that a short timed region still
     # has a clock record taken under this load
     sampler = ClockSampler(local)
@@ -507,14 +483,14 @@ def main():
     time.sleep(0.3)
     t_s = time.perf_counter()
     with torch.cuda.stream(stream):
-        while time.perf_counter() - t_s < SUSTAIN_S:
+        while time.perf_counter() - t_s < args.sustain_s:
             for dst, src in zip(D, D0):      # back to D_0 every 100 steps, as the timed region does
                 dst.copy_(src)
             for k in range(100):
                 ctx.step(D, args.eps)
                 if k % 10 == 9:
                     stream.synchronize()
-                    if time.perf_counter() - t_s >= SUSTAIN_S:
+                    if time.perf_counter() - t_s >= args.sustain_s:
                         break
         for dst, src in zip(D, D0):
             dst.copy_(src)
@@ -575,7 +551,7 @@ def main():
                  "launch_ms": 1e3 * gemm_avg_s,
                  "gemm_share_of_step": 2 * 1e3 * gemm_avg_s / per_step,
                  "timed_launches": gemm_n})
-    clocks["window"] = (f"sampled every 100 ms over {SUSTAIN_S:.1f} s of the same untimed steps directly before "
+    clocks["window"] = (f"sampled every 100 ms over {args.sustain_s:.1f} s of the same untimed steps directly before "
                         f"the timed region and over the timed region")
     line = {"metric": "acse_residual_evals_per_s", "value": value, "unit": "residual evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,

@@ -69,6 +69,43 @@ class ACSE:
         _lib.acse_step(self.ctx, *D, eps, s[0:1], s[1:2], s[2:3])
         return s[0:1], s[1:2], s[2:3]
 
+    def run_until_stop(self, D, cap, eps=0.0, rise_tol=1e-10):
+        """Euler steps on D (in place) until the stopping rule of the Methods section fires, at most `cap`:
+        stop when E or ||A|| rises (D goes back to the state before that step) or when |dE| < 1e-6 Eh.
+        A rise counts when it exceeds the rounding level of the two values compared: ||A||^2 by more than
+        rise_tol of itself, E by more than 1e-12 of |E| (near the floor of ||A||^2 two FP64-accurate
+        evaluations differ by about 1e-13 relative, so a literal comparison decides on rounding).  Reads E
+        and ||A||^2 back after every step.  Returns dict(E = energies of D_0 .. D_last, norm2 = ||A||^2
+        before each step, eps = steps taken, reason, accepted = index of the returned D in E)."""
+        Es = [float(self.energy(D))]
+        n2s, epss = [], []
+        # D_(k-1) and D_k kept while step k runs: ||A(D_k)||^2 is known only once step k has run
+        keep = [tuple(x.clone() for x in D), tuple(x.clone() for x in D)]
+        reason, acc = "cap", None
+        for k in range(cap):
+            for dst, src in zip(keep[k % 2], D):
+                dst.copy_(src)                      # keep[k % 2] = D_k
+            E, n2, e = self.step(D, eps)
+            Es.append(float(E))
+            n2s.append(float(n2))
+            epss.append(float(e))
+            if k >= 1 and n2s[k] > n2s[k - 1] * (1.0 + rise_tol):
+                reason, acc = "norm rose", k - 1    # ||A(D_k)|| rose: back to D_(k-1)
+                for dst, src in zip(D, keep[(k - 1) % 2]):
+                    dst.copy_(src)
+                break
+            if Es[k + 1] > Es[k] + 1e-12 * abs(Es[k]):
+                reason, acc = "energy rose", k      # E(D_(k+1)) rose: back to D_k
+                for dst, src in zip(D, keep[k % 2]):
+                    dst.copy_(src)
+                break
+            if abs(Es[k + 1] - Es[k]) < 1e-6:
+                reason, acc = "converged", k + 1
+                break
+        if acc is None:
+            acc = len(Es) - 1
+        return dict(E=Es, norm2=n2s, eps=epss, reason=reason, accepted=acc, E_stop=Es[acc])
+
     def backward(self, D_ckpt, n_steps, eps, wE=1.0, wN=0.0):
         """Gradient of wE E(D_n) + wN ||A(D_n)||^2 w.r.t. (h, V, D0 blocks)."""
         r = self.r

@@ -193,7 +193,8 @@ def test_golden_config3_fixed_step_trajectory(acse, prec):
     trajectory (tests/golden/cfg3_fixed_eps_5.json, written by make_golden.py from the oracle alone):
     E and ||A||^2 at every step and 64 seeded entries of each block of D_5.  FP64-accurate paths: 1e-10 Eh
     on E and 1e-12 relative on ||A||^2 and D; BF16x3: its error grows with what the steps change, a bound
-    of 1e-5 of the energy drop so far (measured 8e-6 Eh after the first step, whose drop is 6 Eh)."""
+    of 3e-5 of the energy drop so far (measured 1.0e-5, 7.1e-5, 1.1e-4, 1.5e-4, 1.8e-4 Eh after the five
+    steps, whose drops are 6.0, 11.1, 15.7, 20.0, 23.9 Eh: four to eighteen times below the bound)."""
     g = json.load(open(os.path.join(HERE, "golden", "cfg3_fixed_eps_5.json")))
     p = I.config_problem(3)
     assert p.name == g["system"] and p.r == R
@@ -216,6 +217,6 @@ def test_golden_config3_fixed_step_trajectory(acse, prec):
         assert max(dEs) < 1e-10 and max(dNs) < 1e-12 and dD < 1e-12 * scale
     else:
         for k, d in enumerate(dEs):
-            assert d < 1e-5 * abs(g["E"][k + 1] - g["E"][0]), f"step {k}"
+            assert d < 3e-5 * abs(g["E"][k + 1] - g["E"][0]), f"step {k}"
         assert max(dNs) < 1e-4 and dD < 1e-4 * scale
     ctx.close()

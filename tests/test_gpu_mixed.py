@@ -3,10 +3,11 @@
 Tolerances (normwise relative, max|dA| / max|A|), about five times the largest error measured on a
 GB300 over these cases: BF16x3 represents each operand as hi + lo with about 16 significant bits and
 drops the lo.lo product (about 2^-16 = 1.5e-5 relative per product before FP32 accumulation; measured
-3.9e-6 ... 5.5e-6 on the residual): 3e-5.  TF32 (one product, 11 significant bits, 2^-11 = 4.9e-4 per
-product; measured 1.6e-4 ... 3.0e-4): 1.5e-3.  TF32x3 (hi + lo in tf32, about 2^-21 per product, then
-limited by the FP32 intermediates M, Z, w, B and the FP32 accumulation; measured 2.3e-7 ... 3.6e-6):
-2e-5.  ||A||^2 (relative; measured up to 2.9e-6, 4.8e-5 and 5.9e-6): NTOL.
+3.9e-6 ... 7.7e-6 on the residual, r = 4 ... 32): 3e-5.  TF32 (one product, 11 significant bits,
+2^-11 = 4.9e-4 per product; measured 1.6e-4 ... 3.0e-4): 1.5e-3.  TF32x3 (hi + lo in tf32, about 2^-21
+per product, then limited by the FP32 intermediates M, Z, w, B and the FP32 accumulation; measured
+2.3e-7 ... 1.3e-5, growing with r): 5e-5.  ||A||^2 (relative; measured up to 9.5e-6, 4.8e-5 and
+2.1e-5): NTOL.
 """
 import numpy as np
 import pytest
@@ -18,8 +19,8 @@ from tests.gpu_helpers import maxrel, oracle_residual_blocks, oracle_step_blocks
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x3": 3e-5, "tf32": 1.5e-3, "tf32x3": 2e-5}
-NTOL = {"bf16x3": 1.5e-5, "tf32": 2.5e-4, "tf32x3": 3e-5}
+TOL = {"bf16x3": 3e-5, "tf32": 1.5e-3, "tf32x3": 5e-5}
+NTOL = {"bf16x3": 5e-5, "tf32": 2.5e-4, "tf32x3": 1e-4}
 
 
 @pytest.fixture(scope="module")
