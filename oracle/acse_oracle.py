@@ -29,6 +29,7 @@ Readings of places where the paper is garbled or silent (each also pinned by tes
   R6  the active mask zeroes A where all four spatial indices lie in [act_lo, act_hi)
   R7  spin blocks aa, ab, bb (Appendix A's labels all read aa); Tr D_ab = N_a N_b / 2     (App. A)
   R8  line search (not in the paper): f(eps) = ||A(D + eps U)||^2 at {0, e0, 2 e0};
+      a merit flat to rounding (both trial values within 1e-10 f(0) of f(0)) -> e0/4; otherwise a
       convex parabola -> its minimiser clamped to [e0/4, 2 e0], else the better of e0, 2 e0;
       next e0 = accepted eps.
   R13 sigma_a of the NY cumulant: +1 for the first n_alpha alpha and the first n_beta beta spatial
@@ -326,8 +327,13 @@ def step(K, D, N, eps, mask=None, sigma=None):
     return D + eps * U, A, U
 
 
+LS_FLAT = 1e-10   # reading R8: trial values this close to f(0) (relative) are rounding, not a slope
+
+
 def line_search_eps(f0, f1, f2, e0):
     """Reading R8: choose eps from f at {0, e0, 2 e0}."""
+    if abs(f1 - f0) <= LS_FLAT * abs(f0) and abs(f2 - f0) <= LS_FLAT * abs(f0):
+        return 0.25 * e0
     c = (f2 - 2.0 * f1 + f0) / (2.0 * e0 * e0)
     if c > 0.0:
         b = (f1 - f0) / e0 - c * e0

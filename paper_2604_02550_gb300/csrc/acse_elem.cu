@@ -521,11 +521,17 @@ int launch_axpy_energy(acse_ctx* c, double* const D[3], const double* const U[3]
 
 // ------------------------------------------------------------------------ line search
 // scal[2] = e0 (state), scal[4..6] = f(0), f(e0), f(2 e0)  ->  scal[3] = eps, scal[2] = eps.
+// Trial values within LS_FLAT f(0) of f(0) are rounding of the merit, not a slope: the step is then e0/4,
+// so that implementations whose evaluations differ by rounding take the same steps.
+#define LS_FLAT 1e-10
+
 __global__ void k_line_search(double* scal) {
     const double e0 = scal[2], f0 = scal[4], f1 = scal[5], f2 = scal[6];
     const double cc = (f2 - 2.0 * f1 + f0) / (2.0 * e0 * e0);
     double x;
-    if (cc > 0.0) {
+    if (fabs(f1 - f0) <= LS_FLAT * fabs(f0) && fabs(f2 - f0) <= LS_FLAT * fabs(f0)) {
+        x = 0.25 * e0;
+    } else if (cc > 0.0) {
         const double b = (f1 - f0) / e0 - cc * e0;
         x = -b / (2.0 * cc);
         x = fmin(fmax(x, 0.25 * e0), 2.0 * e0);

@@ -324,6 +324,12 @@ def test_line_search_parabola():
     assert x == pytest.approx(2.5, abs=1e-14)           # clamped to e0/4
     g = lambda x: 1.0 - x * x                           # concave: better of e0, 2e0
     assert O.line_search_eps(g(0), g(0.3), g(0.6), 0.3) == pytest.approx(0.6)
+    # a merit flat to rounding (trial values within 1e-10 of f(0), either curvature sign): e0 / 4
+    f0 = 7937.055219104771
+    assert O.line_search_eps(f0, f0 * (1 + 3e-14), f0 * (1 - 2e-14), 1e-9) == 0.25e-9
+    assert O.line_search_eps(f0, f0 * (1 - 3e-14), f0 * (1 + 2e-14), 1e-9) == 0.25e-9
+    # just outside the flat band the parabola decides again
+    assert O.line_search_eps(f0, f0 * (1 - 4e-10), f0 * (1 - 6e-10), 1e-9) != 0.25e-9
 
 
 def test_driver_fixed_steps_and_descent():
