@@ -357,12 +357,14 @@ def run_time_to_e(args):
         if kw.get("refine"):
             ls[label]["switched_after_step"] = nsw if sw else None
     ref = ls["fp64"]
+    E_ref = np.array(ref["E"])
     for label, r_ in ls.items():
-        m = min(len(r_["E"]), len(ref["E"]))
-        dE = np.abs(np.array(r_["E"][:m]) - np.array(ref["E"][:m]))
+        m = min(len(r_["E"]), len(E_ref))
+        dE = np.abs(np.array(r_["E"][:m]) - E_ref[:m])
         r_["abs_dE_stop_vs_fp64"] = abs(r_["E_stop"] - ref["E_stop"])
         r_["speedup_vs_fp64"] = ref["seconds"] / r_["seconds"]
         r_["abs_dE_per_iteration"] = [float(x) for x in dE]
+    for r_ in ls.values():
         del r_["E"]
     fx = out["fixed_step"]
     E64 = None
