@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
     extern __shared__ uint8_t zs_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)zs_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                                  // [hi | lo] K blocks of 128 x 128 B
-    uint8_t* sB = smem + 2 * ZTC_A_SEG;                  // [spin][hi | lo] K blocks of R x 128 B
-    uint64_t* bar = (uint64_t*)(sB + 4 * B_SEG);
+    uint8_t* sB = smem + 2 * ZTC_A_SEG;                  // [hi | lo] K blocks of R x 128 B (1D of one spin)
+    uint64_t* bar = (uint64_t*)(sB + 2 * B_SEG);
     uint32_t* tmem_slot = (uint32_t*)(bar + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -68,33 +68,37 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
         fence_barrier_init();
     }
     if (warp == 0) tmem_alloc(tmem_slot, 64);
-    // B: 1D of both spins, row j, K = q, as [hi | lo], built once per block
-    for (int e = threadIdx.x; e < 2 * R * 8; e += ZTC_THREADS) {
-        const int sp = e / (R * 8), j = (e >> 3) % R, c = e & 7;
-        const double* g = a.gam + (size_t)sp * R2;
-        __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const float x = 8 * c + u < R ? (float)g[j * R + 8 * c + u] : 0.f;
-            hi[u] = __float2bfloat16_rn(x);
-            lo[u] = __float2bfloat16_rn(x - __bfloat162float(hi[u]));
-        }
-        const uint32_t off = sw128(j, c);
-        *reinterpret_cast<uint4*>(sB + (2 * sp) * B_SEG + off) = pack8(hi);
-        *reinterpret_cast<uint4*>(sB + (2 * sp + 1) * B_SEG + off) = pack8(lo);
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
     uint32_t phase = 0;
+    int cur_sp = -1;                                     // spin of the 1D tile in sB
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, phase ^= 1) {
         const int tb = tile / (R * NT);
         const int t = a.tmap[tb];
         const int rem = tile - tb * R * NT;
         const int k = rem / NT;
         const int m0 = (rem - k * NT) * TC_BM;
+        const int sp = (t == 2 || t == 3 || t == 4) ? 1 : 0;
+        if (sp != cur_sp) {   // B: 1D of this tile's spin, row j, K = q, as [hi | lo] (the last MMAs are done)
+            const double* g = a.gam + (size_t)sp * R2;
+            for (int e = threadIdx.x; e < R * 8; e += ZTC_THREADS) {
+                const int j = e >> 3, c = e & 7;
+                __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float x = 8 * c + u < R ? (float)g[j * R + 8 * c + u] : 0.f;
+                    hi[u] = __float2bfloat16_rn(x);
+                    lo[u] = __float2bfloat16_rn(x - __bfloat162float(hi[u]));
+                }
+                const uint32_t off = sw128(j, c);
+                *reinterpret_cast<uint4*>(sB + off) = pack8(hi);
+                *reinterpret_cast<uint4*>(sB + B_SEG + off) = pack8(lo);
+            }
+            cur_sp = sp;
+        }
         // A: row m = p r + s of W_k^T, K = q; the slice W_kp[q][s] of type t (see k_Z_pipe)
         {
             const int ml = threadIdx.x, m = m0 + ml;
@@ -144,9 +148,8 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
         tc_fence_after();
         if (threadIdx.x == 0) {
             const uint32_t idesc = make_idesc<0, R>();
-            const int sp = (t == 2 || t == 3 || t == 4) ? 1 : 0;
             const uint64_t ah = smem_desc(sA), al = smem_desc(sA + ZTC_A_SEG);
-            const uint64_t bh = smem_desc(sB + (2 * sp) * B_SEG), bl = smem_desc(sB + (2 * sp + 1) * B_SEG);
+            const uint64_t bh = smem_desc(sB), bl = smem_desc(sB + B_SEG);
             // hi.hi + lo.hi + hi.lo, FP32 accumulation
 #pragma unroll
             for (int kk = 0; kk < R / 16; ++kk) umma<0>(tmem, ah + 2 * kk, bh + 2 * kk, idesc, kk != 0);
@@ -206,16 +209,18 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
 template <int R>
 static int ztc_launch(const ZtcArgs& a, int ntypes, cudaStream_t st) {
     constexpr int R2 = R * R, NT = (R2 + TC_BM - 1) / TC_BM;
-    const size_t smem = 1024 + 2 * (size_t)ZTC_A_SEG + 4 * (size_t)R * 128 + 64;
+    const size_t smem = 1024 + 2 * (size_t)ZTC_A_SEG + 2 * (size_t)R * 128 + 64;
     static int blocks_per_sm = 0, nsm = 0;
     if (!blocks_per_sm) {
         ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0;
+        int dev = 0, smem_sm = 0;
         ACSE_CUDA_TRY(cudaGetDevice(&dev));
         ACSE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        ACSE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_Z_tc<R>, ZTC_THREADS, smem));
+        ACSE_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        // resident blocks: shared memory (1 KiB of it reserved per block), at most 8 (8 x 64 TMEM columns)
+        blocks_per_sm = (int)((size_t)smem_sm / (smem + 1024));
         if (blocks_per_sm < 1) blocks_per_sm = 1;
-        if (blocks_per_sm > 8) blocks_per_sm = 8;   // 8 x 64 TMEM columns
+        if (blocks_per_sm > 8) blocks_per_sm = 8;
     }
     const int ntiles = ntypes * R * NT;
     const int grid = ntiles < nsm * blocks_per_sm ? ntiles : nsm * blocks_per_sm;
