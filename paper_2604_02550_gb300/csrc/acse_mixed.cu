@@ -460,6 +460,21 @@ int tc_mixed_alloc(acse_ctx* c) {
     ACSE_TRY(mx_alloc((void**)&w.w32, 2 * R2 * sizeof(float), false));
     ACSE_TRY(mx_alloc((void**)&w.Q32, 2 * R2 * sizeof(float), false));
     ACSE_TRY(mx_alloc((void**)&w.tc_err, sizeof(int), true));
+    if (c->opt.prec == ACSE_BF16X3 && r % 16 == 0 && r <= 64) {   // the B products on the tensor cores
+        for (int k = 0; k < 8; ++k) {
+            const size_t items = (k >> 1) < 2 ? P : R2;
+            ACSE_TRY(mx_alloc((void**)&w.bx[k], items * R2 * sizeof(float), false));
+        }
+        int* h = (int*)malloc(P * sizeof(int));
+        if (!h) return ACSE_ERR_NOMEM;
+        for (int i = 0; i < (int)r; ++i)
+            for (int j = i + 1; j < (int)r; ++j) h[pk_pair((int)r, i, j)] = i * (int)r + j;
+        int s = mx_alloc((void**)&w.pair_ij, P * sizeof(int), false);
+        if (s == ACSE_OK && cudaMemcpy(w.pair_ij, h, P * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            s = ACSE_ERR_CUDA;
+        free(h);
+        ACSE_TRY(s);
+    }
     return ACSE_OK;
 }
 
@@ -469,7 +484,8 @@ void tc_mixed_free(acse_ctx* c) {
                     w.tc_pairC[0], w.tc_pairC[1], w.tc_pairC[2], w.M32[0], w.M32[1], w.M32[2], w.tc_Md, w.tc_Zd,
                     w.tc_Mf[0], w.tc_Mf[1], w.tc_Zf[0], w.tc_Zf[1], w.tc_X5f[0], w.tc_X5f[1], w.tc_X5d,
                     w.H32[0], w.H32[1], w.H32[2], w.zdiag32, w.gam32, w.w32, w.Q32, w.tc_err,
-                    w.Kh32[0], w.Kh32[1], w.Kh32[2], w.A32[0], w.A32[1], w.A32[2], w.W32s[0], w.W32s[1], w.W32s[2]};
+                    w.Kh32[0], w.Kh32[1], w.Kh32[2], w.A32[0], w.A32[1], w.A32[2], w.W32s[0], w.W32s[1], w.W32s[2],
+                    w.bx[0], w.bx[1], w.bx[2], w.bx[3], w.bx[4], w.bx[5], w.bx[6], w.bx[7], w.pair_ij};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }

@@ -401,6 +401,8 @@ struct BTiledArgs {
     const T* ny[4];     // NY three-body term per spin type (acse_ny.cu), added to B; null for V
     int flip;           // spin-flip specialisation: no bb items; the b-led particle-hole blocks and the
                         // second flip sector are read as their alpha-led flips
+    const T* bx[8];     // precomputed products (k_B_pipe<.., true>): per type t, x1 rows at bx[2t] and
+                        // x2^T rows at bx[2t + 1], r^2 per item (the type's item number, see acse_btc.cu)
 };
 
 // Block (i, j).  Spin types t = 0 (aaaa), 1 (bbbb), 2 (abab), 3 (abba):
@@ -632,12 +634,15 @@ __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, c
 __device__ __forceinline__ int bp_k(int kind, int kb, int nt, int a) { return kind == 0 ? kb + nt * a : 4 * kb + a; }
 __device__ __forceinline__ int bp_l(int kind, int lb, int nt, int b) { return kind == 2 ? lb + nt * b : 4 * lb + b; }
 
-template <int MAXT, int MINB, int RP>
+// PRE: the products x1 and x2 come precomputed (the tensor-core kernel of acse_btc.cu, r a multiple of
+// 16): no operand staging, each thread reads its 4 x 4 tile of x1 and of x2^T with 16-byte loads; the
+// shared memory holds only the B rows.
+template <int MAXT, int MINB, int RP, bool PRE = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ BTiledArgs<float> a) {
     extern __shared__ __align__(16) unsigned char tl_smem[];
     const int r = a.r, rp = RP ? RP : pad4(r), ld = rp + 4, R2 = r * r, bpitch = r + 1;
     const int nt = rp / 4, nt2 = nt * nt, S = (nt2 + 31) & ~31;
-    const size_t tile = (size_t)rp * ld;
+    const size_t tile = PRE ? 0 : (size_t)rp * ld;
     float* gA = (float*)tl_smem;          // 1D_a [p][l]
     float* gB = gA + tile;                // 1D_b
     float* wAT = gB + tile;               // w_a^T [p][k]
@@ -645,14 +650,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
     float* buf = wBT + tile;              // [2][X, M] operand tiles, element (u, v) of a row at u * ld + v
     float* Bs = buf + 4 * tile;           // [2][r][r + 1]
     const size_t R22 = 2 * (size_t)R2;
-    for (int e = threadIdx.x; e < 8 * (int)tile; e += blockDim.x) gA[e] = 0.f;
-    __syncthreads();
-    for (int e = threadIdx.x; e < R2; e += blockDim.x) {
-        const int u = e / r, v = e - u * r;
-        gA[u * ld + v] = a.gam[e];
-        gB[u * ld + v] = a.gam[R2 + e];
-        wAT[v * ld + u] = a.w[e];          // w[k][p] -> w^T[p][k]
-        wBT[v * ld + u] = a.w[R2 + e];
+    if (!PRE) {
+        for (int e = threadIdx.x; e < 8 * (int)tile; e += blockDim.x) gA[e] = 0.f;
+        __syncthreads();
+        for (int e = threadIdx.x; e < R2; e += blockDim.x) {
+            const int u = e / r, v = e - u * r;
+            gA[u * ld + v] = a.gam[e];
+            gB[u * ld + v] = a.gam[R2 + e];
+            wAT[v * ld + u] = a.w[e];          // w[k][p] -> w^T[p][k]
+            wBT[v * ld + u] = a.w[R2 + e];
+        }
     }
     const bool vec = (r & 3) == 0;
     const bool yvec = (r & 1) == 0;
@@ -688,6 +695,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
     // operands of step s (item blockIdx.x + s gridDim.x): X and M rows of its sector
     // (round 0 -> aa (0), round 1 -> bb (2), round 2 -> ab (1))
     auto issue = [&](int step, int slot) {
+        if (PRE) return;
         int round, ii, jj;
         item((int)blockIdx.x + step * (int)gridDim.x, round, ii, jj);
         const size_t ij = (size_t)ii * r + jj;
@@ -754,6 +762,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             else if (!a.flip) { X5b = a.X5d + R2 * R22; ld5 = R22; X8b = a.X5f2; ld8 = R2; }
             else { X5b = a.X5d + R2; ld5 = R22; X8b = a.X5f1; ld8 = R2; }   // flips of X5d(b,a), X5f2
             float part1[4][4];   // x1 group: (s1 x1 + x7 - x4 - 2 x8) / 9, added after the barrier
+            // this item's number among the type's items (rows of the precomputed products)
+            const int it = round == 0 ? (int)blockIdx.x + step * (int)gridDim.x
+                         : round == 1 ? (int)blockIdx.x + step * (int)gridDim.x - P : ij;
             if (grp == 1) {
                 // x2 = sum_p w[k][p] M(l, p) (types 0, 1, 3: M row holds M[l][p]; type 2: M[p][l]) and the
                 // gathered x5 (loaded before the product)
@@ -771,9 +782,19 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                     }
                 }
                 float acc[4][4];
-                const float* wT = (t == 0 || t == 2) ? wAT : wBT;
-                if (kind == 1) bp_product<1, RP>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
-                else bp_product<2, RP>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                if (PRE) {   // x2[k][l] = x2^T row l, column k: four consecutive k per load
+                    const float* x2t = a.bx[2 * t + 1] + (size_t)it * R2;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int l = bp_l(kind, lb, nt, v);
+                        const float4 q = *reinterpret_cast<const float4*>(x2t + (size_t)l * r + 4 * kb);
+                        acc[0][v] = q.x; acc[1][v] = q.y; acc[2][v] = q.z; acc[3][v] = q.w;
+                    }
+                } else {
+                    const float* wT = (t == 0 || t == 2) ? wAT : wBT;
+                    if (kind == 1) bp_product<1, RP>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                    else bp_product<2, RP>(acc, wT, Ms, ld, r, rp, nt, kb, lb);
+                }
                 const float c2 = t == 2 ? 2.f : -2.f;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -811,9 +832,19 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                         part1[u][v] = x47 - 2.f * x8r[lc];
                     }
                 }
-                const float* g1 = (t == 0 || t == 3) ? gA : gB;
-                if (t == 3) bp_product<1, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
-                else bp_product<0, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                if (PRE) {   // x1 row k, four consecutive l per load
+                    const float* x1r = a.bx[2 * t] + (size_t)it * R2;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = bp_k(kind1, kb, nt, u);
+                        const float4 q = *reinterpret_cast<const float4*>(x1r + (size_t)k * r + 4 * lb);
+                        x1[u][0] = q.x; x1[u][1] = q.y; x1[u][2] = q.z; x1[u][3] = q.w;
+                    }
+                } else {
+                    const float* g1 = (t == 0 || t == 3) ? gA : gB;
+                    if (t == 3) bp_product<1, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                    else bp_product<0, RP>(x1, Xs, g1, ld, r, rp, nt, kb, lb);
+                }
                 const float s1 = t == 3 ? -1.f : 1.f;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
@@ -1030,6 +1061,37 @@ int launch_B_tiled(acse_ctx* c) {
         a.X5d = w.tc_X5d; a.X5f1 = w.tc_X5f[0]; a.X5f2 = w.tc_X5f[1];
         for (int t = 0; t < 4; ++t) a.ny[t] = (const float*)ny_terms(c, t);
         a.gam = w.gam32; a.w = w.w32; a.Q = w.Q32;
+        for (int k = 0; k < 8; ++k) a.bx[k] = w.bx[k];
+        // BF16x3, r a multiple of 16: the products on the tensor cores first, then the B kernel without them
+        const int bs = launch_Bx_tc(c);
+        if (bs == ACSE_OK) {
+            static thread_local int pre_r = -1, pre_flip = -1, pre_grid = 0;
+            const int nt = pad4(r) / 4, nt2 = nt * nt;
+            const int threads = (((nt2 + 31) & ~31) + nt2 + 31) / 32 * 32;
+            const size_t smem = 2 * (size_t)r * (r + 1) * sizeof(float);
+            const bool r48 = r == 48;
+            const void* kern = r48 ? (const void*)k_B_pipe<320, 2, 48, true> : threads <= 320
+                                   ? (const void*)k_B_pipe<320, 2, 0, true> : (const void*)k_B_pipe<BP_MAX_THREADS, 1, 0, true>;
+            if (pre_r != r || pre_flip != a.flip) {
+                int per_sm = 1, nsm = 152, dev = 0;
+                if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+                    per_sm < 1) {
+                    cudaGetLastError();
+                    per_sm = 1;
+                }
+                const int items = (a.flip ? 1 : 2) * (r * (r - 1) / 2) + R2;
+                pre_grid = nsm * per_sm < items ? nsm * per_sm : items;
+                pre_r = r;
+                pre_flip = a.flip;
+            }
+            if (r48) k_B_pipe<320, 2, 48, true><<<pre_grid, threads, smem, c->stream>>>(a);
+            else if (threads <= 320) k_B_pipe<320, 2, 0, true><<<pre_grid, threads, smem, c->stream>>>(a);
+            else k_B_pipe<BP_MAX_THREADS, 1, 0, true><<<pre_grid, threads, smem, c->stream>>>(a);
+            ACSE_LAUNCHED(c);
+            return ACSE_OK;
+        }
+        if (bs != ACSE_ERR_UNSUPPORTED) return bs;
         static thread_local int cached_r = -1, cached_flip = -1, cached_grid = 0;
         const int nt2 = (pad4(r) / 4) * (pad4(r) / 4);
         const int threads = (((nt2 + 31) & ~31) + nt2 + 31) / 32 * 32;

@@ -45,7 +45,7 @@ def _problem(r, n, seed, kind):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "tf32"])
 @pytest.mark.parametrize("r,n,kind", [(4, 2, "state"), (6, 3, "state"), (9, 3, "pair"), (12, 4, "pair"),
-                                      (17, 5, "pair")])
+                                      (16, 5, "pair"), (17, 5, "pair")])
 def test_singlet_residual_parity(acse, prec, r, n, kind):
     p = _problem(r, n, 300 + r, kind)
     Db = (p.Daa, p.Dab, p.Dbb)
