@@ -140,7 +140,7 @@ struct Work {
     float* A32[3];
     float* W32s[3];
     // BF16x3 with r a multiple of 16: the B products x1 and x2^T of the four spin types, precomputed on
-    // the tensor cores (acse_r5tc.cu; class 2 t + {0, 1}, r^2 floats per item), and the same-spin item ->
+    // the tensor cores (acse_btc.cu; class 2 t + {0, 1}, r^2 floats per item), and the same-spin item ->
     // i r + j table (pairs i < j in packed order); null otherwise
     float* bx[8];
     int* pair_ij;
@@ -225,8 +225,8 @@ int launch_W_intermediates(acse_ctx* c, const double* const W[3]);
 int launch_build_B(acse_ctx* c);
 int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32[3]);
 int launch_B_tiled(acse_ctx* c);
-int launch_Z_tc(acse_ctx* c, const float* const W32[3], int ntypes, const int* tmap);   // acse_r5tc.cu
-int launch_Bx_tc(acse_ctx* c);                                                           // acse_r5tc.cu
+int launch_Z_tc(acse_ctx* c, const float* const W32[3], int ntypes, const int* tmap);   // acse_ztc.cu
+int launch_Bx_tc(acse_ctx* c);                                                           // acse_btc.cu
 int tiled_set_attrs();
 int launch_Q(acse_ctx* c);
 int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double* const out[3],

@@ -402,7 +402,7 @@ struct BTiledArgs {
     int flip;           // spin-flip specialisation: no bb items; the b-led particle-hole blocks and the
                         // second flip sector are read as their alpha-led flips
     const T* bx[8];     // precomputed products (k_B_pipe<.., true>): per type t, x1 rows at bx[2t] and
-                        // x2^T rows at bx[2t + 1], r^2 per item (the type's item number, see acse_r5tc.cu)
+                        // x2^T rows at bx[2t + 1], r^2 per item (the type's item number, see acse_btc.cu)
 };
 
 // Block (i, j).  Spin types t = 0 (aaaa), 1 (bbbb), 2 (abab), 3 (abba):
@@ -634,7 +634,7 @@ __device__ __forceinline__ void bp_product(float (&acc)[4][4], const float* A, c
 __device__ __forceinline__ int bp_k(int kind, int kb, int nt, int a) { return kind == 0 ? kb + nt * a : 4 * kb + a; }
 __device__ __forceinline__ int bp_l(int kind, int lb, int nt, int b) { return kind == 2 ? lb + nt * b : 4 * lb + b; }
 
-// PRE: the products x1 and x2 come precomputed (the tensor-core kernel of acse_r5tc.cu, r a multiple of
+// PRE: the products x1 and x2 come precomputed (the tensor-core kernel of acse_btc.cu, r a multiple of
 // 16): no operand staging, each thread reads its 4 x 4 tile of x1 and of x2^T with 16-byte loads; the
 // shared memory holds only the B rows.
 template <int MAXT, int MINB, int RP, bool PRE = false>
@@ -993,7 +993,7 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32
         o.Zd = w.tc_Zd; o.Zf[0] = w.tc_Zf[0]; o.Zf[1] = w.tc_Zf[1];
         o.mode = c->opt.prec == ACSE_BF16X3 ? 1 : (c->opt.prec == ACSE_TF32X3 ? 3 : 2);
         o.ldd = c->nsplit * w.Kp2; o.ldf = c->nsplit * w.Kp1; o.Kp1 = w.Kp1; o.Kp2 = w.Kp2; o.diag = w.zdiag32;
-        // BF16x3 with r a multiple of 16: the products on the tensor cores (acse_r5tc.cu)
+        // BF16x3 with r a multiple of 16: the products on the tensor cores (acse_ztc.cu)
         const int zs = launch_Z_tc(c, W32, o.ntypes, o.tmap);
         if (zs == ACSE_OK) {
             k_w_from_diag<float><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag32, w.w32, sf ? 1 : 0);
