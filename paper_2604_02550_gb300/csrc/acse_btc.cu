@@ -18,7 +18,7 @@
 #include "acse_internal.h"
 #include "tc_ptx.cuh"
 
-#define BXT_THREADS 128
+#define BXT_THREADS 256   // two threads per tile row (producer), two warps per TMEM lane quarter (epilogue)
 #define BXT_A_SEG (TC_BM * 128)
 #define BXT_WAIT_NS 4000000000ull
 
@@ -45,7 +45,7 @@ static __device__ __forceinline__ uint4 bxt_pack8(const __nv_bfloat16 (&x)[8]) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(BXT_THREADS) k_Bx_tc(const __grid_constant__ BxtArgs a) {
+__global__ void __launch_bounds__(BXT_THREADS, 4) k_Bx_tc(const __grid_constant__ BxtArgs a) {
     static_assert(R % 16 == 0 && R <= 64, "N = r must be a multiple of 16 and K = r fit one 64-element block");
     constexpr int R2 = R * R;
     constexpr int B_SEG = R * 128;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(BXT_THREADS) k_Bx_tc(const __grid_constant__ B
         }
         // A: row m = (item, row) of X_ij (x1) or M_ij (x2), K = q; types 3 (x1) and 2 (x2) transposed
         {
-            const int ml = threadIdx.x, m = m0 + ml;
+            const int ml = threadIdx.x & 127, half = threadIdx.x >> 7, m = m0 + ml;
             const bool valid = m < nrows;
             const int item = valid ? m / R : 0, row = valid ? m - item * R : 0;
             const int sec = t == 0 ? 0 : t == 1 ? 2 : 1;
@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(BXT_THREADS) k_Bx_tc(const __grid_constant__ B
             const float* base = (x2 ? a.M[sec] : a.X[sec]) + ij * R2;
             const bool tr = x2 ? (t == 2) : (t == 3);
 #pragma unroll
-            for (int cc = 0; cc < 8; ++cc) {
+            for (int i = 0; i < 4; ++i) {   // this thread's half of the row: chunks cc = half, half + 2, ...
+                const int cc = 2 * i + half;
                 __nv_bfloat16 hi[8], lo[8];
                 if (valid && 8 * cc < R) {
                     float xv[8];
@@ -156,20 +157,20 @@ __global__ void __launch_bounds__(BXT_THREADS) k_Bx_tc(const __grid_constant__ B
         ok = __syncthreads_and(bounded_wait(bar, phase, BXT_WAIT_NS, nullptr)) != 0;
         if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
         tc_fence_after();
-        {   // epilogue: row m of the class's output, r floats, 16-byte stores
-            const int m = m0 + warp * 32 + lane;
-            uint32_t v[2][32];
+        // epilogue: warp w holds TMEM lanes 32 (w mod 4) .. + 31 (rows m), columns 32 (w / 4) .. + 31
+        const int q4 = warp & 3, ch = warp >> 2;
+        if (32 * ch < R) {
+            const int m = m0 + q4 * 32 + lane;
+            uint32_t v[32];
             __syncwarp();
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v[0]);
-            if (R > 32) tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, v[1]);
+            tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(32 * ch), v);
             if (ok && m < nrows) {
-                float* dst = a.out[c] + (size_t)m * R;
+                float* dst = a.out[c] + (size_t)m * R + 32 * ch;
 #pragma unroll
-                for (int n = 0; n < R; n += 4)
-                    *reinterpret_cast<float4*>(dst + n) =
-                        make_float4(__uint_as_float(v[n >> 5][n & 31]), __uint_as_float(v[(n + 1) >> 5][(n + 1) & 31]),
-                                    __uint_as_float(v[(n + 2) >> 5][(n + 2) & 31]),
-                                    __uint_as_float(v[(n + 3) >> 5][(n + 3) & 31]));
+                for (int n = 0; n < 32; n += 4)
+                    if (32 * ch + n < R)
+                        *reinterpret_cast<float4*>(dst + n) = make_float4(__uint_as_float(v[n]), __uint_as_float(v[n + 1]),
+                                                                          __uint_as_float(v[n + 2]), __uint_as_float(v[n + 3]));
             }
         }
         tc_fence_before();

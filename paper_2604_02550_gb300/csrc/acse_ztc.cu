@@ -20,7 +20,7 @@
 #include "acse_internal.h"
 #include "tc_ptx.cuh"
 
-#define ZTC_THREADS 128
+#define ZTC_THREADS 256   // two threads per tile row (producer), two warps per TMEM lane quarter (epilogue)
 #define ZTC_A_SEG (TC_BM * 128)     // one K block of the A tile: 128 rows x 128 bytes
 #define ZTC_WAIT_NS 4000000000ull
 
@@ -49,7 +49,7 @@ static __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&x)[8]) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ ZtcArgs a, int ntiles) {
+__global__ void __launch_bounds__(ZTC_THREADS, 4) k_Z_tc(const __grid_constant__ ZtcArgs a, int ntiles) {
     static_assert(R % 16 == 0 && R <= 64, "N = r must be a multiple of 16 and K = r fit one 64-element block");
     constexpr int R2 = R * R, NT = (R2 + TC_BM - 1) / TC_BM;
     constexpr int B_SEG = R * 128;                       // one K block of a 1D tile: R rows x 128 B
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
         }
         // A: row m = p r + s of W_k^T, K = q; the slice W_kp[q][s] of type t (see k_Z_pipe)
         {
-            const int ml = threadIdx.x, m = m0 + ml;
+            const int ml = threadIdx.x & 127, half = threadIdx.x >> 7, m = m0 + ml;
             const bool valid = m < R2;
             const int p = valid ? m / R : 0, s = valid ? m - p * R : 0;
             const float* base;
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
                 default: tr = false; base = a.W[1] + (size_t)p * r3 + (size_t)k * R2; break;
             }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int i = 0; i < 4; ++i) {   // this thread's half of the row: chunks c = half, half + 2, ...
+                const int c = 2 * i + half;
                 __nv_bfloat16 hi[8], lo[8];
                 if (valid && 8 * c < R) {
                     float x[8];
@@ -167,9 +168,10 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
         ok = __syncthreads_and(bounded_wait(bar, phase, ZTC_WAIT_NS, nullptr)) != 0;
         if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
         tc_fence_after();
-        // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows m), columns j
-        {
-            const int ml = warp * 32 + lane, m = m0 + ml;
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows m), columns 32 (w / 4) .. + 31 (j)
+        const int q4 = warp & 3, ch = warp >> 2;
+        if (32 * ch < R) {
+            const int ml = q4 * 32 + lane, m = m0 + ml;
             const bool valid = ok && m < R2;
             const int p = m / R, s = m - p * R;
             int which, sK, sP;
@@ -180,14 +182,15 @@ __global__ void __launch_bounds__(ZTC_THREADS) k_Z_tc(const __grid_constant__ Zt
             const size_t ld = which < 0 ? (size_t)a.ldd : (size_t)a.ldf;
             const int Kp = which < 0 ? a.Kp2 : a.Kp1;
             const size_t col = (size_t)sP * R2 + m;
-            uint32_t v[2][32];
+            uint32_t v[32];
             __syncwarp();
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v[0]);
-            if (R > 32) tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, v[1]);
+            tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(32 * ch), v);
             if (valid) {
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const float x = __uint_as_float(v[j >> 5][j & 31]);
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = 32 * ch + jj;
+                    if (j >= R) break;
+                    const float x = __uint_as_float(v[jj]);
                     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
                     const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
                     __nv_bfloat16* row = base + ((size_t)sK * R2 + (size_t)k * R + j) * ld + col;
