@@ -187,18 +187,22 @@ def test_golden_line_search_trajectory(acse, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "ozaki", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "ozaki", "bf16x3", "ozaki6->ozaki"])
 def test_golden_config3_fixed_step_trajectory(acse, prec):
     """The headline r = 48 CAS(8e,8o) workload: five Euler steps at eps = 1e-4 against the stored oracle
     trajectory (tests/golden/cfg3_fixed_eps_5.json, written by make_golden.py from the oracle alone):
     E and ||A||^2 at every step and 64 seeded entries of each block of D_5.  FP64-accurate paths: 1e-10 Eh
     on E and 1e-12 relative on ||A||^2 and D; BF16x3: its error grows with what the steps change, a bound
     of 3e-5 of the energy drop so far (measured 1.0e-5, 7.1e-5, 1.1e-4, 1.5e-4, 1.8e-4 Eh after the five
-    steps, whose drops are 6.0, 11.1, 15.7, 20.0, 23.9 Eh: four to eighteen times below the bound)."""
+    steps, whose drops are 6.0, 11.1, 15.7, 20.0, 23.9 Eh: four to eighteen times below the bound); the
+    Ozaki 6 -> 8 slice schedule: 1e-7 Eh (its 6-slice steps carry about 2^-30 relative error)."""
     g = json.load(open(os.path.join(HERE, "golden", "cfg3_fixed_eps_5.json")))
     p = I.config_problem(3)
     assert p.name == g["system"] and p.r == R
-    ctx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec)
+    if prec == "ozaki6->ozaki":   # the precision schedule: 6 slices until ||A||^2 falls by < 10 % a step
+        ctx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, "ozaki", oz_slices=6, refine=True, refine_tol=0.1)
+    else:
+        ctx = acse.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec)
     D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
     E0 = float(ctx.energy(D))
     assert E0 == pytest.approx(g["E"][0], abs=1e-10)
@@ -215,6 +219,9 @@ def test_golden_config3_fixed_step_trajectory(acse, prec):
           f"; max rel ||A||^2 {max(dNs):.2e}; sampled D_5 {dD / scale:.2e}")
     if prec in ("fp64", "ozaki"):
         assert max(dEs) < 1e-10 and max(dNs) < 1e-12 and dD < 1e-12 * scale
+    elif prec == "ozaki6->ozaki":
+        # 6 slices carry about 2^-30 relative per GEMM product (measured 3e-9 Eh per step over 100 steps)
+        assert max(dEs) < 1e-7 and max(dNs) < 1e-8 and dD < 1e-8 * scale
     else:
         for k, d in enumerate(dEs):
             assert d < 3e-5 * abs(g["E"][k + 1] - g["E"][0]), f"step {k}"
