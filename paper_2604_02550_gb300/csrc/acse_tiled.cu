@@ -768,17 +768,24 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
             if (grp == 1) {
                 // x2 = sum_p w[k][p] M(l, p) (types 0, 1, 3: M row holds M[l][p]; type 2: M[p][l]) and the
                 // gathered x5 (loaded before the product)
-                const int kind = t == 2 ? 1 : 2;
+                // PRE: no product, so every type takes the 4 x 4 ownership k = 4 kb + u, l = 4 lb + v, under
+                // which x2^T (four consecutive k) and x5 (four consecutive l) are 16-byte loads (r % 4 == 0)
+                const int kind = (PRE || t == 2) ? 1 : 2;
                 float g5[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = bp_k(kind, kb, nt, u);
                     const int kc = k < r ? k : r - 1;
                     const float* x5r = X5b + ((size_t)kc * r + j) * ld5 + (size_t)i * r;
+                    if (PRE) {
+                        const float4 q = *reinterpret_cast<const float4*>(x5r + 4 * lb);
+                        g5[u][0] = q.x; g5[u][1] = q.y; g5[u][2] = q.z; g5[u][3] = q.w;
+                    } else {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int l = bp_l(kind, lb, nt, v);
-                        g5[u][v] = x5r[l < r ? l : r - 1];
+                        for (int v = 0; v < 4; ++v) {
+                            const int l = bp_l(kind, lb, nt, v);
+                            g5[u][v] = x5r[l < r ? l : r - 1];
+                        }
                     }
                 }
                 float acc[4][4];
@@ -817,19 +824,36 @@ __global__ void __launch_bounds__(MAXT, MINB) k_B_pipe(const __grid_constant__ B
                 const float* g4 = t == 0 ? ga : t == 1 ? gb : t == 2 ? gb : nullptr;
                 const float* Q7 = t == 0 ? a.Q : t == 1 ? a.Q + R2 : t == 3 ? a.Q + R2 : nullptr;
                 const float* g7 = t == 0 ? ga : t == 1 ? gb : t == 3 ? ga : nullptr;
+                if (PRE) {   // r % 4 == 0: the 1D rows and the x8 row as 16-byte loads
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 g7v = g7 ? *reinterpret_cast<const float4*>(g7 + i * r + 4 * lb) : z4;
+                    const float4 g4v = g4 ? *reinterpret_cast<const float4*>(g4 + j * r + 4 * lb) : z4;
+                    const float g7a[4] = {g7v.x, g7v.y, g7v.z, g7v.w}, g4a[4] = {g4v.x, g4v.y, g4v.z, g4v.w};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = bp_k(kind1, kb, nt, u);
-                    const int kc = k < r ? k : r - 1;
-                    const float q4 = Q4 ? Q4[kc * r + i] : 0.f;
-                    const float q7 = Q7 ? Q7[kc * r + j] : 0.f;
-                    const float* x8r = X8b + ((size_t)kc * r + i) * ld8 + (size_t)j * r;
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = bp_k(kind1, kb, nt, u);
+                        const float q4 = Q4 ? Q4[k * r + i] : 0.f;
+                        const float q7 = Q7 ? Q7[k * r + j] : 0.f;
+                        const float4 x8 = *reinterpret_cast<const float4*>(X8b + ((size_t)k * r + i) * ld8 + (size_t)j * r + 4 * lb);
+                        const float x8a[4] = {x8.x, x8.y, x8.z, x8.w};
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int l = 4 * lb + v;
-                        const int lc = l < r ? l : r - 1;
-                        const float x47 = (Q7 ? q7 * g7[i * r + lc] : 0.f) - (Q4 ? q4 * g4[j * r + lc] : 0.f);
-                        part1[u][v] = x47 - 2.f * x8r[lc];
+                        for (int v = 0; v < 4; ++v) part1[u][v] = (q7 * g7a[v] - q4 * g4a[v]) - 2.f * x8a[v];
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = bp_k(kind1, kb, nt, u);
+                        const int kc = k < r ? k : r - 1;
+                        const float q4 = Q4 ? Q4[kc * r + i] : 0.f;
+                        const float q7 = Q7 ? Q7[kc * r + j] : 0.f;
+                        const float* x8r = X8b + ((size_t)kc * r + i) * ld8 + (size_t)j * r;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const int l = 4 * lb + v;
+                            const int lc = l < r ? l : r - 1;
+                            const float x47 = (Q7 ? q7 * g7[i * r + lc] : 0.f) - (Q4 ? q4 * g4[j * r + lc] : 0.f);
+                            part1[u][v] = x47 - 2.f * x8r[lc];
+                        }
                     }
                 }
                 if (PRE) {   // x1 row k, four consecutive l per load
