@@ -52,6 +52,8 @@ def parse():
                     help="copy D_0 back into D every this many steps (keeps long runs on the stable stretch)")
     ap.add_argument("--sustain-s", type=float, default=1.5,
                     help="seconds of untimed steps before the timed region, sampled for the clock record")
+    ap.add_argument("--gemm-tile", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core GEMM tiling: 0 default, 1 one SM per tile, 2 CTA pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="measure FP64/TF32/BF16 matmul peaks and exit")
@@ -472,7 +474,8 @@ def main():
         args.eps = 1e-4 if p.r >= 32 else 1e-3
     stream = torch.cuda.Stream()
     singlet = bool(args.singlet) and prec != "fp64"
-    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream, recon=args.recon, singlet=singlet)
+    ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=stream, recon=args.recon, singlet=singlet,
+                   gemm_tile=args.gemm_tile)
     with torch.cuda.stream(stream):
         D0 = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
         D = tuple(x.clone() for x in D0)

@@ -26,7 +26,7 @@ class AcseOpts(ctypes.Structure):
     _fields_ = [("r", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("prec", c_int), ("recon", c_int),
                 ("mask_active", c_int), ("act_lo", c_int), ("act_hi", c_int), ("line_search", c_int),
                 ("eps0", c_double), ("check_inputs", c_int), ("singlet", c_int), ("oz_slices", c_int),
-                ("refine", c_int), ("refine_slices", c_int), ("refine_tol", c_double)]
+                ("refine", c_int), ("refine_slices", c_int), ("refine_tol", c_double), ("gemm_tile", c_int)]
 
 
 class AcseError(RuntimeError):
@@ -126,7 +126,7 @@ RECON = {"V": 0, "NY": 1}
 
 def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
                 check_inputs=False, stream=None, recon="V", singlet=False, oz_slices=0, refine=False,
-                refine_slices=0, refine_tol=0.0):
+                refine_slices=0, refine_tol=0.0, gemm_tile=0):
     o = AcseOpts()
     o.r, o.n_alpha, o.n_beta = r, n_alpha, n_beta
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -141,6 +141,7 @@ def acse_create(r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=Fa
     o.refine = int(bool(refine))
     o.refine_slices = int(refine_slices)
     o.refine_tol = float(refine_tol)
+    o.gemm_tile = int(gemm_tile)
     h_ = c_void_p()
     st = current_stream_handle() if stream is None else stream
     _check(lib().acse_create(byref(h_), byref(o), ptr(h), ptr(V), st), "acse_create")

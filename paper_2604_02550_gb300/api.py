@@ -21,7 +21,7 @@ class ACSE:
 
     def __init__(self, r, n_alpha, n_beta, h, V, prec="fp64", mask=None, line_search=False, eps0=1e-3,
                  check_inputs=False, device="cuda", stream=None, recon="V", singlet=False, oz_slices=0,
-                 refine=False, refine_slices=0, refine_tol=0.0):
+                 refine=False, refine_slices=0, refine_tol=0.0, gemm_tile=0):
         self.r, self.n_alpha, self.n_beta = r, n_alpha, n_beta
         self.device = torch.device(device)
         self.prec = prec
@@ -32,7 +32,7 @@ class ACSE:
             self.ctx = _lib.acse_create(r, n_alpha, n_beta, h_t, V_t, prec, mask, line_search, eps0, check_inputs,
                                         stream=self.stream.cuda_stream, recon=recon, singlet=singlet,
                                         oz_slices=oz_slices, refine=refine, refine_slices=refine_slices,
-                                        refine_tol=refine_tol)
+                                        refine_tol=refine_tol, gemm_tile=gemm_tile)
         self._scal = torch.zeros(3, dtype=torch.float64, device=self.device)
 
     def close(self):

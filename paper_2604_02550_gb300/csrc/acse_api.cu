@@ -154,6 +154,7 @@ extern "C" int acse_create(acse_ctx** out, const acse_opts* o, const double* h, 
     if (o->singlet && o->n_alpha != o->n_beta) return ACSE_ERR_ARG;
     if (o->mask_active && (o->act_lo < 0 || o->act_hi > o->r || o->act_lo >= o->act_hi)) return ACSE_ERR_SHAPE;
     if (o->refine != 0 && o->refine != 1) return ACSE_ERR_ARG;
+    if (o->gemm_tile < 0 || o->gemm_tile > 2) return ACSE_ERR_ARG;
     if (o->refine && (o->singlet || o->refine_tol < 0.0 || !(o->refine_tol == o->refine_tol) ||
                       (o->refine_slices != 0 && (o->refine_slices < 4 || o->refine_slices > 10))))
         return ACSE_ERR_ARG;

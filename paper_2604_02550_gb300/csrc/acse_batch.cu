@@ -226,7 +226,9 @@ static int build_tables(acse_batch* B, int choice, int split_r2) {
     if (choice == 0) { bns[0] = 256; B->ntab = 1; }
     else if (choice == 1) { bns[0] = 128; B->ntab = 1; }
     else { bns[0] = 128; bns[1] = 256; B->ntab = 2; }
-    for (int t = 0; t < B->ntab; ++t) ACSE_TRY(tc_table_init(&B->tab[t], kind, bns[t]));
+    // 256-wide tables run on CTA pairs unless the instances ask for one SM per tile (acse_opts.gemm_tile)
+    const int pairs = B->ctx[0]->opt.gemm_tile != 1;
+    for (int t = 0; t < B->ntab; ++t) ACSE_TRY(tc_table_init_mode(&B->tab[t], kind, bns[t], pairs));
     for (int i = 0; i < B->n; ++i) {
         acse_ctx* c = B->ctx[i];
         int t = 0;

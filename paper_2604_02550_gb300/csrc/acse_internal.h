@@ -49,6 +49,9 @@ struct TcTable {
     TcBatch* host;
     int kind;        // 0 = bf16 (kind::f16), 1 = tf32
     int bn;          // tile width
+    int bm;          // tile height: 128, or 256 for CTA pairs
+    int pair;        // 1: CTA-pair kernel (cta_group::2, 256 x 256 tiles, one cluster of two CTAs per tile)
+    int nclusters;   // CTA pairs of the persistent grid (co-resident clusters)
     int stages;
     size_t smem;
     int pers;        // 1: persistent kernel (one CTA per SM, double-buffered TMEM accumulators)
@@ -60,6 +63,8 @@ struct TcTable {
 // indices CTA by CTA (costliest first within a CTA), CTA c owning order[start[c] .. start[c+1]).
 void tc_lpt_schedule(const long long* cost, int T, int G, int* order, int* start);
 int tc_table_init(TcTable* t, int kind, int bn);
+int tc_table_init_mode(TcTable* t, int kind, int bn, int pair);
+int tc_use_pairs(const struct acse_ctx* c);   // CTA-pair GEMM tiles for this context (acse_opts.gemm_tile)
 void tc_table_free(TcTable* t);
 int tc_table_upload(TcTable* t);
 int tc_table_append(TcTable* t, struct acse_ctx* c);

@@ -376,7 +376,7 @@ int ny_alloc(acse_ctx* c) {
         const int ops = kind == 0 ? 2 : 4;
         const size_t ld = (size_t)4 * y->Kbw;
         for (int s = 0; s < 2; ++s) {
-            ACSE_TRY(tc_table_init(&y->st[s], kind, tc_default_bn(r)));
+            ACSE_TRY(tc_table_init_mode(&y->st[s], kind, tc_default_bn(r), tc_use_pairs(c)));
             for (int g = 3 * s; g < 3 * s + 3; ++g)
                 for (int k = 0; k < y->nprob[g]; ++k) {
                     const int rb = y->prob[g][k][0], cb = y->prob[g][k][1], q0 = y->prob[g][k][2], cnt = y->prob[g][k][3];

@@ -391,6 +391,194 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_pers(const TcBatch* _
     }
 }
 
+// ------------------------------------------------------------ persistent CTA-pair variant
+// A cluster of two CTAs on two SMs computes 256 x 256 output tiles with the pair MMA (cta_group::2,
+// M = 256, N = 256): each CTA loads its 128 rows of A and its 128 rows of B (the rows n0 .. n0 + 127
+// in the even CTA, n0 + 128 .. n0 + 255 in the odd one) per K block, so per SM a K block moves
+// 32 KB through shared memory for 128 x 256 x 64 MACs instead of the 48 KB of a one-SM 128 x 256
+// tile; shared-memory bandwidth, which the TMA writes and the MMA reads share, bounds the one-SM
+// kernel.  The even CTA's thread issues the MMAs and the commits, which arrive on the barriers of
+// both CTAs (empty[s], accf[ab], drainb); both CTAs' TMA loads complete on the even CTA's full[s]
+// (it expects the bytes of both); the epilogue warps of both CTAs arrive on the even CTA's acce[ab].
+// The clusters walk the tile lists of the host's LPT schedule (one list per cluster); every wait is
+// bounded as in k_gemm_tc_pers, and the CTAs meet at a cluster barrier before the TMEM is freed.
+template <int KIND, int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc2_pers(const TcBatch* __restrict__ bp) {
+    const TcBatch& b = *bp;
+    constexpr int BN = 256;
+    constexpr int A_BYTES = TC_BM * 128;     // this CTA's 128 rows of A per K block
+    constexpr int B_BYTES = 128 * 128;       // this CTA's 128 rows of B per K block
+    constexpr int KELEM = KIND == 0 ? 64 : 32;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;   // [2]
+    uint64_t* acce = accf + 2;         // [2], used in the even CTA
+    uint64_t* never = acce + 2;
+    uint64_t* drainb = never + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drainb + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const int cl = blockIdx.x >> 1;
+    const int q0 = b.cta_start[cl], q1 = b.cta_start[cl + 1];   // this cluster's tiles
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], 8);
+        }
+        mbar_init(never, 1);
+        mbar_init(drainb, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_slot, 2 * BN);
+    tc_fence_before();
+    cluster_sync_all();   // both CTAs' barriers are initialised before either signals the other's
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t full0 = mapa_rank(smem_u32(full), 0);   // the even CTA's full[0]
+            int it = 0;
+            bool stop = false;
+            for (int qi = q0; qi < q1 && !stop; ++qi) {
+                const int t = b.order[qi];
+                const int pi = tc_find_problem(b, t);
+                const TcProb& P = b.p[pi];
+                const int local = t - P.tile_start;
+                const int m0 = (local / P.tiles_n) * 256 + (int)rank * 128;
+                const int n0 = (local % P.tiles_n) * BN + (int)rank * 128;
+                for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !bounded_wait(&empty[s], ((it / STAGES) & 1) ^ 1, b.wait_ns, abort_flag)) {
+                        raise_abort(b.err, abort_flag);
+                        stop = true;
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
+                    tma_load_2d_pair(sA + s * A_BYTES, &b.tmA[pi], kb * KELEM, m0, full0 + 8u * s);
+                    tma_load_2d_pair(sB + s * B_BYTES, &b.tmB[pi], kb * KELEM, n0, full0 + 8u * s);
+                }
+            }
+            // every issued copy must have landed before the CTA may exit: the even CTA's full[s]
+            // counts both CTAs' bytes (and the CTAs leave together, after the cluster barrier below);
+            // the odd CTA also waits for the MMAs that read its last stages, briefly after an abort
+            for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k) {
+                const unsigned long long lim = *abort_flag ? b.wait_ns : TC_DRAIN_NS;
+                const bool ok = rank == 0 ? bounded_wait(&full[k % STAGES], (k / STAGES) & 1, lim, nullptr)
+                                          : bounded_wait(&empty[k % STAGES], (k / STAGES) & 1, lim, nullptr);
+                if (!ok) {
+                    raise_abort(b.err, abort_flag);
+                    if (rank != 0) break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            const uint32_t idesc = make_idesc_pair<KIND, BN>();
+            if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
+            int it = 0, lt = 0;
+            for (int qi = q0; qi < q1 && !*abort_flag; ++qi, ++lt) {
+                const int t = b.order[qi];
+                const int pi = tc_find_problem(b, t);
+                const int nk = b.p[pi].kblocks;
+                const int ab = lt & 1, use = lt >> 1;
+                if (use >= 1 &&
+                    !bounded_wait_cluster(&acce[ab], (use - 1) & 1, b.wait_ns + TC_DRAIN_NS, abort_flag)) {
+                    raise_abort(b.err, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(ab * BN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!bounded_wait(&full[s], (it / STAGES) & 1, b.wait_ns, abort_flag)) {
+                        raise_abort(b.err, abort_flag);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = smem_desc(sA + s * A_BYTES);
+                    const uint64_t db = smem_desc(sB + s * B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_pair<KIND>(acc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                    umma_commit_pair(&empty[s]);
+                }
+                umma_commit_pair(&accf[ab]);
+            }
+            umma_commit_pair(drainb);
+        }
+        // both CTAs: no MMA of the pair is in flight past this point (bounded)
+        if (lane == 0 && !bounded_wait(drainb, 0, b.wait_ns + 2 * TC_DRAIN_NS, nullptr)) raise_abort(b.err, abort_flag);
+    } else {
+        const int q = warp & 3;   // TMEM lane quadrant this warp may access
+        const uint32_t acce0 = mapa_rank(smem_u32(acce), 0);
+        int lt = 0;
+        for (int qi = q0; qi < q1; ++qi, ++lt) {
+            const int t = b.order[qi];
+            const int ab = lt & 1, use = lt >> 1;
+            int go = 0;
+            if (lane == 0) {
+                const bool ok = bounded_wait(&accf[ab], use & 1, b.wait_ns + TC_DRAIN_NS, abort_flag);
+                if (!ok) raise_abort(b.err, abort_flag);
+                go = ok && !*abort_flag;
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) break;
+            tc_fence_after();
+            const int pi = tc_find_problem(b, t);
+            const TcProb& P = b.p[pi];
+            const int local = t - P.tile_start;
+            const int row = (local / P.tiles_n) * 256 + (int)rank * 128 + q * 32 + lane;
+            const int n0 = (local % P.tiles_n) * BN;
+            float* Crow = P.C + (size_t)row * P.ldc;
+            const bool vec = (P.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0;
+            const bool store = P.kblocks > 0;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                __syncwarp();
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);   // warp-collective
+                const int col0 = n0 + c * 32;
+                if (store && row < P.M && col0 < P.N) {
+                    if (vec && col0 + 32 <= P.N) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            float4 o = make_float4(P.alpha * __uint_as_float(v[j]), P.alpha * __uint_as_float(v[j + 1]),
+                                                   P.alpha * __uint_as_float(v[j + 2]),
+                                                   P.alpha * __uint_as_float(v[j + 3]));
+                            *reinterpret_cast<float4*>(Crow + col0 + j) = o;
+                        }
+                    } else {
+                        for (int j = 0; j < 32 && col0 + j < P.N; ++j) Crow[col0 + j] = P.alpha * __uint_as_float(v[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(acce0 + 8u * ab);   // this warp's quarter is free
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    cluster_sync_all();   // neither CTA exits while the other may still signal its barriers
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 2 * BN);
+    }
+}
+
 // --------------------------------------------------------------------------- host plan
 // A table (TcTable, acse_internal.h) holds the problems of one grouped launch; its TcBatch lives in
 // device memory (the tensor maps are written by the host before any launch reads them).
@@ -402,6 +590,27 @@ struct TcPlan {
 static int stages_for(int bn) { return bn == 256 ? 4 : 6; }
 
 static size_t smem_for(int bn, int stages) { return (size_t)stages * (TC_BM + bn) * 128 + 1024 + 256; }
+
+#define TC2_STAGES 6                         // ring depth of the CTA-pair kernel (32 KB a stage per CTA)
+static size_t smem_pair() { return (size_t)TC2_STAGES * (TC_BM + 128) * 128 + 1024 + 256; }
+
+// Clusters of the CTA-pair kernel that fit on the device at once (its persistent grid).
+template <int KIND>
+static int pair_attr_and_clusters(int nsm, int* nclusters) {
+    auto kern = k_gemm_tc2_pers<KIND, TC2_STAGES>;
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pair()));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (nsm / 2), 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem_pair();
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = nsm / 2;
+    }
+    *nclusters = n < nsm / 2 ? n : nsm / 2;
+    return ACSE_OK;
+}
 
 template <int KIND, int BN>
 static int set_attr() {
@@ -452,12 +661,14 @@ int tc_encode_map_bf16(void* map, const void* base, int rows, int inner_elems, i
     return encode_map(0, (CUtensorMap*)map, base, rows, inner_elems, box_rows, row_stride);
 }
 
-int tc_table_init(TcTable* t, int kind, int bn) {
+int tc_table_init_mode(TcTable* t, int kind, int bn, int pair) {
     memset(t, 0, sizeof(*t));
     t->kind = kind;
     t->bn = bn;
-    t->stages = stages_for(bn);
-    t->smem = smem_for(bn, t->stages);
+    t->pair = pair && bn == 256;
+    t->bm = t->pair ? 2 * TC_BM : TC_BM;
+    t->stages = t->pair ? TC2_STAGES : stages_for(bn);
+    t->smem = t->pair ? smem_pair() : smem_for(bn, t->stages);
     if (kind == 0) ACSE_TRY(bn == 256 ? (set_attr<0, 256>()) : (set_attr<0, 128>()));
     else ACSE_TRY(bn == 256 ? (set_attr<1, 256>()) : (set_attr<1, 128>()));
     t->pers = 1;
@@ -468,6 +679,8 @@ int tc_table_init(TcTable* t, int kind, int bn) {
         cudaGetLastError();
         t->nsm = 152;
     }
+    if (t->pair) ACSE_TRY(kind == 0 ? pair_attr_and_clusters<0>(t->nsm, &t->nclusters)
+                                    : pair_attr_and_clusters<1>(t->nsm, &t->nclusters));
     t->host = (TcBatch*)calloc(1, sizeof(TcBatch));
     if (!t->host) return ACSE_ERR_NOMEM;
     t->host->wait_ns = TC_WAIT_NS;
@@ -477,6 +690,8 @@ int tc_table_init(TcTable* t, int kind, int bn) {
     }
     return ACSE_OK;
 }
+
+int tc_table_init(TcTable* t, int kind, int bn) { return tc_table_init_mode(t, kind, bn, 0); }
 
 void tc_table_free(TcTable* t) {
     if (t->dev) cudaFree(t->dev);
@@ -512,11 +727,12 @@ void tc_lpt_schedule(const long long* cost, int T, int G, int* order, int* start
 int tc_table_upload(TcTable* t) {
     TcBatch& b = *t->host;
     const int T = b.total_tiles;
-    const int G = T < t->nsm ? T : t->nsm;
+    const int slots = t->pair ? t->nclusters : t->nsm;   // CTAs, or CTA pairs, of the persistent grid
+    const int G = T < slots ? T : slots;
     if (T > 0) {
         std::vector<long long> cost(T);
         for (int p = 0; p < b.nprob; ++p) {
-            const int n = ((b.p[p].M + TC_BM - 1) / TC_BM) * b.p[p].tiles_n;
+            const int n = ((b.p[p].M + t->bm - 1) / t->bm) * b.p[p].tiles_n;
             for (int k = 0; k < n; ++k) cost[b.p[p].tile_start + k] = b.p[p].kblocks + 4;
         }
         const int need = T + G + 1;
@@ -549,7 +765,7 @@ int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t
     if (b.nprob + 1 > TC_MAXP || L % kel || lda < (size_t)L || ldb < (size_t)L) return ACSE_ERR_SHAPE;
     const int n = b.nprob;
     ACSE_TRY(encode_map(t->kind, &b.tmA[n], A, M, L, TC_BM, lda));
-    ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->bn, ldb));
+    ACSE_TRY(encode_map(t->kind, &b.tmB[n], B, N, L, t->pair ? t->bn / 2 : t->bn, ldb));
     TcProb& p = b.p[n];
     p.C = C;
     p.M = M;
@@ -560,7 +776,7 @@ int tc_table_add_ld(TcTable* t, const void* A, size_t lda, const void* B, size_t
     p.tiles_n = (N + t->bn - 1) / t->bn;
     p.tile_start = b.total_tiles;
     p.perm_r = 0;
-    b.total_tiles += ((M + TC_BM - 1) / TC_BM) * p.tiles_n;
+    b.total_tiles += ((M + t->bm - 1) / t->bm) * p.tiles_n;
     b.nprob = n + 1;
     return ACSE_OK;
 }
@@ -602,6 +818,13 @@ int tc_table_append(TcTable* t, acse_ctx* c) {
 int tc_table_launch(const TcTable* t, cudaStream_t st) {
     const int tiles = t->host->total_tiles;
     if (tiles == 0) return ACSE_OK;
+    if (t->pair) {
+        const int g = tiles < t->nclusters ? tiles : t->nclusters;
+        if (t->kind == 0) k_gemm_tc2_pers<0, TC2_STAGES><<<2 * g, TC_THREADS, t->smem, st>>>(t->dev);
+        else k_gemm_tc2_pers<1, TC2_STAGES><<<2 * g, TC_THREADS, t->smem, st>>>(t->dev);
+        ACSE_CUDA_TRY(cudaGetLastError());
+        return ACSE_OK;
+    }
     if (t->pers) {
         const int g = tiles < t->nsm ? tiles : t->nsm;
         if (t->kind == 0) {
@@ -627,6 +850,9 @@ int tc_table_launch(const TcTable* t, cudaStream_t st) {
 
 int tc_default_bn(int r) { return r * r >= 256 ? 256 : 128; }
 
+// The CTA-pair form is the default of the 256-wide tiles; acse_opts.gemm_tile = 1 keeps one SM per tile.
+int tc_use_pairs(const acse_ctx* c) { return c->opt.gemm_tile != 1 && tc_default_bn(c->r) == 256; }
+
 int tc_mixed_alloc(acse_ctx* c);
 void tc_mixed_free(acse_ctx* c);
 
@@ -636,7 +862,8 @@ int tc_plan_create(acse_ctx* c) {
     c->tc_plan = pl;
     ACSE_TRY(get_encode(&pl->encode));
     ACSE_TRY(tc_mixed_alloc(c));
-    ACSE_TRY(tc_table_init(&pl->tab, (c->opt.prec == ACSE_TF32 || c->opt.prec == ACSE_TF32X3) ? 1 : 0, tc_default_bn(c->r)));
+    ACSE_TRY(tc_table_init_mode(&pl->tab, (c->opt.prec == ACSE_TF32 || c->opt.prec == ACSE_TF32X3) ? 1 : 0,
+                                tc_default_bn(c->r), tc_use_pairs(c)));
     ACSE_TRY(tc_table_append(&pl->tab, c));
     return tc_table_upload(&pl->tab);
 }

@@ -58,6 +58,7 @@ def _create(L, opts, with_h=True, with_V=True, with_out=True):
     (dict(refine=2), ARG), (dict(refine=1, singlet=1), ARG), (dict(refine=1, refine_slices=3), ARG),
     (dict(refine=1, refine_slices=11), ARG), (dict(refine=1, refine_tol=-1e-3), ARG),
     (dict(refine=1, refine_tol=float("nan")), ARG),
+    (dict(gemm_tile=-1), ARG), (dict(gemm_tile=3), ARG),
 ])
 def test_create_rejects_invalid_options(L, kw, want):
     assert _create(L, _opts(**kw)) == want
