@@ -112,13 +112,13 @@ typedef struct {
                         * acse_energy run in the precision in force.  Not with opts.singlet.            */
     int refine_slices; /* slices of the refined precision, 4..10; 0 -> 8                                */
     double refine_tol; /* relative fall of ||A||^2 per step below which the schedule switches; 0 -> 1e-2 */
-    int gemm_tile;     /* tiling of the tensor-core O(r^6) GEMMs (ACSE_BF16X3, ACSE_TF32, ACSE_TF32X3; r >= 16):
+    int gemm_tile;     /* tiling of the tensor-core O(r^6) GEMMs (every precision but ACSE_FP64; r >= 16):
                         * 0 default (the CTA-pair form), 1 one SM per 128 x 256 output tile, 2 CTA pairs:
                         * clusters of two CTAs on two SMs share each 256 x 256 tile through the pair MMA
                         * (tcgen05 cta_group::2), each CTA loading half of both operand tiles.  The results
                         * are the same in both forms (same products, same FP32 accumulation order).  For
-                        * r < 16 the tiles are 128 x 128 on one SM whatever the value.  The NY GEMMs follow
-                        * it; a batch follows its first instance's value.                               */
+                        * r < 16 the tiles are 128 x 128 on one SM whatever the value.  The NY GEMMs and the
+                        * adjoint's Ozaki GEMMs follow it; a batch follows its first instance's value.   */
 } acse_opts;
 
 /* Create a context for one problem.  h (r*r) and V (r^4, chemist's (pq|rs)) are read once to

@@ -37,6 +37,7 @@
 #define OZ_THREADS 192
 #define OZ_BN 256
 #define OZ_STAGES 4
+#define OZ2_STAGES 6         // ring depth of the CTA-pair form (32 KB a stage per CTA)
 #define OZ_DRAIN_NS 2000000000ull
 #define OZ_WAIT_NS 4000000000ull
 #define OZ_SLICE_PPT 16      // element pairs per thread of a sliced row: K <= 2 * 256 * 16 = 2 * 64^2
@@ -215,11 +216,16 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSlic
 }
 
 // ------------------------------------------------------------------------------- GEMM
-template <int BN, int STAGES>
+// PAIR: the CTA-pair form of gemm_tc.cu (launched in clusters of two CTAs; pair MMA of M = 256 on
+// 256 x BN tiles, each CTA loading its 128 rows of A and BN / 2 rows of B; the even CTA issues the MMAs
+// and commits to the barriers of both; both CTAs' loads complete on the even CTA's full[s]; both
+// CTAs' epilogue warps arrive on the even CTA's acce[ab]).
+template <int BN, int STAGES, bool PAIR>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __restrict__ bp) {
     const OzBatch& b = *bp;
     constexpr int A_BYTES = TC_BM * 128;
-    constexpr int B_BYTES = BN * 128;
+    constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * 128;
+    constexpr int BM = PAIR ? 2 * TC_BM : TC_BM;   // rows of an output tile
     constexpr int KELEM = 64;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -236,7 +242,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = b.S;
-    const int q0 = b.cta_start[blockIdx.x], q1 = b.cta_start[blockIdx.x + 1];   // this CTA's tiles
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // CTA, or CTA pair
+    const int q0 = b.cta_start[unit], q1 = b.cta_start[unit + 1];        // this unit's tiles
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -244,21 +252,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accf[a], 1);
-            mbar_init(&acce[a], 4);
+            mbar_init(&acce[a], PAIR ? 8 : 4);
         }
         mbar_init(never, 1);
         mbar_init(drainb, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
+    if (warp == 1) {
+        if constexpr (PAIR) tmem_alloc_pair(tmem_slot, 2 * BN);
+        else tmem_alloc(tmem_slot, 2 * BN);
+    }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
         if (lane == 0) {
+            const uint32_t full0 = PAIR ? mapa_rank(smem_u32(full), 0) : 0u;   // the even CTA's full[0]
             int it = 0;
             bool stop = false;
             for (int qi = q0; qi < q1 && !stop; ++qi) {
@@ -266,7 +279,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                 const int pi = oz_find_problem(b, t);
                 const OzProb& P = b.p[pi];
                 const int local = t - P.tile_start;
-                const int m0 = (local / P.tiles_n) * TC_BM, n0 = (local % P.tiles_n) * BN;
+                const int m0 = (local / P.tiles_n) * BM + (int)rank * TC_BM;
+                const int n0 = (local % P.tiles_n) * BN + (int)rank * (BN / 2);
                 for (int gi = 0; gi < P.ngroups && !stop; ++gi) {
                     int L, s0, s1;
                     oz_group(S, P.g, gi, L, s0, s1);
@@ -278,20 +292,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                             stop = true;
                             break;
                         }
-                        mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
-                        tma_load_2d(sA + s * A_BYTES, &b.tmA[pi], (ka + kb) * KELEM, m0, &full[s]);
-                        tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], (kb0 + kb) * KELEM, n0, &full[s]);
+                        if constexpr (PAIR) {
+                            if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
+                            tma_load_2d_pair(sA + s * A_BYTES, &b.tmA[pi], (ka + kb) * KELEM, m0, full0 + 8u * s);
+                            tma_load_2d_pair(sB + s * B_BYTES, &b.tmB[pi], (kb0 + kb) * KELEM, n0, full0 + 8u * s);
+                        } else {
+                            mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                            tma_load_2d(sA + s * A_BYTES, &b.tmA[pi], (ka + kb) * KELEM, m0, &full[s]);
+                            tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], (kb0 + kb) * KELEM, n0, &full[s]);
+                        }
                     }
                 }
             }
-            // every issued copy must have landed before the CTA may exit
-            for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k)
-                if (!bounded_wait(&full[k % STAGES], (k / STAGES) & 1, OZ_DRAIN_NS, nullptr))
+            // every issued copy must have landed before the CTA may exit (with pairs: the even CTA's
+            // full[s] counts both CTAs' bytes; the odd CTA also waits for the MMAs that read its last
+            // stages, briefly after an abort)
+            for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k) {
+                const unsigned long long lim = *abort_flag ? b.wait_ns : OZ_DRAIN_NS;
+                const bool ok = rank == 0 ? bounded_wait(&full[k % STAGES], (k / STAGES) & 1, lim, nullptr)
+                                          : bounded_wait(&empty[k % STAGES], (k / STAGES) & 1, lim, nullptr);
+                if (!ok) {
                     raise_abort(b.err, abort_flag);
+                    if (rank != 0) break;
+                }
+            }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            const uint32_t idesc = make_idesc<0, BN>();
+        if (lane == 0 && rank == 0) {
+            const uint32_t idesc = PAIR ? make_idesc_pair<0, BN>() : make_idesc<0, BN>();
             if (b.inject_stall && !bounded_wait(never, 0, b.wait_ns, abort_flag)) raise_abort(b.err, abort_flag);
             int it = 0, lt = 0;
             for (int qi = q0; qi < q1 && !*abort_flag; ++qi) {
@@ -301,9 +329,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                     oz_group(S, P.g, gi, L, s0, s1);
                     const int n = (s1 - s0 + 1) * P.kbs;
                     const int ab = lt & 1, use = lt >> 1;
-                    if (use >= 1 && !bounded_wait(&acce[ab], (use - 1) & 1, b.wait_ns + OZ_DRAIN_NS, abort_flag)) {
-                        raise_abort(b.err, abort_flag);
-                        break;
+                    if (use >= 1) {
+                        const bool ok = PAIR ? bounded_wait_cluster(&acce[ab], (use - 1) & 1, b.wait_ns + OZ_DRAIN_NS, abort_flag)
+                                             : bounded_wait(&acce[ab], (use - 1) & 1, b.wait_ns + OZ_DRAIN_NS, abort_flag);
+                        if (!ok) {
+                            raise_abort(b.err, abort_flag);
+                            break;
+                        }
                     }
                     tc_fence_after();
                     const uint32_t acc = tmem + (uint32_t)(ab * BN);
@@ -317,24 +349,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                         const uint64_t da = smem_desc(sA + s * A_BYTES);
                         const uint64_t db = smem_desc(sB + s * B_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) umma<0>(acc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
-                        umma_commit(&empty[s]);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if constexpr (PAIR) umma_pair<0>(acc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                            else umma<0>(acc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                        }
+                        if constexpr (PAIR) umma_commit_pair(&empty[s]);
+                        else umma_commit(&empty[s]);
                     }
-                    umma_commit(&accf[ab]);   // the epilogue of this group may start when its MMAs are done
+                    // the epilogue of this group may start when its MMAs are done
+                    if constexpr (PAIR) umma_commit_pair(&accf[ab]);
+                    else umma_commit(&accf[ab]);
                 }
             }
-            umma_commit(drainb);
-            if (!bounded_wait(drainb, 0, OZ_DRAIN_NS, nullptr)) raise_abort(b.err, abort_flag);
+            if constexpr (PAIR) umma_commit_pair(drainb);
+            else umma_commit(drainb);
         }
+        // no MMA is in flight past this point (bounded; with pairs in both CTAs)
+        if (lane == 0 && (PAIR || rank == 0) && !bounded_wait(drainb, 0, b.wait_ns + 2 * OZ_DRAIN_NS, nullptr))
+            raise_abort(b.err, abort_flag);
     } else {
         const int q = warp & 3;   // TMEM lane quadrant this warp may access
+        const uint32_t acce0 = PAIR ? mapa_rank(smem_u32(acce), 0) : 0u;
         int lt = 0;
         bool run = true;
         for (int qi = q0; qi < q1 && run; ++qi) {
             const int t = b.order[qi];
             const OzProb& P = b.p[oz_find_problem(b, t)];
             const int local = t - P.tile_start;
-            const int m0 = (local / P.tiles_n) * TC_BM, n0 = (local % P.tiles_n) * BN;
+            const int m0 = (local / P.tiles_n) * BM + (int)rank * TC_BM, n0 = (local % P.tiles_n) * BN;
             const int row = m0 + q * 32 + lane;
             const bool rok = row < P.M;
             const bool vec = (P.N & 3) == 0 && (reinterpret_cast<uintptr_t>(P.stage) & 15) == 0;
@@ -376,15 +418,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[ab]);   // this warp's quarter of the buffer is free
+                if (lane == 0) {   // this warp's quarter of the buffer is free
+                    if constexpr (PAIR) mbar_arrive_cluster(acce0 + 8u * ab);
+                    else mbar_arrive(&acce[ab]);
+                }
             }
         }
     }
+    __syncwarp();
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();   // neither CTA exits while the other may still signal it
+    else __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        if constexpr (PAIR) tmem_dealloc_pair(tmem, 2 * BN);
+        else tmem_dealloc(tmem, 2 * BN);
     }
 }
 
@@ -521,6 +569,9 @@ struct OzPlan {
     OzBatch* host;
     OzBatch* dev;
     int S, bn;
+    int pair;           // 1: CTA-pair kernel (256 x 256 tiles on clusters of two CTAs)
+    int bm;             // rows of a tile: 128, or 256 with pairs
+    int nclusters;      // co-resident CTA pairs (the persistent grid of the pair kernel)
     size_t smem;
     int nsm;
     int tiles;
@@ -537,6 +588,33 @@ struct OzPlan {
 };
 
 static size_t oz_smem(int bn) { return (size_t)OZ_STAGES * (TC_BM + bn) * 128 + 1024 + 256; }
+static size_t oz_smem_pair() { return (size_t)OZ2_STAGES * (TC_BM + OZ_BN / 2) * 128 + 1024 + 256; }
+
+// Launch of the GEMM kernel of plan pl (pl->tiles > 0): one CTA per SM, or one cluster of two per pair.
+static int oz_launch_gemm(const OzPlan* pl, cudaStream_t st) {
+    if (pl->pair) {
+        const int g = pl->tiles < pl->nclusters ? pl->tiles : pl->nclusters;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * g, 1, 1);
+        cfg.blockDim = dim3(OZ_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = pl->smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        ACSE_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gemm_oz<OZ_BN, OZ2_STAGES, true>, (const OzBatch*)pl->dev));
+        return ACSE_OK;
+    }
+    const int g = pl->tiles < pl->nsm ? pl->tiles : pl->nsm;
+    if (pl->bn == 256) k_gemm_oz<256, OZ_STAGES, false><<<g, OZ_THREADS, pl->smem, st>>>(pl->dev);
+    else k_gemm_oz<128, OZ_STAGES, false><<<g, OZ_THREADS, pl->smem, st>>>(pl->dev);
+    ACSE_CUDA_TRY(cudaGetLastError());
+    return ACSE_OK;
+}
 
 static int oz_op_alloc(OzOp& o, int rows, int K, int S) {
     o.rows = rows;
@@ -557,7 +635,7 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
     const int n = B.nprob;
     const size_t ld = (size_t)pl->S * a.Kp;
     ACSE_TRY(tc_encode_map_bf16(&B.tmA[n], a.sl, a.rows, (int)ld, TC_BM, ld));
-    ACSE_TRY(tc_encode_map_bf16(&B.tmB[n], b.sl, b.rows, (int)ld, pl->bn, ld));
+    ACSE_TRY(tc_encode_map_bf16(&B.tmB[n], b.sl, b.rows, (int)ld, pl->pair ? pl->bn / 2 : pl->bn, ld));
     OzProb& p = B.p[n];
     p.C = C;
     p.sa = a.scale;
@@ -581,7 +659,7 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
     }
     p.tiles_n = (p.N + pl->bn - 1) / pl->bn;
     p.tile_start = B.total_tiles;
-    B.total_tiles += ((p.M + TC_BM - 1) / TC_BM) * p.tiles_n;
+    B.total_tiles += ((p.M + pl->bm - 1) / pl->bm) * p.tiles_n;
     B.nprob = n + 1;
     return cap < 1 ? ACSE_ERR_SHAPE : ACSE_OK;
 }
@@ -589,20 +667,46 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
 static int oz_plan_finish(OzPlan* pl);
 
 // Kernel attributes, SM count and the zeroed problem table of a plan.
-static int oz_plan_init(OzPlan* pl, int S, int bn) {
+static int oz_plan_init(OzPlan* pl, int S, int bn, int pair) {
     pl->S = S;
     pl->bn = bn;
-    pl->smem = oz_smem(pl->bn);
-    if (pl->bn == 256)
-        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<256, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+    pl->pair = pair && bn == OZ_BN;
+    pl->bm = pl->pair ? 2 * TC_BM : TC_BM;
+    pl->smem = pl->pair ? oz_smem_pair() : oz_smem(pl->bn);
+    if (pl->pair)
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<OZ_BN, OZ2_STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pl->smem));
+    else if (pl->bn == 256)
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<256, OZ_STAGES, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pl->smem));
     else
-        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<128, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_oz<128, OZ_STAGES, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pl->smem));
     pl->nsm = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         pl->nsm = 152;
+    }
+    if (pl->pair) {   // co-resident clusters of two (the persistent grid)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * (pl->nsm / 2), 1, 1);
+        cfg.blockDim = dim3(OZ_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = pl->smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (void*)k_gemm_oz<OZ_BN, OZ2_STAGES, true>, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = pl->nsm / 2;
+        }
+        pl->nclusters = n < pl->nsm / 2 ? n : pl->nsm / 2;
     }
     pl->host = (OzBatch*)calloc(1, sizeof(OzBatch));
     if (!pl->host) return ACSE_ERR_NOMEM;
@@ -616,7 +720,7 @@ int oz_plan_create(acse_ctx* c) {
     if (!pl) return ACSE_ERR_NOMEM;
     c->oz_plan = pl;
     const int r = c->r, R2 = r * r, R22 = 2 * R2, P = r * (r - 1) / 2;
-    ACSE_TRY(oz_plan_init(pl, c->opt.oz_slices, R2 >= 256 ? OZ_BN : 128));
+    ACSE_TRY(oz_plan_init(pl, c->opt.oz_slices, R2 >= 256 ? OZ_BN : 128, c->opt.gemm_tile != 1));
     ACSE_TRY(oz_op_alloc(pl->A[0], 2 * P, P, pl->S));
     ACSE_TRY(oz_op_alloc(pl->A[1], R2, R2, pl->S));
     ACSE_TRY(oz_op_alloc(pl->A[2], R2, R2, pl->S));
@@ -674,7 +778,8 @@ static int oz_plan_finish(OzPlan* pl) {
     OzBatch& B = *pl->host;
     pl->tiles = B.total_tiles;
     if (pl->tiles > 0) {
-        const int T = pl->tiles, G = T < pl->nsm ? T : pl->nsm;
+        const int units = pl->pair ? pl->nclusters : pl->nsm;   // CTAs, or CTA pairs, of the persistent grid
+        const int T = pl->tiles, G = T < units ? T : units;
         const int nprod = pl->S * (pl->S + 1) / 2;
         int* hs = (int*)malloc((size_t)(T + G + 1) * sizeof(int));
         long long* cost = (long long*)malloc((size_t)T * sizeof(long long));
@@ -684,7 +789,7 @@ static int oz_plan_finish(OzPlan* pl) {
             return ACSE_ERR_NOMEM;
         }
         for (int p = 0; p < B.nprob; ++p) {
-            const int n = ((B.p[p].M + TC_BM - 1) / TC_BM) * B.p[p].tiles_n;
+            const int n = ((B.p[p].M + pl->bm - 1) / pl->bm) * B.p[p].tiles_n;
             for (int k = 0; k < n; ++k) cost[B.p[p].tile_start + k] = (long long)nprod * B.p[p].kbs + 4 * B.p[p].ngroups;
         }
         tc_lpt_schedule(cost, T, G, hs, hs + T);
@@ -799,10 +904,8 @@ int oz_gemm_launch(acse_ctx* c) {
     OzPlan* pl = (OzPlan*)c->oz_plan;
     if (!pl) return ACSE_ERR_UNSUPPORTED;
     if (pl->tiles == 0) return ACSE_OK;
-    const int g = pl->tiles < pl->nsm ? pl->tiles : pl->nsm;
     ACSE_TRY(prof_begin(c));
-    if (pl->bn == 256) k_gemm_oz<256, OZ_STAGES><<<g, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
-    else k_gemm_oz<128, OZ_STAGES><<<g, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
+    ACSE_TRY(oz_launch_gemm(pl, c->stream));
     ACSE_LAUNCHED(c);
     k_oz_reduce<<<dim3(2 * pl->nsm, pl->host->nprob), 256, 0, c->stream>>>(pl->dev);
     ACSE_LAUNCHED(c);
@@ -865,7 +968,7 @@ static int oz_list_create(OzPlan* root, const GemmF64* g, int n, OzPlan** out) {
     *out = pl;
     int maxN = 0;
     for (int i = 0; i < n; ++i) maxN = g[i].N > maxN ? g[i].N : maxN;
-    ACSE_TRY(oz_plan_init(pl, root->S, maxN >= 256 ? OZ_BN : 128));
+    ACSE_TRY(oz_plan_init(pl, root->S, maxN >= 256 ? OZ_BN : 128, root->pair));
     pl->host->err = root->err;
     for (int i = 0; i < n; ++i) {
         ACSE_TRY(oz_op_alloc(pl->A[i], g[i].M, g[i].K, pl->S));
@@ -937,9 +1040,7 @@ int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
     B.inject_stall = root->host->inject_stall;
     ACSE_CUDA_TRY(cudaMemcpyAsync(pl->dev, pl->host, sizeof(OzBatch), cudaMemcpyHostToDevice, c->stream));
     if (pl->tiles == 0) return ACSE_OK;
-    const int grid = pl->tiles < pl->nsm ? pl->tiles : pl->nsm;
-    if (pl->bn == 256) k_gemm_oz<256, OZ_STAGES><<<grid, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
-    else k_gemm_oz<128, OZ_STAGES><<<grid, OZ_THREADS, pl->smem, c->stream>>>(pl->dev);
+    ACSE_TRY(oz_launch_gemm(pl, c->stream));
     ACSE_LAUNCHED(c);
     k_oz_reduce<<<dim3(2 * pl->nsm, B.nprob), 256, 0, c->stream>>>(pl->dev);
     ACSE_LAUNCHED(c);

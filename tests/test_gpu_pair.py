@@ -104,3 +104,53 @@ def test_pair_timeout_status_and_recovery(acse):
     want, _ = oracle_residual_blocks(p, (p.Daa, p.Dab, p.Dbb))
     assert maxrel(to_np(A), want) < TOL["bf16x3"]
     ctx.close()
+
+
+@pytest.mark.parametrize("r,na,nb", [(16, 5, 4), (20, 6, 5), (32, 7, 6)])
+def test_pair_ozaki(acse, r, na, nb):
+    """The Ozaki GEMMs on CTA pairs: the exact integer group sums make the residual identical to the
+    one-SM form's; against the oracle the FP64-accurate bound (1e-12 relative) holds."""
+    p = _problem(r, na, nb, 400 + r)
+    A2, n2 = _residual(acse, p, "ozaki", 2)
+    A1, n1 = _residual(acse, p, "ozaki", 1)
+    want, n2w = oracle_residual_blocks(p, (p.Daa, p.Dab, p.Dbb))
+    err = maxrel(A2, want)
+    d12 = max(float(np.max(np.abs(a - b))) for a, b in zip(A2, A1))
+    print(f"ozaki r={r}: pair vs oracle {err:.3e}; pair vs one-SM max |dA| {d12:.3e}")
+    assert err < 1e-12
+    assert d12 == 0.0 and n2 == n1
+
+
+def test_pair_ozaki_adjoint(acse):
+    """The adjoint's Ozaki GEMM lists run on CTA pairs too (r = 16: 256-wide tiles): gradients identical
+    to the one-SM form's."""
+    p = _problem(16, 5, 4, 77)
+    grads = []
+    for tile in (2, 1):
+        ctx = acse.ACSE(16, 5, 4, p.h, p.V, "ozaki", gemm_tile=tile)
+        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+        dh, dV, dD = ctx.backward([D], 2, 1e-4, 1.0, 0.5)
+        grads.append([dh.cpu().numpy(), dV.cpu().numpy()] + [x.cpu().numpy() for x in dD])
+        ctx.close()
+    d = max(float(np.max(np.abs(a - b))) for a, b in zip(*grads))
+    print(f"ozaki adjoint: pair vs one-SM max |d grad| {d:.3e}")
+    assert d == 0.0
+
+
+def test_pair_ozaki_timeout_status_and_recovery(acse):
+    from paper_2604_02550_gb300 import _lib
+    p = _problem(16, 5, 4, 6)
+    ctx = acse.ACSE(16, 5, 4, p.h, p.V, "ozaki", gemm_tile=2)
+    D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+    _lib.acse_set_wait_bound_ns(ctx.ctx, 1_000_000, inject_stall=True)
+    ctx.residual(D)
+    with pytest.raises(_lib.AcseError) as ei:
+        _lib.acse_sync_status(ctx.ctx)
+    assert ei.value.status == -6
+    _lib.acse_set_wait_bound_ns(ctx.ctx, 0, inject_stall=False)
+    _lib.acse_clear_status(ctx.ctx)
+    A, _ = ctx.residual(D)
+    _lib.acse_sync_status(ctx.ctx)
+    want, _ = oracle_residual_blocks(p, (p.Daa, p.Dab, p.Dbb))
+    assert maxrel(to_np(A), want) < 1e-12
+    ctx.close()
