@@ -591,7 +591,9 @@ static int stages_for(int bn) { return bn == 256 ? 4 : 6; }
 
 static size_t smem_for(int bn, int stages) { return (size_t)stages * (TC_BM + bn) * 128 + 1024 + 256; }
 
+#ifndef TC2_STAGES
 #define TC2_STAGES 6                         // ring depth of the CTA-pair kernel (32 KB a stage per CTA)
+#endif
 static size_t smem_pair() { return (size_t)TC2_STAGES * (TC_BM + 128) * 128 + 1024 + 256; }
 
 // Clusters of the CTA-pair kernel that fit on the device at once (its persistent grid).
