@@ -70,7 +70,7 @@ typedef enum {
  *                whose levels s + t <= slices + 1 are summed exactly in FP32 in groups small enough that
  *                no partial sum reaches 2^24, and the groups are added in FP64.  With the default 8
  *                slices (48 bits) the GEMM error is of the order of 2^-45 |A||B| K, that of FP64.  The
- *                adjoint runs in FP64 FMA. */
+ *                adjoint's O(r^6) GEMMs run by the same scheme. */
 typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2, ACSE_TF32X3 = 3, ACSE_OZAKI = 4 } acse_prec;
 /* 3-RDM reconstruction (Eq. 3rdm_recon / Eq. NY):
  *   ACSE_RECON_V   Valdemoro: the 3-cumulant is neglected;
@@ -128,8 +128,8 @@ typedef struct {
  * doubles plus the split-precision operand copies, and the FP64-accurate context of a precision
  * schedule), so acse_energy, acse_residual and acse_step allocate nothing.  The one exception is
  * acse_residual_backward: its first call on a context allocates the adjoint workspace (about 65 r^4
- * doubles, 2.8 GB at r = 48) and, for a split precision, the FP64 companion context; both stay until
- * acse_destroy.  On any failure *ctx is set to NULL (when ctx itself is not NULL) and nothing stays
+ * doubles, 2.8 GB at r = 48) and, for a split precision, the ACSE_OZAKI companion context; both stay
+ * until acse_destroy.  On any failure *ctx is set to NULL (when ctx itself is not NULL) and nothing stays
  * allocated. */
 int acse_create(acse_ctx** ctx, const acse_opts* opts, const double* h, const double* V,
                 void* cuda_stream);
@@ -165,10 +165,12 @@ int acse_step(acse_ctx* ctx, double* Daa, double* Dab, double* Dbb, double eps,
  * NULL except D_0; missing ones are recomputed from the previous one).  dh and dV are
  * symmetrised (h: p<->q; V: the 8-fold permutational symmetry); dD is projected onto tensors
  * with the symmetries of a 2-RDM (antisymmetric within pairs, pair-Hermitian).  Each output
- * may be NULL.  The reverse sweep always runs in FP64; for a context in a split precision it runs
- * in an FP64 companion context the library creates on first use (same integrals and options), so
- * the gradient is the FP64 adjoint along the trajectory the checkpoints describe: pass every
- * checkpoint of the split-precision forward run (checkpoints left NULL are recomputed in FP64). */
+ * may be NULL.  The reverse sweep is FP64-accurate: FP64 FMA GEMMs in an ACSE_FP64 context, GEMMs by
+ * the Ozaki scheme on the tensor cores in an ACSE_OZAKI context; a context in a split precision runs it
+ * in an ACSE_OZAKI companion context the library creates on first use (same integrals and options,
+ * 8 slices), so the gradient is the FP64-accurate adjoint along the trajectory the checkpoints
+ * describe: pass every checkpoint of the split-precision forward run (checkpoints left NULL are
+ * recomputed in the companion's precision). */
 int acse_residual_backward(acse_ctx* ctx, const double* const* D_ckpt, int n_steps, double eps,
                            double wE, double wN, double* dh, double* dV,
                            double* dDaa, double* dDab, double* dDbb);
@@ -193,7 +195,12 @@ int acse_schedule_state(const acse_ctx* ctx, int* refined, int* steps);
  *     ||A||^2 at the current D, accepted steps, stop reason (0 running, 1 E or ||A|| rose, 2 converged).
  *   acse_batch_info: the tile choice (0 all 256 wide, 1 all 128 wide, 2 split at r^2 = split_r2) and
  *     the kernels launched so far.  1 <= n <= 64 (ACSE_ERR_ARG otherwise, and for mixed precisions);
- *     ACSE_ERR_UNSUPPORTED for the NY reconstruction or ACSE_OZAKI; a failed create leaves *batch NULL. */
+ *     ACSE_ERR_UNSUPPORTED for the NY reconstruction or ACSE_OZAKI; a failed create leaves *batch NULL.
+ *   acse_batch_residual_backward: acse_residual_backward for instance i (its integrals and options; the
+ *     checkpoints D_ckpt as there, for example read with acse_batch_get_D after one-step runs), run in
+ *     the instance's own context once the batch's pending replays are done; synchronous (returns when
+ *     the outputs are written).  Its first call on an instance allocates that instance's adjoint
+ *     workspace as acse_create describes. */
 typedef struct acse_batch acse_batch;
 int acse_batch_create(acse_batch** batch, int n, const acse_opts* opts, const double* const* h,
                       const double* const* V, void* cuda_stream);
@@ -204,6 +211,9 @@ int acse_batch_get_D(acse_batch* batch, int i, double* Daa, double* Dab, double*
 int acse_batch_run(acse_batch* batch, int nsteps, int stop_rule, double* E_out, double* norm2_out,
                    int* steps_out, int* reason_out);
 int acse_batch_info(const acse_batch* batch, int* tune_choice, int* split_r2, long long* launches);
+int acse_batch_residual_backward(acse_batch* batch, int i, const double* const* D_ckpt, int n_steps, double eps,
+                                 double wE, double wN, double* dh, double* dV, double* dDaa, double* dDab,
+                                 double* dDbb);
 
 /* Fit of the asymptotic regime of an energy trajectory.  The Results section describes the energy along
  * lambda = eps n (eps the Euler step, n the iteration; with varying steps lambda_n is the sum of the steps

@@ -19,6 +19,7 @@ EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_
            "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_batch_create",
            "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D", "acse_batch_run", "acse_batch_info",
            "acse_extrapolate", "acse_batch_history", "acse_batch_extrapolate", "acse_schedule_state",
+           "acse_batch_residual_backward",
            "acse_strerror", "acse_last_error", "acse_version")
 
 
@@ -71,11 +72,13 @@ def lib():
         L.acse_extrapolate.argtypes = [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
         L.acse_batch_history.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, POINTER(c_int)]
         L.acse_batch_extrapolate.argtypes = [c_void_p, c_int, c_void_p]
+        L.acse_batch_residual_backward.argtypes = [c_void_p, c_int, POINTER(c_void_p), c_int, c_double, c_double,
+                                                   c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.acse_schedule_state.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int)]
         L.acse_schedule_state.restype = c_int
         for name in ("acse_batch_create", "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D",
                      "acse_batch_run", "acse_batch_info", "acse_extrapolate", "acse_batch_history",
-                     "acse_batch_extrapolate"):
+                     "acse_batch_extrapolate", "acse_batch_residual_backward"):
             getattr(L, name).restype = c_int
         L.acse_sync_status.argtypes = [c_void_p]
         L.acse_clear_status.argtypes = [c_void_p]
@@ -170,6 +173,13 @@ def acse_residual_backward(ctx, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab
     arr = (c_void_p * len(D_ckpt))(*[ptr(x) for x in D_ckpt])
     _check(lib().acse_residual_backward(ctx, arr, int(n_steps), float(eps), float(wE), float(wN), ptr(dh),
                                         ptr(dV), ptr(dDaa), ptr(dDab), ptr(dDbb)), "acse_residual_backward")
+
+
+def acse_batch_residual_backward(b, i, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb):
+    arr = (c_void_p * len(D_ckpt))(*[ptr(x) for x in D_ckpt])
+    _check(lib().acse_batch_residual_backward(b, int(i), arr, int(n_steps), float(eps), float(wE), float(wN),
+                                              ptr(dh), ptr(dV), ptr(dDaa), ptr(dDab), ptr(dDbb)),
+           "acse_batch_residual_backward")
 
 
 def acse_profile(ctx, enable):

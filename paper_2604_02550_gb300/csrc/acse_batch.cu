@@ -483,3 +483,17 @@ extern "C" int acse_batch_info(const acse_batch* B, int* tune_choice, int* split
     }
     return ACSE_OK;
 }
+
+// The adjoint of one instance: acse_residual_backward in the instance's context, ordered after the
+// batch's replays (its intermediate buffers are the replays' scratch; the trajectory state of the
+// batch, D, the previous D and the per-instance scalars, is not touched).
+extern "C" int acse_batch_residual_backward(acse_batch* B, int i, const double* const* D_ckpt, int n_steps,
+                                            double eps, double wE, double wN, double* dh, double* dV, double* dDaa,
+                                            double* dDab, double* dDbb) {
+    if (!B || i < 0 || i >= B->n) return ACSE_ERR_ARG;
+    ACSE_CUDA_TRY(cudaStreamSynchronize(B->stream));
+    acse_ctx* c = B->ctx[i];
+    ACSE_TRY(acse_residual_backward(c, D_ckpt, n_steps, eps, wE, wN, dh, dV, dDaa, dDab, dDbb));
+    ACSE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ACSE_OK;
+}

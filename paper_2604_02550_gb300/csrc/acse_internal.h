@@ -161,7 +161,7 @@ struct acse_ctx {
     Work w;
     void* tc_plan;        // tensor-core GEMM plan (tensor maps etc.)
     void* adj;            // adjoint workspace (allocated by the first acse_residual_backward call)
-    struct acse_ctx* shadow;   // FP64 companion of a split-precision context (its adjoint), or null
+    struct acse_ctx* shadow;   // ACSE_OZAKI companion of a split-precision context (its adjoint), or null
     void* ny;             // NY reconstruction workspace (acse_ny.cu), or null for V
     cudaStream_t aux[3];  // host <-> device copies of the three blocks run concurrently on these
     cudaEvent_t ev_fork, ev_join[3];

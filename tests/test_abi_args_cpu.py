@@ -133,3 +133,4 @@ def test_batch_entry_points_reject_a_null_batch(L):
     assert L.acse_batch_get_D(None, 0, None, None, None) == ARG
     assert L.acse_batch_run(None, 1, 0, None, None, None, None) == ARG
     assert L.acse_batch_info(None, None, None, None) == ARG
+    assert L.acse_batch_residual_backward(None, 0, None, 1, 1e-3, 1.0, 0.0, None, None, None, None, None) == ARG

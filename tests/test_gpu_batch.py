@@ -128,3 +128,44 @@ def test_batch_config4_sixteen_instances(libs):
     tune, split, launches = _lib.acse_batch_info(b)
     print(f"config 4 batch: tile choice {tune} (split r^2 {split}), steps {list(S)}, reasons {list(R)}")
     _lib.acse_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_batch_instance_adjoint(libs, prec):
+    """acse_batch_residual_backward: the gradient of one instance, from checkpoints read off the batch
+    after one-step runs, equals that of a single context with the same checkpoints; the batch's
+    trajectory continues unchanged after it."""
+    _lib, api = libs
+    probs = _mixed_set()
+    eps, nsteps, wE, wN, i = 1e-4, 2, 1.0, 0.5, 2
+    b = _lib.acse_batch_create(probs, prec)
+    for k, p in enumerate(probs):
+        _lib.acse_batch_set_D(b, k, p.Daa, p.Dab, p.Dbb, eps)
+    p = probs[i]
+    ck = [[p.Daa.copy(), p.Dab.copy(), p.Dbb.copy()]]
+    for _ in range(nsteps):
+        _lib.acse_batch_run(b, len(probs), 1, stop_rule=False)
+        ck.append(_get_D(_lib, b, i, p.r))
+    r = p.r
+    dev = lambda x: torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+    ckd = [dev(x) for blk in ck for x in blk]
+    out_b = [torch.zeros((r, r), dtype=torch.float64, device="cuda"), torch.zeros((r,) * 4, dtype=torch.float64, device="cuda")]
+    out_b += [torch.zeros((r,) * 4, dtype=torch.float64, device="cuda") for _ in range(3)]
+    _lib.acse_batch_residual_backward(b, i, ckd, nsteps, eps, wE, wN, *out_b)
+    ctx = api.ACSE(r, p.n_alpha, p.n_beta, p.h, p.V, prec)
+    dh, dV, dD = ctx.backward([tuple(ckd[3 * k:3 * k + 3]) for k in range(nsteps + 1)], nsteps, eps, wE, wN)
+    torch.cuda.synchronize()
+    for a, c in zip(out_b, [dh, dV, *dD]):
+        a, c = a.cpu().numpy(), c.cpu().numpy()
+        assert np.abs(c).max() > 0
+        assert np.abs(a - c).max() <= 1e-13 * np.abs(c).max()
+    ctx.close()
+    # the batch goes on from where it was: one more step equals a single context's third step
+    E, _, _, _ = _lib.acse_batch_run(b, len(probs), 1, stop_rule=False)
+    c2 = api.ACSE(r, p.n_alpha, p.n_beta, p.h, p.V, prec)
+    D = c2.to_blocks((p.Daa, p.Dab, p.Dbb))
+    for _ in range(nsteps + 1):
+        Es, _, _ = c2.step(D, eps)
+    assert E[i] == pytest.approx(float(Es), rel=1e-12)
+    c2.close()
+    _lib.acse_batch_destroy(b)
