@@ -157,20 +157,37 @@ __global__ void __launch_bounds__(BXT_THREADS, 4) k_Bx_tc(const __grid_constant_
         ok = __syncthreads_and(bounded_wait(bar, phase, BXT_WAIT_NS, nullptr)) != 0;
         if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
         tc_fence_after();
-        // epilogue: warp w holds TMEM lanes 32 (w mod 4) .. + 31 (rows m), columns 32 (w / 4) .. + 31
+        // epilogue: warp w holds TMEM lanes 32 (w mod 4) .. + 31 (rows m), columns 32 (w / 4) .. + 31; the rows
+        // go through shared memory (the A tile is free once the MMAs are done; row stride SP floats, 16-byte
+        // chunks XOR-permuted by the row when r is a multiple of 32) and out as the contiguous block of the
+        // tile's 128 output rows, coalesced 16-byte stores
+        constexpr int SP = (R % 32 == 0) ? R : R + 4;
+        static_assert(TC_BM * SP * 4 <= 2 * BXT_A_SEG, "staging fits the A tile");
+        float* stg = reinterpret_cast<float*>(sA);
         const int q4 = warp & 3, ch = warp >> 2;
         if (32 * ch < R) {
-            const int m = m0 + q4 * 32 + lane;
+            const int ml = q4 * 32 + lane;
             uint32_t v[32];
             __syncwarp();
             tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(32 * ch), v);
-            if (ok && m < nrows) {
-                float* dst = a.out[c] + (size_t)m * R + 32 * ch;
 #pragma unroll
-                for (int n = 0; n < 32; n += 4)
-                    if (32 * ch + n < R)
-                        *reinterpret_cast<float4*>(dst + n) = make_float4(__uint_as_float(v[n]), __uint_as_float(v[n + 1]),
-                                                                          __uint_as_float(v[n + 2]), __uint_as_float(v[n + 3]));
+            for (int n = 0; n < 32; n += 4)
+                if (32 * ch + n < R) {
+                    const int cq = (32 * ch + n) >> 2;
+                    const int pc = (R % 32 == 0) ? (cq ^ (ml & 7)) : cq;
+                    *reinterpret_cast<float4*>(stg + ml * SP + 4 * pc) =
+                        make_float4(__uint_as_float(v[n]), __uint_as_float(v[n + 1]), __uint_as_float(v[n + 2]),
+                                    __uint_as_float(v[n + 3]));
+                }
+        }
+        __syncthreads();
+        if (ok) {
+            float* dst = a.out[c] + (size_t)m0 * R;
+            for (int e = threadIdx.x; e < TC_BM * (R / 4); e += BXT_THREADS) {
+                const int row = e / (R / 4), cq = e - row * (R / 4);
+                if (m0 + row >= nrows) break;
+                const int pc = (R % 32 == 0) ? (cq ^ (row & 7)) : cq;
+                *reinterpret_cast<float4*>(dst + (size_t)e * 4) = *reinterpret_cast<const float4*>(stg + row * SP + 4 * pc);
             }
         }
         tc_fence_before();

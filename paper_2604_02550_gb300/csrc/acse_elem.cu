@@ -264,6 +264,19 @@ struct GArgs {
 };
 
 #define G_GRID (152 * 16)
+#define G_ASM_GRID (152 * 8)   // k_assemble_G: eight resident blocks of 256 threads per SM, one wave
+
+// Tile pair u of the upper triangle (ti <= tj, row by row) of an n x n tile grid: row ti starts at
+// ti n - ti (ti - 1) / 2.  The float estimate is corrected by exact integer steps.
+__device__ __forceinline__ void tri_decode(int u, int n, int& ti, int& tj) {
+    const float b = 2.0f * (float)n + 1.0f;
+    int t = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)u, 0.0f))));
+    t = max(0, min(n - 1, t));
+    while (t > 0 && t * n - t * (t - 1) / 2 > u) --t;
+    while (t + 1 < n && (t + 1) * n - (t + 1) * t / 2 <= u) ++t;
+    ti = t;
+    tj = t + (u - (t * n - t * (t - 1) / 2));
+}
 
 // Per-thread accumulator of the norm: FP64 on the FP64 path; on the FP32 path a double-float pair
 // (hi, lo) fed with exact products (v*v and its FMA residual) through Knuth's TwoSum, so that the
@@ -295,15 +308,16 @@ struct NormAcc<float> {
 template <typename T>
 __device__ __forceinline__ void g_put(const GArgs<T>& a, int blk, int r, int R2, int ij, int kl, T v, NormAcc<T>& nrm) {
     nrm.add(v, blk == 1 ? (T)4 : (a.flip ? (T)2 : (T)1));
-    double o = (double)v;
+    T o = v;
     if (a.mask) {
         const int i = ij / r, j = ij - i * r, k = kl / r, l = kl - k * r;
-        if (i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo && l < a.hi) o = 0.0;
+        if (i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo && l < a.hi) o = (T)0;
     }
-    a.out[blk][(size_t)ij * R2 + kl] = o;
-    if (a.flip && blk == 0) a.out[2][(size_t)ij * R2 + kl] = o;
-    if (a.out32[0]) {
-        a.out32[blk][(size_t)ij * R2 + kl] = (float)o;   // exact: o is an FP32 value (or 0)
+    const double od = (double)o;   // the one conversion of the FP32 path (FP64 conversions are slow here)
+    a.out[blk][(size_t)ij * R2 + kl] = od;
+    if (a.flip && blk == 0) a.out[2][(size_t)ij * R2 + kl] = od;
+    if (a.out32[0]) {   // the split path's FP32 copy: o itself (an FP32 value)
+        a.out32[blk][(size_t)ij * R2 + kl] = (float)o;
         if (a.flip && blk == 0) a.out32[2][(size_t)ij * R2 + kl] = (float)o;
     }
 }
@@ -322,10 +336,11 @@ __global__ void __launch_bounds__(256) k_assemble_G(const __grid_constant__ GArg
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     NormAcc<T> nrm;
     const int nblk = a.flip ? 2 : 3;
-    for (int w = blockIdx.x; w < nblk * nT * nT; w += gridDim.x) {
-        const int blk = w / (nT * nT);
-        const int ti = (w / nT) % nT, tj = w % nT;
-        if (ti > tj) continue;                              // block-uniform
+    const int ntri = nT * (nT + 1) / 2;   // tile pairs ti <= tj of one block, dealt out evenly
+    for (int w = blockIdx.x; w < nblk * ntri; w += gridDim.x) {
+        const int blk = w / ntri;
+        int ti, tj;
+        tri_decode(w - blk * ntri, nT, ti, tj);
         const T* H = a.H[blk];
         for (int y = ty; y < 32; y += 8) {
             const int pr = ti * 32 + y, pc = tj * 32 + tx;
@@ -376,7 +391,7 @@ int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double*
         GArgs<double> a;
         fill_G(c, a, sW, scale, apply_mask, out);
         for (int s = 0; s < 3; ++s) a.H[s] = c->w.H[s];
-        k_assemble_G<double><<<G_GRID, 256, 0, c->stream>>>(a);
+        k_assemble_G<double><<<G_ASM_GRID, 256, 0, c->stream>>>(a);
     } else {
         GArgs<float> a;
         fill_G(c, a, sW, scale, apply_mask, out);
@@ -386,11 +401,11 @@ int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double*
         if (intoA)
             for (int s = 0; s < 3; ++s) a.out32[s] = c->w.A32[s];
         c->a32_valid = intoA ? 1 : c->a32_valid;
-        k_assemble_G<float><<<G_GRID, 256, 0, c->stream>>>(a);
+        k_assemble_G<float><<<G_ASM_GRID, 256, 0, c->stream>>>(a);
     }
     ACSE_LAUNCHED(c);
     if (norm2_dst) {
-        k_sum_partials<<<1, TPB, 0, c->stream>>>(c->w.partial, G_GRID, norm2_dst);
+        k_sum_partials<<<1, TPB, 0, c->stream>>>(c->w.partial, G_ASM_GRID, norm2_dst);
         ACSE_LAUNCHED(c);
     }
     return ACSE_OK;
