@@ -154,7 +154,13 @@ int acse_residual(acse_ctx* ctx, const double* Daa, const double* Dab, const dou
  * them when it is convex, clamped to [e0/4, 2 e0], otherwise the better of e0 and 2 e0; the
  * next step's e0 is the accepted eps).
  * Outputs (each may be NULL): E_out = E after the step, norm2_out = ||A||^2 at the D before the
- * step, eps_used = the step taken. */
+ * step, eps_used = the step taken.
+ * When the blocks and outputs are device memory (or NULL), input checks, the precision schedule and
+ * profiling are off and cuda_stream is a stream of the caller's (not the legacy default stream, not being
+ * captured), a call whose arguments (pointers and eps) repeat those of the previous call is captured
+ * into a CUDA graph, and later calls with those arguments replay it (two graphs are kept per context);
+ * the replay runs the same kernels with the same arguments in the same order, so the results are those
+ * of a direct call.  If a capture fails, the context runs every later step directly. */
 int acse_step(acse_ctx* ctx, double* Daa, double* Dab, double* Dbb, double eps,
               double* E_out, double* norm2_out, double* eps_used);
 
@@ -240,9 +246,11 @@ int acse_batch_extrapolate(acse_batch* batch, int n_skip, double* out);
 
 /* Profiling (not part of the method).  acse_profile(ctx, 1) resets the counters and starts
  * recording a CUDA-event pair around every O(r^6) GEMM launch of this context (up to 256
- * launches between reads); acse_profile(ctx, 0) stops.  acse_profile_read synchronises the
+ * launches between reads; while it is on, acse_step runs directly, without its CUDA graph);
+ * acse_profile(ctx, 0) stops and resets the counters too.  acse_profile_read synchronises the
  * context's stream and returns the summed GEMM time in ms, the number of timed GEMM launches,
- * and the number of kernels this context launched since the last reset.  Host pointers. */
+ * and the number of kernels this context launched since the last reset (a graph replay counts the
+ * kernels it runs).  Host pointers. */
 int acse_profile(acse_ctx* ctx, int enable);
 int acse_profile_read(acse_ctx* ctx, double* gemm_ms, long long* gemm_launches, long long* launches);
 

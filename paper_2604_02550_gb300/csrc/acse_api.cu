@@ -43,9 +43,12 @@ static int latch(acse_ctx* c, int s) {
     return s;
 }
 
+// Set while a step is captured into a graph, whose pointers were all found to be device memory first.
+static thread_local int tl_capturing = 0;
+
 // 1 if p is host memory (pageable or pinned), 0 if device or managed, -1 on error.
 static int is_host_ptr(const void* p) {
-    if (!p) return 0;
+    if (!p || tl_capturing) return 0;
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);
     if (e != cudaSuccess) {
@@ -237,6 +240,8 @@ extern "C" int acse_destroy(acse_ctx* c) {
         if (c->ev_join[b]) cudaEventDestroy(c->ev_join[b]);
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (int g = 0; g < 2; ++g)
+        if (c->sg[g].exec) cudaGraphExecDestroy(c->sg[g].exec);
     ny_free(c);
     adj_free(c);
     oz_plan_destroy(c);
@@ -519,10 +524,91 @@ static int sched_after_step(acse_ctx* c) {
     return ACSE_OK;
 }
 
+// A step runs as a CUDA graph when nothing in it needs the host: device blocks and outputs (or none),
+// no input checks, no precision schedule, no profiling, and a stream of the caller's that is neither
+// the legacy default stream nor being captured already.  The graph of a set of arguments is captured
+// the second time in a row they are passed (so that a caller who changes them every call pays no
+// capture) and replayed from then on; the replay launches the same kernels with the same arguments in
+// the same order as a direct call, so results are identical.  A capture that fails (an API call the
+// capture refuses) switches the context to direct calls.
+static int step_graph_eligible(acse_ctx* c, double* const ptrs[6]) {
+    if (c->sg_refused || c->fine || c->prof_on || c->opt.check_inputs || c->stream == nullptr) return 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return 0;
+    for (int i = 0; i < 6; ++i)
+        if (ptrs[i] && is_host_ptr(ptrs[i])) return 0;
+    return 1;
+}
+
+static int step_graph_launch(acse_ctx* c, int g) {
+    ACSE_CUDA_TRY(cudaGraphLaunch(c->sg[g].exec, c->stream));
+    c->launches += c->sg[g].launches;
+    c->sg[g].used = ++c->sg_tick;
+    return ACSE_OK;
+}
+
+// Capture the step with these arguments into slot g (the least recently used) and run it.  Returns
+// ACSE_ERR_UNSUPPORTED, having run nothing, when the capture failed.
+static int step_graph_capture(acse_ctx* c, double* const ptrs[6], double eps) {
+    const int g = c->sg[0].used <= c->sg[1].used ? 0 : 1;
+    if (c->sg[g].exec) {
+        cudaGraphExecDestroy(c->sg[g].exec);
+        c->sg[g].exec = nullptr;
+    }
+    const long long l0 = c->launches;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return ACSE_ERR_UNSUPPORTED;
+    }
+    tl_capturing = 1;
+    const int s = step_impl(c, ptrs[0], ptrs[1], ptrs[2], eps, ptrs[3], ptrs[4], ptrs[5]);
+    tl_capturing = 0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = s == ACSE_OK && e == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        c->launches = l0;
+        return ACSE_ERR_UNSUPPORTED;
+    }
+    c->sg[g].exec = exec;
+    for (int i = 0; i < 6; ++i) c->sg[g].key[i] = ptrs[i];
+    c->sg[g].eps = eps;
+    c->sg[g].launches = c->launches - l0;
+    c->launches = l0;
+    return step_graph_launch(c, g);
+}
+
 extern "C" int acse_step(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double eps, double* E_out,
                          double* norm2_out, double* eps_used) {
     if (!c) return ACSE_ERR_ARG;
     if (c->refined) return latch(c, acse_step(c->fine, Daa, Dab, Dbb, eps, E_out, norm2_out, eps_used));
+    double* const ptrs[6] = {Daa, Dab, Dbb, E_out, norm2_out, eps_used};
+    if (Daa && Dab && Dbb && step_graph_eligible(c, ptrs)) {
+        auto same = [&](const void* const* key, double keps) {
+            for (int i = 0; i < 6; ++i)
+                if (key[i] != ptrs[i]) return false;
+            return memcmp(&keps, &eps, sizeof(double)) == 0;
+        };
+        for (int g = 0; g < 2; ++g)
+            if (c->sg[g].exec && same(c->sg[g].key, c->sg[g].eps)) return latch(c, step_graph_launch(c, g));
+        if (c->sg_seen_valid && same(c->sg_seen, c->sg_seen_eps)) {
+            const int s = step_graph_capture(c, ptrs, eps);
+            if (s != ACSE_ERR_UNSUPPORTED) return latch(c, s);
+            c->sg_refused = 1;
+        }
+        for (int i = 0; i < 6; ++i) c->sg_seen[i] = ptrs[i];
+        c->sg_seen_eps = eps;
+        c->sg_seen_valid = 1;
+    }
     int s = step_impl(c, Daa, Dab, Dbb, eps, E_out, norm2_out, eps_used);
     if (s == ACSE_OK && c->fine) s = sched_after_step(c);
     return latch(c, s);

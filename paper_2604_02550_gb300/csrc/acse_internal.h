@@ -184,6 +184,21 @@ struct acse_ctx {
     int refined;
     double sched_n2;
     int sched_steps;      // steps taken in the starting precision
+    // CUDA graphs of acse_step: a call whose arguments (block and output pointers, eps) repeat those of
+    // the previous call is captured once and replayed from then on (two executables kept, least
+    // recently used replaced)
+    struct StepGraph {
+        cudaGraphExec_t exec;
+        const void* key[6];
+        double eps;
+        long long launches;   // kernels one replay runs
+        unsigned long long used;
+    } sg[2];
+    const void* sg_seen[6];   // arguments of the previous direct call
+    double sg_seen_eps;
+    int sg_seen_valid;
+    int sg_refused;           // a capture failed once: direct calls only
+    unsigned long long sg_tick;
 };
 #define ACSE_PROF_MAX 256
 
