@@ -348,8 +348,11 @@ def run_time_to_e(args):
            "line_search": {}, "fixed_step": {"eps": eps_fixed}}
     ls = out["line_search"]
     for label, prec, kw in TTE_VARIANTS:
-        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, line_search=True, eps0=eps0, **kw)
-        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+        # a stream of its own: acse_step then replays its CUDA graph (not on the legacy default stream)
+        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, line_search=True, eps0=eps0,
+                       stream=torch.cuda.Stream(), **kw)
+        with torch.cuda.stream(ctx.stream):
+            D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = ctx.run_until_stop(D, args.cap)
@@ -374,15 +377,16 @@ def run_time_to_e(args):
     E64 = None
     for label, prec, kw in (("fp64", "fp64", {}), ("ozaki", "ozaki", {}), ("ozaki6", "ozaki", dict(oz_slices=6)),
                             ("bf16x3", "bf16x3", {}), ("tf32x3", "tf32x3", {})):
-        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, **kw)
-        D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
-        Es = [float(ctx.energy(D))]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.cap):
-            E, _, _ = ctx.step(D, eps_fixed)
-            Es.append(float(E))
-        dt = time.perf_counter() - t0
+        ctx = api.ACSE(p.r, p.n_alpha, p.n_beta, p.h, p.V, prec, stream=torch.cuda.Stream(), **kw)
+        with torch.cuda.stream(ctx.stream):
+            D = ctx.to_blocks((p.Daa, p.Dab, p.Dbb))
+            Es = [float(ctx.energy(D))]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.cap):
+                E, _, _ = ctx.step(D, eps_fixed)
+                Es.append(float(E))
+            dt = time.perf_counter() - t0
         ctx.close()
         if E64 is None:
             E64 = np.array(Es)

@@ -77,6 +77,10 @@ class ACSE:
         evaluations differ by about 1e-13 relative, so a literal comparison decides on rounding).  Reads E
         and ||A||^2 back after every step.  Returns dict(E = energies of D_0 .. D_last, norm2 = ||A||^2
         before each step, eps = steps taken, reason, accepted = index of the returned D in E)."""
+        with torch.cuda.stream(self.stream):   # every read-back below waits for this context's stream
+            return self._run_until_stop(D, cap, eps, rise_tol)
+
+    def _run_until_stop(self, D, cap, eps, rise_tol):
         Es = [float(self.energy(D))]
         n2s, epss = [], []
         # D_(k-1) and D_k kept while step k runs: ||A(D_k)||^2 is known only once step k has run
