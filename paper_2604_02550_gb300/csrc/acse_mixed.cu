@@ -52,22 +52,24 @@ static MxPtrs mx_ptrs(acse_ctx* c) {
 // --------------------------------------------------------------------------- per D
 // M = 3 2D - 2 (1D^1D) in FP32 (App. C), stored plain (M32) and as rows 0..r^2-1 of the pair
 // operand [M; D]; rows r^2..2r^2-1 hold D.  Also rounds the FP64 1-RDM to FP32.  One block per
-// (sector, row of [M; D]); each thread handles groups of four consecutive columns (16-byte loads
-// and vector stores when r is even); the two 1-RDM rows a row needs are staged in shared memory.
-template <int PREC>
-__global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restrict__ gam, const double* __restrict__ Daa,
+// (sector, pair ij): the D row ij is read and rounded to FP32 once and gives both the M row ij and the
+// D row r^2 + ij (the FP64 -> FP32 conversions run on the slow FP64 pipe); each thread handles groups
+// of four consecutive columns (16-byte loads and vector stores when r is even); the two 1-RDM rows the
+// M row needs are staged in shared memory.  RC: r as a compile-time constant (0: runtime r).
+template <int PREC, int RC>
+__global__ void __launch_bounds__(192) k_mx_prepD(int r_, const double* __restrict__ gam, const double* __restrict__ Daa,
                                                   const double* __restrict__ Dab, const double* __restrict__ Dbb,
                                                   const __grid_constant__ MxPtrs p) {
     __shared__ float g1[ACSE_MAX_R], g2[ACSE_MAX_R];
+    const int r = RC ? RC : r_;
     const int R2 = r * r;
     const int c4 = (R2 + 3) >> 2;
-    const int s = blockIdx.x / (2 * R2);
-    const int row = blockIdx.x - s * 2 * R2;
+    const int s = blockIdx.x / R2;
+    const int row = blockIdx.x - s * R2;   // pair ij: M row ij and D row r^2 + ij
     if (blockIdx.x == 0)
         for (int e = threadIdx.x; e < 2 * R2; e += blockDim.x) p.gam32[e] = (float)gam[e];
-    const bool mrow = row < R2;
-    const int i = mrow ? row / r : 0, j = mrow ? row - (row / r) * r : 0;
-    if (mrow) {
+    const int i = row / r, j = row - (row / r) * r;
+    {
         // s = 0: rows i, j of 1D_a; s = 2: of 1D_b; s = 1: row i of 1D_a and row j of 1D_b
         const double* G1 = gam + (s == 2 ? R2 : 0) + (size_t)i * r;
         const double* G2 = gam + (s == 0 ? 0 : R2) + (size_t)j * r;
@@ -79,20 +81,16 @@ __global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restric
     __syncthreads();
     const size_t ld = (size_t)p.ns * p.Kp1;
     const size_t ldP = (size_t)p.ns * p.KpP;
-    // packed row of a same-spin sector: M rows 0..P-1, D rows P..2P-1 (pairs i < j only)
+    // packed rows of a same-spin sector (pairs i < j only): M at pk(i, j), D at P + pk(i, j)
     const int P = r * (r - 1) / 2;
-    int prow = -1;
-    {
-        const int rr = mrow ? row : row - R2, ii = rr / r, jj = rr - (rr / r) * r;
-        if (ii < jj) prow = (mrow ? 0 : P) + pk_pair(r, ii, jj);
-    }
-    const double* D = (s == 0 ? Daa : (s == 1 ? Dab : Dbb)) + (size_t)(mrow ? row : row - R2) * R2;
+    const int prow = i < j ? pk_pair(r, i, j) : -1;
+    const double* D = (s == 0 ? Daa : (s == 1 ? Dab : Dbb)) + (size_t)row * R2;
     float* Mrow = p.M32[s] + (size_t)row * R2;
     const bool vec = (r & 1) == 0 && ((reinterpret_cast<uintptr_t>(s == 0 ? Daa : (s == 1 ? Dab : Dbb)) & 15) == 0);
     for (int q4 = threadIdx.x; q4 < c4; q4 += blockDim.x) {
         const int k0 = q4 * 4;
         const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        float x[4] = {0.f, 0.f, 0.f, 0.f}, m[4] = {0.f, 0.f, 0.f, 0.f};
         if (vec && nk == 4) {
             const double2 d01 = *reinterpret_cast<const double2*>(D + k0);
             const double2 d23 = *reinterpret_cast<const double2*>(D + k0 + 2);
@@ -100,32 +98,52 @@ __global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restric
         } else {
             for (int u = 0; u < nk; ++u) x[u] = (float)D[k0 + u];
         }
-        if (mrow) {
+        {
             int kk = k0 / r, l = k0 - kk * r;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (u < nk) {
-                    x[u] = s == 1 ? 3.0f * x[u] - g1[kk] * g2[l] : 3.0f * x[u] - (g1[kk] * g2[l] - g2[kk] * g1[l]);
-                }
+                if (u < nk) m[u] = s == 1 ? 3.0f * x[u] - g1[kk] * g2[l] : 3.0f * x[u] - (g1[kk] * g2[l] - g2[kk] * g1[l]);
                 if (++l == r) { l = 0; ++kk; }
             }
-            if (vec && nk == 4) *reinterpret_cast<float4*>(Mrow + k0) = make_float4(x[0], x[1], x[2], x[3]);
-            else
-                for (int u = 0; u < nk; ++u) Mrow[k0 + u] = x[u];
         }
+        if (vec && nk == 4) *reinterpret_cast<float4*>(Mrow + k0) = make_float4(m[0], m[1], m[2], m[3]);
+        else
+            for (int u = 0; u < nk; ++u) Mrow[k0 + u] = m[u];
         if (s == 1) {
-            if (vec && nk == 4) put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, x);
-            else
-                for (int u = 0; u < nk; ++u) put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, x[u]);
+            if (vec && nk == 4) {
+                put4<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0, m);
+                put4<PREC, 0>(p.pairA[s], (size_t)R2 + row, ld, p.Kp1, k0, x);
+            } else {
+                for (int u = 0; u < nk; ++u) {
+                    put<PREC, 0>(p.pairA[s], row, ld, p.Kp1, k0 + u, m[u]);
+                    put<PREC, 0>(p.pairA[s], (size_t)R2 + row, ld, p.Kp1, k0 + u, x[u]);
+                }
+            }
         } else if (prow >= 0) {
             // same-spin sector: rows and K restricted to pairs a < b (antisymmetry; the GEMM's alpha
             // carries the factor 2 of the (r, s) sum)
             int kk = k0 / r, l = k0 - kk * r;
             for (int u = 0; u < nk; ++u) {
-                if (kk < l) put<PREC, 0>(p.pairA[s], (size_t)prow, ldP, p.KpP, pk_pair(r, kk, l), x[u]);
+                if (kk < l) {
+                    const int kq = pk_pair(r, kk, l);
+                    put<PREC, 0>(p.pairA[s], (size_t)prow, ldP, p.KpP, kq, m[u]);
+                    put<PREC, 0>(p.pairA[s], (size_t)(P + prow), ldP, p.KpP, kq, x[u]);
+                }
                 if (++l == r) { l = 0; ++kk; }
             }
         }
+    }
+}
+
+template <int PREC>
+static void launch_prepD(acse_ctx* c, int nsec, const double* const D[3], const MxPtrs& p) {
+    const int r = c->r, g = nsec * r * r;
+    switch (r) {
+        case 16: k_mx_prepD<PREC, 16><<<g, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p); break;
+        case 32: k_mx_prepD<PREC, 32><<<g, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p); break;
+        case 48: k_mx_prepD<PREC, 48><<<g, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p); break;
+        case 64: k_mx_prepD<PREC, 64><<<g, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p); break;
+        default: k_mx_prepD<PREC, 0><<<g, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p); break;
     }
 }
 
@@ -134,9 +152,10 @@ __global__ void __launch_bounds__(192) k_mx_prepD(int r, const double* __restric
 //   t=2 Md(b,a) rows (b,i,l) cols (a,p,s) <- Mab[p][i][s][l]      t=3 Md(b,b) <- Mbb[i][p][l][s]
 //   t=4 Mf1[(i,l)][(p,s)] <- Mab[i][p][s][l]                        t=5 Mf2[(i,l)][(p,s)] <- Mab[p][i][l][s]
 // (transposed source blocks go through shared memory so that reads and writes stay coalesced).
-template <int PREC>
-__global__ void __launch_bounds__(256) k_mx_pack_Mph(int r, const __grid_constant__ MxPtrs p) {
+template <int PREC, int RC>
+__global__ void __launch_bounds__(256) k_mx_pack_Mph(int r_, const __grid_constant__ MxPtrs p) {
     __shared__ float tile[ACSE_MAX_R][ACSE_MAX_R + 1];
+    const int r = RC ? RC : r_;   // compile-time r where it is one of the tensor-core sizes
     const int R2 = r * r;
     const int t = blockIdx.x / R2, ip = blockIdx.x % R2;
     const int i = ip / r, pp = ip % r;
@@ -194,10 +213,20 @@ __global__ void __launch_bounds__(256) k_mx_pack_Mph(int r, const __grid_constan
     }
 }
 
+template <int PREC>
+static void launch_pack_Mph(acse_ctx* c, int nph, const MxPtrs& q) {
+    const int r = c->r, g = nph * r * r;
+    switch (r) {
+        case 16: k_mx_pack_Mph<PREC, 16><<<g, 256, 0, c->stream>>>(r, q); break;
+        case 32: k_mx_pack_Mph<PREC, 32><<<g, 256, 0, c->stream>>>(r, q); break;
+        case 48: k_mx_pack_Mph<PREC, 48><<<g, 256, 0, c->stream>>>(r, q); break;
+        case 64: k_mx_pack_Mph<PREC, 64><<<g, 256, 0, c->stream>>>(r, q); break;
+        default: k_mx_pack_Mph<PREC, 0><<<g, 256, 0, c->stream>>>(r, q); break;
+    }
+}
+
 int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
-    const int r = c->r;
     MxPtrs p = mx_ptrs(c);
-    const int R2 = r * r;
     // spin-flip specialisation: M_bb = M_aa (the bb sector of [M; D] is not formed) and Mf2 feeds only
     // the second spin-flip GEMM, which is not run
     const bool sf = acse_singlet(c);
@@ -205,17 +234,17 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
     MxPtrs q = p;
     if (sf) q.M32[2] = q.M32[0];
     if (c->opt.prec == ACSE_BF16X3) {
-        k_mx_prepD<ACSE_BF16X3><<<nsec * 2 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        launch_prepD<ACSE_BF16X3>(c, nsec, D, p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_BF16X3><<<nph * R2, 256, 0, c->stream>>>(r, q);
+        launch_pack_Mph<ACSE_BF16X3>(c, nph, q);
     } else if (c->opt.prec == ACSE_TF32X3) {
-        k_mx_prepD<ACSE_TF32X3><<<nsec * 2 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        launch_prepD<ACSE_TF32X3>(c, nsec, D, p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_TF32X3><<<nph * R2, 256, 0, c->stream>>>(r, q);
+        launch_pack_Mph<ACSE_TF32X3>(c, nph, q);
     } else {
-        k_mx_prepD<ACSE_TF32><<<nsec * 2 * R2, 192, 0, c->stream>>>(r, c->w.gam, D[0], D[1], D[2], p);
+        launch_prepD<ACSE_TF32>(c, nsec, D, p);
         ACSE_LAUNCHED(c);
-        k_mx_pack_Mph<ACSE_TF32><<<nph * R2, 256, 0, c->stream>>>(r, q);
+        launch_pack_Mph<ACSE_TF32>(c, nph, q);
     }
     ACSE_LAUNCHED(c);
     return ACSE_OK;
@@ -223,10 +252,11 @@ int tc_mixed_prep_D(acse_ctx* c, const double* const D[3]) {
 
 // --------------------------------------------------------------------------- per W
 // Pair operand B: W blocks as (kp) x (rs) rows.
-template <int PREC>
-__global__ void k_mx_pack_W(int r, const float* __restrict__ Waa, const float* __restrict__ Wab,
+template <int PREC, int RC>
+__global__ void k_mx_pack_W(int r_, const float* __restrict__ Waa, const float* __restrict__ Wab,
                             const float* __restrict__ Wbb, const __grid_constant__ MxPtrs p) {
-    // grid: x over groups of four columns, y over (sector, row)
+    // grid: x over groups of four columns, y over (sector, row); RC: compile-time r (0: runtime)
+    const int r = RC ? RC : r_;
     const int R2 = r * r;
     const int c4 = (R2 + 3) >> 2;
     const int q4 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -238,7 +268,12 @@ __global__ void k_mx_pack_W(int r, const float* __restrict__ Waa, const float* _
     const int k0 = q4 * 4;
     const int nk = R2 - k0 < 4 ? R2 - k0 : 4;
     float x[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int u = 0; u < nk; ++u) x[u] = W[k0 + u];
+    if ((r & 1) == 0 && nk == 4) {   // r^2 % 4 == 0: every row starts on a 16-byte boundary
+        const float4 v = *reinterpret_cast<const float4*>(W + k0);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+        for (int u = 0; u < nk; ++u) x[u] = W[k0 + u];
+    }
     if (s == 1) {
         if ((r & 1) == 0 && nk == 4) put4<PREC, 1>(p.pairB[s], row, ld, p.Kp1, k0, x);
         else
@@ -381,6 +416,18 @@ int tc_make_Kh32(acse_ctx* c) {
     return to_f32(c, W, c->w.Kh32);
 }
 
+template <int PREC>
+static void launch_pack_W(acse_ctx* c, dim3 grid, const float* const W32[3], const MxPtrs& p) {
+    const int r = c->r;
+    switch (r) {
+        case 16: k_mx_pack_W<PREC, 16><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p); break;
+        case 32: k_mx_pack_W<PREC, 32><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p); break;
+        case 48: k_mx_pack_W<PREC, 48><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p); break;
+        case 64: k_mx_pack_W<PREC, 64><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p); break;
+        default: k_mx_pack_W<PREC, 0><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p); break;
+    }
+}
+
 int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     const int r = c->r;
     Work& w = c->w;
@@ -398,11 +445,11 @@ int tc_mixed_prep_W(acse_ctx* c, const double* const W[3]) {
     }
     const dim3 grid((r * r / 4 + 128) / 128, (acse_singlet(c) ? 2 : 3) * r * r);   // no bb pair GEMM under the spin flip
     if (c->opt.prec == ACSE_BF16X3)
-        k_mx_pack_W<ACSE_BF16X3><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p);
+        launch_pack_W<ACSE_BF16X3>(c, grid, W32, p);
     else if (c->opt.prec == ACSE_TF32X3)
-        k_mx_pack_W<ACSE_TF32X3><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p);
+        launch_pack_W<ACSE_TF32X3>(c, grid, W32, p);
     else
-        k_mx_pack_W<ACSE_TF32><<<grid, 128, 0, c->stream>>>(r, W32[0], W32[1], W32[2], p);
+        launch_pack_W<ACSE_TF32>(c, grid, W32, p);
     ACSE_LAUNCHED(c);
     return launch_Z_tiled(c, W, W32);   // Z packs and w (the diagonal of Z)
 }
