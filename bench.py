@@ -297,6 +297,7 @@ def run_batch(args, rank, world):
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
     time.sleep(0.3)
+    _, _, l0 = _lib.acse_batch_info(b)
     t0 = time.perf_counter()
     E, N2, S, R = _lib.acse_batch_run(b, len(probs), args.steps, stop_rule=False)
     dt = time.perf_counter() - t0
@@ -313,7 +314,7 @@ def run_batch(args, rank, world):
                        "step": "one graph replay: every instance's residual + update + axpy + energy (two "
                                "residual evaluations per instance)",
                        "tile_choice": tune, "split_r2": split},
-            "tflops": world * fl * args.steps / dt / 1e12, "clocks": clocks,
+            "tflops": world * fl * args.steps / dt / 1e12, "clocks": clocks, "gpu_launches": launches - l0,
             "energies_finite": bool(np.all(np.isfinite(E)))}
     if rank == 0:
         print(json.dumps(line), flush=True)

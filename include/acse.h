@@ -200,7 +200,7 @@ int acse_schedule_state(const acse_ctx* ctx, int* refined, int* steps);
  *   acse_batch_run: nsteps graph replays; per instance (host arrays of n, each may be NULL): E and
  *     ||A||^2 at the current D, accepted steps, stop reason (0 running, 1 E or ||A|| rose, 2 converged).
  *   acse_batch_info: the tile choice (0 all 256 wide, 1 all 128 wide, 2 split at r^2 = split_r2) and
- *     the kernels launched so far.  1 <= n <= 64 (ACSE_ERR_ARG otherwise, and for mixed precisions);
+ *     the kernels launched so far (a graph replay counts the kernels it runs).  1 <= n <= 64 (ACSE_ERR_ARG otherwise, and for mixed precisions);
  *     ACSE_ERR_UNSUPPORTED for the NY reconstruction or ACSE_OZAKI; a failed create leaves *batch NULL.
  *   acse_batch_residual_backward: acse_residual_backward for instance i (its integrals and options; the
  *     checkpoints D_ckpt as there, for example read with acse_batch_get_D after one-step runs), run in

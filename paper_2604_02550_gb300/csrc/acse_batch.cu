@@ -53,6 +53,10 @@ struct acse_batch {
     double* hist;
     int* hcount;
     double* fitout;    // 6 doubles per instance: the last acse_batch_extrapolate results (device)
+    // kernel count of the graph: per replay (counted while it was captured) and over all replays so far
+    long long per_replay;
+    long long replayed;
+    long long tab_launches;   // grouped tensor-core GEMM launches issued (counted during the capture)
 };
 #define ACSE_HIST_CAP 4096
 
@@ -145,7 +149,10 @@ static int gemm_pass(acse_batch* B) {
         }
         return gemm_f64_grouped(B->ctx[0], all.data(), (int)all.size(), B->stream);
     }
-    for (int t = 0; t < B->ntab; ++t) ACSE_TRY(tc_table_launch(&B->tab[t], B->stream));
+    for (int t = 0; t < B->ntab; ++t) {
+        ACSE_TRY(tc_table_launch(&B->tab[t], B->stream));
+        B->tab_launches++;
+    }
     return ACSE_OK;
 }
 
@@ -425,9 +432,18 @@ extern "C" int acse_batch_run(acse_batch* B, int nsteps, int stop_rule, double* 
     B->stop_rule = stop_rule;
     if (!B->graph_ready) {
         cudaGraph_t g;
+        // the kernels the capture records are counted once per replay, not at the capture
+        long long before[64];
+        for (int i = 0; i < B->n; ++i) before[i] = B->ctx[i]->launches;
+        B->tab_launches = 0;
         ACSE_CUDA_TRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
         int s = batch_step(B);
         cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+        B->per_replay = B->tab_launches;
+        for (int i = 0; i < B->n; ++i) {
+            B->per_replay += B->ctx[i]->launches - before[i];
+            B->ctx[i]->launches = before[i];
+        }
         if (s != ACSE_OK) return s;
         if (e != cudaSuccess) return ACSE_ERR_CUDA;
         e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -435,7 +451,10 @@ extern "C" int acse_batch_run(acse_batch* B, int nsteps, int stop_rule, double* 
         if (e != cudaSuccess) return ACSE_ERR_CUDA;
         B->graph_ready = 1;
     }
-    for (int k = 0; k < nsteps; ++k) ACSE_CUDA_TRY(cudaGraphLaunch(B->graph, B->stream));
+    for (int k = 0; k < nsteps; ++k) {
+        ACSE_CUDA_TRY(cudaGraphLaunch(B->graph, B->stream));
+        B->replayed += B->per_replay;
+    }
     ACSE_CUDA_TRY(cudaStreamSynchronize(B->stream));
     for (int i = 0; i < B->n; ++i) {
         double sc[16];
@@ -477,7 +496,7 @@ extern "C" int acse_batch_info(const acse_batch* B, int* tune_choice, int* split
     if (tune_choice) *tune_choice = B->tune_choice;
     if (split_r2) *split_r2 = B->split_r2;
     if (launches) {
-        long long s = 0;
+        long long s = B->replayed;
         for (int i = 0; i < B->n; ++i) s += B->ctx[i]->launches;
         *launches = s;
     }

@@ -58,6 +58,12 @@ def test_batch_matches_single_contexts(libs, prec):
         ctx.close()
     tune, split, launches = _lib.acse_batch_info(b)
     assert launches > 0 and tune in (0, 1, 2)
+    # every replay counts the kernels it runs, the same number each time
+    _lib.acse_batch_run(b, len(probs), 1, stop_rule=False)
+    _, _, l1 = _lib.acse_batch_info(b)
+    _lib.acse_batch_run(b, len(probs), 2, stop_rule=False)
+    _, _, l2 = _lib.acse_batch_info(b)
+    assert l1 > launches and l2 - l1 == 2 * (l1 - launches)
     _lib.acse_batch_destroy(b)
 
 
