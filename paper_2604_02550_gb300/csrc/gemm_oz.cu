@@ -40,7 +40,8 @@
 #define OZ2_STAGES 6         // ring depth of the CTA-pair form (32 KB a stage per CTA)
 #define OZ_DRAIN_NS 2000000000ull
 #define OZ_WAIT_NS 4000000000ull
-#define OZ_SLICE_PPT 16      // element pairs per thread of a sliced row: K <= 2 * 256 * 16 = 2 * 64^2
+#define OZ_SLICE_PPT 8       // element pairs per thread of a sliced row: K <= 2 * 512 * 8 = 2 * 64^2 with
+                             // 512 threads; rows with K <= 2048 / 4096 take 128 / 256 threads
 
 struct OzProb {
     double* C;
@@ -151,8 +152,9 @@ __device__ __forceinline__ long long oz_fixed(unsigned long long bits, int S, in
 // digits from the least significant one up (d = ((X + 32) mod 64) - 32, X <- (X - d) / 64, exact;
 // the last quotient is the leading digit, of magnitude at most 32).  Digits go out as bf16 pairs,
 // each slice to its K segment of the row.
-__global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSliceBatch b) {
-    __shared__ unsigned long long red[8];
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_oz_slice(const __grid_constant__ OzSliceBatch b) {
+    __shared__ unsigned long long red[THREADS / 32];
     __shared__ unsigned short tab[65];   // bf16 bits of the digits -32..32
     if (threadIdx.x < 65) tab[threadIdx.x] = __bfloat16_as_ushort(__float2bfloat16_rn((float)((int)threadIdx.x - 32)));
     int ji = 0;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSlic
     unsigned long long mx = 0;
 #pragma unroll
     for (int u = 0; u < OZ_SLICE_PPT; ++u) {
-        const int k = 2 * ((int)threadIdx.x + u * 256);
+        const int k = 2 * ((int)threadIdx.x + u * THREADS);
         v[2 * u] = k < K ? src[cm ? cm[k] : k] : 0ull;
         v[2 * u + 1] = k + 1 < K ? src[cm ? cm[k + 1] : k + 1] : 0ull;
         mx = max(mx, max(v[2 * u] & 0x7FFFFFFFFFFFFFFFull, v[2 * u + 1] & 0x7FFFFFFFFFFFFFFFull));
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSlic
     __syncthreads();
     mx = red[0];
 #pragma unroll
-    for (int i = 1; i < 8; ++i) mx = max(mx, red[i]);
+    for (int i = 1; i < THREADS / 32; ++i) mx = max(mx, red[i]);
     // non-negative doubles order like their bit patterns; an all-ones exponent is Inf or NaN
     const bool bad = mx >= 0x7FF0000000000000ull;
     int e = 0;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzSlic
     const int S = b.S;
 #pragma unroll
     for (int u = 0; u < OZ_SLICE_PPT; ++u) {
-        const int k = 2 * ((int)threadIdx.x + u * 256);
+        const int k = 2 * ((int)threadIdx.x + u * THREADS);
         if (k >= K) continue;
         long long X0 = bad ? 0 : oz_fixed(v[2 * u], S, e);
         long long X1 = bad ? 0 : oz_fixed(v[2 * u + 1], S, e);
@@ -473,33 +475,48 @@ __device__ __forceinline__ long long oz_term(int v, int w) {
 }
 
 __global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ bp) {
+    __shared__ signed char wtab[64];   // the weight 36 - 6 (L - 2) of every group, in the staging order
     const OzBatch& b = *bp;
     const OzProb& P = b.p[blockIdx.y];
-    const int N = P.N, g = P.g, S = b.S;
+    const int N = P.N, g = P.g, S = b.S, ng = P.ngroups;
+    if (threadIdx.x == 0) {
+        int gi = 0;
+        for (int L = 2; L <= S + 1; ++L)
+            for (int q = 0; q < (L - 2) / g + 1 && gi < 64; ++q) wtab[gi++] = (signed char)(36 - OZ_BETA * (L - 2));
+    }
+    __syncthreads();
     const size_t MN = (size_t)P.M * N;
     const int* __restrict__ st = P.stage;
-    // four consecutive elements of one row per thread (int4 loads) when N % 4 == 0, else one
+    // four consecutive elements of one row per thread (int4 loads) when N % 4 == 0, else one; the group
+    // sums are loaded eight at a time before they are added
     const int vw = (N & 3) == 0 ? 4 : 1;
     const size_t nunit = MN / vw;
     for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < nunit; u += (size_t)gridDim.x * blockDim.x) {
         const size_t e = u * vw;
         long long acc[4] = {0, 0, 0, 0};
-        size_t off = e;
-        for (int L = 2; L <= S + 1; ++L) {
-            const int w = 36 - OZ_BETA * (L - 2);
-            const int nl = (L - 2) / g + 1;
+        for (int g0 = 0; g0 < ng; g0 += 8) {
             if (vw == 4) {
-#pragma unroll 4
-                for (int q = 0; q < nl; ++q, off += MN) {
-                    const int4 v = *reinterpret_cast<const int4*>(st + off);
-                    acc[0] += oz_term(v.x, w);
-                    acc[1] += oz_term(v.y, w);
-                    acc[2] += oz_term(v.z, w);
-                    acc[3] += oz_term(v.w, w);
-                }
+                int4 vv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (g0 + q < ng) vv[q] = *reinterpret_cast<const int4*>(st + e + (size_t)(g0 + q) * MN);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (g0 + q < ng) {
+                        const int w = wtab[g0 + q];
+                        acc[0] += oz_term(vv[q].x, w);
+                        acc[1] += oz_term(vv[q].y, w);
+                        acc[2] += oz_term(vv[q].z, w);
+                        acc[3] += oz_term(vv[q].w, w);
+                    }
             } else {
-#pragma unroll 4
-                for (int q = 0; q < nl; ++q, off += MN) acc[0] += oz_term(st[off], w);
+                int vv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (g0 + q < ng) vv[q] = st[e + (size_t)(g0 + q) * MN];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (g0 + q < ng) acc[0] += oz_term(vv[q], wtab[g0 + q]);
             }
         }
         const int i = (int)(e / N), j0 = (int)(e - (size_t)i * N);
@@ -865,6 +882,32 @@ static void oz_job(OzSliceBatch& b, int& rows, const OzOp& o, int orow, int nrow
     rows += nrows;
 }
 
+// Launch the slicing of every job of `all`: the jobs go to up to three launches by row length (128 threads
+// a row for K <= 2048, 256 for K <= 4096, 512 above), so that short rows keep more blocks resident.
+static int oz_slice_launch(acse_ctx* c, const OzSliceBatch& all) {
+    for (int cls = 0; cls < 3; ++cls) {
+        OzSliceBatch b;
+        memset(&b, 0, sizeof(b));
+        b.S = all.S;
+        int rows = 0;
+        for (int i = 0; i < all.njobs; ++i) {
+            const int K = all.j[i].K;
+            const int jc = K <= 2 * 128 * OZ_SLICE_PPT ? 0 : K <= 2 * 256 * OZ_SLICE_PPT ? 1 : 2;
+            if (jc != cls) continue;
+            b.j[b.njobs] = all.j[i];
+            b.j[b.njobs].row0 = rows;
+            rows += all.j[i].rows;
+            b.njobs++;
+        }
+        if (b.njobs == 0) continue;
+        if (cls == 0) k_oz_slice<128><<<rows, 128, 0, c->stream>>>(b);
+        else if (cls == 1) k_oz_slice<256><<<rows, 256, 0, c->stream>>>(b);
+        else k_oz_slice<512><<<rows, 512, 0, c->stream>>>(b);
+        ACSE_LAUNCHED(c);
+    }
+    return ACSE_OK;
+}
+
 int oz_slice_operands(acse_ctx* c, int prep_D) {
     OzPlan* pl = (OzPlan*)c->oz_plan;
     if (!pl) return ACSE_ERR_UNSUPPORTED;
@@ -895,9 +938,8 @@ int oz_slice_operands(acse_ctx* c, int prep_D) {
     oz_job(b, rows, pl->A[4], 0, 2 * iR2, w.Zd, 2 * R2, nullptr, nullptr, 0);
     oz_job(b, rows, pl->A[5], 0, iR2, w.Zf1, R2, nullptr, nullptr, 0);
     oz_job(b, rows, pl->A[6], 0, iR2, w.Zf2, R2, nullptr, nullptr, 0);
-    k_oz_slice<<<rows, 256, 0, c->stream>>>(b);
-    ACSE_LAUNCHED(c);
-    return ACSE_OK;
+    (void)rows;
+    return oz_slice_launch(c, b);
 }
 
 int oz_gemm_launch(acse_ctx* c) {
@@ -1013,8 +1055,7 @@ int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
             if (tr) ACSE_TRY(oz_colmap(root, o.K, ld, &cm));
             oz_job(sb, rows, o, 0, o.rows, src, tr ? 1 : (size_t)ld, nullptr, cm, side);
             if (sb.njobs == OZ_MAXJ) {
-                k_oz_slice<<<rows, 256, 0, c->stream>>>(sb);
-                ACSE_LAUNCHED(c);
+                ACSE_TRY(oz_slice_launch(c, sb));
                 memset(&sb, 0, sizeof(sb));
                 sb.S = pl->S;
                 rows = 0;
@@ -1022,8 +1063,7 @@ int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
         }
     }
     if (sb.njobs) {
-        k_oz_slice<<<rows, 256, 0, c->stream>>>(sb);
-        ACSE_LAUNCHED(c);
+        ACSE_TRY(oz_slice_launch(c, sb));
     }
     // this call's outputs, scales and accumulation
     for (int i = 0; i < n; ++i) {
