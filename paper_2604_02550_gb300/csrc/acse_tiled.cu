@@ -45,7 +45,24 @@ struct __align__(8) dfl {
     float h, l;
     __device__ __forceinline__ operator double() const { return (double)h + (double)l; }
 };
+// h = x rounded to the nearest float (ties to even), l = x - h rounded to the nearest float.  With integer
+// operations from the bit pattern where x is a normal double whose h and l are normal floats (the FP64
+// conversions run on the slow FP64 pipe); the same values through FP64 otherwise.
 __device__ __forceinline__ dfl to_dfl(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    if (e >= 949 && e <= 1149) {   // 2^(e - 1075) and h are normal floats
+        const unsigned sign = hi & 0x80000000u;
+        const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);    // the 23 fraction bits kept
+        const unsigned rem = lo & 0x1FFFFFFFu;                        // the 29 dropped ones
+        const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+        const float h = __uint_as_float(sign | (((unsigned)(e - 1023 + 127) << 23) + m23 + up));
+        const int rr = up ? (int)rem - 0x20000000 : (int)rem;        // x - h in units of 2^(e - 1075)
+        const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+        const float l = __fmul_rn(__int2float_rn(sign ? -rr : rr), scale);
+        return dfl{h, l};
+    }
     const float h = (float)x;
     return dfl{h, (float)(x - (double)h)};   // x - h is exact in FP64
 }
