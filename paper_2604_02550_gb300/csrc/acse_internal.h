@@ -246,6 +246,7 @@ int launch_build_B(acse_ctx* c);
 int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32[3]);
 int launch_B_tiled(acse_ctx* c);
 int launch_Z_tc(acse_ctx* c, const float* const W32[3], int ntypes, const int* tmap);   // acse_ztc.cu
+int launch_Z_oz(struct acse_ctx* c, const double* const W[3], int ntypes, const int* tmap);   // acse_zoz.cu
 int launch_Bx_tc(acse_ctx* c);                                                           // acse_btc.cu
 int tiled_set_attrs();
 int launch_Q(acse_ctx* c);

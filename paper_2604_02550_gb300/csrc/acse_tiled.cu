@@ -1021,7 +1021,14 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32
     if (c->opt.prec == ACSE_FP64) {
         o.Zd = w.Zd; o.Zf[0] = w.Zf1; o.Zf[1] = w.Zf2;
         o.mode = 0; o.ldd = 2 * R2; o.ldf = R2; o.Kp1 = o.Kp2 = 0; o.diag = w.zdiag;
-        if (c->oz) {   // Ozaki path: double-float products, FP64 output
+        if (c->oz) {   // Ozaki path: the products on the tensor cores (acse_zoz.cu), else in double-float
+            const int zs = launch_Z_oz(c, W, o.ntypes, o.tmap);
+            if (zs == ACSE_OK) {
+                k_w_from_diag<double><<<2 * r, 256, 0, c->stream>>>(r, w.zdiag, w.w, 0);
+                ACSE_LAUNCHED(c);
+                return ACSE_OK;
+            }
+            if (zs != ACSE_ERR_UNSUPPORTED) return zs;
             const ZPlan zp = z_plan(r, 4, sizeof(double), (const void*)k_Z_pipe<4>);
             k_Z_pipe<4><<<zp.blocks / 6 * o.ntypes, zp.threads, zp.smem, c->stream>>>(r, zp.ipb, zp.pchunk, W[0], W[1], W[2], w.gam, o);
         } else {

@@ -1,0 +1,314 @@
+// Z = 1D . W_kp on the tensor cores in an FP64-accurate (Ozaki) context: the O(r^5) particle-hole operand
+// of a contraction pass, Z^{kp}_{js} = sum_q W^{kp}_{qs} 1D^j_q, by the error-free splitting of the Ozaki
+// scheme (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012) that gemm_oz.cu applies to the O(r^6)
+// GEMMs, instead of double-float FMAs on the CUDA cores.
+//
+// Tile: 128 consecutive (p, s) of one (spin type, k), rows m = p r + s, as in acse_ztc.cu:
+//     Z[m][j] = sum_q A[m][q] B[j][q],   A[m][q] = W_kp[q][s] (FP64),  B[j][q] = 1D[j][q] (FP64).
+// Every row of A and of B gets a power-of-two scale 2^e (|x| 2^-e < 1/2 over the row) and each element the
+// fixed-point value X = round(x 2^(6S - e)), cut into S balanced base-64 digits (most significant first,
+// each exact in bf16).  The digit tiles A_s, B_t sit in shared memory in the 128-byte-swizzled K-major
+// layout (K = q, one 64-element block); the products of one level L = s + t <= S + 1 are accumulated in
+// FP32 in their own TMEM accumulator (columns (L - 2) r .. (L - 1) r): a level holds at most S products
+// of K <= 64 terms of magnitude <= 2^10, below 2^24, so every level sum is an exact integer.  The epilogue
+// adds the levels exactly in int64 (sum_L v_L 2^(6 (S + 1 - L)), below 2^61 for S <= 8) and rounds once
+// to FP64, scaled by 2^(e_m + e_j - 6 (S + 1)).  The levels dropped (s + t > S + 1) and the fixed-point
+// rounding leave an error of order 2^-6S of |A_m| |B_j| r, that of the Ozaki GEMMs.
+//
+// One block per SM (the S digit tiles of A and B take up to 192 KB of shared memory) walks a contiguous
+// range of tiles; the B tiles are rebuilt only when the spin of the tile's 1D changes.  Producer: two
+// threads per A row (partners in one warp share the row maximum); one thread issues the MMAs; epilogue:
+// each warp reads its TMEM lane quarter (one row m per thread) for half of the columns j and writes the
+// FP64 rows of Zd / Zf (row (sK, k, j), column (sP, p, s)) and the diagonal rows j = p of w.  The wait for
+// the MMAs is bounded; on expiry the kernel raises the device flag and stops.  Used for r a multiple of
+// 16 (r <= 64) and S <= 8; other cases take the double-float kernel of acse_tiled.cu.
+#include <cuda_bf16.h>
+
+#include "acse_internal.h"
+#include "oz_arith.cuh"
+#include "tc_ptx.cuh"
+
+#define ZOZ_THREADS 256
+#define ZOZ_SMAX 8                       // digit slices this kernel holds
+#define ZOZ_A_SLICE (TC_BM * 128)        // one digit tile of A: 128 rows x 128 bytes
+#define ZOZ_WAIT_NS 4000000000ull
+
+struct ZozArgs {
+    const double* W[3];     // FP64 W blocks aa, ab, bb (r^4 each)
+    const double* gam;      // 1D per spin [2][r][r]
+    double* Zd;             // (2 r^2) rows of ldd doubles
+    double* Zf[2];          // r^2 rows of ldf doubles
+    double* diag;           // [4][r][r][r]: rows j = p of Zd(a,a), Zd(b,b), Zf1, Zf2
+    int ldd, ldf;
+    int tmap[6];            // block type index -> spin type t
+    int S;                  // slices (<= ZOZ_SMAX)
+    int* err;
+};
+
+static __device__ __forceinline__ uint32_t zoz_sw128(int n, int c) {
+    return (uint32_t)n * 128u + (uint32_t)((c ^ (n & 7)) << 4);
+}
+
+// Row scale from the largest magnitude's bit pattern (non-negative doubles order like their bits): e with
+// |x| 2^-e < 1/2, 0 for an all-zero row, ZOZ_BAD for a row holding Inf or NaN.
+#define ZOZ_BAD 0x7FFF
+static __device__ __forceinline__ int zoz_row_exp(unsigned long long mx) {
+    if (mx >= 0x7FF0000000000000ull) return ZOZ_BAD;
+    if (mx == 0) return 0;
+    return min(1000, max(-1000, (int)(mx >> 52) - 1023 + 2));
+}
+
+// The S digits of the eight elements x[0..7] (scale e) as bf16, written to the 16-byte chunk `off` of the
+// S digit tiles at base, base + stride, ...: digit tile s - 1 holds digit s (most significant first).
+// Balanced base-64 digits from the least significant one up: d = ((X + 32) mod 64) - 32, X <- (X - d) / 64;
+// the last quotient is the leading digit (|d| <= 32).
+static __device__ __forceinline__ void zoz_digits8(const unsigned long long (&x)[8], int e, int S, uint8_t* base,
+                                                   uint32_t stride, uint32_t off, const unsigned short* tab) {
+    long long X[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) X[u] = (e == ZOZ_BAD) ? 0 : oz_fixed(x[u], S, e);
+    for (int t = 0; t < S; ++t) {   // digit s = S - t
+        unsigned short h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            int d;
+            if (t < S - 1) {
+                d = (int)(((X[u] + 32) & 63) - 32);
+                X[u] = (X[u] - d) >> 6;
+            } else {
+                d = (int)X[u];
+            }
+            h[u] = tab[d + 32];
+        }
+        uint4 v;
+        v.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+        v.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+        v.z = (uint32_t)h[4] | ((uint32_t)h[5] << 16);
+        v.w = (uint32_t)h[6] | ((uint32_t)h[7] << 16);
+        *reinterpret_cast<uint4*>(base + (size_t)(S - t - 1) * stride + off) = v;
+    }
+}
+
+static __device__ __forceinline__ void zoz_tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
+template <int R>
+__global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Z_oz(const __grid_constant__ ZozArgs a, int ntiles) {
+    static_assert(R % 16 == 0 && R <= 64, "N = r a multiple of 16, K = r within one 64-element block");
+    constexpr int R2 = R * R, NT = R2 / TC_BM, NCH = R / 8;   // 16-byte chunks of a digit row
+    static_assert(R2 % TC_BM == 0, "whole tiles");
+    constexpr int B_SLICE = R * 128;                            // one digit tile of B: R rows x 128 B
+    const int S = a.S;
+    extern __shared__ uint8_t zo_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)zo_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;                                         // [S][128 x 128 B]
+    uint8_t* sB = sA + ZOZ_SMAX * ZOZ_A_SLICE;                  // [S][R x 128 B]
+    int* eA = reinterpret_cast<int*>(sB + ZOZ_SMAX * B_SLICE);  // row scales of the A tile [128]
+    int* eB = eA + TC_BM;                                       // row scales of B [64]
+    unsigned short* tab = reinterpret_cast<unsigned short*>(eB + 64);   // bf16 of the digits -32 .. 32
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tab + 72);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t r3 = (size_t)R * R2;
+    if (threadIdx.x < 65) tab[threadIdx.x] = __bfloat16_as_ushort(__float2bfloat16_rn((float)((int)threadIdx.x - 32)));
+    // the K padding q >= R of every digit tile stays zero
+    for (int e = threadIdx.x; e < (ZOZ_SMAX * ZOZ_A_SLICE + ZOZ_SMAX * B_SLICE) / 16; e += ZOZ_THREADS)
+        reinterpret_cast<uint4*>(sA)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+    uint32_t phase = 0;
+    int cur_sp = -1;
+    const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t_end = min(ntiles, ((int)blockIdx.x + 1) * per);
+    for (int tile = (int)blockIdx.x * per; tile < t_end && ok; ++tile, phase ^= 1) {
+        const int tb = tile / (R * NT);
+        const int t = a.tmap[tb];
+        const int rem = tile - tb * R * NT;
+        const int k = rem / NT;
+        const int m0 = (rem - k * NT) * TC_BM;
+        const int sp = (t == 2 || t == 3 || t == 4) ? 1 : 0;
+        if (sp != cur_sp) {   // B: the digits of 1D of this tile's spin, rows j, K = q (the last MMAs are done)
+            const unsigned long long* g = reinterpret_cast<const unsigned long long*>(a.gam + (size_t)sp * R2);
+            for (int j = threadIdx.x; j < R; j += ZOZ_THREADS) {
+                unsigned long long mx = 0;
+                for (int q = 0; q < R; ++q) mx = max(mx, g[j * R + q] & 0x7FFFFFFFFFFFFFFFull);
+                eB[j] = zoz_row_exp(mx);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < R * NCH; e += ZOZ_THREADS) {
+                const int j = e / NCH, c = e - j * NCH;
+                unsigned long long x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = g[j * R + 8 * c + u];
+                zoz_digits8(x, eB[j], S, sB, B_SLICE, zoz_sw128(j, c), tab);
+            }
+            cur_sp = sp;
+        }
+        // A: row m = p r + s of W_k^T, K = q: W_kp[q][s] of type t (see k_Z_pipe); two threads per row
+        {
+            const int ml = threadIdx.x >> 1, half = threadIdx.x & 1, m = m0 + ml;
+            const int p = m / R, s = m - p * R;
+            const double* base;
+            bool tr;
+            switch (t) {
+                case 0: tr = false; base = a.W[0] + k * r3 + (size_t)p * R2; break;
+                case 1: tr = false; base = a.W[1] + k * r3 + (size_t)p * R2; break;
+                case 2: tr = true; base = a.W[1] + (size_t)p * r3 + (size_t)k * R2; break;
+                case 3: tr = false; base = a.W[2] + k * r3 + (size_t)p * R2; break;
+                case 4: tr = true; base = a.W[1] + k * r3 + (size_t)p * R2; break;
+                default: tr = false; base = a.W[1] + (size_t)p * r3 + (size_t)k * R2; break;
+            }
+            const unsigned long long* b64 = reinterpret_cast<const unsigned long long*>(base);
+            constexpr int MYCH = (NCH + 1) / 2;   // chunks c = half, half + 2, ... of this thread
+            unsigned long long x[MYCH][8];
+            unsigned long long mx = 0;
+#pragma unroll
+            for (int i = 0; i < MYCH; ++i) {
+                const int c = 2 * i + half;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = 8 * c + u;
+                    x[i][u] = c < NCH ? (tr ? b64[(size_t)s * R + q] : b64[(size_t)q * R + s]) : 0ull;
+                    mx = max(mx, x[i][u] & 0x7FFFFFFFFFFFFFFFull);
+                }
+            }
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            const int e = zoz_row_exp(mx);
+            if (half == 0) eA[ml] = e;
+#pragma unroll
+            for (int i = 0; i < MYCH; ++i) {
+                const int c = 2 * i + half;
+                if (c < NCH) zoz_digits8(x[i], e, S, sA, ZOZ_A_SLICE, zoz_sw128(ml, c), tab);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor cores
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t idesc = make_idesc<0, R>();
+            for (int L = 2; L <= S + 1; ++L) {
+                const uint32_t acc = tmem + (uint32_t)((L - 2) * R);
+                bool first = true;
+                for (int sa = max(1, L - S); sa <= min(S, L - 1); ++sa) {
+                    const uint64_t da = smem_desc(sA + (size_t)(sa - 1) * ZOZ_A_SLICE);
+                    const uint64_t db = smem_desc(sB + (size_t)(L - sa - 1) * B_SLICE);
+#pragma unroll
+                    for (int kk = 0; kk < R / 16; ++kk) {
+                        umma<0>(acc, da + 2 * kk, db + 2 * kk, idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+                }
+            }
+            umma_commit(bar);
+        }
+        ok = __syncthreads_and(bounded_wait(bar, phase, ZOZ_WAIT_NS, nullptr)) != 0;
+        if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+        tc_fence_after();
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows m) for the columns j of its half
+        {
+            const int q4 = warp & 3, jh = warp >> 2;
+            const int ml = q4 * 32 + lane, m = m0 + ml;
+            const int p = m / R, s = m - p * R;
+            const int em = eA[ml];
+            int which, sK, sP;
+            if (t < 4) { which = -1; sK = t >> 1; sP = t & 1; }
+            else { which = t - 4; sK = 0; sP = 0; }
+            const int dslot = t == 0 ? 0 : t == 3 ? 1 : t == 4 ? 2 : t == 5 ? 3 : -1;
+            double* zb = which < 0 ? a.Zd : a.Zf[which];
+            const size_t ld = which < 0 ? (size_t)a.ldd : (size_t)a.ldf;
+            const size_t col = (size_t)sP * R2 + m;
+            for (int j0 = jh * (R / 2); j0 < (jh + 1) * (R / 2); j0 += 8) {
+                long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int L = 2; L <= S + 1; ++L) {
+                    uint32_t v[8];
+                    __syncwarp();
+                    zoz_tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((L - 2) * R + j0), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int sh = 6 * (S + 1 - L);
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) acc[jj] += (long long)__float2int_rn(__uint_as_float(v[jj])) * (1ll << sh);
+                }
+                if (!ok) continue;
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = j0 + jj;
+                    const int ej = eB[j];
+                    const double z = (em == ZOZ_BAD || ej == ZOZ_BAD) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                                      : oz_ll_scaled(acc[jj], em + ej - 6 * (S + 1));
+                    zb[((size_t)sK * R2 + (size_t)k * R + j) * ld + col] = z;
+                    if (dslot >= 0 && j == p) a.diag[(((size_t)dslot * R2 + (size_t)k * R + p) * R) + s] = z;
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();   // TMEM read and the A tiles free before the next tile's digits and MMAs
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+template <int R>
+static int zoz_launch(const ZozArgs& a, int ntypes, cudaStream_t st) {
+    constexpr int R2 = R * R, NT = R2 / TC_BM;
+    const size_t smem = 1024 + (size_t)ZOZ_SMAX * ZOZ_A_SLICE + (size_t)ZOZ_SMAX * R * 128 + 4 * (TC_BM + 64) + 2 * 72 + 64;
+    static int nsm = 0;
+    if (!nsm) {
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_oz<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0;
+        ACSE_CUDA_TRY(cudaGetDevice(&dev));
+        ACSE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int ntiles = ntypes * R * NT;
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    k_Z_oz<R><<<grid, ZOZ_THREADS, smem, st>>>(a, ntiles);
+    ACSE_CUDA_TRY(cudaGetLastError());
+    return ACSE_OK;
+}
+
+// Z (FP64 rows of Zd, Zf) and the diagonal rows of w on the tensor cores for an Ozaki context with r a
+// multiple of 16 (r <= 64) and at most 8 slices; ACSE_ERR_UNSUPPORTED otherwise (the caller then runs
+// the double-float kernel).
+int launch_Z_oz(acse_ctx* c, const double* const W[3], int ntypes, const int* tmap) {
+    const int r = c->r;
+    if (!c->oz || r % 16 != 0 || r > 64 || c->opt.oz_slices > ZOZ_SMAX) return ACSE_ERR_UNSUPPORTED;
+    Work& w = c->w;
+    ZozArgs a;
+    for (int s = 0; s < 3; ++s) a.W[s] = W[s];
+    a.gam = w.gam;
+    a.Zd = w.Zd;
+    a.Zf[0] = w.Zf1;
+    a.Zf[1] = w.Zf2;
+    a.diag = w.zdiag;
+    a.ldd = 2 * r * r;
+    a.ldf = r * r;
+    for (int i = 0; i < 6; ++i) a.tmap[i] = tmap[i];
+    a.S = c->opt.oz_slices;
+    a.err = c->w.tc_err;
+    int s;
+    switch (r) {
+        case 16: s = zoz_launch<16>(a, ntypes, c->stream); break;
+        case 32: s = zoz_launch<32>(a, ntypes, c->stream); break;
+        case 48: s = zoz_launch<48>(a, ntypes, c->stream); break;
+        default: s = zoz_launch<64>(a, ntypes, c->stream); break;
+    }
+    if (s == ACSE_OK) c->launches++;
+    return s;
+}

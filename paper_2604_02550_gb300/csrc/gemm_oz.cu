@@ -29,6 +29,7 @@
 #include <string.h>
 
 #include "acse_internal.h"
+#include "oz_arith.cuh"
 #include "tc_ptx.cuh"
 
 #define OZ_BETA 6            // bits per digit (base 2^6, |digit| <= 32)
@@ -93,18 +94,6 @@ __device__ __forceinline__ void oz_group(int S, int g, int idx, int& L, int& s0,
     s0 = s1 = 1;
 }
 
-// 2^n for -1022 <= n <= 1023, built from its bit pattern (exact)
-__host__ __device__ __forceinline__ double oz_pow2(int n) {
-#ifdef __CUDA_ARCH__
-    return __longlong_as_double((long long)(n + 1023) << 52);
-#else
-    const long long bits = (long long)(n + 1023) << 52;
-    double d;
-    memcpy(&d, &bits, sizeof(d));
-    return d;
-#endif
-}
-
 __device__ __forceinline__ int oz_find_problem(const OzBatch& b, int t) {
     int lo = 0, hi = b.nprob - 1;
     while (lo < hi) {
@@ -132,20 +121,6 @@ struct OzSliceBatch {
     int njobs;
     int S;
 };
-
-// Fixed-point value of one element: X = round(a 2^(6S - e)) from the bit pattern of a, |X| < 2^(6S-1)
-// (integer arithmetic only: FP64 is slow on this GPU).  The rounding drops bits below 2^-6S of the
-// row scale, as the remainder x_{S+1} of the digit recursion does.
-__device__ __forceinline__ long long oz_fixed(unsigned long long bits, int S, int e) {
-    const int E = (int)((bits >> 52) & 0x7FF);
-    const long long m = (long long)(bits & 0xFFFFFFFFFFFFFull) | (E ? (1ll << 52) : 0ll);
-    const int sh = (E ? E : 1) - 1075 + 6 * S - e;   // a = m 2^((E ? E : 1) - 1075)
-    long long X;
-    if (sh >= 0) X = m << sh;                         // < 2^(6S-1) by the choice of e
-    else if (sh > -63) X = (m + (1ll << (-sh - 1))) >> -sh;
-    else X = 0;
-    return (bits >> 63) ? -X : X;
-}
 
 // One block per operand row.  The row's bit patterns are held in registers, its largest magnitude
 // fixes e (|a| 2^-e < 1/2), and every element's fixed-point value X is cut into S balanced base-64
@@ -436,33 +411,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
         if constexpr (PAIR) tmem_dealloc_pair(tmem, 2 * BN);
         else tmem_dealloc(tmem, 2 * BN);
     }
-}
-
-// acc 2^ex rounded to the nearest double (ties to even), with integer operations only (FP64 is slow on
-// this GPU): the leading bit of |acc| fixes the exponent, the 53 bits below it the significand, the
-// rest decides the rounding.  Results outside the normal range take the FP64 route.
-__device__ __forceinline__ double oz_ll_scaled(long long acc, int ex) {
-    if (acc == 0) return 0.0;
-    const unsigned long long sign = acc < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned long long u = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
-    int msb = 63 - __clzll((long long)u);
-    unsigned long long mant;
-    if (msb <= 52) {
-        mant = u << (52 - msb);
-    } else {
-        const int sh = msb - 52;
-        mant = u >> sh;
-        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1))) {
-            if (++mant == (1ull << 53)) {
-                mant >>= 1;
-                ++msb;
-            }
-        }
-    }
-    const int E = msb + ex + 1023;
-    if (E < 1 || E > 2046) return __ll2double_rn(acc) * oz_pow2(min(1023, max(-1022, ex)));
-    return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 // C = alpha 2^(ea_i + eb_j) sum_g 2^-6L_g v_g for every element, from the staged group sums v_g.
