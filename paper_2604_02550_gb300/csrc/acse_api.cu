@@ -623,8 +623,11 @@ static int step_impl(acse_ctx* c, double* Daa, double* Dab, double* Dbb, double 
     if (s == ACSE_OK) s = check_D(c, Din);
     double* D[3] = {(double*)Din[0], (double*)Din[1], (double*)Din[2]};
     const double* Dc[3] = {D[0], D[1], D[2]};
-    // A at D (masked), ||A||^2 before the mask -> scal[0]
+    // A at D (masked), ||A||^2 before the mask -> scal[0]; on the split path (V reconstruction) only its FP32
+    // copy is written: the update pass reads that, and the FP64 A of a step is not an output
+    c->a64_skip = c->opt.prec != ACSE_FP64 && !c->ny;
     if (s == ACSE_OK) s = residual_dev(c, Dc, w.A, w.scal + 0);
+    c->a64_skip = 0;
     const double* Ac[3] = {w.A[0], w.A[1], w.A[2]};
     if (s == ACSE_OK) s = update_dev(c, Dc, Ac, w.U);
     const double* Uc[3] = {w.U[0], w.U[1], w.U[2]};

@@ -313,9 +313,11 @@ __device__ __forceinline__ void g_put(const GArgs<T>& a, int blk, int r, int R2,
         const int i = ij / r, j = ij - i * r, k = kl / r, l = kl - k * r;
         if (i >= a.lo && i < a.hi && j >= a.lo && j < a.hi && k >= a.lo && k < a.hi && l >= a.lo && l < a.hi) o = (T)0;
     }
-    const double od = (double)o;   // the one conversion of the FP32 path (FP64 conversions are slow here)
-    a.out[blk][(size_t)ij * R2 + kl] = od;
-    if (a.flip && blk == 0) a.out[2][(size_t)ij * R2 + kl] = od;
+    if (a.out[blk]) {
+        const double od = (double)o;   // the one conversion of the FP32 path (FP64 conversions are slow here)
+        a.out[blk][(size_t)ij * R2 + kl] = od;
+        if (a.flip && blk == 0) a.out[2][(size_t)ij * R2 + kl] = od;
+    }
     if (a.out32[0]) {   // the split path's FP32 copy: o itself (an FP32 value)
         a.out32[blk][(size_t)ij * R2 + kl] = (float)o;
         if (a.flip && blk == 0) a.out32[2][(size_t)ij * R2 + kl] = (float)o;
@@ -399,7 +401,10 @@ int launch_assemble_G(acse_ctx* c, int sW, double scale, int apply_mask, double*
         // into the context's A: also its FP32 copy, the W of the update pass that follows
         const bool intoA = out[0] == c->w.A[0] && out[1] == c->w.A[1] && out[2] == c->w.A[2];
         if (intoA)
-            for (int s = 0; s < 3; ++s) a.out32[s] = c->w.A32[s];
+            for (int s = 0; s < 3; ++s) {
+                a.out32[s] = c->w.A32[s];
+                if (c->a64_skip) a.out[s] = nullptr;   // only the FP32 copy is read after this pass
+            }
         c->a32_valid = intoA ? 1 : c->a32_valid;
         k_assemble_G<float><<<G_ASM_GRID, 256, 0, c->stream>>>(a);
     }

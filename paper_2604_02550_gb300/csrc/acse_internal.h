@@ -166,6 +166,8 @@ struct acse_ctx {
     cudaStream_t aux[3];  // host <-> device copies of the three blocks run concurrently on these
     cudaEvent_t ev_fork, ev_join[3];
     int a32_valid;        // split path: w.A32 holds the FP32 values of the last A written to w.A
+    int a64_skip;         // set by acse_step around its residual pass on the split path: the G assembly
+                          // into w.A writes only the FP32 copy (all the update pass reads)
     int oz;               // ACSE_OZAKI: an FP64 context (opt.prec = ACSE_FP64) whose pass GEMMs run by
                           // the Ozaki scheme on the BF16 tensor cores (gemm_oz.cu)
     void* oz_plan;
