@@ -16,9 +16,9 @@
 // rounding leave an error of order 2^-6S of |A_m| |B_j| r, that of the Ozaki GEMMs.
 //
 // One block per SM (the S digit tiles of A and B take up to 192 KB of shared memory) walks a contiguous
-// range of tiles; the B tiles are rebuilt only when the spin of the tile's 1D changes.  Producer: two
+// range of tiles; the B tiles are rebuilt only when the spin of the tile's 1D changes.  Producer: four
 // threads per A row (partners in one warp share the row maximum); one thread issues the MMAs; epilogue:
-// each warp reads its TMEM lane quarter (one row m per thread) for half of the columns j and writes the
+// each warp reads its TMEM lane quarter (one row m per thread) for a quarter of the columns j and writes the
 // FP64 rows of Zd / Zf (row (sK, k, j), column (sP, p, s)) and the diagonal rows j = p of w.  The wait for
 // the MMAs is bounded; on expiry the kernel raises the device flag and stops.  Used for r a multiple of
 // 16 (r <= 64) and S <= 8; other cases take the double-float kernel of acse_tiled.cu.
@@ -28,7 +28,8 @@
 #include "oz_arith.cuh"
 #include "tc_ptx.cuh"
 
-#define ZOZ_THREADS 256
+#define ZOZ_THREADS 512                  // four threads per A row; four warps per TMEM lane quarter
+#define ZOZ_TPR (ZOZ_THREADS / TC_BM)
 #define ZOZ_SMAX 8                       // digit slices this kernel holds
 #define ZOZ_A_SLICE (TC_BM * 128)        // one digit tile of A: 128 rows x 128 bytes
 #define ZOZ_WAIT_NS 4000000000ull
@@ -89,9 +90,9 @@ static __device__ __forceinline__ void zoz_digits8(const unsigned long long (&x)
     }
 }
 
-static __device__ __forceinline__ void zoz_tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+static __device__ __forceinline__ void zoz_tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                  : "r"(taddr));
 }
 
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Z_oz(const __grid_constant__
             }
             cur_sp = sp;
         }
-        // A: row m = p r + s of W_k^T, K = q: W_kp[q][s] of type t (see k_Z_pipe); two threads per row
+        // A: row m = p r + s of W_k^T, K = q: W_kp[q][s] of type t (see k_Z_pipe); ZOZ_TPR threads per row
         {
-            const int ml = threadIdx.x >> 1, half = threadIdx.x & 1, m = m0 + ml;
+            const int ml = threadIdx.x / ZOZ_TPR, half = threadIdx.x % ZOZ_TPR, m = m0 + ml;
             const int p = m / R, s = m - p * R;
             const double* base;
             bool tr;
@@ -171,12 +172,12 @@ __global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Z_oz(const __grid_constant__
                 default: tr = false; base = a.W[1] + (size_t)p * r3 + (size_t)k * R2; break;
             }
             const unsigned long long* b64 = reinterpret_cast<const unsigned long long*>(base);
-            constexpr int MYCH = (NCH + 1) / 2;   // chunks c = half, half + 2, ... of this thread
+            constexpr int MYCH = (NCH + ZOZ_TPR - 1) / ZOZ_TPR;   // chunks c = half, half + TPR, ... of this thread
             unsigned long long x[MYCH][8];
             unsigned long long mx = 0;
 #pragma unroll
             for (int i = 0; i < MYCH; ++i) {
-                const int c = 2 * i + half;
+                const int c = ZOZ_TPR * i + half;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int q = 8 * c + u;
@@ -184,12 +185,13 @@ __global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Z_oz(const __grid_constant__
                     mx = max(mx, x[i][u] & 0x7FFFFFFFFFFFFFFFull);
                 }
             }
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+#pragma unroll
+            for (int o = 1; o < ZOZ_TPR; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             const int e = zoz_row_exp(mx);
             if (half == 0) eA[ml] = e;
 #pragma unroll
             for (int i = 0; i < MYCH; ++i) {
-                const int c = 2 * i + half;
+                const int c = ZOZ_TPR * i + half;
                 if (c < NCH) zoz_digits8(x[i], e, S, sA, ZOZ_A_SLICE, zoz_sw128(ml, c), tab);
             }
         }
@@ -217,8 +219,10 @@ __global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Z_oz(const __grid_constant__
         ok = __syncthreads_and(bounded_wait(bar, phase, ZOZ_WAIT_NS, nullptr)) != 0;
         if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
         tc_fence_after();
-        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows m) for the columns j of its half
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows m) for its share of the columns j
         {
+            constexpr int NJG = ZOZ_THREADS / 128, JW = R / NJG;   // warps per lane quarter, columns each
+            static_assert(JW % 4 == 0, "whole groups of four columns");
             const int q4 = warp & 3, jh = warp >> 2;
             const int ml = q4 * 32 + lane, m = m0 + ml;
             const int p = m / R, s = m - p * R;
@@ -230,20 +234,20 @@ __global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Z_oz(const __grid_constant__
             double* zb = which < 0 ? a.Zd : a.Zf[which];
             const size_t ld = which < 0 ? (size_t)a.ldd : (size_t)a.ldf;
             const size_t col = (size_t)sP * R2 + m;
-            for (int j0 = jh * (R / 2); j0 < (jh + 1) * (R / 2); j0 += 8) {
-                long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int j0 = jh * JW; j0 < (jh + 1) * JW; j0 += 4) {
+                long long acc[4] = {0, 0, 0, 0};
                 for (int L = 2; L <= S + 1; ++L) {
-                    uint32_t v[8];
+                    uint32_t v[4];
                     __syncwarp();
-                    zoz_tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((L - 2) * R + j0), v);
+                    zoz_tmem_ld4(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((L - 2) * R + j0), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     const int sh = 6 * (S + 1 - L);
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) acc[jj] += (long long)__float2int_rn(__uint_as_float(v[jj])) * (1ll << sh);
+                    for (int jj = 0; jj < 4; ++jj) acc[jj] += (long long)__float2int_rn(__uint_as_float(v[jj])) * (1ll << sh);
                 }
                 if (!ok) continue;
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
+                for (int jj = 0; jj < 4; ++jj) {
                     const int j = j0 + jj;
                     const int ej = eB[j];
                     const double z = (em == ZOZ_BAD || ej == ZOZ_BAD) ? __longlong_as_double(0x7ff8000000000000ll)
