@@ -149,6 +149,7 @@ struct Work {
     // i r + j table (pairs i < j in packed order); null otherwise
     float* bx[8];
     int* pair_ij;
+    double* bx64[8];   // Ozaki contexts: x1 and x2^T of the four B spin types for every pair (acse_zoz.cu)
 };
 
 struct acse_ctx {
@@ -249,6 +250,7 @@ int launch_Z_tiled(acse_ctx* c, const double* const W[3], const float* const W32
 int launch_B_tiled(acse_ctx* c);
 int launch_Z_tc(acse_ctx* c, const float* const W32[3], int ntypes, const int* tmap);   // acse_ztc.cu
 int launch_Z_oz(struct acse_ctx* c, const double* const W[3], int ntypes, const int* tmap);   // acse_zoz.cu
+int launch_Bx_oz(struct acse_ctx* c);                                                           // acse_zoz.cu
 int launch_Bx_tc(acse_ctx* c);                                                           // acse_btc.cu
 int tiled_set_attrs();
 int launch_Q(acse_ctx* c);

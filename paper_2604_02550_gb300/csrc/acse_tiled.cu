@@ -432,7 +432,9 @@ struct BTiledArgs {
 // memory with coalesced loads before the products (off when shared memory would not fit).
 // DF (T = double, the Ozaki path): the two products in double-float (C = dfl, the same 8 bytes as
 // double in shared memory), everything else in FP64.
-template <typename T, bool STAGE, bool DF = false>
+// PREX (Ozaki path): x1 and x2^T come precomputed for every pair (a.bx, k_Bx_oz of acse_zoz.cu): no operand
+// staging, each thread reads its 4 x 4 tile of both.
+template <typename T, bool STAGE, bool DF = false, bool PREX = false>
 __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTiledArgs<T> a) {
     using C = typename std::conditional<DF, dfl, T>::type;
     static_assert(sizeof(C) == sizeof(T), "product operands share the layout of T");
@@ -488,10 +490,12 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
             __syncthreads();
             for (int e = threadIdx.x; e < R2; e += blockDim.x) {
                 const int u = e / r, v = e - u * r;
-                XT[xT ? u * rp + v : v * rp + u] = tconv<C>(Xrow[e]);   // T3 uses Xab[ij][p][k]
-                G1[u * rp + v] = tconv<C>(g1[e]);
-                WT[v * rp + u] = tconv<C>(wv[e]);                      // w[k][p] -> WT[p][k]
-                MT[mT ? v * rp + u : u * rp + v] = tconv<C>(Mrow[e]);  // M[(l,p)] -> MT[p][l]  or  M[(p,l)]
+                if (!PREX) {
+                    XT[xT ? u * rp + v : v * rp + u] = tconv<C>(Xrow[e]);   // T3 uses Xab[ij][p][k]
+                    G1[u * rp + v] = tconv<C>(g1[e]);
+                    WT[v * rp + u] = tconv<C>(wv[e]);                      // w[k][p] -> WT[p][k]
+                    MT[mT ? v * rp + u : u * rp + v] = tconv<C>(Mrow[e]);  // M[(l,p)] -> MT[p][l]  or  M[(p,l)]
+                }
                 if (STAGE) {
                     X5s[e] = X5b[((size_t)u * r + j) * ld5 + (size_t)i * r + v];   // (k, l) = (u, v)
                     X8s[e] = X8b[((size_t)u * r + i) * ld8 + (size_t)j * r + v];
@@ -513,8 +517,29 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) x1[u][v] = x2[u][v] = tconv<C>(0.0);
-                mma4x4<C>(x1, XT, G1, rp, r, k0, l0);
-                mma4x4<C>(x2, WT, MT, rp, r, k0, l0);
+                T p1[4][4], p2[4][4];   // PREX: x1[k][l] = bx[2t] row (ij, k), x2[k][l] = bx[2t + 1] row (ij, l)
+                if constexpr (PREX) {
+                    const T* b1 = a.bx[2 * t] + ij * R2;
+                    const T* b2 = a.bx[2 * t + 1] + ij * R2;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const int k = min(k0 + u, r - 1), l = min(l0 + v, r - 1);
+                            p1[u][v] = b1[(size_t)k * r + l];
+                            p2[u][v] = b2[(size_t)l * r + k];
+                        }
+                } else {
+                    mma4x4<C>(x1, XT, G1, rp, r, k0, l0);
+                    mma4x4<C>(x2, WT, MT, rp, r, k0, l0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            p1[u][v] = (T)x1[u][v];
+                            p2[u][v] = (T)x2[u][v];
+                        }
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = k0 + u;
@@ -535,7 +560,7 @@ __global__ void __launch_bounds__(TL_TPB) k_B_tiled(const __grid_constant__ BTil
                             x5 = X5b[((size_t)k * r + j) * ld5 + (size_t)i * r + l];
                             x8 = X8b[((size_t)k * r + i) * ld8 + (size_t)j * r + l];
                         }
-                        Bt[k * r + l] = (sgn1 * (T)x1[u][v] - (T)2 * sgn2 * (T)x2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
+                        Bt[k * r + l] = (sgn1 * p1[u][v] - (T)2 * sgn2 * p2[u][v] - x4 + (T)2 * x5 + x7 - (T)2 * x8) *
                                             (T)(1.0 / 9.0) +
                                         (a.ny[t] ? a.ny[t][ij * R2 + (size_t)k * r + l] : (T)0);
                     }
@@ -1088,8 +1113,18 @@ int launch_B_tiled(acse_ctx* c) {
         a.gam = w.gam; a.w = w.w; a.Q = w.Q;
         const bool st = b_smem(r, sizeof(double), true) <= k_smem_cap;
         const size_t sm = b_smem(r, sizeof(double), st);
-        if (c->oz) {   // Ozaki path: double-float products; without staging two blocks fit an SM
-            k_B_tiled<double, false, true><<<R2, TL_TPB, b_smem(r, sizeof(double), false), c->stream>>>(a);
+        if (c->oz) {
+            // Ozaki path: the products on the tensor cores (acse_zoz.cu) where it applies, else in
+            // double-float; without staging two blocks fit an SM
+            const int bs = launch_Bx_oz(c);
+            if (bs == ACSE_OK) {
+                for (int k = 0; k < 8; ++k) a.bx[k] = w.bx64[k];
+                k_B_tiled<double, false, true, true><<<R2, TL_TPB, b_smem(r, sizeof(double), false), c->stream>>>(a);
+            } else if (bs == ACSE_ERR_UNSUPPORTED) {
+                k_B_tiled<double, false, true><<<R2, TL_TPB, b_smem(r, sizeof(double), false), c->stream>>>(a);
+            } else {
+                return bs;
+            }
         } else {
             if (st) k_B_tiled<double, true><<<R2, TL_TPB, sm, c->stream>>>(a);
             else k_B_tiled<double, false><<<R2, TL_TPB, sm, c->stream>>>(a);
@@ -1174,6 +1209,8 @@ int tiled_set_attrs() {
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
+    ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_tiled<double, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)b_smem(ACSE_MAX_R, sizeof(double), false)));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Z_pipe<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k_smem_cap));
     ACSE_CUDA_TRY(cudaFuncSetAttribute(k_B_pipe<320, 2, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -316,3 +316,224 @@ int launch_Z_oz(acse_ctx* c, const double* const W[3], int ntypes, const int* tm
     if (s == ACSE_OK) c->launches++;
     return s;
 }
+
+// ---------------------------------------------------------------------------------- B products
+// The two r x r x r products of every B spin type in an Ozaki context, for every pair (i, j) (the B kernel
+// of the FP64 paths, k_B_tiled, walks all r^2 pairs):
+//     x1[k][l] = sum_q X_ij[k][q] 1D[q][l]      (types 0, 1, 2; type 3 reads X_ij transposed)
+//     x2[k][l] = sum_p w[k][p] M_ij[l][p]       (types 0, 1, 3; type 2 reads M_ij transposed)
+// as tall GEMMs over the rows (ij, k) of x1 against 1D^T and (ij, l) of x2^T against w (the class
+// structure of acse_btc.cu), each by the Ozaki splitting of k_Z_oz: digit tiles in shared memory, one
+// exact FP32 accumulator per level, the levels added in int64 and rounded once to FP64.  Outputs: class
+// c = 2 t + (0: x1, 1: x2^T), rows (ij, .) of r doubles, read by k_B_tiled in its precomputed mode.
+struct BxozArgs {
+    const double* X[3];     // pair GEMM outputs (rows ij of r^2: X^{ij}_{kq} at [k][q])
+    const double* M[3];     // M blocks (rows ij: M^{ij}_{lp} at [l][p])
+    const double* gam;      // 1D per spin [2][r][r]
+    const double* w;        // w per spin [2][r][r], w[k][p]
+    double* out[8];
+    int S;
+    int* err;
+};
+
+template <int R>
+__global__ void __launch_bounds__(ZOZ_THREADS, 1) k_Bx_oz(const __grid_constant__ BxozArgs a, int ntiles) {
+    constexpr int R2 = R * R, NCH = R / 8, TPC = R * R2 / TC_BM;   // tiles per class
+    static_assert((R * R2) % TC_BM == 0, "whole tiles");
+    constexpr int B_SLICE = R * 128;
+    const int S = a.S;
+    extern __shared__ uint8_t zo_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)zo_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = sA + ZOZ_SMAX * ZOZ_A_SLICE;
+    int* eA = reinterpret_cast<int*>(sB + ZOZ_SMAX * B_SLICE);
+    int* eB = eA + TC_BM;
+    unsigned short* tab = reinterpret_cast<unsigned short*>(eB + 64);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tab + 72);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < 65) tab[threadIdx.x] = __bfloat16_as_ushort(__float2bfloat16_rn((float)((int)threadIdx.x - 32)));
+    for (int e = threadIdx.x; e < (ZOZ_SMAX * ZOZ_A_SLICE + ZOZ_SMAX * B_SLICE) / 16; e += ZOZ_THREADS)
+        reinterpret_cast<uint4*>(sA)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+    uint32_t phase = 0;
+    int cur_sel = -1;
+    const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t_end = min(ntiles, ((int)blockIdx.x + 1) * per);
+    for (int tile = (int)blockIdx.x * per; tile < t_end && ok; ++tile, phase ^= 1) {
+        const int c = tile / TPC;
+        const int t = c >> 1, x2 = c & 1;
+        const int m0 = (tile - c * TPC) * TC_BM;
+        // x1: 1D^T of spin a for types 0, 3, b for 1, 2;  x2: w of spin a for types 0, 2, b for 1, 3
+        const int sel = x2 ? ((t == 0 || t == 2) ? 2 : 3) : ((t == 0 || t == 3) ? 0 : 1);
+        if (sel != cur_sel) {   // B rows n, K = q: 1D^T[n][q] = 1D[q][n], or w[n][q]
+            const unsigned long long* g =
+                reinterpret_cast<const unsigned long long*>((sel < 2 ? a.gam : a.w) + (size_t)(sel & 1) * R2);
+            for (int n = threadIdx.x; n < R; n += ZOZ_THREADS) {
+                unsigned long long mx = 0;
+                for (int q = 0; q < R; ++q) mx = max(mx, (sel < 2 ? g[q * R + n] : g[n * R + q]) & 0x7FFFFFFFFFFFFFFFull);
+                eB[n] = zoz_row_exp(mx);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < R * NCH; e += ZOZ_THREADS) {
+                const int n = e / NCH, cc = e - n * NCH;
+                unsigned long long x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = 8 * cc + u;
+                    x[u] = sel < 2 ? g[q * R + n] : g[n * R + q];
+                }
+                zoz_digits8(x, eB[n], S, sB, B_SLICE, zoz_sw128(n, cc), tab);
+            }
+            cur_sel = sel;
+        }
+        // A: row m = (ij, row) of X_ij (x1) or M_ij (x2), K = q; types 3 (x1) and 2 (x2) transposed
+        {
+            const int ml = threadIdx.x / ZOZ_TPR, part = threadIdx.x % ZOZ_TPR, m = m0 + ml;
+            const int ij = m / R, row = m - ij * R;
+            const int sec = t == 0 ? 0 : t == 1 ? 2 : 1;
+            const unsigned long long* base =
+                reinterpret_cast<const unsigned long long*>((x2 ? a.M[sec] : a.X[sec]) + (size_t)ij * R2);
+            const bool tr = x2 ? (t == 2) : (t == 3);
+            constexpr int MYCH = (NCH + ZOZ_TPR - 1) / ZOZ_TPR;
+            unsigned long long x[MYCH][8];
+            unsigned long long mx = 0;
+#pragma unroll
+            for (int i = 0; i < MYCH; ++i) {
+                const int cc = ZOZ_TPR * i + part;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = 8 * cc + u;
+                    x[i][u] = cc < NCH ? (tr ? base[(size_t)q * R + row] : base[(size_t)row * R + q]) : 0ull;
+                    mx = max(mx, x[i][u] & 0x7FFFFFFFFFFFFFFFull);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < ZOZ_TPR; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int e = zoz_row_exp(mx);
+            if (part == 0) eA[ml] = e;
+#pragma unroll
+            for (int i = 0; i < MYCH; ++i) {
+                const int cc = ZOZ_TPR * i + part;
+                if (cc < NCH) zoz_digits8(x[i], e, S, sA, ZOZ_A_SLICE, zoz_sw128(ml, cc), tab);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t idesc = make_idesc<0, R>();
+            for (int L = 2; L <= S + 1; ++L) {
+                const uint32_t acc = tmem + (uint32_t)((L - 2) * R);
+                bool first = true;
+                for (int sa = max(1, L - S); sa <= min(S, L - 1); ++sa) {
+                    const uint64_t da = smem_desc(sA + (size_t)(sa - 1) * ZOZ_A_SLICE);
+                    const uint64_t db = smem_desc(sB + (size_t)(L - sa - 1) * B_SLICE);
+#pragma unroll
+                    for (int kk = 0; kk < R / 16; ++kk) {
+                        umma<0>(acc, da + 2 * kk, db + 2 * kk, idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+                }
+            }
+            umma_commit(bar);
+        }
+        ok = __syncthreads_and(bounded_wait(bar, phase, ZOZ_WAIT_NS, nullptr)) != 0;
+        if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+        tc_fence_after();
+        {
+            constexpr int NJG = ZOZ_THREADS / 128, JW = R / NJG;
+            static_assert(JW % 4 == 0, "whole groups of four columns");
+            const int q4 = warp & 3, jh = warp >> 2;
+            const int ml = q4 * 32 + lane;
+            const int em = eA[ml];
+            double* orow = a.out[c] + (size_t)(m0 + ml) * R;
+            for (int n0 = jh * JW; n0 < (jh + 1) * JW; n0 += 4) {
+                long long acc[4] = {0, 0, 0, 0};
+                for (int L = 2; L <= S + 1; ++L) {
+                    uint32_t v[4];
+                    __syncwarp();
+                    zoz_tmem_ld4(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((L - 2) * R + n0), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int sh = 6 * (S + 1 - L);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) acc[jj] += (long long)__float2int_rn(__uint_as_float(v[jj])) * (1ll << sh);
+                }
+                if (!ok) continue;
+                double z[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int en = eB[n0 + jj];
+                    z[jj] = (em == ZOZ_BAD || en == ZOZ_BAD) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                             : oz_ll_scaled(acc[jj], em + en - 6 * (S + 1));
+                }
+                *reinterpret_cast<double2*>(orow + n0) = make_double2(z[0], z[1]);
+                *reinterpret_cast<double2*>(orow + n0 + 2) = make_double2(z[2], z[3]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+template <int R>
+static int bxoz_launch(const BxozArgs& a, cudaStream_t st) {
+    const size_t smem = 1024 + (size_t)ZOZ_SMAX * ZOZ_A_SLICE + (size_t)ZOZ_SMAX * R * 128 + 4 * (TC_BM + 64) + 2 * 72 + 64;
+    static int nsm = 0;
+    if (!nsm) {
+        ACSE_CUDA_TRY(cudaFuncSetAttribute(k_Bx_oz<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0;
+        ACSE_CUDA_TRY(cudaGetDevice(&dev));
+        ACSE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int ntiles = 8 * (R * R * R / TC_BM);
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    k_Bx_oz<R><<<grid, ZOZ_THREADS, smem, st>>>(a, ntiles);
+    ACSE_CUDA_TRY(cudaGetLastError());
+    return ACSE_OK;
+}
+
+// x1 and x2^T of every B spin type and every pair into w.bx64 (Ozaki contexts with the scratch allocated:
+// r a multiple of 16, r <= 64, at most 8 slices); ACSE_ERR_UNSUPPORTED otherwise (the B kernel then forms
+// the products itself in double-float).
+int launch_Bx_oz(acse_ctx* c) {
+    const int r = c->r;
+    Work& w = c->w;
+    if (!c->oz || !w.bx64[0] || r % 16 != 0 || r > 64 || c->opt.oz_slices > ZOZ_SMAX) return ACSE_ERR_UNSUPPORTED;
+    BxozArgs a;
+    for (int s = 0; s < 3; ++s) {
+        a.X[s] = w.X[s];
+        a.M[s] = w.M[s];
+    }
+    a.gam = w.gam;
+    a.w = w.w;
+    for (int k = 0; k < 8; ++k) a.out[k] = w.bx64[k];
+    a.S = c->opt.oz_slices;
+    a.err = w.tc_err;
+    int s;
+    switch (r) {
+        case 16: s = bxoz_launch<16>(a, c->stream); break;
+        case 32: s = bxoz_launch<32>(a, c->stream); break;
+        case 48: s = bxoz_launch<48>(a, c->stream); break;
+        default: s = bxoz_launch<64>(a, c->stream); break;
+    }
+    if (s == ACSE_OK) c->launches++;
+    return s;
+}

@@ -686,6 +686,14 @@ int oz_plan_create(acse_ctx* c) {
     c->oz_plan = pl;
     const int r = c->r, R2 = r * r, R22 = 2 * R2, P = r * (r - 1) / 2;
     ACSE_TRY(oz_plan_init(pl, c->opt.oz_slices, R2 >= 256 ? OZ_BN : 128, c->opt.gemm_tile != 1));
+    // the B products on the tensor cores (acse_zoz.cu): x1 and x2^T of the four types for every pair
+    if (r % 16 == 0 && r <= 64 && c->opt.oz_slices <= 8)
+        for (int k = 0; k < 8; ++k)
+            if (cudaMalloc((void**)&c->w.bx64[k], (size_t)R2 * R2 * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                c->w.bx64[k] = nullptr;
+                return ACSE_ERR_NOMEM;
+            }
     ACSE_TRY(oz_op_alloc(pl->A[0], 2 * P, P, pl->S));
     ACSE_TRY(oz_op_alloc(pl->A[1], R2, R2, pl->S));
     ACSE_TRY(oz_op_alloc(pl->A[2], R2, R2, pl->S));
@@ -803,6 +811,11 @@ static void oz_plan_free(OzPlan* pl) {
 }
 
 void oz_plan_destroy(acse_ctx* c) {
+    for (int k = 0; k < 8; ++k)
+        if (c->w.bx64[k]) {
+            cudaFree(c->w.bx64[k]);
+            c->w.bx64[k] = nullptr;
+        }
     OzPlan* pl = (OzPlan*)c->oz_plan;
     if (!pl) return;
     if (pl->err && c->w.tc_err == pl->err) c->w.tc_err = nullptr;
