@@ -107,6 +107,17 @@ def gemm_traffic(prec):
 
 
 OZ_SLICES = 8   # default slices of ACSE_OZAKI
+# moduli of the modular Ozaki GEMM, largest first; a context uses the least T whose product covers
+# 4 Kmax 2^(2 min(6S, 53)), Kmax = 2 r^2 its longest contraction
+OZ_MODULI = (127, 125, 123, 121, 119, 113, 109, 107, 103, 101, 97, 89, 83, 79, 73, 71, 67, 61, 59)
+
+
+def oz_moduli_count(S, Kmax):
+    need, P, T = Kmax << (2 * min(6 * S, 53) + 2), 1, 0
+    while T < len(OZ_MODULI) and P < need:
+        P *= OZ_MODULI[T]
+        T += 1
+    return T
 
 
 def flops_per_pass(r, packed=False, singlet=False):
@@ -548,7 +559,7 @@ def main():
     fl = fl_alg if prec == "fp64" else flops_per_pass(p.r, packed=True, singlet=singlet)
     split = 3 if prec in ("bf16x3", "tf32x3") else 1
     if prec == "ozaki":
-        split = OZ_SLICES * (OZ_SLICES + 1) // 2      # bf16 slice products per FP64 GEMM
+        split = oz_moduli_count(OZ_SLICES, 2 * p.r * p.r)   # bf16 residue products per FP64 GEMM
     # dominant kernel: the grouped O(r^6) GEMM launch (one per contraction pass)
     gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1e3
     peaks = {}
@@ -571,8 +582,10 @@ def main():
                  "kernel": "grouped O(r^6) GEMM",
                  "flops_per_launch": split * fl,
                  "flops_note": {"fp64": "2MNK, 32 r^6 per pass",
-                                "ozaki": f"bf16 slice products of the Ozaki scheme: {split} per FP64 GEMM "
-                                         f"({OZ_SLICES} slices), 2MNK each, same-spin pair GEMMs on pairs i<j"}.get(
+                                "ozaki": f"bf16 residue products of the modular Ozaki scheme: {split} per FP64 "
+                                         f"GEMM ({OZ_SLICES} slices: {min(6 * OZ_SLICES, 53)}-bit integer rows, "
+                                         f"{split} moduli), 2MNK each, same-spin pair GEMMs on pairs i<j; the "
+                                         f"timed launch includes the reconstruction kernel"}.get(
                      prec, "2MNK of the GEMMs the launch executes (same-spin pair GEMMs on pairs i<j)"),
                  "launch_ms": 1e3 * gemm_avg_s,
                  "launch_timing": "CUDA events around each GEMM launch on the context's stream, over a second run "
@@ -586,7 +599,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
             "evals_per_step": EVALS_PER_STEP, "acse_steps_per_s": value / EVALS_PER_STEP,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "ozaki": "f64 (Ozaki: bf16 slices, exact f32 groups, f64 sums)"}.get(
+            "dtype": {"fp64": "f64", "ozaki": "f64 (Ozaki: bf16 residues, exact f32 chunk sums, CRT to f64)"}.get(
                 prec, f"{prec} (f32 accumulate)"),
             "data": "synthetic",
             "config": {"workload": p.name, "r": p.r, "N": p.N, "prec": prec, "recon": args.recon, "eps": args.eps,

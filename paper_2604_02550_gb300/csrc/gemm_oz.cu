@@ -1,29 +1,31 @@
-// FP64-accurate GEMMs of the contraction pass on the BF16 tensor cores by the Ozaki scheme
-// (error-free splitting: K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, Numer. Algorithms 59 (2012)).
+// FP64-accurate GEMMs of the contraction pass on the BF16 tensor cores by the modular form of the Ozaki
+// scheme (K. Ozaki, Y. Uchino, T. Imamura, "Ozaki Scheme II: a GEMM-oriented emulation of floating-point
+// matrix multiplication using an integer modular technique", 2025).
 //
-// C = alpha A B^T with A (M x K) and B (N x K) FP64, both K-major.  Each operand row is scaled by a
-// power of two 2^e chosen so that |a| 2^-e < 1/2 over the row, and cut into S signed digits of base
-// 2^6:  x_1 = a 2^-e,  d_s = rint(2^6 x_s),  x_{s+1} = 2^6 x_s - d_s,  so that
-//     a = 2^e (sum_{s=1..S} d_s 2^-6s + x_{S+1} 2^-6S),   |d_s| <= 32,  |x_{S+1}| <= 1/2,
-// every step exact in FP64 and every digit exact in bf16.  Then
-//     A B^T = 2^(ea + eb) sum_{s,t} 2^-6(s+t) D_s E_t^T,
-// of which the levels L = s + t <= S + 1 are kept (the rest is below 2^-6(S+1) relative).  A product
-// of digit matrices is an integer matrix with entries of at most K 32^2; g products of one level
-// summed in one FP32 accumulator stay exact while g K 2^10 < 2^24, so each level is run as
-// ceil((L-1)/g) such groups, and the groups are added in FP64.
-//
-// Operand layout: slice s of an A row at K segment s-1, slice t of a B row at K segment S-t
-// (reversed), each segment Kp = K rounded up to 64 elements (zero padded).  The products (s, L-s),
-// s0 <= s <= s1, of level L are then one contiguous K range of A, [(s0-1) Kp, s1 Kp), against one
-// of B, [(S-L+s0) Kp, (S-L+s1+1) Kp): a single UMMA accumulation of (s1-s0+1) Kp.
+// C = alpha A B^T with A (M x K) and B (N x K) FP64, both K-major.  Every operand row is scaled by a power
+// of two and rounded to an integer row: with |a| 2^-e < 1/2 over the row, X = round(a 2^(nb - e)), so that
+// |X| <= 2^(nb-1) and a = 2^(e - nb) X up to half a unit of the last kept bit (nb - 1 = min(6S, 53) bits
+// below the row's leading bit for oz_slices = S).  The integer product X_A X_B^T then has entries of at
+// most K 2^(2 nb - 2) in magnitude.  It is computed modulo T pairwise coprime moduli p_t <= 127 (the
+// first T of a fixed list, T the least with 4 K 2^(2 nb - 2) <= P = prod p_t):
+//   * the slicing kernel writes near-balanced residues X mod p_t (|.| <= 64, exact in bf16), the B rows
+//     premultiplied by y_t = (P / p_t)^-1 mod p_t, each modulus to its K segment of the row;
+//   * the tensor cores multiply the residue matrices of each modulus in FP32; a chunk of at most 64 * 64
+//     K elements keeps every partial sum an integer of magnitude at most 64 * 64 * 64^2 = 2^24, so the
+//     accumulation is exact, and the epilogue stores a residue w (|w| <= 65) of the chunk sum (one byte);
+//   * the reconstruction kernel forms s = sum_t w_t (P / p_t) exactly in base-2^28 limbs, which is
+//     congruent to X_A X_B^T modulo every p_t and hence modulo P (Chinese remainder theorem), takes
+//     q = round(s / P) (the product lies within P / 4 of zero, so a float estimate of s / P decides q),
+//     and x = s - q P is the exact integer product, rounded once to FP64 and scaled by alpha 2^(ea + eb - 2 nb).
+// The result is the FP64 product up to the rounding of the operands to nb - 1 bits below each row's
+// leading bit and one final rounding: no product level is dropped.  Against the six-bit slice form of
+// the scheme (36 slice products at S = 8) this takes 17 residue products at S = 8 and r = 48.
 //
 // Kernels: the persistent tcgen05 GEMM of gemm_tc.cu with the accumulation unit changed from a tile
-// to a (tile, group): the MMA thread runs the groups of a tile one after another into the two TMEM
-// buffers, and the epilogue warps store each group's exact integer sum (int32) to a staging array.
-// A second, HBM-bound kernel adds the groups of every element exactly in int64 and writes the FP64
-// result with one rounding.  (Adding the groups into the FP64 output from the epilogue instead, a
-// read-modify-write of the tile per group, measured eight times slower.)  Every wait is bounded as
-// in gemm_tc.cu.
+// to a (tile, modulus, K chunk) group: the MMA thread runs the groups of a tile one after another into the
+// two TMEM buffers, and the epilogue warps store each group's residue (int8) to a staging array.  A
+// second kernel rebuilds every element from its residues and writes the FP64 result once.  Every wait
+// is bounded as in gemm_tc.cu.
 #include <cuda.h>
 #include <math.h>
 #include <string.h>
@@ -32,7 +34,9 @@
 #include "oz_arith.cuh"
 #include "tc_ptx.cuh"
 
-#define OZ_BETA 6            // bits per digit (base 2^6, |digit| <= 32)
+#define OZ_NMOD 19           // moduli of the fixed list
+#define OZ_CHUNK_KB 64       // 64-element K blocks of one exactly accumulated chunk: 64 * 64 * 64^2 = 2^24
+#define OZ_MAXCH 2           // chunks of one residue product (K <= 2 * 64 * 64 = 8192)
 #define OZ_MAXP 12           // GEMMs of one launch
 #define OZ_MAXJ 16           // operands of one slicing launch
 #define OZ_THREADS 192
@@ -41,20 +45,39 @@
 #define OZ2_STAGES 6         // ring depth of the CTA-pair form (32 KB a stage per CTA)
 #define OZ_DRAIN_NS 2000000000ull
 #define OZ_WAIT_NS 4000000000ull
-#define OZ_SLICE_PPT 8       // element pairs per thread of a sliced row: K <= 2 * 512 * 8 = 2 * 64^2 with
-                             // 512 threads; rows with K <= 2048 / 4096 take 128 / 256 threads
+#define OZ_LB 10             // bits of a limb of the reconstruction
+#define OZ_NL 14             // limbs of the reconstruction (140 bits)
+#ifndef OZ_CRT_MINB
+#define OZ_CRT_MINB 3        // resident blocks of 256 threads per SM the reconstruction is compiled for
+#endif
+
+// Pairwise coprime moduli, largest first: 127, 5^3, 3 * 41, 11^2, 7 * 17 and the primes 113 .. 59.
+static const int oz_moduli[OZ_NMOD] = {127, 125, 123, 121, 119, 113, 109, 107, 103, 101, 97, 89, 83, 79, 73, 71, 67, 61, 59};
+
+// The constants of a set of T moduli (host-computed, exact).
+struct OzMods {
+    int T;
+    float p[OZ_NMOD];         // p_t
+    float pinv[OZ_NMOD];      // 1 / p_t, rounded
+    float cA[OZ_NMOD][4];     // 2^(14 l) mod p_t, l = 0..3 (limb weights of an A row)
+    float cB[OZ_NMOD][4];     // 2^(14 l) y_t mod p_t, y_t = (P / p_t)^-1 mod p_t (limb weights of a B row)
+    float q[OZ_NMOD][OZ_NL];  // P / p_t in base-2^10 limbs, least significant first (exact floats)
+    float P[OZ_NL];           // P in base-2^10 limbs
+    float pinvs;              // 2^120 / P, rounded (between 2^-5 and 2^114)
+};
 
 struct OzProb {
     double* C;
-    int* stage;         // [ngroups][M][N]: the exact integer sum of each group
+    unsigned char* stage;   // [ngroups][M][N]: the residue w + 128 of each (modulus, chunk) group
     const double* sa;   // 2^ea per row of A
     const double* sb;   // 2^eb per row of B
     double alpha;
     int ealpha;         // alpha = 2^ealpha
     int M, N, ldc;
-    int kbs;            // 64-element K blocks per slice segment
-    int g;              // slice products per exactly accumulated group
-    int ngroups;
+    int kbs;            // 64-element K blocks per modulus segment
+    int nch, cb;        // K chunks per modulus and 64-element blocks per chunk (the last may be shorter)
+    int nb;             // operand rows rounded to X = round(a 2^(nb - e))
+    int ngroups;        // T nch, modulus-major
     int tiles_n, tile_start;
     int accum;          // 1: C += result (one FP64 addition), 0: C = result
 };
@@ -63,36 +86,15 @@ struct __align__(128) OzBatch {
     CUtensorMap tmA[OZ_MAXP];
     CUtensorMap tmB[OZ_MAXP];
     OzProb p[OZ_MAXP];
+    OzMods mods;
     int nprob;
     int total_tiles;
-    int S;
     int* err;
     unsigned long long wait_ns;
     int inject_stall;
     const int* order;     // tiles of CTA c: order[cta_start[c] .. cta_start[c+1]) (longest first)
     const int* cta_start;
 };
-
-__host__ __device__ inline int oz_ngroups(int S, int g) {
-    int n = 0;
-    for (int L = 2; L <= S + 1; ++L) n += (L - 2) / g + 1;   // ceil((L - 1) / g)
-    return n;
-}
-
-// group index -> level L and the A slices [s0, s1] of its products (s, L - s)
-__device__ __forceinline__ void oz_group(int S, int g, int idx, int& L, int& s0, int& s1) {
-    for (L = 2; L <= S + 1; ++L) {
-        const int n = (L - 2) / g + 1;
-        if (idx < n) {
-            s0 = 1 + idx * g;
-            s1 = min(L - 1, s0 + g - 1);
-            return;
-        }
-        idx -= n;
-    }
-    L = S + 1;
-    s0 = s1 = 1;
-}
 
 __device__ __forceinline__ int oz_find_problem(const OzBatch& b, int t) {
     int lo = 0, hi = b.nprob - 1;
@@ -104,6 +106,16 @@ __device__ __forceinline__ int oz_find_problem(const OzBatch& b, int t) {
     return lo;
 }
 
+// Near-balanced residue of an integer-valued float |v| <= 2^24 modulo p <= 127: q = round(v pinv) (the
+// fused multiply-add rounds v pinv + 1.5 * 2^23 once, to an integer), r = v - q p exactly.  pinv = 1/p
+// rounded moves v / p by at most |v / p| 2^-24 <= 0.017 of a unit, so |r| <= p (1/2 + 0.017): at most 64
+// for |v| < 2^23 and at most 65 for |v| <= 2^24.  No correction into the balanced range is needed: the
+// residue products and the reconstruction are bounded with these limits.
+__device__ __forceinline__ float oz_bal_mod(float v, float p, float pinv) {
+    const float q = fmaf(v, pinv, 12582912.0f) - 12582912.0f;
+    return fmaf(-q, p, v);
+}
+
 // ------------------------------------------------------------------------------ slicing
 struct OzSliceJob {
     const double* src;
@@ -111,84 +123,94 @@ struct OzSliceJob {
     const int* rowmap;      // source row of each output row (null: the same row)
     const int* colmap;      // source column of each K index (null: the same column)
     __nv_bfloat16* dst;     // first output row of the job
-    size_t ldd;             // S * Kp
+    size_t ldd;             // T * Kp
     double* scale;          // 2^e per output row (NaN for a row with a non-finite entry)
-    int rows, K, Kp, reverse, row0;
+    int rows, K, Kp, nb, mul_y, row0;
 };
 
 struct OzSliceBatch {
     OzSliceJob j[OZ_MAXJ];
     int njobs;
-    int S;
+    int T;
+    float p[OZ_NMOD], pinv[OZ_NMOD];
+    float cA[OZ_NMOD][4], cB[OZ_NMOD][4];
 };
 
-// One block per operand row.  The row's bit patterns are held in registers, its largest magnitude
-// fixes e (|a| 2^-e < 1/2), and every element's fixed-point value X is cut into S balanced base-64
-// digits from the least significant one up (d = ((X + 32) mod 64) - 32, X <- (X - d) / 64, exact;
-// the last quotient is the leading digit, of magnitude at most 32).  Digits go out as bf16 pairs,
-// each slice to its K segment of the row.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_oz_slice(const __grid_constant__ OzSliceBatch b) {
-    __shared__ unsigned long long red[THREADS / 32];
-    __shared__ unsigned short tab[65];   // bf16 bits of the digits -32..32
-    if (threadIdx.x < 65) tab[threadIdx.x] = __bfloat16_as_ushort(__float2bfloat16_rn((float)((int)threadIdx.x - 32)));
+// Row scales: one warp per operand row takes the largest magnitude over the row (through the maps), which
+// fixes e (|a| 2^-e < 1/2); scale = 2^e, NaN for a row with a non-finite entry.
+__global__ void __launch_bounds__(256) k_oz_rowscale(const __grid_constant__ OzSliceBatch b, int rows) {
+    const int grow = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (grow >= rows) return;
     int ji = 0;
-    while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= (int)blockIdx.x) ++ji;
+    while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= grow) ++ji;
     const OzSliceJob& J = b.j[ji];
-    const int row = (int)blockIdx.x - J.row0;
+    const int row = grow - J.row0;
     const int srow = J.rowmap ? J.rowmap[row] : row;
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(J.src + (size_t)srow * J.lds);
-    const int K = J.K;
     const int* cm = J.colmap;
-    unsigned long long v[2 * OZ_SLICE_PPT];
     unsigned long long mx = 0;
-#pragma unroll
-    for (int u = 0; u < OZ_SLICE_PPT; ++u) {
-        const int k = 2 * ((int)threadIdx.x + u * THREADS);
-        v[2 * u] = k < K ? src[cm ? cm[k] : k] : 0ull;
-        v[2 * u + 1] = k + 1 < K ? src[cm ? cm[k + 1] : k + 1] : 0ull;
-        mx = max(mx, max(v[2 * u] & 0x7FFFFFFFFFFFFFFFull, v[2 * u + 1] & 0x7FFFFFFFFFFFFFFFull));
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = lane; k < J.K; k += 32) mx = max(mx, src[cm ? cm[k] : k] & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[w] = mx;
-    __syncthreads();
-    mx = red[0];
-#pragma unroll
-    for (int i = 1; i < THREADS / 32; ++i) mx = max(mx, red[i]);
-    // non-negative doubles order like their bit patterns; an all-ones exponent is Inf or NaN
-    const bool bad = mx >= 0x7FF0000000000000ull;
-    int e = 0;
-    if (!bad && mx != 0) e = min(1000, max(-1000, (int)(mx >> 52) - 1023 + 2));
-    if (threadIdx.x == 0) J.scale[row] = bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_pow2(e);
-    __nv_bfloat16* drow = J.dst + (size_t)row * J.ldd;
-    const int S = b.S;
-#pragma unroll
-    for (int u = 0; u < OZ_SLICE_PPT; ++u) {
-        const int k = 2 * ((int)threadIdx.x + u * THREADS);
-        if (k >= K) continue;
-        long long X0 = bad ? 0 : oz_fixed(v[2 * u], S, e);
-        long long X1 = bad ? 0 : oz_fixed(v[2 * u + 1], S, e);
-        for (int t = 0; t < S; ++t) {   // slice s = S - t
-            int d0, d1;
-            if (t < S - 1) {
-                d0 = (int)(((X0 + 32) & 63) - 32);
-                d1 = (int)(((X1 + 32) & 63) - 32);
-                X0 = (X0 - d0) >> 6;
-                X1 = (X1 - d1) >> 6;
-            } else {
-                d0 = (int)X0;
-                d1 = (int)X1;
-            }
-            const int sl = S - t;
-            const int seg = J.reverse ? S - sl : sl - 1;
-            __nv_bfloat16* dst = drow + (size_t)seg * J.Kp + k;
-            if (k + 1 < K)
-                *reinterpret_cast<unsigned int*>(dst) = (unsigned int)tab[d0 + 32] | ((unsigned int)tab[d1 + 32] << 16);
-            else
-                *reinterpret_cast<unsigned short*>(dst) = tab[d0 + 32];
-        }
+    if (lane == 0) {
+        // non-negative doubles order like their bit patterns; an all-ones exponent is Inf or NaN
+        const bool bad = mx >= 0x7FF0000000000000ull;
+        const int e = (bad || mx == 0) ? 0 : min(1000, max(-1000, (int)(mx >> 52) - 1023 + 2));
+        J.scale[row] = bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_pow2(e);
+    }
+}
+
+// Residues: block (x, y) covers element pairs 256 x .. 256 x + 255 of operand row y (rows of all jobs in
+// order), two consecutive elements a thread.  The integer X = round(a 2^(nb - e)) (|X| <= 2^53) is cut into
+// four base-2^14 limbs of |X|, each made an exact float through the bits of 2^23 + limb (no 64-bit
+// conversion: those run on the slow FP64 unit) and given the sign of X; modulus by modulus, the residue
+// is sum_l limb_l c_l (c_l = 2^(14 l) mod p_t, times y_t for a B operand; an integer below 2^23 in
+// magnitude, exact in FP32) reduced by oz_bal_mod (|residue| <= 64, exact in bf16: the upper half of its
+// float).  Residues go out as bf16 pairs, modulus t to K segment t of the row.
+__device__ __forceinline__ void oz_limbs(unsigned long long bits, int nb, int e, bool bad, float* L) {
+    const long long X = bad ? 0 : oz_fixedb(bits, nb, e);
+    const unsigned long long uX = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
+    const float sg = X < 0 ? -1.0f : 1.0f;
+    const unsigned int lo = (unsigned int)uX, hi = (unsigned int)(uX >> 32);
+    const unsigned int l0 = lo & 0x3FFF, l1 = (lo >> 14) & 0x3FFF, l2 = (lo >> 28) | ((hi & 0x3FF) << 4), l3 = hi >> 10;
+    L[0] = sg * (__uint_as_float(0x4B000000u | l0) - 8388608.0f);
+    L[1] = sg * (__uint_as_float(0x4B000000u | l1) - 8388608.0f);
+    L[2] = sg * (__uint_as_float(0x4B000000u | l2) - 8388608.0f);
+    L[3] = sg * (__uint_as_float(0x4B000000u | l3) - 8388608.0f);
+}
+
+__global__ void __launch_bounds__(256) k_oz_residue(const __grid_constant__ OzSliceBatch b) {
+    const int grow = (int)blockIdx.y;
+    int ji = 0;
+    while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= grow) ++ji;
+    const OzSliceJob& J = b.j[ji];
+    const int hk = (J.K + 1) >> 1;
+    const int pi = (int)blockIdx.x * 256 + (int)threadIdx.x;
+    if (pi >= hk) return;
+    const int row = grow - J.row0, k = 2 * pi;
+    const int srow = J.rowmap ? J.rowmap[row] : row;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(J.src + (size_t)srow * J.lds);
+    const int* cm = J.colmap;
+    const unsigned long long v0 = src[cm ? cm[k] : k];
+    const unsigned long long v1 = k + 1 < J.K ? src[cm ? cm[k + 1] : k + 1] : 0ull;
+    const int es = (int)((__double_as_longlong(J.scale[row]) >> 52) & 0x7FF);   // 2^e, or NaN
+    const bool bad = es == 0x7FF;
+    float L0[4], L1[4];
+    oz_limbs(v0, J.nb, es - 1023, bad, L0);
+    oz_limbs(v1, J.nb, es - 1023, bad, L1);
+    __nv_bfloat16* dst = J.dst + (size_t)row * J.ldd + k;
+    const bool pair = k + 1 < J.K;
+    const float(*c)[4] = J.mul_y ? b.cB : b.cA;
+    const int T = b.T;
+#pragma unroll 4
+    for (int t = 0; t < T; ++t, dst += J.Kp) {
+        const float p = b.p[t], pinv = b.pinv[t];
+        const float c0 = c[t][0], c1 = c[t][1], c2 = c[t][2], c3 = c[t][3];
+        const float r0 = oz_bal_mod(fmaf(L0[3], c3, fmaf(L0[2], c2, fmaf(L0[1], c1, L0[0] * c0))), p, pinv);
+        const float r1 = oz_bal_mod(fmaf(L1[3], c3, fmaf(L1[2], c2, fmaf(L1[1], c1, L1[0] * c0))), p, pinv);
+        // |r| <= 64: the bf16 of r is the upper half of its float (exact)
+        if (pair) *reinterpret_cast<unsigned int*>(dst) = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
+        else *reinterpret_cast<unsigned short*>(dst) = (unsigned short)(__float_as_uint(r0) >> 16);
     }
 }
 
@@ -218,7 +240,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = b.S;
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
     const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // CTA, or CTA pair
     const int q0 = b.cta_start[unit], q1 = b.cta_start[unit + 1];        // this unit's tiles
@@ -259,9 +280,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                 const int m0 = (local / P.tiles_n) * BM + (int)rank * TC_BM;
                 const int n0 = (local % P.tiles_n) * BN + (int)rank * (BN / 2);
                 for (int gi = 0; gi < P.ngroups && !stop; ++gi) {
-                    int L, s0, s1;
-                    oz_group(S, P.g, gi, L, s0, s1);
-                    const int ka = (s0 - 1) * P.kbs, kb0 = (S - L + s0) * P.kbs, n = (s1 - s0 + 1) * P.kbs;
+                    // group gi = (modulus t, chunk c): the same K range of A and B
+                    const int tm = gi / P.nch, c = gi - tm * P.nch;
+                    const int ka = tm * P.kbs + c * P.cb, n = min(P.cb, P.kbs - c * P.cb);
                     for (int kb = 0; kb < n; ++kb, ++it) {
                         const int s = it % STAGES;
                         if (it >= STAGES && !bounded_wait(&empty[s], ((it / STAGES) & 1) ^ 1, b.wait_ns, abort_flag)) {
@@ -272,11 +293,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                         if constexpr (PAIR) {
                             if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
                             tma_load_2d_pair(sA + s * A_BYTES, &b.tmA[pi], (ka + kb) * KELEM, m0, full0 + 8u * s);
-                            tma_load_2d_pair(sB + s * B_BYTES, &b.tmB[pi], (kb0 + kb) * KELEM, n0, full0 + 8u * s);
+                            tma_load_2d_pair(sB + s * B_BYTES, &b.tmB[pi], (ka + kb) * KELEM, n0, full0 + 8u * s);
                         } else {
                             mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
                             tma_load_2d(sA + s * A_BYTES, &b.tmA[pi], (ka + kb) * KELEM, m0, &full[s]);
-                            tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], (kb0 + kb) * KELEM, n0, &full[s]);
+                            tma_load_2d(sB + s * B_BYTES, &b.tmB[pi], (ka + kb) * KELEM, n0, &full[s]);
                         }
                     }
                 }
@@ -302,9 +323,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
             for (int qi = q0; qi < q1 && !*abort_flag; ++qi) {
                 const OzProb& P = b.p[oz_find_problem(b, b.order[qi])];
                 for (int gi = 0; gi < P.ngroups && !*abort_flag; ++gi, ++lt) {
-                    int L, s0, s1;
-                    oz_group(S, P.g, gi, L, s0, s1);
-                    const int n = (s1 - s0 + 1) * P.kbs;
+                    const int c = gi % P.nch;
+                    const int n = min(P.cb, P.kbs - c * P.cb);
                     const int ab = lt & 1, use = lt >> 1;
                     if (use >= 1) {
                         const bool ok = PAIR ? bounded_wait_cluster(&acce[ab], (use - 1) & 1, b.wait_ns + OZ_DRAIN_NS, abort_flag)
@@ -356,7 +376,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
             const int m0 = (local / P.tiles_n) * BM + (int)rank * TC_BM, n0 = (local % P.tiles_n) * BN;
             const int row = m0 + q * 32 + lane;
             const bool rok = row < P.M;
-            const bool vec = (P.N & 3) == 0 && (reinterpret_cast<uintptr_t>(P.stage) & 15) == 0;
+            // 16- or 8-byte stores of a row's 32 residues when the row starts on such a boundary
+            const int vec = (reinterpret_cast<uintptr_t>(P.stage) & 15) ? 0 : (P.N & 15) == 0 ? 16 : (P.N & 7) == 0 ? 8 : 0;
             for (int gi = 0; gi < P.ngroups; ++gi, ++lt) {
                 const int ab = lt & 1, use = lt >> 1;
                 int go = 0;
@@ -371,8 +392,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                     break;
                 }
                 tc_fence_after();
-                // the group's sum is an integer below 2^24 in magnitude: exact in FP32 and in int32
-                int* srow = P.stage + (size_t)gi * P.M * P.N + (size_t)(rok ? row : 0) * P.N;
+                const int tm = gi / P.nch;
+                const float pm = b.mods.p[tm], pinv = b.mods.pinv[tm];
+                // the chunk sum is an integer of magnitude at most 2^24 (exact in FP32); its residue w modulo
+                // p_t (|w| <= 65) goes out as the byte w + 128 (the low byte of the float w + 128 + 1.5 * 2^23)
+                unsigned char* srow = P.stage + (size_t)gi * P.M * P.N + (size_t)(rok ? row : 0) * P.N;
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t v[32];
@@ -380,17 +404,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);   // warp-collective
                     const int col0 = n0 + c * 32;
                     if (!rok || col0 >= P.N) continue;
-                    if (vec && col0 + 32 <= P.N) {
+                    uint32_t wd[8];
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<int4*>(srow + col0 + j) =
-                                make_int4(__float2int_rn(__uint_as_float(v[j])), __float2int_rn(__uint_as_float(v[j + 1])),
-                                          __float2int_rn(__uint_as_float(v[j + 2])), __float2int_rn(__uint_as_float(v[j + 3])));
+                    for (int j = 0; j < 32; j += 4) {
+                        uint32_t x[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            x[i] = __float_as_uint(oz_bal_mod(__uint_as_float(v[j + i]), pm, pinv) + 12583040.0f);
+                        wd[j / 4] = __byte_perm(__byte_perm(x[0], x[1], 0x0040), __byte_perm(x[2], x[3], 0x0040), 0x5410);
+                    }
+                    if (col0 + 32 <= P.N && vec == 16) {
+                        *reinterpret_cast<uint4*>(srow + col0) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                        *reinterpret_cast<uint4*>(srow + col0 + 16) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+                    } else if (col0 + 32 <= P.N && vec == 8) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint2*>(srow + col0 + 8 * j) = make_uint2(wd[2 * j], wd[2 * j + 1]);
                     } else {
                         const int nc = min(32, P.N - col0);
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (j < nc) srow[col0 + j] = __float2int_rn(__uint_as_float(v[j]));
+                            if (j < nc) srow[col0 + j] = (unsigned char)((wd[j / 4] >> (8 * (j & 3))) & 0xFF);
                     }
                 }
                 tc_fence_before();
@@ -413,73 +446,131 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
     }
 }
 
-// C = alpha 2^(ea_i + eb_j) sum_g 2^-6L_g v_g for every element, from the staged group sums v_g.
-// With w_L = 36 - 6 (L - 2) the terms v_g 2^w_L (an arithmetic right shift where w_L < 0, which drops
-// only bits below 2^-48 of the level-2 unit) are added in int64 (|sum| < 2^61), and the conversion of
-// the sum, scaled by the power of two alpha 2^(ea + eb - 48), to FP64 is the single rounding.
-// HBM-bound: the groups of an element are read once, coalesced, and C is written once.
-__device__ __forceinline__ long long oz_term(int v, int w) {
-    return w >= 0 ? (long long)v * (1ll << w) : ((long long)v >> -w);   // arithmetic shift: floor
+// --------------------------------------------------------------------------- reconstruction
+// s = sum_t w_t (P / p_t) is accumulated in OZ_NL float limb sums of weight 2^(10 l): each is a sum of
+// w_t times a limb of P / p_t below 2^10, so with |w_t| <= 130 (two chunks) and T <= 19 it stays an
+// integer below 2^21.3 in magnitude (exact, and within the 2^22 of the float-to-int step below).
+
+// x = s - round(s / P) P from the limb sums, rounded once to FP64 and scaled by 2^ex.  The product lies
+// within P / 4 of zero, so q needs s / P to within 1/4: the estimate is summed from the limb sums as they
+// are (each a sum of w_t times non-negative limbs of P / p_t, so the float rounding errors stay near
+// 2^-20 sum_t |w_t| / p_t of s / P).  x's limbs (integers below 2^22) become int32 through the float
+// 1.5 * 2^23 + x, carries normalise them to [0, 2^10) under a top limb of 0 or -1, and a negative x is
+// negated as a 128-bit two's complement (|x| < 2^123).
+__device__ __forceinline__ double oz_crt_value(const float* a, const float* Pl, float pinvs, int ex) {
+    float sf = 0.0f;
+#pragma unroll
+    for (int l = 0; l < OZ_NL; ++l) sf = fmaf(a[l], __int_as_float((127 + OZ_LB * l - 120) << 23), sf);   // s 2^-120
+    const float q = fmaf(sf, pinvs, 12582912.0f) - 12582912.0f;
+    int x[OZ_NL];
+#pragma unroll
+    for (int l = 0; l < OZ_NL; ++l) x[l] = __float_as_int(fmaf(-q, Pl[l], a[l]) + 12582912.0f) - 0x4B400000;
+    int c = x[0];
+#pragma unroll
+    for (int l = 0; l < OZ_NL - 1; ++l) {
+        const int cl = c;
+        x[l] = cl & ((1 << OZ_LB) - 1);
+        c = (cl >> OZ_LB) + x[l + 1];   // arithmetic shift: floor
+    }
+    const bool neg = c < 0;   // the top limb: 0, or -1 for x < 0 (2^130 + x in the limbs below)
+    x[OZ_NL - 1] = c;
+    typedef unsigned long long u64;
+    const u64 lo = (u64)x[0] | ((u64)x[1] << 10) | ((u64)x[2] << 20) | ((u64)x[3] << 30) | ((u64)x[4] << 40) |
+                   ((u64)x[5] << 50) | ((u64)x[6] << 60);
+    u64 hi = ((u64)x[6] >> 4) | ((u64)x[7] << 6) | ((u64)x[8] << 16) | ((u64)x[9] << 26) | ((u64)x[10] << 36) |
+             ((u64)x[11] << 46) | ((u64)x[12] << 56);
+    if (neg) {   // |x| = 2^130 - (limbs) = -(limbs) modulo 2^128, since |x| < 2^128
+        const u64 nlo = 0ull - lo;
+        hi = ~hi + (lo == 0 ? 1ull : 0ull);
+        return oz_u128_scaled(hi, nlo, true, ex);
+    }
+    return oz_u128_scaled(hi, lo, false, ex);
 }
 
-__global__ void __launch_bounds__(256) k_oz_reduce(const OzBatch* __restrict__ bp) {
-    __shared__ signed char wtab[64];   // the weight 36 - 6 (L - 2) of every group, in the staging order
-    const OzBatch& b = *bp;
-    const OzProb& P = b.p[blockIdx.y];
-    const int N = P.N, g = P.g, S = b.S, ng = P.ngroups;
-    if (threadIdx.x == 0) {
-        int gi = 0;
-        for (int L = 2; L <= S + 1; ++L)
-            for (int q = 0; q < (L - 2) / g + 1 && gi < 64; ++q) wtab[gi++] = (signed char)(36 - OZ_BETA * (L - 2));
-    }
-    __syncthreads();
+// The constants of the reconstruction, passed as a kernel parameter: with the modulus and limb loops
+// unrolled, every limb of P / p_t is an immediate constant-bank operand of its FMA (no load).
+struct OzCrtParams {
+    float q[OZ_NMOD][OZ_NL];
+    float P[OZ_NL];
+    float pinvs;
+    int T;
+};
+
+// Two consecutive elements of one row per thread (16-bit loads of their residue bytes when N is even):
+// every residue word of the element pair (all moduli and chunks) is loaded before any is used, so that
+// about 2 KB per warp is in flight.  A byte b = w + 128 becomes the float 2^23 + b by a byte permute
+// (exact), so w = that - (2^23 + 128).
+template <int NCH, int VW>
+__device__ __forceinline__ void oz_crt_rows(const OzProb& P, const OzCrtParams& cp) {
+    const int T = cp.T, N = P.N;
     const size_t MN = (size_t)P.M * N;
-    const int* __restrict__ st = P.stage;
-    // four consecutive elements of one row per thread (int4 loads) when N % 4 == 0, else one; the group
-    // sums are loaded eight at a time before they are added
-    const int vw = (N & 3) == 0 ? 4 : 1;
-    const size_t nunit = MN / vw;
+    const size_t nunit = MN / VW;
     for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < nunit; u += (size_t)gridDim.x * blockDim.x) {
-        const size_t e = u * vw;
-        long long acc[4] = {0, 0, 0, 0};
-        for (int g0 = 0; g0 < ng; g0 += 8) {
-            if (vw == 4) {
-                int4 vv[8];
+        const size_t e = u * VW;
+        const unsigned char* __restrict__ sp = P.stage + e;
+        unsigned int xw[OZ_NMOD][NCH];
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (g0 + q < ng) vv[q] = *reinterpret_cast<const int4*>(st + e + (size_t)(g0 + q) * MN);
+        for (int t = 0; t < OZ_NMOD; ++t)
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (g0 + q < ng) {
-                        const int w = wtab[g0 + q];
-                        acc[0] += oz_term(vv[q].x, w);
-                        acc[1] += oz_term(vv[q].y, w);
-                        acc[2] += oz_term(vv[q].z, w);
-                        acc[3] += oz_term(vv[q].w, w);
-                    }
-            } else {
-                int vv[8];
+            for (int c = 0; c < NCH; ++c) {
+                xw[t][c] = 0x8080u;   // w = 0 past the last modulus
+                if (t < T) {
+                    xw[t][c] = VW == 2 ? (unsigned int)__ldg(reinterpret_cast<const unsigned short*>(sp)) : (unsigned int)__ldg(sp);
+                    sp += MN;
+                }
+            }
+        float acc[VW][OZ_NL];
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (g0 + q < ng) vv[q] = st[e + (size_t)(g0 + q) * MN];
+        for (int k = 0; k < VW; ++k)
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (g0 + q < ng) acc[0] += oz_term(vv[q], wtab[g0 + q]);
+            for (int l = 0; l < OZ_NL; ++l) acc[k][l] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < OZ_NMOD; ++t) {
+            if (t >= T) break;
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                float w = 0.0f;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) w += __uint_as_float(__byte_perm(xw[t][c], 0x4B000000u, 0x7540u | k)) - 8388736.0f;
+#pragma unroll
+                for (int l = 0; l < OZ_NL; ++l) acc[k][l] = fmaf(w, cp.q[t][l], acc[k][l]);
             }
         }
         const int i = (int)(e / N), j0 = (int)(e - (size_t)i * N);
         const int ea = (int)((__double_as_longlong(P.sa[i]) >> 52) & 0x7FF);   // row scales are powers of two
         double* crow = P.C + (size_t)i * P.ldc;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (k < vw) {
-                const int eb = (int)((__double_as_longlong(P.sb[j0 + k]) >> 52) & 0x7FF);
-                const double v = (ea == 0x7FF || eb == 0x7FF) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                               : oz_ll_scaled(acc[k], ea + eb - 2046 + P.ealpha - 48);
-                crow[j0 + k] = P.accum ? crow[j0 + k] + v : v;
-            }
+        for (int k = 0; k < VW; ++k) {
+            const int eb = (int)((__double_as_longlong(P.sb[j0 + k]) >> 52) & 0x7FF);
+            const double v = (ea == 0x7FF || eb == 0x7FF)
+                                 ? __longlong_as_double(0x7ff8000000000000ll)
+                                 : oz_crt_value(acc[k], cp.P, cp.pinvs, ea + eb - 2046 + P.ealpha - 2 * P.nb);
+            crow[j0 + k] = P.accum ? crow[j0 + k] + v : v;
         }
     }
+}
+
+// C = alpha 2^(e_i + e_j - 2 nb) x for every element, x rebuilt from the staged residues.  The residues of
+// an element are read once, coalesced, and C is written once.
+__global__ void __launch_bounds__(256, OZ_CRT_MINB) k_oz_crt(const OzBatch* __restrict__ bp, const __grid_constant__ OzCrtParams cp) {
+    const OzProb& P = bp->p[blockIdx.y];
+    const bool v2 = (P.N & 1) == 0;
+    if (P.nch == 1) v2 ? oz_crt_rows<1, 2>(P, cp) : oz_crt_rows<1, 1>(P, cp);
+    else v2 ? oz_crt_rows<2, 2>(P, cp) : oz_crt_rows<2, 1>(P, cp);
+}
+
+// The reconstruction launch of a plan.
+static int oz_launch_crt(const OzBatch* host, const OzBatch* dev, int nsm, cudaStream_t st) {
+    OzCrtParams cp;
+    memset(&cp, 0, sizeof(cp));
+    const OzMods& m = host->mods;
+    cp.T = m.T;
+    memcpy(cp.q, m.q, sizeof(cp.q));
+    memcpy(cp.P, m.P, sizeof(cp.P));
+    cp.pinvs = m.pinvs;
+    k_oz_crt<<<dim3(2 * nsm, host->nprob), 256, 0, st>>>(dev, cp);
+    ACSE_CUDA_TRY(cudaGetLastError());
+    return ACSE_OK;
 }
 
 // Same-spin pair GEMMs on packed pairs (as on the split path): in the aa and bb sectors the rows (ij),
@@ -528,12 +619,15 @@ struct OzOp {
     __nv_bfloat16* sl;
     double* scale;
     int rows, K, Kp;
+    int nb;             // rows rounded to X = round(a 2^(nb - e)), |X| <= 2^(nb-1)
 };
 
 struct OzPlan {
     OzBatch* host;
     OzBatch* dev;
     int S, bn;
+    int bits;           // bits kept below a row's leading bit: min(6S, 53)
+    unsigned __int128 P;   // product of the plan's moduli
     int pair;           // 1: CTA-pair kernel (256 x 256 tiles on clusters of two CTAs)
     int bm;             // rows of a tile: 128, or 256 with pairs
     int nclusters;      // co-resident CTA pairs (the persistent grid of the pair kernel)
@@ -581,11 +675,56 @@ static int oz_launch_gemm(const OzPlan* pl, cudaStream_t st) {
     return ACSE_OK;
 }
 
-static int oz_op_alloc(OzOp& o, int rows, int K, int S) {
+// The moduli of a plan: the least T whose product P covers 4 Kmax 2^(2 bits) (every product of the plan
+// then lies within P / 4 of zero), at most the whole list, and the exact constants of the set.
+static int oz_mods_init(OzPlan* pl, int S, long long Kmax) {
+    const int bt = 6 * S < 53 ? 6 * S : 53;
+    if (Kmax < 1) Kmax = 1;
+    if (Kmax > (1ll << 18)) return ACSE_ERR_SHAPE;
+    pl->bits = bt;
+    const unsigned __int128 need = (unsigned __int128)Kmax << (2 * bt + 2);   // below 2^126
+    unsigned __int128 P = 1;
+    int T = 0;
+    while (T < OZ_NMOD && P < need) P *= (unsigned __int128)oz_moduli[T++];
+    pl->P = P;
+    OzMods& m = pl->host->mods;
+    memset(&m, 0, sizeof(m));
+    m.T = T;
+    const unsigned __int128 lmask = ((unsigned __int128)1 << OZ_LB) - 1;
+    for (int t = 0; t < T; ++t) {
+        const int pt = oz_moduli[t];
+        const unsigned __int128 Q = P / (unsigned __int128)pt;
+        const int qm = (int)(Q % (unsigned __int128)pt);
+        int y = 1;
+        while (y < pt && (qm * y) % pt != 1) ++y;   // pairwise coprime: the inverse exists
+        m.p[t] = (float)pt;
+        m.pinv[t] = 1.0f / (float)pt;
+        for (int l = 0; l < 4; ++l) {
+            const long long cl = (1ll << (14 * l)) % pt;
+            m.cA[t][l] = (float)cl;
+            m.cB[t][l] = (float)((cl * y) % pt);
+        }
+        for (int l = 0; l < OZ_NL; ++l) m.q[t][l] = (float)(int)((Q >> (OZ_LB * l)) & lmask);
+    }
+    for (int l = 0; l < OZ_NL; ++l) m.P[l] = (float)(int)((P >> (OZ_LB * l)) & lmask);
+    m.pinvs = (float)(ldexp(1.0, 120) / (double)P);
+    return ACSE_OK;
+}
+
+// nb of an operand of contraction length K: the largest b <= bits with 4 K 2^(2b) <= P, plus one.
+static int oz_op_nb(const OzPlan* pl, int K) {
+    int b = pl->bits;
+    while (b > 0 && ((unsigned __int128)K << (2 * b + 2)) > pl->P) --b;
+    return b + 1;
+}
+
+static int oz_op_alloc(OzPlan* pl, OzOp& o, int rows, int K) {
     o.rows = rows;
     o.K = K;
     o.Kp = (K + 63) / 64 * 64;
-    const size_t bytes = (size_t)rows * S * o.Kp * sizeof(__nv_bfloat16);
+    o.nb = oz_op_nb(pl, K);
+    if (o.nb < 2) return ACSE_ERR_SHAPE;
+    const size_t bytes = (size_t)rows * pl->host->mods.T * o.Kp * sizeof(__nv_bfloat16);
     if (cudaMalloc((void**)&o.sl, bytes) != cudaSuccess || cudaMalloc((void**)&o.scale, rows * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return ACSE_ERR_NOMEM;
@@ -596,9 +735,9 @@ static int oz_op_alloc(OzOp& o, int rows, int K, int S) {
 
 static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, double alpha) {
     OzBatch& B = *pl->host;
-    if (B.nprob >= OZ_MAXP || a.K != b.K || a.Kp != b.Kp) return ACSE_ERR_SHAPE;
+    if (B.nprob >= OZ_MAXP || a.K != b.K || a.Kp != b.Kp || a.nb != b.nb) return ACSE_ERR_SHAPE;
     const int n = B.nprob;
-    const size_t ld = (size_t)pl->S * a.Kp;
+    const size_t ld = (size_t)B.mods.T * a.Kp;
     ACSE_TRY(tc_encode_map_bf16(&B.tmA[n], a.sl, a.rows, (int)ld, TC_BM, ld));
     ACSE_TRY(tc_encode_map_bf16(&B.tmB[n], b.sl, b.rows, (int)ld, pl->pair ? pl->bn / 2 : pl->bn, ld));
     OzProb& p = B.p[n];
@@ -613,11 +752,13 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
     p.N = b.rows;
     p.ldc = ldc;
     p.kbs = a.Kp / 64;
-    // g K 2^(2 (OZ_BETA - 1)) < 2^24: the FP32 accumulation of a group is exact
-    const long long cap = ((1ll << 24) - 1) / ((long long)a.K << (2 * (OZ_BETA - 1)));
-    p.g = cap < 1 ? 1 : (int)(cap < pl->S ? cap : pl->S);
-    p.ngroups = oz_ngroups(pl->S, p.g);
-    if (cudaMalloc((void**)&p.stage, (size_t)p.ngroups * p.M * p.N * sizeof(int)) != cudaSuccess) {
+    p.nb = a.nb;
+    // chunks of at most OZ_CHUNK_KB blocks: every partial sum of residue products stays below 2^24
+    p.nch = (p.kbs + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+    if (p.nch > OZ_MAXCH) return ACSE_ERR_SHAPE;
+    p.cb = (p.kbs + p.nch - 1) / p.nch;
+    p.ngroups = B.mods.T * p.nch;
+    if (cudaMalloc((void**)&p.stage, (size_t)p.ngroups * p.M * p.N) != cudaSuccess) {
         cudaGetLastError();
         p.stage = nullptr;
         return ACSE_ERR_NOMEM;
@@ -626,13 +767,14 @@ static int oz_add(OzPlan* pl, const OzOp& a, const OzOp& b, double* C, int ldc, 
     p.tile_start = B.total_tiles;
     B.total_tiles += ((p.M + pl->bm - 1) / pl->bm) * p.tiles_n;
     B.nprob = n + 1;
-    return cap < 1 ? ACSE_ERR_SHAPE : ACSE_OK;
+    return ACSE_OK;
 }
 
 static int oz_plan_finish(OzPlan* pl);
 
-// Kernel attributes, SM count and the zeroed problem table of a plan.
-static int oz_plan_init(OzPlan* pl, int S, int bn, int pair) {
+// Kernel attributes, SM count, the moduli for the plan's longest contraction Kmax and the zeroed problem
+// table of a plan.
+static int oz_plan_init(OzPlan* pl, int S, int bn, int pair, long long Kmax) {
     pl->S = S;
     pl->bn = bn;
     pl->pair = pair && bn == OZ_BN;
@@ -675,9 +817,8 @@ static int oz_plan_init(OzPlan* pl, int S, int bn, int pair) {
     }
     pl->host = (OzBatch*)calloc(1, sizeof(OzBatch));
     if (!pl->host) return ACSE_ERR_NOMEM;
-    pl->host->S = S;
     pl->host->wait_ns = OZ_WAIT_NS;
-    return ACSE_OK;
+    return oz_mods_init(pl, S, Kmax);
 }
 
 int oz_plan_create(acse_ctx* c) {
@@ -685,7 +826,7 @@ int oz_plan_create(acse_ctx* c) {
     if (!pl) return ACSE_ERR_NOMEM;
     c->oz_plan = pl;
     const int r = c->r, R2 = r * r, R22 = 2 * R2, P = r * (r - 1) / 2;
-    ACSE_TRY(oz_plan_init(pl, c->opt.oz_slices, R2 >= 256 ? OZ_BN : 128, c->opt.gemm_tile != 1));
+    ACSE_TRY(oz_plan_init(pl, c->opt.oz_slices, R2 >= 256 ? OZ_BN : 128, c->opt.gemm_tile != 1, R22));
     // the B products on the tensor cores (acse_zoz.cu): x1 and x2^T of the four types for every pair
     if (r % 16 == 0 && r <= 64 && c->opt.oz_slices <= 8)
         for (int k = 0; k < 8; ++k)
@@ -694,19 +835,19 @@ int oz_plan_create(acse_ctx* c) {
                 c->w.bx64[k] = nullptr;
                 return ACSE_ERR_NOMEM;
             }
-    ACSE_TRY(oz_op_alloc(pl->A[0], 2 * P, P, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[1], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[2], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[3], 2 * P, P, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[4], R22, R22, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[5], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->A[6], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->B[0], P, P, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->B[1], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->B[2], P, P, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->B[3], R22, R22, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->B[4], R2, R2, pl->S));
-    ACSE_TRY(oz_op_alloc(pl->B[5], R2, R2, pl->S));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[0], 2 * P, P));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[1], R2, R2));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[2], R2, R2));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[3], 2 * P, P));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[4], R22, R22));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[5], R2, R2));
+    ACSE_TRY(oz_op_alloc(pl, pl->A[6], R2, R2));
+    ACSE_TRY(oz_op_alloc(pl, pl->B[0], P, P));
+    ACSE_TRY(oz_op_alloc(pl, pl->B[1], R2, R2));
+    ACSE_TRY(oz_op_alloc(pl, pl->B[2], P, P));
+    ACSE_TRY(oz_op_alloc(pl, pl->B[3], R22, R22));
+    ACSE_TRY(oz_op_alloc(pl, pl->B[4], R2, R2));
+    ACSE_TRY(oz_op_alloc(pl, pl->B[5], R2, R2));
     {
         int* hm = (int*)malloc((size_t)P * sizeof(int));
         if (!hm) return ACSE_ERR_NOMEM;
@@ -753,7 +894,7 @@ static int oz_plan_finish(OzPlan* pl) {
     if (pl->tiles > 0) {
         const int units = pl->pair ? pl->nclusters : pl->nsm;   // CTAs, or CTA pairs, of the persistent grid
         const int T = pl->tiles, G = T < units ? T : units;
-        const int nprod = pl->S * (pl->S + 1) / 2;
+        const int nmod = B.mods.T;
         int* hs = (int*)malloc((size_t)(T + G + 1) * sizeof(int));
         long long* cost = (long long*)malloc((size_t)T * sizeof(long long));
         if (!hs || !cost) {
@@ -763,7 +904,7 @@ static int oz_plan_finish(OzPlan* pl) {
         }
         for (int p = 0; p < B.nprob; ++p) {
             const int n = ((B.p[p].M + pl->bm - 1) / pl->bm) * B.p[p].tiles_n;
-            for (int k = 0; k < n; ++k) cost[B.p[p].tile_start + k] = (long long)nprod * B.p[p].kbs + 4 * B.p[p].ngroups;
+            for (int k = 0; k < n; ++k) cost[B.p[p].tile_start + k] = (long long)nmod * B.p[p].kbs + 4 * B.p[p].ngroups;
         }
         tc_lpt_schedule(cost, T, G, hs, hs + T);
         const bool ok = cudaMalloc((void**)&pl->sched, (size_t)(T + G + 1) * sizeof(int)) == cudaSuccess &&
@@ -823,49 +964,52 @@ void oz_plan_destroy(acse_ctx* c) {
     c->oz_plan = nullptr;
 }
 
+// The moduli constants of a slicing launch.
+static void oz_slice_batch_init(OzSliceBatch& b, const OzMods& m) {
+    memset(&b, 0, sizeof(b));
+    b.T = m.T;
+    for (int t = 0; t < m.T; ++t) {
+        b.p[t] = m.p[t];
+        b.pinv[t] = m.pinv[t];
+        for (int l = 0; l < 4; ++l) {
+            b.cA[t][l] = m.cA[t][l];
+            b.cB[t][l] = m.cB[t][l];
+        }
+    }
+}
+
 // One slicing job: `rows` rows of operand o starting at output row `orow`, read from src (row stride
-// lds) through the optional row / column maps.
+// lds) through the optional row / column maps; mul_y for a B operand (residues times y_t).
 static void oz_job(OzSliceBatch& b, int& rows, const OzOp& o, int orow, int nrows, const double* src, size_t lds,
-                   const int* rowmap, const int* colmap, int reverse) {
+                   const int* rowmap, const int* colmap, int mul_y) {
     OzSliceJob& j = b.j[b.njobs++];
     j.src = src;
     j.lds = lds;
     j.rowmap = rowmap;
     j.colmap = colmap;
-    j.ldd = (size_t)b.S * o.Kp;
+    j.ldd = (size_t)b.T * o.Kp;
     j.dst = o.sl + (size_t)orow * j.ldd;
     j.scale = o.scale + orow;
     j.rows = nrows;
     j.K = o.K;
     j.Kp = o.Kp;
-    j.reverse = reverse;
+    j.nb = o.nb;
+    j.mul_y = mul_y;
     j.row0 = rows;
     rows += nrows;
 }
 
-// Launch the slicing of every job of `all`: the jobs go to up to three launches by row length (128 threads
-// a row for K <= 2048, 256 for K <= 4096, 512 above), so that short rows keep more blocks resident.
-static int oz_slice_launch(acse_ctx* c, const OzSliceBatch& all) {
-    for (int cls = 0; cls < 3; ++cls) {
-        OzSliceBatch b;
-        memset(&b, 0, sizeof(b));
-        b.S = all.S;
-        int rows = 0;
-        for (int i = 0; i < all.njobs; ++i) {
-            const int K = all.j[i].K;
-            const int jc = K <= 2 * 128 * OZ_SLICE_PPT ? 0 : K <= 2 * 256 * OZ_SLICE_PPT ? 1 : 2;
-            if (jc != cls) continue;
-            b.j[b.njobs] = all.j[i];
-            b.j[b.njobs].row0 = rows;
-            rows += all.j[i].rows;
-            b.njobs++;
-        }
-        if (b.njobs == 0) continue;
-        if (cls == 0) k_oz_slice<128><<<rows, 128, 0, c->stream>>>(b);
-        else if (cls == 1) k_oz_slice<256><<<rows, 256, 0, c->stream>>>(b);
-        else k_oz_slice<512><<<rows, 512, 0, c->stream>>>(b);
-        ACSE_LAUNCHED(c);
-    }
+// Launch the slicing of every job of `all`: the row scales (a warp per row), then the residues (a
+// block row per operand row, 256 element pairs a block).
+static int oz_slice_launch(acse_ctx* c, const OzSliceBatch& all, int rows) {
+    if (all.njobs == 0 || rows == 0) return ACSE_OK;
+    if (rows > 65535) return ACSE_ERR_SHAPE;
+    k_oz_rowscale<<<(rows + 7) / 8, 256, 0, c->stream>>>(all, rows);
+    ACSE_LAUNCHED(c);
+    int maxhk = 1;
+    for (int i = 0; i < all.njobs; ++i) maxhk = (all.j[i].K + 1) / 2 > maxhk ? (all.j[i].K + 1) / 2 : maxhk;
+    k_oz_residue<<<dim3((maxhk + 255) / 256, rows), 256, 0, c->stream>>>(all);
+    ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
 
@@ -877,11 +1021,10 @@ int oz_slice_operands(acse_ctx* c, int prep_D) {
     const int iR2 = (int)R2;
     Work& w = c->w;
     OzSliceBatch b;
-    memset(&b, 0, sizeof(b));
-    b.S = pl->S;
+    oz_slice_batch_init(b, pl->host->mods);
     int rows = 0;
     const int* pm = pl->pmap;
-    // A slices in order (segment s - 1), B slices reversed (segment S - t)
+    // A residues as they are, B residues times y_t
     if (prep_D) {
         oz_job(b, rows, pl->A[0], 0, P, w.M[0], R2, pm, pm, 0);
         oz_job(b, rows, pl->A[0], P, P, c->cur_D[0], R2, pm, pm, 0);
@@ -899,8 +1042,7 @@ int oz_slice_operands(acse_ctx* c, int prep_D) {
     oz_job(b, rows, pl->A[4], 0, 2 * iR2, w.Zd, 2 * R2, nullptr, nullptr, 0);
     oz_job(b, rows, pl->A[5], 0, iR2, w.Zf1, R2, nullptr, nullptr, 0);
     oz_job(b, rows, pl->A[6], 0, iR2, w.Zf2, R2, nullptr, nullptr, 0);
-    (void)rows;
-    return oz_slice_launch(c, b);
+    return oz_slice_launch(c, b, rows);
 }
 
 int oz_gemm_launch(acse_ctx* c) {
@@ -910,7 +1052,7 @@ int oz_gemm_launch(acse_ctx* c) {
     ACSE_TRY(prof_begin(c));
     ACSE_TRY(oz_launch_gemm(pl, c->stream));
     ACSE_LAUNCHED(c);
-    k_oz_reduce<<<dim3(2 * pl->nsm, pl->host->nprob), 256, 0, c->stream>>>(pl->dev);
+    ACSE_TRY(oz_launch_crt(pl->host, pl->dev, pl->nsm, c->stream));
     ACSE_LAUNCHED(c);
     ACSE_TRY(prof_end(c));
     Work& w = c->w;
@@ -935,7 +1077,7 @@ int oz_set_wait_ns(acse_ctx* c, unsigned long long ns, int inject_stall) {
 // stored transposed (GemmF64::transA / transB).  A transposed operand is sliced through a column map
 // (K index k at source offset k ld, row n at offset n): its reads are strided, one 8-byte element per
 // 32-byte sector, cheap next to the GEMM.  One plan per list slot, built on the first call (its slices
-// and group-sum staging stay until the context is destroyed); a later call whose shapes differ from
+// and residue staging stay until the context is destroyed); a later call whose shapes differ from
 // the slot's plan is refused (ACSE_ERR_SHAPE).
 
 // Column map k -> k ld for K indices, cached per (K, ld).
@@ -971,11 +1113,13 @@ static int oz_list_create(OzPlan* root, const GemmF64* g, int n, OzPlan** out) {
     *out = pl;
     int maxN = 0;
     for (int i = 0; i < n; ++i) maxN = g[i].N > maxN ? g[i].N : maxN;
-    ACSE_TRY(oz_plan_init(pl, root->S, maxN >= 256 ? OZ_BN : 128, root->pair));
+    long long maxK = 1;
+    for (int i = 0; i < n; ++i) maxK = g[i].K > maxK ? g[i].K : maxK;
+    ACSE_TRY(oz_plan_init(pl, root->S, maxN >= 256 ? OZ_BN : 128, root->pair, maxK));
     pl->host->err = root->err;
     for (int i = 0; i < n; ++i) {
-        ACSE_TRY(oz_op_alloc(pl->A[i], g[i].M, g[i].K, pl->S));
-        ACSE_TRY(oz_op_alloc(pl->B[i], g[i].N, g[i].K, pl->S));
+        ACSE_TRY(oz_op_alloc(pl, pl->A[i], g[i].M, g[i].K));
+        ACSE_TRY(oz_op_alloc(pl, pl->B[i], g[i].N, g[i].K));
         ACSE_TRY(oz_add(pl, pl->A[i], pl->B[i], g[i].C, g[i].ldc, g[i].alpha));
     }
     return oz_plan_finish(pl);
@@ -1001,10 +1145,9 @@ int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
     if (B.nprob != n) return ACSE_ERR_SHAPE;
     for (int i = 0; i < n; ++i)
         if (B.p[i].M != g[i].M || B.p[i].N != g[i].N || pl->A[i].K != g[i].K) return ACSE_ERR_SHAPE;
-    // slices of every operand (A in order, B reversed), at most OZ_MAXJ jobs a launch
+    // residues of every operand (B times y_t), at most OZ_MAXJ jobs a launch
     OzSliceBatch sb;
-    memset(&sb, 0, sizeof(sb));
-    sb.S = pl->S;
+    oz_slice_batch_init(sb, B.mods);
     int rows = 0;
     for (int i = 0; i < n; ++i) {
         for (int side = 0; side < 2; ++side) {
@@ -1016,16 +1159,13 @@ int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
             if (tr) ACSE_TRY(oz_colmap(root, o.K, ld, &cm));
             oz_job(sb, rows, o, 0, o.rows, src, tr ? 1 : (size_t)ld, nullptr, cm, side);
             if (sb.njobs == OZ_MAXJ) {
-                ACSE_TRY(oz_slice_launch(c, sb));
-                memset(&sb, 0, sizeof(sb));
-                sb.S = pl->S;
+                ACSE_TRY(oz_slice_launch(c, sb, rows));
+                oz_slice_batch_init(sb, B.mods);
                 rows = 0;
             }
         }
     }
-    if (sb.njobs) {
-        ACSE_TRY(oz_slice_launch(c, sb));
-    }
+    ACSE_TRY(oz_slice_launch(c, sb, rows));
     // this call's outputs, scales and accumulation
     for (int i = 0; i < n; ++i) {
         OzProb& p = B.p[i];
@@ -1043,7 +1183,7 @@ int oz_gemm_list(acse_ctx* c, const GemmF64* g, int n, int slot) {
     if (pl->tiles == 0) return ACSE_OK;
     ACSE_TRY(oz_launch_gemm(pl, c->stream));
     ACSE_LAUNCHED(c);
-    k_oz_reduce<<<dim3(2 * pl->nsm, B.nprob), 256, 0, c->stream>>>(pl->dev);
+    ACSE_TRY(oz_launch_crt(&B, pl->dev, pl->nsm, c->stream));
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }
