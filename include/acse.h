@@ -64,13 +64,17 @@ typedef enum {
  *   ACSE_TF32X3  x = hi + lo (two tf32), products hi.hi + hi.lo + lo.hi, FP32 accumulation (about 2^-21;
  *                limited by the FP32 intermediates);
  *   ACSE_OZAKI   FP64-accurate: every intermediate is FP64 as in ACSE_FP64, and each O(r^6) GEMM runs by
- *                the Ozaki scheme (error-free splitting, Ozaki, Ogita, Oishi and Rump, Numer. Algorithms
- *                59, 2012) on the BF16 tensor cores: each row of an operand is scaled by a power of two and
- *                cut into `oz_slices` signed 6-bit integer slices (exact in bf16); the slice products
- *                whose levels s + t <= slices + 1 are summed exactly in FP32 in groups small enough that
- *                no partial sum reaches 2^24, and the groups are added in FP64.  With the default 8
- *                slices (48 bits) the GEMM error is of the order of 2^-45 |A||B| K, that of FP64.  The
- *                adjoint's O(r^6) GEMMs run by the same scheme. */
+ *                the modular form of the Ozaki scheme (Ozaki, Uchino and Imamura, "Ozaki Scheme II",
+ *                2025) on the BF16 tensor cores: each row of an operand is scaled by a power of two and
+ *                rounded to an integer of min(6 oz_slices, 53) bits below its leading bit; the integer
+ *                product is computed modulo T pairwise coprime moduli <= 127 (residues exact in bf16,
+ *                sums exact in FP32, T the least count that covers the product: 17 at r = 48 with 8
+ *                slices) and rebuilt exactly by the Chinese remainder theorem, with one rounding to FP64.
+ *                With the default 8 (48 bits) the GEMM error is of the order of 2^-48 |A||B| K, below
+ *                that of FP64 FMA.  The O(r^5) products of the pass (Z and the B products, r a multiple
+ *                of 16) run by the six-bit slice form of the scheme (error-free splitting, Ozaki, Ogita,
+ *                Oishi and Rump, Numer. Algorithms 59, 2012) with `oz_slices` slices.  The adjoint's
+ *                O(r^6) GEMMs run by the modular form. */
 typedef enum { ACSE_FP64 = 0, ACSE_BF16X3 = 1, ACSE_TF32 = 2, ACSE_TF32X3 = 3, ACSE_OZAKI = 4 } acse_prec;
 /* 3-RDM reconstruction (Eq. 3rdm_recon / Eq. NY):
  *   ACSE_RECON_V   Valdemoro: the 3-cumulant is neglected;
@@ -100,7 +104,9 @@ typedef struct {
                         * by ACSE_FP64 and ACSE_OZAKI; rejected (ACSE_ERR_ARG) when n_alpha !=
                         * n_beta.  The library does not symmetrise D: on an asymmetric D the
                         * beta-beta results are those of the alpha-alpha block.             */
-    int oz_slices;     /* ACSE_OZAKI: 6-bit slices per operand row, 4..10; 0 -> 8            */
+    int oz_slices;     /* ACSE_OZAKI: accuracy in 6-bit units, 4..10; 0 -> 8: the O(r^6) GEMM
+                        * operands keep min(6 oz_slices, 53) bits, the O(r^5) products use
+                        * oz_slices six-bit slices                                          */
     int refine;        /* precision schedule of acse_step: 0 off; 1 the steps run in `prec` (any precision,
                         * ACSE_OZAKI with oz_slices included) until the switch rule fires, every later step
                         * in ACSE_OZAKI with refine_slices slices (FP64-accurate), from the same D and
