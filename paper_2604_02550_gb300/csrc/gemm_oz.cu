@@ -45,8 +45,12 @@
 #define OZ2_STAGES 6         // ring depth of the CTA-pair form (32 KB a stage per CTA)
 #define OZ_DRAIN_NS 2000000000ull
 #define OZ_WAIT_NS 4000000000ull
-#define OZ_LB 10             // bits of a limb of the reconstruction
-#define OZ_NL 14             // limbs of the reconstruction (140 bits)
+// limbs of the reconstruction: 14 of 10 bits for two K chunks, 12 of 11 bits for one (their limb sums stay
+// below 2^22 in magnitude either way)
+#define OZ_LB2 10
+#define OZ_NL2 14
+#define OZ_LB1 11
+#define OZ_NL1 12
 #ifndef OZ_CRT_MINB
 #define OZ_CRT_MINB 3        // resident blocks of 256 threads per SM the reconstruction is compiled for
 #endif
@@ -61,8 +65,10 @@ struct OzMods {
     float pinv[OZ_NMOD];      // 1 / p_t, rounded
     float cA[OZ_NMOD][4];     // 2^(14 l) mod p_t, l = 0..3 (limb weights of an A row)
     float cB[OZ_NMOD][4];     // 2^(14 l) y_t mod p_t, y_t = (P / p_t)^-1 mod p_t (limb weights of a B row)
-    float q[OZ_NMOD][OZ_NL];  // P / p_t in base-2^10 limbs, least significant first (exact floats)
-    float P[OZ_NL];           // P in base-2^10 limbs
+    float q10[OZ_NMOD][OZ_NL2];   // P / p_t in base-2^10 limbs, least significant first (exact floats)
+    float P10[OZ_NL2];            // P in base-2^10 limbs
+    float q11[OZ_NMOD][OZ_NL1];   // the same in base-2^11 limbs
+    float P11[OZ_NL1];
     float pinvs;              // 2^120 / P, rounded (between 2^-5 and 2^114)
 };
 
@@ -160,13 +166,13 @@ __global__ void __launch_bounds__(256) k_oz_rowscale(const __grid_constant__ OzS
     }
 }
 
-// Residues: block (x, y) covers element pairs 256 x .. 256 x + 255 of operand row y (rows of all jobs in
-// order), two consecutive elements a thread.  The integer X = round(a 2^(nb - e)) (|X| <= 2^53) is cut into
+// Residues: block (x, y) covers elements 1024 x .. 1024 x + 1023 of operand row y (rows of all jobs in
+// order), four consecutive elements a thread (8-byte stores of their four bf16 residues per modulus).  The integer X = round(a 2^(nb - e)) (|X| <= 2^53) is cut into
 // four base-2^14 limbs of |X|, each made an exact float through the bits of 2^23 + limb (no 64-bit
 // conversion: those run on the slow FP64 unit) and given the sign of X; modulus by modulus, the residue
 // is sum_l limb_l c_l (c_l = 2^(14 l) mod p_t, times y_t for a B operand; an integer below 2^23 in
 // magnitude, exact in FP32) reduced by oz_bal_mod (|residue| <= 64, exact in bf16: the upper half of its
-// float).  Residues go out as bf16 pairs, modulus t to K segment t of the row.
+// float).  Modulus t goes to K segment t of the row.
 __device__ __forceinline__ void oz_limbs(unsigned long long bits, int nb, int e, bool bad, float* L) {
     const long long X = bad ? 0 : oz_fixedb(bits, nb, e);
     const unsigned long long uX = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
@@ -184,33 +190,40 @@ __global__ void __launch_bounds__(256) k_oz_residue(const __grid_constant__ OzSl
     int ji = 0;
     while (ji + 1 < b.njobs && b.j[ji + 1].row0 <= grow) ++ji;
     const OzSliceJob& J = b.j[ji];
-    const int hk = (J.K + 1) >> 1;
-    const int pi = (int)blockIdx.x * 256 + (int)threadIdx.x;
-    if (pi >= hk) return;
-    const int row = grow - J.row0, k = 2 * pi;
+    const int K = J.K;
+    const int qi = (int)blockIdx.x * 256 + (int)threadIdx.x;
+    if (qi >= (K + 3) >> 2) return;
+    const int row = grow - J.row0, k = 4 * qi;
     const int srow = J.rowmap ? J.rowmap[row] : row;
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(J.src + (size_t)srow * J.lds);
     const int* cm = J.colmap;
-    const unsigned long long v0 = src[cm ? cm[k] : k];
-    const unsigned long long v1 = k + 1 < J.K ? src[cm ? cm[k + 1] : k + 1] : 0ull;
+    unsigned long long v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = k + i < K ? src[cm ? cm[k + i] : k + i] : 0ull;
     const int es = (int)((__double_as_longlong(J.scale[row]) >> 52) & 0x7FF);   // 2^e, or NaN
     const bool bad = es == 0x7FF;
-    float L0[4], L1[4];
-    oz_limbs(v0, J.nb, es - 1023, bad, L0);
-    oz_limbs(v1, J.nb, es - 1023, bad, L1);
+    float L[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) oz_limbs(v[i], J.nb, es - 1023, bad, L[i]);
     __nv_bfloat16* dst = J.dst + (size_t)row * J.ldd + k;
-    const bool pair = k + 1 < J.K;
+    const int nk = min(4, K - k);
     const float(*c)[4] = J.mul_y ? b.cB : b.cA;
     const int T = b.T;
-#pragma unroll 4
+#pragma unroll 2
     for (int t = 0; t < T; ++t, dst += J.Kp) {
         const float p = b.p[t], pinv = b.pinv[t];
         const float c0 = c[t][0], c1 = c[t][1], c2 = c[t][2], c3 = c[t][3];
-        const float r0 = oz_bal_mod(fmaf(L0[3], c3, fmaf(L0[2], c2, fmaf(L0[1], c1, L0[0] * c0))), p, pinv);
-        const float r1 = oz_bal_mod(fmaf(L1[3], c3, fmaf(L1[2], c2, fmaf(L1[1], c1, L1[0] * c0))), p, pinv);
-        // |r| <= 64: the bf16 of r is the upper half of its float (exact)
-        if (pair) *reinterpret_cast<unsigned int*>(dst) = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
-        else *reinterpret_cast<unsigned short*>(dst) = (unsigned short)(__float_as_uint(r0) >> 16);
+        unsigned int h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)   // |r| <= 64: the bf16 of r is the upper half of its float (exact)
+            h[i] = __float_as_uint(oz_bal_mod(fmaf(L[i][3], c3, fmaf(L[i][2], c2, fmaf(L[i][1], c1, L[i][0] * c0))), p, pinv));
+        if (nk == 4) {
+            *reinterpret_cast<uint2*>(dst) = make_uint2(__byte_perm(h[0], h[1], 0x7632), __byte_perm(h[2], h[3], 0x7632));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i < nk) reinterpret_cast<unsigned short*>(dst)[i] = (unsigned short)(h[i] >> 16);
+        }
     }
 }
 
@@ -447,39 +460,49 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const OzBatch* __rest
 }
 
 // --------------------------------------------------------------------------- reconstruction
-// s = sum_t w_t (P / p_t) is accumulated in OZ_NL float limb sums of weight 2^(10 l): each is a sum of
-// w_t times a limb of P / p_t below 2^10, so with |w_t| <= 130 (two chunks) and T <= 19 it stays an
-// integer below 2^21.3 in magnitude (exact, and within the 2^22 of the float-to-int step below).
+// s = sum_t w_t (P / p_t) is accumulated in NL float limb sums of weight 2^(LB l): each is a sum of w_t
+// times a limb of P / p_t below 2^LB, so with T <= 19 it stays an integer below 2^22 in magnitude
+// (|w_t| <= 130 with two chunks and 10-bit limbs: 2^21.3; |w_t| <= 65 with one chunk and 11-bit limbs:
+// 2^21.3) -- exact, and within the range of the float-to-int step below.
 
 // x = s - round(s / P) P from the limb sums, rounded once to FP64 and scaled by 2^ex.  The product lies
 // within P / 4 of zero, so q needs s / P to within 1/4: the estimate is summed from the limb sums as they
 // are (each a sum of w_t times non-negative limbs of P / p_t, so the float rounding errors stay near
 // 2^-20 sum_t |w_t| / p_t of s / P).  x's limbs (integers below 2^22) become int32 through the float
-// 1.5 * 2^23 + x, carries normalise them to [0, 2^10) under a top limb of 0 or -1, and a negative x is
-// negated as a 128-bit two's complement (|x| < 2^123).
+// 1.5 * 2^23 + x, carries normalise them to [0, 2^LB) under a signed top limb, the value is assembled
+// modulo 2^128 (|x| < 2^123), and a negative x is negated as a 128-bit two's complement.
+template <int LB, int NL>
 __device__ __forceinline__ double oz_crt_value(const float* a, const float* Pl, float pinvs, int ex) {
     float sf = 0.0f;
 #pragma unroll
-    for (int l = 0; l < OZ_NL; ++l) sf = fmaf(a[l], __int_as_float((127 + OZ_LB * l - 120) << 23), sf);   // s 2^-120
+    for (int l = 0; l < NL; ++l) sf = fmaf(a[l], __int_as_float((127 + LB * l - 120) << 23), sf);   // s 2^-120
     const float q = fmaf(sf, pinvs, 12582912.0f) - 12582912.0f;
-    int x[OZ_NL];
+    int x[NL];
 #pragma unroll
-    for (int l = 0; l < OZ_NL; ++l) x[l] = __float_as_int(fmaf(-q, Pl[l], a[l]) + 12582912.0f) - 0x4B400000;
+    for (int l = 0; l < NL; ++l) x[l] = __float_as_int(fmaf(-q, Pl[l], a[l]) + 12582912.0f) - 0x4B400000;
     int c = x[0];
 #pragma unroll
-    for (int l = 0; l < OZ_NL - 1; ++l) {
+    for (int l = 0; l < NL - 1; ++l) {
         const int cl = c;
-        x[l] = cl & ((1 << OZ_LB) - 1);
-        c = (cl >> OZ_LB) + x[l + 1];   // arithmetic shift: floor
+        x[l] = cl & ((1 << LB) - 1);
+        c = (cl >> LB) + x[l + 1];   // arithmetic shift: floor
     }
-    const bool neg = c < 0;   // the top limb: 0, or -1 for x < 0 (2^130 + x in the limbs below)
-    x[OZ_NL - 1] = c;
     typedef unsigned long long u64;
-    const u64 lo = (u64)x[0] | ((u64)x[1] << 10) | ((u64)x[2] << 20) | ((u64)x[3] << 30) | ((u64)x[4] << 40) |
-                   ((u64)x[5] << 50) | ((u64)x[6] << 60);
-    u64 hi = ((u64)x[6] >> 4) | ((u64)x[7] << 6) | ((u64)x[8] << 16) | ((u64)x[9] << 26) | ((u64)x[10] << 36) |
-             ((u64)x[11] << 46) | ((u64)x[12] << 56);
-    if (neg) {   // |x| = 2^130 - (limbs) = -(limbs) modulo 2^128, since |x| < 2^128
+    u64 lo = 0, hi = 0;
+#pragma unroll
+    for (int l = 0; l < NL - 1; ++l) {   // limbs in [0, 2^LB) at bit LB l
+        const int pos = LB * l;
+        const u64 v = (u64)(unsigned int)x[l];
+        if (pos < 64) {
+            lo |= v << pos;
+            if (pos + LB > 64) hi |= v >> (64 - pos);
+        } else if (pos < 128) {
+            hi |= v << (pos - 64);
+        }
+    }
+    constexpr int TOP = LB * (NL - 1);   // the signed top limb c: sign-extended, modulo 2^128
+    if constexpr (TOP < 128) hi |= (u64)(long long)c << (TOP - 64);
+    if (c < 0) {   // |x| = -(the assembled value) modulo 2^128, since |x| < 2^128
         const u64 nlo = 0ull - lo;
         hi = ~hi + (lo == 0 ? 1ull : 0ull);
         return oz_u128_scaled(hi, nlo, true, ex);
@@ -490,8 +513,10 @@ __device__ __forceinline__ double oz_crt_value(const float* a, const float* Pl, 
 // The constants of the reconstruction, passed as a kernel parameter: with the modulus and limb loops
 // unrolled, every limb of P / p_t is an immediate constant-bank operand of its FMA (no load).
 struct OzCrtParams {
-    float q[OZ_NMOD][OZ_NL];
-    float P[OZ_NL];
+    float q10[OZ_NMOD][OZ_NL2];
+    float P10[OZ_NL2];
+    float q11[OZ_NMOD][OZ_NL1];
+    float P11[OZ_NL1];
     float pinvs;
     int T;
 };
@@ -502,6 +527,9 @@ struct OzCrtParams {
 // (exact), so w = that - (2^23 + 128).
 template <int NCH, int VW>
 __device__ __forceinline__ void oz_crt_rows(const OzProb& P, const OzCrtParams& cp) {
+    constexpr int LB = NCH == 1 ? OZ_LB1 : OZ_LB2, NL = NCH == 1 ? OZ_NL1 : OZ_NL2;
+    const float(*qt)[NL] = NCH == 1 ? (const float(*)[NL])cp.q11 : (const float(*)[NL])cp.q10;
+    const float* Pl = NCH == 1 ? cp.P11 : cp.P10;
     const int T = cp.T, N = P.N;
     const size_t MN = (size_t)P.M * N;
     const size_t nunit = MN / VW;
@@ -519,11 +547,11 @@ __device__ __forceinline__ void oz_crt_rows(const OzProb& P, const OzCrtParams& 
                     sp += MN;
                 }
             }
-        float acc[VW][OZ_NL];
+        float acc[VW][NL];
 #pragma unroll
         for (int k = 0; k < VW; ++k)
 #pragma unroll
-            for (int l = 0; l < OZ_NL; ++l) acc[k][l] = 0.0f;
+            for (int l = 0; l < NL; ++l) acc[k][l] = 0.0f;
 #pragma unroll
         for (int t = 0; t < OZ_NMOD; ++t) {
             if (t >= T) break;
@@ -533,7 +561,7 @@ __device__ __forceinline__ void oz_crt_rows(const OzProb& P, const OzCrtParams& 
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) w += __uint_as_float(__byte_perm(xw[t][c], 0x4B000000u, 0x7540u | k)) - 8388736.0f;
 #pragma unroll
-                for (int l = 0; l < OZ_NL; ++l) acc[k][l] = fmaf(w, cp.q[t][l], acc[k][l]);
+                for (int l = 0; l < NL; ++l) acc[k][l] = fmaf(w, qt[t][l], acc[k][l]);
             }
         }
         const int i = (int)(e / N), j0 = (int)(e - (size_t)i * N);
@@ -544,7 +572,7 @@ __device__ __forceinline__ void oz_crt_rows(const OzProb& P, const OzCrtParams& 
             const int eb = (int)((__double_as_longlong(P.sb[j0 + k]) >> 52) & 0x7FF);
             const double v = (ea == 0x7FF || eb == 0x7FF)
                                  ? __longlong_as_double(0x7ff8000000000000ll)
-                                 : oz_crt_value(acc[k], cp.P, cp.pinvs, ea + eb - 2046 + P.ealpha - 2 * P.nb);
+                                 : oz_crt_value<LB, NL>(acc[k], Pl, cp.pinvs, ea + eb - 2046 + P.ealpha - 2 * P.nb);
             crow[j0 + k] = P.accum ? crow[j0 + k] + v : v;
         }
     }
@@ -565,8 +593,10 @@ static int oz_launch_crt(const OzBatch* host, const OzBatch* dev, int nsm, cudaS
     memset(&cp, 0, sizeof(cp));
     const OzMods& m = host->mods;
     cp.T = m.T;
-    memcpy(cp.q, m.q, sizeof(cp.q));
-    memcpy(cp.P, m.P, sizeof(cp.P));
+    memcpy(cp.q10, m.q10, sizeof(cp.q10));
+    memcpy(cp.P10, m.P10, sizeof(cp.P10));
+    memcpy(cp.q11, m.q11, sizeof(cp.q11));
+    memcpy(cp.P11, m.P11, sizeof(cp.P11));
     cp.pinvs = m.pinvs;
     k_oz_crt<<<dim3(2 * nsm, host->nprob), 256, 0, st>>>(dev, cp);
     ACSE_CUDA_TRY(cudaGetLastError());
@@ -690,7 +720,7 @@ static int oz_mods_init(OzPlan* pl, int S, long long Kmax) {
     OzMods& m = pl->host->mods;
     memset(&m, 0, sizeof(m));
     m.T = T;
-    const unsigned __int128 lmask = ((unsigned __int128)1 << OZ_LB) - 1;
+    const unsigned __int128 m10 = ((unsigned __int128)1 << OZ_LB2) - 1, m11 = ((unsigned __int128)1 << OZ_LB1) - 1;
     for (int t = 0; t < T; ++t) {
         const int pt = oz_moduli[t];
         const unsigned __int128 Q = P / (unsigned __int128)pt;
@@ -704,9 +734,11 @@ static int oz_mods_init(OzPlan* pl, int S, long long Kmax) {
             m.cA[t][l] = (float)cl;
             m.cB[t][l] = (float)((cl * y) % pt);
         }
-        for (int l = 0; l < OZ_NL; ++l) m.q[t][l] = (float)(int)((Q >> (OZ_LB * l)) & lmask);
+        for (int l = 0; l < OZ_NL2; ++l) m.q10[t][l] = (float)(int)((Q >> (OZ_LB2 * l)) & m10);
+        for (int l = 0; l < OZ_NL1; ++l) m.q11[t][l] = (float)(int)((Q >> (OZ_LB1 * l)) & m11);
     }
-    for (int l = 0; l < OZ_NL; ++l) m.P[l] = (float)(int)((P >> (OZ_LB * l)) & lmask);
+    for (int l = 0; l < OZ_NL2; ++l) m.P10[l] = (float)(int)((P >> (OZ_LB2 * l)) & m10);
+    for (int l = 0; l < OZ_NL1; ++l) m.P11[l] = (float)(int)((P >> (OZ_LB1 * l)) & m11);
     m.pinvs = (float)(ldexp(1.0, 120) / (double)P);
     return ACSE_OK;
 }
@@ -1000,15 +1032,15 @@ static void oz_job(OzSliceBatch& b, int& rows, const OzOp& o, int orow, int nrow
 }
 
 // Launch the slicing of every job of `all`: the row scales (a warp per row), then the residues (a
-// block row per operand row, 256 element pairs a block).
+// block row per operand row, 1024 elements a block).
 static int oz_slice_launch(acse_ctx* c, const OzSliceBatch& all, int rows) {
     if (all.njobs == 0 || rows == 0) return ACSE_OK;
     if (rows > 65535) return ACSE_ERR_SHAPE;
     k_oz_rowscale<<<(rows + 7) / 8, 256, 0, c->stream>>>(all, rows);
     ACSE_LAUNCHED(c);
-    int maxhk = 1;
-    for (int i = 0; i < all.njobs; ++i) maxhk = (all.j[i].K + 1) / 2 > maxhk ? (all.j[i].K + 1) / 2 : maxhk;
-    k_oz_residue<<<dim3((maxhk + 255) / 256, rows), 256, 0, c->stream>>>(all);
+    int maxq = 1;
+    for (int i = 0; i < all.njobs; ++i) maxq = (all.j[i].K + 3) / 4 > maxq ? (all.j[i].K + 3) / 4 : maxq;
+    k_oz_residue<<<dim3((maxq + 255) / 256, rows), 256, 0, c->stream>>>(all);
     ACSE_LAUNCHED(c);
     return ACSE_OK;
 }

@@ -16,9 +16,9 @@ The O(r^6) GEMMs use the modular form of the scheme (K. Ozaki, Y. Uchino, T. Ima
   exact in bf16; a K chunk of 64 * 64 products of such residues stays within 2^24 (exact FP32
   accumulation), 65 blocks would not.
 * The number T of moduli chosen for S slices covers 4 K 2^(2 min(6S, 53)) for the longest contraction.
-* The reconstruction (s = sum_t w_t P / p_t in FP32 sums of base-2^10 limbs, each an integer below 2^22,
-  q = round(s / P) estimated in FP32 from those sums, x = s - q P) returns every x with |x| <= P / 4,
-  for every T and one or two chunks.
+* The reconstruction (s = sum_t w_t P / p_t in FP32 sums of base-2^11 limbs for one chunk, base-2^10
+  for two, each an integer below 2^22; q = round(s / P) estimated in FP32 from those sums; x = s - q P)
+  returns every x with |x| <= P / 4, for every T.
 * The whole product (integer rows, residues, chunked exact sums, reconstruction) equals the exact
   product of the integer rows, and its error against the real product falls by about 2^6 a slice.
 The CUDA path (paper_2604_02550_gb300/csrc/gemm_oz.cu) is checked against the oracle on the GPU in
@@ -145,7 +145,7 @@ def test_truncation_error_falls_with_slices():
 
 # ------------------------------------------------------------------ the modular form (Ozaki scheme II)
 MODULI = [127, 125, 123, 121, 119, 113, 109, 107, 103, 101, 97, 89, 83, 79, 73, 71, 67, 61, 59]
-LB, NL = 10, 14   # limbs of the reconstruction: 14 of 10 bits
+LIMBS = {1: (11, 12), 2: (10, 14)}   # limbs of the reconstruction by K chunks: (bits, count)
 
 
 def moduli_count(S, Kmax):
@@ -170,30 +170,32 @@ def balanced(v, p):
     return r - p if r > (p - 1) // 2 else r
 
 
-def limbs(v):
-    return [(v >> (LB * l)) & ((1 << LB) - 1) for l in range(NL)]
+def limbs(v, nch):
+    lb, nl = LIMBS[nch]
+    return [(v >> (lb * l)) & ((1 << lb) - 1) for l in range(nl)]
 
 
-def limb_sums(ws, Q):
+def limb_sums(ws, Q, nch):
     """FP32 limb sums of s = sum_t w_t Q_t: every partial sum is an integer below 2^22 (exact)."""
     f = np.float32
-    acc = [f(0)] * NL
+    acc = [f(0)] * LIMBS[nch][1]
     for w, q in zip(ws, Q):
-        for l, ql in enumerate(limbs(q)):
+        for l, ql in enumerate(limbs(q, nch)):
             acc[l] = f(acc[l] + f(w) * f(ql))
             assert abs(float(acc[l])) < 2 ** 22
     return acc
 
 
-def reconstruct(acc, P):
+def reconstruct(acc, P, nch):
     """x from the limb sums: q from an FP32 estimate of s / P summed from the limb sums as they are,
     then exact integer steps."""
     f = np.float32
+    lb = LIMBS[nch][0]
     sf = f(0)
-    for l in range(NL):
-        sf = f(sf + acc[l] * f(2.0 ** (LB * l - 120)))
+    for l in range(len(acc)):
+        sf = f(sf + acc[l] * f(2.0 ** (lb * l - 120)))
     q = int(np.rint(sf * f(2.0 ** 120 / float(P))))
-    return sum(int(a) * (1 << (LB * l)) for l, a in enumerate(acc)) - q * P
+    return sum(int(a) * (1 << (lb * l)) for l, a in enumerate(acc)) - q * P
 
 
 def test_moduli_coprime_and_residues_exact_in_bf16():
@@ -259,7 +261,7 @@ def test_reconstruction_exact_within_quarter_P(T):
             last = balanced(x * y[t] - sum(ws), p)
             ws.append(last + p if last < 0 and rnd.random() < 0.3 and last + p <= 65 else last)
             wt.append(sum(ws))
-        assert reconstruct(limb_sums(wt, Q), P) == x
+        assert reconstruct(limb_sums(wt, Q, nch), P, nch) == x
 
 
 def modular_product(A, B, S, Kmax=None):
@@ -292,7 +294,7 @@ def modular_product(A, B, S, Kmax=None):
                     assert abs(part) <= 2 ** 24
                     w += balanced(part, p)
                 wt.append(w)
-            x = reconstruct(limb_sums(wt, Q), P)
+            x = reconstruct(limb_sums(wt, Q, nch), P, nch)
             assert x == sum(a * v for a, v in zip(XA[i], XB[j]))
             C[i, j] = float(Fraction(x) * Fraction(2) ** (ea[i] + eb[j] - 2 * nb))
     return C
