@@ -8,13 +8,13 @@
 // below the row's leading bit for oz_slices = S).  The integer product X_A X_B^T then has entries of at
 // most K 2^(2 nb - 2) in magnitude.  It is computed modulo T pairwise coprime moduli p_t <= 127 (the
 // first T of a fixed list, T the least with 4 K 2^(2 nb - 2) <= P = prod p_t):
-//   * the slicing kernel writes near-balanced residues X mod p_t (|.| <= 64, exact in bf16), the B rows
+//   * the residue kernel writes near-balanced residues X mod p_t (|.| <= 64, exact in bf16), the B rows
 //     premultiplied by y_t = (P / p_t)^-1 mod p_t, each modulus to its K segment of the row;
 //   * the tensor cores multiply the residue matrices of each modulus in FP32; a chunk of at most 64 * 64
 //     K elements keeps every partial sum an integer of magnitude at most 64 * 64 * 64^2 = 2^24, so the
 //     accumulation is exact, and the epilogue stores a residue w (|w| <= 65) of the chunk sum (one byte);
-//   * the reconstruction kernel forms s = sum_t w_t (P / p_t) exactly in base-2^28 limbs, which is
-//     congruent to X_A X_B^T modulo every p_t and hence modulo P (Chinese remainder theorem), takes
+//   * the reconstruction kernel forms s = sum_t w_t (P / p_t) exactly in FP32 sums of 10- or 11-bit
+//     limbs, which is congruent to X_A X_B^T modulo every p_t and hence modulo P (Chinese remainder theorem), takes
 //     q = round(s / P) (the product lies within P / 4 of zero, so a float estimate of s / P decides q),
 //     and x = s - q P is the exact integer product, rounded once to FP64 and scaled by alpha 2^(ea + eb - 2 nb).
 // The result is the FP64 product up to the rounding of the operands to nb - 1 bits below each row's
@@ -23,7 +23,7 @@
 //
 // Kernels: the persistent tcgen05 GEMM of gemm_tc.cu with the accumulation unit changed from a tile
 // to a (tile, modulus, K chunk) group: the MMA thread runs the groups of a tile one after another into the
-// two TMEM buffers, and the epilogue warps store each group's residue (int8) to a staging array.  A
+// two TMEM buffers, and the epilogue warps store each group's residue (a byte) to a staging array.  A
 // second kernel rebuilds every element from its residues and writes the FP64 result once.  Every wait
 // is bounded as in gemm_tc.cu.
 #include <cuda.h>
