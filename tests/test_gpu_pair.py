@@ -108,8 +108,9 @@ def test_pair_timeout_status_and_recovery(acse):
 
 @pytest.mark.parametrize("r,na,nb", [(16, 5, 4), (20, 6, 5), (32, 7, 6)])
 def test_pair_ozaki(acse, r, na, nb):
-    """The Ozaki GEMMs on CTA pairs: the exact integer group sums make the residual identical to the
-    one-SM form's; against the oracle the FP64-accurate bound (1e-12 relative) holds."""
+    """The Ozaki GEMMs on CTA pairs: the exact residue sums and the exact reconstruction make the
+    residual identical to the one-SM form's; against the oracle the FP64-accurate bound (1e-12 relative)
+    holds."""
     p = _problem(r, na, nb, 400 + r)
     A2, n2 = _residual(acse, p, "ozaki", 2)
     A1, n1 = _residual(acse, p, "ozaki", 1)
