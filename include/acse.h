@@ -300,6 +300,16 @@ int acse_energy_noalloc(int r, int n_alpha, int n_beta, const double* h, const d
                         const double* Daa, const double* Dab, const double* Dbb, double* E,
                         void* cuda_stream);
 
+/* Plan of the modular Ozaki GEMM (ACSE_OZAKI), on the host only (no device access; not part of the
+ * method): for a context with oz_slices = S (4..10) whose longest O(r^6) contraction has length kmax
+ * (2 r^2 for the pass; 1 <= kmax <= 8192), and one of its GEMMs of contraction length k (1 <= k <= kmax),
+ * the number T of moduli (the least whose product P covers 4 kmax 2^(2 min(6S, 53))), the bits kept below
+ * a row's leading bit (min(6S, 53), fewer only if P cannot cover the product at that k), the K chunks of
+ * one residue product (64 * 64 elements at most each), and the moduli themselves (moduli: room for 19
+ * ints, or NULL; any other output may be NULL too).  ACSE_ERR_ARG outside those ranges. */
+int acse_ozaki_plan_info(int oz_slices, int kmax, int k, int* moduli_count, int* bits, int* chunks,
+                         int* moduli);
+
 /* Text of a status code. */
 const char* acse_strerror(int status);
 

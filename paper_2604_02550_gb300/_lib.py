@@ -19,7 +19,7 @@ EXPORTS = ("acse_create", "acse_destroy", "acse_energy", "acse_residual", "acse_
            "acse_clear_status", "acse_set_wait_bound_ns", "acse_energy_noalloc", "acse_batch_create",
            "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D", "acse_batch_run", "acse_batch_info",
            "acse_extrapolate", "acse_batch_history", "acse_batch_extrapolate", "acse_schedule_state",
-           "acse_batch_residual_backward",
+           "acse_batch_residual_backward", "acse_ozaki_plan_info",
            "acse_strerror", "acse_last_error", "acse_version")
 
 
@@ -76,6 +76,9 @@ def lib():
                                                    c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.acse_schedule_state.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int)]
         L.acse_schedule_state.restype = c_int
+        L.acse_ozaki_plan_info.argtypes = [c_int, c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                           POINTER(c_int)]
+        L.acse_ozaki_plan_info.restype = c_int
         for name in ("acse_batch_create", "acse_batch_destroy", "acse_batch_set_D", "acse_batch_get_D",
                      "acse_batch_run", "acse_batch_info", "acse_extrapolate", "acse_batch_history",
                      "acse_batch_extrapolate", "acse_batch_residual_backward"):
@@ -201,6 +204,15 @@ def acse_sync_status(ctx):
 
 def acse_clear_status(ctx):
     _check(lib().acse_clear_status(ctx), "acse_clear_status")
+
+
+def acse_ozaki_plan_info(oz_slices, kmax, k):
+    """The modular Ozaki GEMM's plan for one GEMM (host only): moduli count, kept bits, K chunks, moduli."""
+    T, bits, ch = c_int(), c_int(), c_int()
+    mods = (c_int * 19)()
+    _check(lib().acse_ozaki_plan_info(int(oz_slices), int(kmax), int(k), ctypes.byref(T), ctypes.byref(bits),
+                                      ctypes.byref(ch), mods), "acse_ozaki_plan_info")
+    return {"moduli_count": T.value, "bits": bits.value, "chunks": ch.value, "moduli": list(mods[:T.value])}
 
 
 def acse_set_wait_bound_ns(ctx, ns, inject_stall=False):

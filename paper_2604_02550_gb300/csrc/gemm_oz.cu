@@ -853,6 +853,27 @@ static int oz_plan_init(OzPlan* pl, int S, int bn, int pair, long long Kmax) {
     return oz_mods_init(pl, S, Kmax);
 }
 
+// The plan figures of one GEMM, on the host only (acse_ozaki_plan_info in include/acse.h).
+extern "C" int acse_ozaki_plan_info(int oz_slices, int kmax, int k, int* moduli_count, int* bits, int* chunks,
+                                    int* moduli) {
+    if (oz_slices < 4 || oz_slices > 10 || kmax < 1 || kmax > 8192 || k < 1 || k > kmax) return ACSE_ERR_ARG;
+    OzPlan pl;
+    memset(&pl, 0, sizeof(pl));
+    pl.host = (OzBatch*)calloc(1, sizeof(OzBatch));
+    if (!pl.host) return ACSE_ERR_NOMEM;
+    const int st = oz_mods_init(&pl, oz_slices, kmax);
+    if (st == ACSE_OK) {
+        const int T = pl.host->mods.T, kbs = (k + 63) / 64;
+        if (moduli_count) *moduli_count = T;
+        if (bits) *bits = oz_op_nb(&pl, k) - 1;
+        if (chunks) *chunks = (kbs + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+        if (moduli)
+            for (int t = 0; t < T; ++t) moduli[t] = oz_moduli[t];
+    }
+    free(pl.host);
+    return st;
+}
+
 int oz_plan_create(acse_ctx* c) {
     OzPlan* pl = (OzPlan*)calloc(1, sizeof(OzPlan));
     if (!pl) return ACSE_ERR_NOMEM;
